@@ -1,0 +1,211 @@
+"""FP64 CPU oracle for GMM-EM (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does; the
+oracle shares no code with the CUDA path.  The arithmetic lives in
+``gira_oracle.c`` (plain single-threaded C, binary64); this module only
+marshals numpy arrays.  See the header of ``gira_oracle.c`` for the passages
+of GIRA (arXiv 2307.00071, Sec. V) each function follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_PD, ERR_OOM = 0, 1, 2, 3, 5
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"oracle {where} failed with status {code}")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp, fp, i64p, i32p = (C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int32))
+        L.oracle_splitmix64.restype = C.c_uint64
+        L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+        L.oracle_uniform.restype = C.c_double
+        L.oracle_uniform.argtypes = [C.c_uint64, C.c_uint64]
+        L.oracle_cholesky3.argtypes = [dp, dp]
+        L.oracle_tri_inverse3.argtypes = [dp, dp]
+        L.oracle_log_gaussian.restype = C.c_double
+        L.oracle_log_gaussian.argtypes = [dp, dp, dp]
+        L.oracle_estep.argtypes = [fp, C.c_int64, C.c_int, dp, dp, dp, dp, dp, dp]
+        L.oracle_mstep.argtypes = [fp, C.c_int64, C.c_int, dp, C.c_double, dp, dp, dp]
+        L.oracle_dist2_f32.restype = C.c_float
+        L.oracle_dist2_f32.argtypes = [fp, fp]
+        L.oracle_kmeanspp.argtypes = [fp, C.c_int64, C.c_int, C.c_uint64, fp, i64p]
+        L.oracle_lloyd.argtypes = [fp, C.c_int64, C.c_int, fp, C.c_int, i32p, C.POINTER(C.c_int)]
+        L.oracle_init_from_labels.argtypes = [fp, C.c_int64, C.c_int, i32p, C.c_double, dp, dp, dp]
+        L.oracle_em.argtypes = [fp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, dp,
+                                C.POINTER(C.c_int), dp]
+        L.oracle_gmm_fit.argtypes = [fp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
+                                     C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int), dp]
+        L.oracle_last_bad_component.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t)) if a is not None else None
+
+
+def _check(st, where):
+    if st != OK:
+        raise OracleError(st, where)
+
+
+def last_bad_component() -> int:
+    return int(lib().oracle_last_bad_component())
+
+
+# ----------------------------------------------------------------------------- RNG
+def splitmix64(seed: int, j: int) -> int:
+    return int(lib().oracle_splitmix64(seed, j))
+
+
+def uniform(seed: int, j: int) -> float:
+    return float(lib().oracle_uniform(seed, j))
+
+
+# ----------------------------------------------------------------------------- algebra
+def cholesky3(S):
+    S = _f64(S).reshape(3, 3).copy()
+    L = np.zeros((3, 3))
+    st = lib().oracle_cholesky3(_p(S, C.c_double), _p(L, C.c_double))
+    if st != 0:
+        raise OracleError(ERR_NOT_PD, "cholesky3")
+    return L
+
+
+def tri_inverse3(L):
+    L = _f64(L).reshape(3, 3).copy()
+    P = np.zeros((3, 3))
+    lib().oracle_tri_inverse3(_p(L, C.c_double), _p(P, C.c_double))
+    return P
+
+
+def log_gaussian(x, mu, cov) -> float:
+    """Eq. (simplifiedGaussian) at one point."""
+    P = tri_inverse3(cholesky3(cov))
+    x, mu = _f64(x).copy(), _f64(mu).copy()
+    return float(lib().oracle_log_gaussian(_p(x, C.c_double), _p(mu, C.c_double), _p(P, C.c_double)))
+
+
+def dist2_f32(x, c) -> np.float32:
+    x, c = _f32(x).copy(), _f32(c).copy()
+    return np.float32(lib().oracle_dist2_f32(_p(x, C.c_float), _p(c, C.c_float)))
+
+
+# ----------------------------------------------------------------------------- EM steps
+def estep(pts, weights, means, covs, want_resp: bool = True, want_lse: bool = False):
+    """Returns (mean_ll, resp or None, lse or None)."""
+    pts = _f32(pts)
+    N, K = pts.shape[0], len(weights)
+    w, m, c = _f64(weights), _f64(means), _f64(covs)
+    resp = np.empty((N, K)) if want_resp else None
+    lse = np.empty(N) if want_lse else None
+    ll = C.c_double()
+    st = lib().oracle_estep(_p(pts, C.c_float), N, K, _p(w, C.c_double), _p(m, C.c_double), _p(c, C.c_double),
+                            _p(resp, C.c_double), _p(lse, C.c_double), C.byref(ll))
+    _check(st, "estep")
+    return ll.value, resp, lse
+
+
+def mstep(pts, resp, reg: float):
+    pts, resp = _f32(pts), _f64(resp)
+    N, K = resp.shape
+    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
+    st = lib().oracle_mstep(_p(pts, C.c_float), N, K, _p(resp, C.c_double), reg, _p(w, C.c_double),
+                            _p(m, C.c_double), _p(c, C.c_double))
+    _check(st, "mstep")
+    return w, m, c
+
+
+def kmeanspp(pts, K: int, seed: int):
+    """Returns (centers (K,3) float32, chosen indices (K,) int64)."""
+    pts = _f32(pts)
+    N = pts.shape[0]
+    centers = np.empty((K, 3), np.float32)
+    chosen = np.empty(K, np.int64)
+    st = lib().oracle_kmeanspp(_p(pts, C.c_float), N, K, seed, _p(centers, C.c_float), _p(chosen, C.c_int64))
+    _check(st, "kmeanspp")
+    return centers, chosen
+
+
+def lloyd(pts, centers, lloyd_iters: int):
+    """Returns (centers (K,3) float32, labels (N,) int32, iterations done)."""
+    pts = _f32(pts)
+    centers = _f32(centers).copy()
+    N, K = pts.shape[0], centers.shape[0]
+    labels = np.empty(N, np.int32)
+    done = C.c_int()
+    st = lib().oracle_lloyd(_p(pts, C.c_float), N, K, _p(centers, C.c_float), lloyd_iters,
+                            _p(labels, C.c_int32), C.byref(done))
+    _check(st, "lloyd")
+    return centers, labels, done.value
+
+
+def init_from_labels(pts, labels, K: int, reg: float):
+    pts = _f32(pts)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    N = pts.shape[0]
+    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
+    st = lib().oracle_init_from_labels(_p(pts, C.c_float), N, K, _p(labels, C.c_int32), reg, _p(w, C.c_double),
+                                       _p(m, C.c_double), _p(c, C.c_double))
+    _check(st, "init_from_labels")
+    return w, m, c
+
+
+def em(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-6):
+    """EM from explicit parameters.  Returns a dict (weights, means, covs, trace, iters_done, final_ll)."""
+    pts = _f32(pts)
+    N = pts.shape[0]
+    w, m, c = _f64(weights).copy(), _f64(means).copy(), _f64(covs).copy()
+    K = w.shape[0]
+    trace = np.full(max(iters, 1), np.nan)
+    done, fll = C.c_int(), C.c_double()
+    st = lib().oracle_em(_p(pts, C.c_float), N, K, iters, tol, reg, _p(w, C.c_double), _p(m, C.c_double),
+                         _p(c, C.c_double), _p(trace, C.c_double), C.byref(done), C.byref(fll))
+    _check(st, "em")
+    return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
+
+
+def gmm_fit(pts, K: int, iters: int, tol: float = 0.0, reg: float = 1e-6, seed: int = 0, lloyd_iters: int = 10):
+    pts = _f32(pts)
+    N = pts.shape[0]
+    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
+    trace = np.full(max(iters, 1), np.nan)
+    done, fll = C.c_int(), C.c_double()
+    st = lib().oracle_gmm_fit(_p(pts, C.c_float), N, K, iters, tol, reg, seed, lloyd_iters, _p(w, C.c_double),
+                              _p(m, C.c_double), _p(c, C.c_double), _p(trace, C.c_double), C.byref(done),
+                              C.byref(fll))
+    _check(st, "gmm_fit")
+    return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
+
+
+def kinit(pts, K: int, seed: int, lloyd_iters: int, reg: float):
+    """k-means++ + Lloyd + one-hot M-step: the initial parameters gmm_fit starts EM from."""
+    centers, chosen = kmeanspp(pts, K, seed)
+    centers, labels, done = lloyd(pts, centers, lloyd_iters)
+    w, m, c = init_from_labels(pts, labels, K, reg)
+    return dict(weights=w, means=m, covs=c, centers=centers, labels=labels, chosen=chosen, lloyd_done=done)

@@ -1,0 +1,371 @@
+/*
+ * gira_oracle.c -- plain, slow, obviously-correct FP64 CPU reference for GMM-EM.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, calls or
+ * includes this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code with the CUDA path.
+ *
+ * What it computes (GIRA, arXiv 2307.00071, Sec. V "Expectation Maximization"):
+ *   E-step   responsibilities, Eq. (estep), evaluated in the log domain of
+ *            Eq. (logestep), with the per-component log-density of
+ *            Eq. (simplifiedGaussian):  Sigma = L L^T,  P = L^{-1},
+ *            ln N(x|mu,Sigma) = -1/2 (D ln 2pi + ||P (x-mu)||^2) + sum_j ln P_jj.
+ *   M-step   the paper names it but does not write it; the standard
+ *            maximum-likelihood full-covariance update is used, with the
+ *            conventions of the scikit-learn derivation the paper defers to:
+ *            N_b = sum_n r_nb + 10 eps64,  pi_b = N_b / sum_a N_a,
+ *            mu_b = sum_n r_nb x_n / N_b,
+ *            Sigma_b = sum_n r_nb (x_n-mu_b)(x_n-mu_b)^T / N_b + reg I
+ *            (two passes: exact centring about the new mean).
+ *   KInit    Fig. "information flow": k-means initialisation produces the
+ *            responsibility matrix the EM starts from.  Read as k-means++
+ *            seeding (one candidate per step) followed by Lloyd iterations, then
+ *            the M-step above applied to one-hot responsibilities.
+ *
+ * Precision: every floating-point quantity is binary64, except the k-means
+ * point-to-centre squared distances, which are evaluated in binary32 in the
+ * fixed order   d_i = x_i - c_i;  s = (d0*d0 + d1*d1) + d2*d2   (no fused
+ * multiply-add; compiled with -ffp-contract=off) because they decide integers
+ * (a sampled index, an argmin label) and the GPU takes the same decisions in
+ * that same precision.  k-means centres are rounded to binary32 after each
+ * update, as the GPU stores them.
+ *
+ * Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
+ * counter-based generator: draw j of seed s is the (j+1)-th output of the
+ * SplitMix64 stream started at state s;  u_j = (r_j >> 11) * 2^-53.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+
+#define D 3
+
+/* binary32 expressions must be evaluated in binary32 (no excess precision) */
+#if defined(__FLT_EVAL_METHOD__) && __FLT_EVAL_METHOD__ != 0
+#error "the oracle needs FLT_EVAL_METHOD == 0"
+#endif
+#if defined(__FAST_MATH__)
+#error "the oracle must not be built with -ffast-math"
+#endif
+
+/* status codes (same numbering as the library's, redefined here on purpose) */
+enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_NONFINITE = 2, OR_ERR_NOT_PD = 3, OR_ERR_OOM = 5 };
+
+static int g_last_bad_component = -1;
+int oracle_last_bad_component(void) { return g_last_bad_component; }
+
+/* ---------------------------------------------------------------- RNG -- */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t j) {
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double oracle_uniform(uint64_t seed, uint64_t j) {
+    return (double)(oracle_splitmix64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------ 3x3 algebra --- */
+/* Cholesky Sigma = L L^T (row-major, L lower).  Returns 0, or -1 if a pivot
+ * is not strictly positive (Sigma not positive definite). */
+int oracle_cholesky3(const double *S, double *L) {
+    memset(L, 0, 9 * sizeof(double));
+    for (int j = 0; j < D; ++j) {
+        double s = S[j * D + j];
+        for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
+        if (!(s > 0.0)) return -1;
+        L[j * D + j] = sqrt(s);
+        for (int i = j + 1; i < D; ++i) {
+            double t = S[i * D + j];
+            for (int k = 0; k < j; ++k) t -= L[i * D + k] * L[j * D + k];
+            L[i * D + j] = t / L[j * D + j];
+        }
+    }
+    return 0;
+}
+
+/* P = L^{-1} for lower-triangular L (forward substitution on the identity). */
+void oracle_tri_inverse3(const double *L, double *P) {
+    memset(P, 0, 9 * sizeof(double));
+    for (int c = 0; c < D; ++c) {
+        for (int i = c; i < D; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) t -= L[i * D + k] * P[k * D + c];
+            P[i * D + c] = t / L[i * D + i];
+        }
+    }
+}
+
+/* Eq. (simplifiedGaussian): ln N(x | mu, Sigma) with P = L^{-1}. */
+double oracle_log_gaussian(const double *x, const double *mu, const double *P) {
+    double q = 0.0, logdet = 0.0;
+    for (int i = 0; i < D; ++i) {
+        double y = 0.0;
+        for (int j = 0; j <= i; ++j) y += P[i * D + j] * (x[j] - mu[j]);
+        q += y * y;
+        logdet += log(P[i * D + i]);
+    }
+    return -0.5 * (D * log(2.0 * M_PI) + q) + logdet;
+}
+
+static int all_finite_f(const float *a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(a[i])) return 0;
+    return 1;
+}
+static int all_finite_d(const double *a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(a[i])) return 0;
+    return 1;
+}
+
+/* Precision factors of every component: P_b = chol(Sigma_b)^{-1}. */
+static int precision_factors(int K, const double *covs, double *P) {
+    for (int b = 0; b < K; ++b) {
+        double L[9];
+        if (oracle_cholesky3(covs + 9 * b, L) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
+        oracle_tri_inverse3(L, P + 9 * b);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------ E-step -- */
+/* Eq. (estep) in the form of Eq. (logestep).  Writes resp (N x K, row-major;
+ * may be NULL) and lse_n = ln sum_a pi_a N(x_n|a) (may be NULL); returns the
+ * mean per-point log-likelihood (1/N) sum_n lse_n in *mean_ll. */
+int oracle_estep(const float *pts, int64_t N, int K, const double *weights, const double *means,
+                 const double *covs, double *resp, double *lse, double *mean_ll) {
+    if (N < 1 || K < 1 || !pts || !weights || !means || !covs) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, 3 * N)) return OR_ERR_NONFINITE;
+    if (!all_finite_d(weights, K) || !all_finite_d(means, 3 * K) || !all_finite_d(covs, 9 * K))
+        return OR_ERR_NONFINITE;
+    double *P = (double *)malloc(sizeof(double) * 9 * K);
+    double *a = (double *)malloc(sizeof(double) * K);
+    if (!P || !a) { free(P); free(a); return OR_ERR_OOM; }
+    int st = precision_factors(K, covs, P);
+    if (st != OR_OK) { free(P); free(a); return st; }
+    double total = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        double x[3] = {pts[3 * n], pts[3 * n + 1], pts[3 * n + 2]};
+        double m = -INFINITY;
+        for (int b = 0; b < K; ++b) {
+            a[b] = log(weights[b]) + oracle_log_gaussian(x, means + 3 * b, P + 9 * b);
+            if (a[b] > m) m = a[b];
+        }
+        double s = 0.0;
+        for (int b = 0; b < K; ++b) s += exp(a[b] - m);
+        double l = m + log(s);
+        if (lse) lse[n] = l;
+        if (resp)
+            for (int b = 0; b < K; ++b) resp[n * K + b] = exp(a[b] - l);
+        total += l;
+    }
+    *mean_ll = total / (double)N;
+    free(P);
+    free(a);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------ M-step -- */
+int oracle_mstep(const float *pts, int64_t N, int K, const double *resp, double reg, double *weights,
+                 double *means, double *covs) {
+    if (N < 1 || K < 1 || !pts || !resp || !weights || !means || !covs || !(reg >= 0.0))
+        return OR_ERR_INVALID_ARG;
+    const double tiny = 10.0 * DBL_EPSILON;
+    double nsum = 0.0;
+    for (int b = 0; b < K; ++b) {
+        double nb = 0.0, sx[3] = {0, 0, 0};
+        for (int64_t n = 0; n < N; ++n) {
+            double r = resp[n * K + b];
+            nb += r;
+            for (int i = 0; i < 3; ++i) sx[i] += r * (double)pts[3 * n + i];
+        }
+        nb += tiny;
+        double mu[3];
+        for (int i = 0; i < 3; ++i) mu[i] = sx[i] / nb;
+        double c[9] = {0};
+        for (int64_t n = 0; n < N; ++n) {
+            double r = resp[n * K + b];
+            double d[3];
+            for (int i = 0; i < 3; ++i) d[i] = (double)pts[3 * n + i] - mu[i];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) c[i * 3 + j] += r * d[i] * d[j];
+        }
+        for (int i = 0; i < 9; ++i) c[i] /= nb;
+        for (int i = 0; i < 3; ++i) c[i * 3 + i] += reg;
+        weights[b] = nb;
+        nsum += nb;
+        memcpy(means + 3 * b, mu, sizeof mu);
+        memcpy(covs + 9 * b, c, sizeof c);
+    }
+    for (int b = 0; b < K; ++b) weights[b] /= nsum;
+    /* the new covariances must admit a Cholesky factor for the next E-step */
+    for (int b = 0; b < K; ++b) {
+        double L[9];
+        if (oracle_cholesky3(covs + 9 * b, L) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------ k-means -- */
+/* squared distance in binary32, fixed order, no FMA (see header) */
+static float dist2_f32(const float *x, const float *c) {
+    float d0 = x[0] - c[0], d1 = x[1] - c[1], d2 = x[2] - c[2];
+    float p0 = d0 * d0, p1 = d1 * d1, p2 = d2 * d2;
+    float s = p0 + p1;
+    return s + p2;
+}
+float oracle_dist2_f32(const float *x, const float *c) { return dist2_f32(x, c); }
+
+/* k-means++ seeding (Arthur & Vassilvitskii 2007, one candidate per step).
+ * centers: K x 3 float (out); chosen: K indices into pts (out, may be NULL). */
+int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *centers, int64_t *chosen) {
+    if (N < 1 || K < 1 || K > N || !pts || !centers) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, 3 * N)) return OR_ERR_NONFINITE;
+    float *d2 = (float *)malloc(sizeof(float) * N);
+    if (!d2) return OR_ERR_OOM;
+    int64_t idx = (int64_t)floor(oracle_uniform(seed, 0) * (double)N);
+    if (idx > N - 1) idx = N - 1;
+    for (int j = 0; j < K; ++j) {
+        if (j > 0) {
+            /* D^2(x) = min over the centres chosen so far */
+            double total = 0.0;
+            for (int64_t n = 0; n < N; ++n) {
+                float dn = dist2_f32(pts + 3 * n, centers + 3 * (j - 1));
+                if (j == 1 || dn < d2[n]) d2[n] = dn;
+                total += (double)d2[n];
+            }
+            double u = oracle_uniform(seed, (uint64_t)j);
+            if (total > 0.0) {
+                double t = u * total, prefix = 0.0;
+                idx = -1;
+                int64_t last_pos = -1;
+                for (int64_t n = 0; n < N; ++n) {
+                    prefix += (double)d2[n];
+                    if (d2[n] > 0.0f) last_pos = n;
+                    if (prefix > t) { idx = n; break; }
+                }
+                if (idx < 0) idx = last_pos;  /* t rounded up to the total */
+            } else {
+                idx = (int64_t)floor(u * (double)N);  /* every point is a chosen centre */
+                if (idx > N - 1) idx = N - 1;
+            }
+        }
+        for (int i = 0; i < 3; ++i) centers[3 * j + i] = pts[3 * idx + i];
+        if (chosen) chosen[j] = idx;
+    }
+    free(d2);
+    return OR_OK;
+}
+
+/* labels_n = argmin_b ||x_n - c_b||^2 in binary32, ties to the lowest b. */
+static int64_t assign_labels(const float *pts, int64_t N, int K, const float *centers, int32_t *labels) {
+    int64_t changed = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        int best = 0;
+        float bd = dist2_f32(pts + 3 * n, centers);
+        for (int b = 1; b < K; ++b) {
+            float d = dist2_f32(pts + 3 * n, centers + 3 * b);
+            if (d < bd) { bd = d; best = b; }
+        }
+        if (labels[n] != best) ++changed;
+        labels[n] = best;
+    }
+    return changed;
+}
+
+/* Lloyd iterations from the given centres (in/out).  Each iteration: centres
+ * = FP64 mean of their points (rounded to binary32; an empty cluster keeps its
+ * centre), then re-assign; stop after lloyd_iters or when no label changed.
+ * labels (out, N) hold the final assignment. */
+int oracle_lloyd(const float *pts, int64_t N, int K, float *centers, int lloyd_iters, int32_t *labels,
+                 int *iters_done) {
+    if (N < 1 || K < 1 || K > N || lloyd_iters < 0 || !pts || !centers || !labels) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, 3 * N) || !all_finite_f(centers, 3 * K)) return OR_ERR_NONFINITE;
+    for (int64_t n = 0; n < N; ++n) labels[n] = -1;
+    assign_labels(pts, N, K, centers, labels);
+    double *sum = (double *)malloc(sizeof(double) * 4 * K);
+    if (!sum) return OR_ERR_OOM;
+    int it = 0;
+    while (it < lloyd_iters) {
+        memset(sum, 0, sizeof(double) * 4 * K);
+        for (int64_t n = 0; n < N; ++n) {
+            int b = labels[n];
+            for (int i = 0; i < 3; ++i) sum[4 * b + i] += (double)pts[3 * n + i];
+            sum[4 * b + 3] += 1.0;
+        }
+        for (int b = 0; b < K; ++b)
+            if (sum[4 * b + 3] > 0.0)
+                for (int i = 0; i < 3; ++i) centers[3 * b + i] = (float)(sum[4 * b + i] / sum[4 * b + 3]);
+        ++it;
+        if (assign_labels(pts, N, K, centers, labels) == 0) break;
+    }
+    if (iters_done) *iters_done = it;
+    free(sum);
+    return OR_OK;
+}
+
+/* One-hot responsibilities from labels, then the M-step. */
+int oracle_init_from_labels(const float *pts, int64_t N, int K, const int32_t *labels, double reg,
+                            double *weights, double *means, double *covs) {
+    if (N < 1 || K < 1 || !labels) return OR_ERR_INVALID_ARG;
+    double *resp = (double *)calloc((size_t)N * (size_t)K, sizeof(double));
+    if (!resp) return OR_ERR_OOM;
+    for (int64_t n = 0; n < N; ++n) {
+        if (labels[n] < 0 || labels[n] >= K) { free(resp); return OR_ERR_INVALID_ARG; }
+        resp[n * K + labels[n]] = 1.0;
+    }
+    int st = oracle_mstep(pts, N, K, resp, reg, weights, means, covs);
+    free(resp);
+    return st;
+}
+
+/* ------------------------------------------------------------ EM fit -- */
+/* EM from the given parameters (in/out).  Iteration t (1-based): E-step with
+ * the current parameters gives ll_t (mean per-point log-likelihood, stored in
+ * trace[t-1]), then the M-step.  Stops after `iters` iterations or when
+ * t > 1 and |ll_t - ll_{t-1}| < tol.  final_ll (may be NULL) is the mean
+ * log-likelihood of the returned parameters. */
+int oracle_em(const float *pts, int64_t N, int K, int iters, double tol, double reg, double *weights,
+              double *means, double *covs, double *trace, int *iters_done, double *final_ll) {
+    if (N < 1 || K < 1 || iters < 0 || !(tol >= 0.0) || !(reg >= 0.0)) return OR_ERR_INVALID_ARG;
+    double *resp = (double *)malloc(sizeof(double) * (size_t)N * (size_t)K);
+    if (!resp) return OR_ERR_OOM;
+    double prev = -INFINITY;
+    int t = 0, st = OR_OK;
+    while (t < iters) {
+        double ll;
+        st = oracle_estep(pts, N, K, weights, means, covs, resp, NULL, &ll);
+        if (st != OR_OK) break;
+        st = oracle_mstep(pts, N, K, resp, reg, weights, means, covs);
+        if (st != OR_OK) break;
+        if (trace) trace[t] = ll;
+        ++t;
+        if (fabs(ll - prev) < tol) break;
+        prev = ll;
+    }
+    if (iters_done) *iters_done = t;
+    if (st == OR_OK && final_ll) st = oracle_estep(pts, N, K, weights, means, covs, NULL, NULL, final_ll);
+    free(resp);
+    return st;
+}
+
+/* Full fit: k-means++ (seed) + Lloyd (lloyd_iters) + init M-step, then EM. */
+int oracle_gmm_fit(const float *pts, int64_t N, int K, int iters, double tol, double reg, uint64_t seed,
+                   int lloyd_iters, double *weights, double *means, double *covs, double *trace,
+                   int *iters_done, double *final_ll) {
+    if (N < 1 || K < 1 || K > N) return OR_ERR_INVALID_ARG;
+    float *c = (float *)malloc(sizeof(float) * 3 * K);
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * N);
+    if (!c || !lab) { free(c); free(lab); return OR_ERR_OOM; }
+    int st = oracle_kmeanspp(pts, N, K, seed, c, NULL);
+    if (st == OR_OK) st = oracle_lloyd(pts, N, K, c, lloyd_iters, lab, NULL);
+    if (st == OR_OK) st = oracle_init_from_labels(pts, N, K, lab, reg, weights, means, covs);
+    free(c);
+    free(lab);
+    if (st != OR_OK) return st;
+    return oracle_em(pts, N, K, iters, tol, reg, weights, means, covs, trace, iters_done, final_ll);
+}

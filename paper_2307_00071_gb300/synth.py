@@ -1,0 +1,176 @@
+"""Seeded synthetic point clouds for the GMM-EM workloads.
+
+This module only *generates inputs*; it contains none of the EM arithmetic (no
+log-densities, responsibilities, k-means or sufficient statistics). Both the
+CUDA path (tests, bench) and the FP64 oracle (tests) consume what it returns,
+so it imports neither of them.
+
+Workloads (all numpy PCG64 ``default_rng(seed)``):
+
+* :func:`gmm_cloud` -- points drawn from a random full-covariance 3D GMM:
+  means uniform in ``[-2, 2]^3`` m, covariance ``R diag(lam) R^T`` with
+  ``lam`` log-uniform in ``[1e-4, 1e-2]`` m^2 and ``R`` Haar-random, weights
+  Dirichlet(1), per-component counts multinomial.  The 20k-point, K=8 cloud is
+  the small workload; it stands in for no dataset.
+* :func:`depth_frame` -- a 640x480 pinhole depth image (fx = fy = 525,
+  cx = 319.5, cy = 239.5) of a procedural scene (ground plane, far wall,
+  20 boxes and spheres of 0.2-1.5 m at 0.5-8 m), with N(0, 5 mm) depth noise
+  and 10 % pixel dropout, back-projected to ~276k camera-frame points.  It
+  stands in for the Augmented ICL-NUIM ``livingroom1`` frame that the paper
+  times SOGMM on (Sec. IV-A), which is not available here; only its image
+  shape and intrinsics are reproduced.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+FX = FY = 525.0
+CX, CY = 319.5, 239.5
+WIDTH, HEIGHT = 640, 480
+
+
+@dataclasses.dataclass
+class GMMCloud:
+    points: np.ndarray      # (N, 3) float32
+    weights: np.ndarray     # (K,)   float64, generating weights
+    means: np.ndarray       # (K, 3) float64
+    covs: np.ndarray        # (K, 3, 3) float64
+    labels: np.ndarray      # (N,)   int32 generating component of each point
+
+
+def haar_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed orthogonal 3x3 matrix (QR of a Gaussian, sign-fixed)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def gmm_cloud(n: int = 20_000, k: int = 8, seed: int = 0, lam_lo: float = 1e-4, lam_hi: float = 1e-2,
+              box: float = 2.0, shuffle: bool = True) -> GMMCloud:
+    """Sample ``n`` points from a random K-component full-covariance GMM."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-box, box, size=(k, 3))
+    covs = np.empty((k, 3, 3))
+    factors = np.empty((k, 3, 3))
+    for b in range(k):
+        rot = haar_rotation(rng)
+        lam = np.exp(rng.uniform(np.log(lam_lo), np.log(lam_hi), size=3))
+        covs[b] = (rot * lam[None, :]) @ rot.T
+        factors[b] = rot * np.sqrt(lam)[None, :]
+    weights = rng.dirichlet(np.ones(k))
+    counts = rng.multinomial(n, weights)
+    pts = np.empty((n, 3))
+    labels = np.empty(n, dtype=np.int32)
+    at = 0
+    for b in range(k):
+        c = int(counts[b])
+        z = rng.standard_normal((c, 3))
+        pts[at:at + c] = means[b] + z @ factors[b].T
+        labels[at:at + c] = b
+        at += c
+    if shuffle:
+        perm = rng.permutation(n)
+        pts, labels = pts[perm], labels[perm]
+    return GMMCloud(pts.astype(np.float32), weights, means, covs, labels)
+
+
+# --------------------------------------------------------------------------------------
+# Procedural depth frame
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class DepthFrame:
+    points: np.ndarray      # (N, 3) float32, camera frame (x right, y down, z forward), metres
+    depth: np.ndarray       # (H, W) float32, 0 where dropped
+    pitch_deg: float
+
+
+def _rays_world(pitch: float):
+    """Unit-free ray directions for every pixel, in a world frame with z up.
+
+    Camera frame is OpenCV (x right, y down, z forward).  World: X right,
+    Y forward (horizontal), Z up; the camera is pitched down by ``pitch``.
+    Returns (dirs_world (H*W, 3), dirs_cam (H*W, 3)) with dirs_cam[:, 2] == 1.
+    """
+    u, v = np.meshgrid(np.arange(WIDTH, dtype=np.float64), np.arange(HEIGHT, dtype=np.float64))
+    dc = np.stack([(u - CX) / FX, (v - CY) / FY, np.ones_like(u)], axis=-1).reshape(-1, 3)
+    c, s = np.cos(pitch), np.sin(pitch)
+    # camera axes expressed in world coordinates
+    x_w = np.array([1.0, 0.0, 0.0])
+    z_w = np.array([0.0, c, -s])            # forward, tilted down
+    y_w = np.array([0.0, -s, -c])           # image-down axis
+    rot = np.stack([x_w, y_w, z_w], axis=1)  # columns: camera axes in world
+    return dc @ rot.T, dc, rot
+
+
+def depth_frame(seed: int = 1, n_objects: int = 20, noise_sigma: float = 0.005, dropout: float = 0.1,
+                wall_dist: float = 8.0, cam_height: float = 1.5) -> DepthFrame:
+    """Ray-cast a procedural scene into a 640x480 depth image and back-project it."""
+    rng = np.random.default_rng(seed)
+    pitch = np.deg2rad(rng.uniform(20.0, 30.0))
+    dw, dc, rot = _rays_world(pitch)
+    origin = np.array([0.0, 0.0, cam_height])
+    n_rays = dw.shape[0]
+    t_best = np.full(n_rays, np.inf)
+
+    def take(t):
+        ok = (t > 1e-6) & (t < t_best)
+        t_best[ok] = t[ok]
+
+    # ground plane Z = 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        take(np.where(dw[:, 2] < 0, -origin[2] / dw[:, 2], np.inf))
+        # far wall Y = wall_dist (tall enough to catch every upward ray)
+        take(np.where(dw[:, 1] > 0, (wall_dist - origin[1]) / dw[:, 1], np.inf))
+    half_fov = np.arctan(CX / FX)
+    for _ in range(n_objects):
+        size = rng.uniform(0.2, 1.5)
+        dist = rng.uniform(0.5, wall_dist)
+        lateral = rng.uniform(-1.0, 1.0) * np.tan(half_fov) * dist
+        if rng.uniform() < 0.5:     # sphere resting on the ground
+            r = 0.5 * size
+            ctr = np.array([lateral, dist, r])
+            oc = origin - ctr
+            b = dw @ oc
+            a = np.einsum("ij,ij->i", dw, dw)
+            cc = oc @ oc - r * r
+            disc = b * b - a * cc
+            with np.errstate(invalid="ignore"):
+                t = np.where(disc >= 0, (-b - np.sqrt(np.maximum(disc, 0))) / a, np.inf)
+            take(t)
+        else:                       # yawed box resting on the ground
+            half = 0.5 * rng.uniform(0.2, 1.5, size=3)
+            half[0] = 0.5 * size
+            yaw = rng.uniform(0, np.pi)
+            cy_, sy_ = np.cos(yaw), np.sin(yaw)
+            rz = np.array([[cy_, -sy_, 0], [sy_, cy_, 0], [0, 0, 1.0]])
+            ctr = np.array([lateral, dist, half[2]])
+            o_l = rz.T @ (origin - ctr)
+            d_l = dw @ rz             # (rz^T d) for every ray
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t1 = (-half[None, :] - o_l[None, :]) / d_l
+                t2 = (half[None, :] - o_l[None, :]) / d_l
+            tmin = np.nanmax(np.minimum(t1, t2), axis=1)
+            tmax = np.nanmin(np.maximum(t1, t2), axis=1)
+            take(np.where((tmax >= tmin) & (tmax > 0), tmin, np.inf))
+    hit = np.isfinite(t_best)
+    # depth along the optical axis: dirs_cam has z == 1, so z_cam == t
+    z = np.where(hit, t_best, 0.0)
+    z = z + rng.normal(0.0, noise_sigma, size=n_rays) * hit
+    keep = hit & (rng.uniform(size=n_rays) >= dropout) & (z > 0)
+    depth = np.where(keep, z, 0.0).reshape(HEIGHT, WIDTH).astype(np.float32)
+    u, v = np.meshgrid(np.arange(WIDTH, dtype=np.float64), np.arange(HEIGHT, dtype=np.float64))
+    zz = depth.astype(np.float64)
+    m = zz > 0
+    pts = np.stack([(u[m] - CX) * zz[m] / FX, (v[m] - CY) * zz[m] / FY, zz[m]], axis=1)
+    n = pts.shape[0]
+    if not 250_000 <= n <= 300_000:
+        raise AssertionError(f"depth frame produced {n} points, outside [250k, 300k]")
+    return DepthFrame(pts.astype(np.float32), depth, float(np.rad2deg(pitch)))
+
+
+def uniform_cloud(n: int, seed: int = 0, scale: float = 1.0) -> np.ndarray:
+    """Plain uniform points in a cube (edge cases, ragged sizes)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, size=(n, 3)).astype(np.float32)

@@ -1,0 +1,307 @@
+#!/usr/bin/env python
+"""Benchmark: EM fit of a K=512 full-covariance GMM to a synthetic 640x480 depth frame.
+
+One step = one full ``gira_gmm_fit`` (pack, k-means++ seeding, Lloyd, one-hot
+M-step, up to 30 EM iterations with tol 1e-4 on the mean log-likelihood, final
+log-likelihood) on a ~276k-point frame already resident in HBM.  Prints one
+JSON line (rank 0).
+
+value       EM point-component-iterations per second, whole job:
+            sum over ranks of N*K*iters_done / max over ranks of summed step time
+            (k-means++/Lloyd time is inside the step time, its work is not counted)
+roofline    the fused E-step/statistics kernel against the FP32-pipe roofline
+            (23 FP32-pipe operations per point-component-iteration)
+e2e         the same metric through the C ABI with host buffers (pinned points in,
+            model and log-likelihood trace out, copies inside the timed region)
+cpu_baseline  the FP64 oracle on the host cores, one EM iteration of the frame
+
+``--impl reference`` times the oracle alone (rank 0; the baseline arm).
+Multi-GPU (torchrun): every rank fits its own frame (weak scaling, no collective
+on the data path; barriers only bracket the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EM point-component-iters/sec and ms per 300k-pt K=512 frame; % FP32/SFU roofline"
+UNIT = "point-component-iters/s"
+K, ITERS, TOL, REG, SEED, LLOYD = 512, 30, 1e-4, 1e-6, 0, 10
+FP32_OPS_PER_UNIT = 23          # algorithmic FP32-pipe operations per (point, component, iteration)
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "estep_frame276k_k512.traffic.json")
+EM_SOURCE = os.path.join(ROOT, "paper_2307_00071_gb300", "csrc", "em_kernels.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gira", "reference"], default="gira")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(n_points):
+    return {"workload": f"synthetic 640x480 depth frame (procedural scene, 5 mm noise, 10% dropout) -> "
+                        f"{n_points} points; K={K} full-covariance GMM; k-means++ + {LLOYD} Lloyd + up to "
+                        f"{ITERS} EM iters, tol {TOL:g}",
+            "N": int(n_points), "K": K, "iters": ITERS, "tol": TOL, "reg_covar": REG,
+            "l2": "flushed between steps (256 MB write); frame (4.4 MB) is L2-resident within a fit"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("sm_max_mhz", 2070.0)), "MEASURED_PEAKS.json sm_max_mhz"
+    return 2070.0, "fallback 2070 MHz"
+
+
+def source_hash():
+    with open(EM_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per E-step launch from the committed ncu capture, if the kernel is unchanged."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("em_kernels_sha256_16") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i] and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2307_00071_gb300 import synth
+    frame = synth.depth_frame(seed=1)
+    rng = np.random.default_rng(123)
+    m = 32_768
+    sample = frame.points[np.sort(rng.choice(len(frame.points), m, replace=False))]
+    ki = oracle.kinit(sample, K, seed=SEED, lloyd_iters=LLOYD, reg=REG)
+    w, mu, cov = ki["weights"], ki["means"], ki["covs"]
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, resp, _ = oracle.estep(sample, w, mu, cov)
+        w, mu, cov = oracle.mstep(sample, resp, REG)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = m * K * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(len(frame.points)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one EM iteration (E-step + M-step) per step on a {m}-point random subset "
+                                       f"of the frame, K={K}, from the oracle's own k-means init"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- gira arm
+def cpu_baseline(frame_pts, init):
+    import oracle
+    w, mu, cov = init
+    t0 = time.perf_counter()
+    _, resp, _ = oracle.estep(frame_pts, w, mu, cov)
+    oracle.mstep(frame_pts, resp, REG)
+    dt = time.perf_counter() - t0
+    n = len(frame_pts)
+    return {"value": n * K / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one EM iteration (E-step + M-step, binary64, single thread) on the full {n}-point frame, "
+                      f"K={K}, from the library's KInit parameters; {dt:.1f} s"}
+
+
+def run_gira(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2307_00071_gb300 import gira, synth
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    frame = synth.depth_frame(seed=1 + rank)
+    n = len(frame.points)
+    pts = torch.as_tensor(frame.points, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = dict(weights=torch.empty(K, device="cuda"), means=torch.empty(K, 3, device="cuda"),
+               covs=torch.empty(K, 3, 3, device="cuda"))
+
+    def fit(p, **kw):
+        return gira.gira_gmm_fit(p, K, iters=ITERS, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD, **kw)
+
+    for _ in range(args.warmup):
+        fit(pts, **out)
+    gira.gira_profile_enable(True)
+    gira.gira_profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    units, iters_seen = 0, []
+    barrier()
+    clocks = ClockSampler(local)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        r = fit(pts, **out)
+        ev[i][1].record()
+        units += n * K * r["iters_done"]
+        iters_seen.append(r["iters_done"])
+    barrier()
+    clk = clocks.stop()
+    prof = gira.gira_profile_read(reset=True)
+    gira.gira_profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    pinned = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+    pinned.copy_(torch.as_tensor(frame.points))
+    host_out = dict(weights=np.empty(K, np.float32), means=np.empty((K, 3), np.float32),
+                    covs=np.empty((K, 3, 3), np.float32))
+    fit(pinned, **host_out)   # warm
+    e2e_units, e2e_t = 0, 0.0
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fit(pinned, **host_out)
+        e2e_t += time.perf_counter() - t0
+        e2e_units += n * K * r["iters_done"]
+    h2d = pinned.numel() * 4
+    d2h = sum(a.nbytes for a in host_out.values()) + 8 * ITERS
+
+    # aggregate over ranks
+    vals = torch.tensor([units, total_s, e2e_units, e2e_t], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        dist.all_gather(gathered, vals)
+        g = torch.stack(gathered).cpu().numpy()
+        units_all, t_max, e2e_units_all, e2e_tmax = g[:, 0].sum(), g[:, 1].max(), g[:, 2].sum(), g[:, 3].max()
+    else:
+        units_all, t_max, e2e_units_all, e2e_tmax = units, total_s, e2e_units, e2e_t
+
+    if rank == 0:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz, mhz_src = measured_peaks()
+        peak_units = FP32_LANES_PER_SM * sms * mhz * 1e6 / FP32_OPS_PER_UNIT
+        est_launches = max(prof["estep_launches"], 1)
+        avg_estep_s = prof["estep_ms"] / est_launches / 1e3
+        achieved = n * K / avg_estep_s if avg_estep_s > 0 else 0.0
+        tr = traffic_per_launch()
+        line = {
+            "metric": METRIC, "value": units_all / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n),
+            "ms_per_frame": {"with_init": 1e3 * t_max / args.steps,
+                             "em_only": prof["em_ms"] / args.steps, "init": prof["init_ms"] / args.steps},
+            "em_only_units_per_s": n * K * prof["em_iters"] / (prof["em_ms"] / 1e3) if prof["em_ms"] else None,
+            "iters_done": iters_seen,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_units, "unit": UNIT,
+                         "frac": achieved / peak_units, "traffic": tr,
+                         "kernel": "estep_kernel<2,128,3,true> (fused E-step + M-step statistics)",
+                         "launch_ms": avg_estep_s * 1e3,
+                         "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {mhz:.0f} MHz ({mhz_src}) / "
+                                       f"{FP32_OPS_PER_UNIT} FP32 ops per unit"},
+            "e2e": {"value": e2e_units_all / e2e_tmax, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": prof["kernel_launches"],
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
+                                     final_loglik=False)
+            line["cpu_baseline"] = cpu_baseline(frame.points, (init["weights"], init["means"], init["covs"]))
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gira(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * gira.h -- C ABI of libgira: EM fitting of full-covariance 3D Gaussian mixture
+ * models to point clouds on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow GIRA (Goel & Tabib, arXiv 2307.00071), Sec. V
+ * "Implementation Details": KInit (Fig. "information flow": a k-means
+ * initialisation yields the responsibilities EM starts from), the E-step
+ * (Eq. estep, computed in the log form of Eq. logestep with the Cholesky
+ * log-density of Eq. simplifiedGaussian) and the M-step.  The model layout is
+ * the paper's (Sec. V: weights (1,K,1), means (1,K,D), covariances (1,K,D,D))
+ * with D = 3.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Points are N x 3 binary32, row-major (x0,y0,z0,x1,...), N >= 1.
+ *  - Pointer arguments marked [host|device] may point to host memory or to
+ *    device memory of the current CUDA device; the library detects which
+ *    (cudaPointerGetAttributes).  Host buffers are staged through
+ *    library-owned device memory; the copies are part of the call.
+ *    Pointers marked [host] must be host memory.
+ *  - The caller owns every buffer it passes.  The library owns a device
+ *    workspace cached per device (grown on demand, freed by
+ *    gira_release_workspace).  Calls on one device are serialised by a
+ *    per-device lock.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All GPU
+ *    work is issued on it; every call synchronises that stream before it
+ *    returns, so outputs are ready when the call returns.
+ *  - Errors are returned as gira_status; nothing aborts.  On error the
+ *    outputs are unspecified; gira_last_error_message() (thread-local) says
+ *    why and gira_last_error_component() names the offending component for
+ *    GIRA_ERR_NOT_PD.
+ */
+#ifndef GIRA_H
+#define GIRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GIRA_OK = 0,
+    GIRA_ERR_INVALID_ARG = 1,      /* N < 1, K < 1, K > N, K > GIRA_MAX_K, iters < 0, tol < 0 or NaN,
+                                      reg_covar < 0 or NaN, a required pointer NULL, weights <= 0 */
+    GIRA_ERR_NONFINITE_INPUT = 2,  /* NaN or Inf in the points or in caller-supplied parameters */
+    GIRA_ERR_NOT_PD = 3,           /* a covariance has no Cholesky factor (pivot <= 0 after reg_covar) */
+    GIRA_ERR_CUDA = 4,             /* a CUDA runtime call failed; the message carries cudaGetErrorString */
+    GIRA_ERR_OOM = 5,              /* the device workspace could not be allocated */
+    GIRA_ERR_TIMEOUT = 6,          /* reserved for bounded device-side waits */
+    GIRA_ERR_NUMERIC = 7           /* a point's likelihood underflows binary32 under every component */
+} gira_status;
+
+/* Largest number of mixture components one call accepts. */
+#define GIRA_MAX_K 1024
+
+typedef enum {
+    GIRA_INIT_KMEANS = 0,  /* k-means++ (seed) + Lloyd (lloyd_iters) + one-hot M-step */
+    GIRA_INIT_PARAMS = 1   /* start from the weights/means/covs passed in (they are read, then overwritten) */
+} gira_init_mode;
+
+typedef struct {
+    int iters;          /* maximum EM iterations (>= 0) */
+    double tol;         /* stop after iteration t > 1 when |l_t - l_{t-1}| < tol (mean per-point loglik); 0 = never */
+    double reg_covar;   /* added to every covariance diagonal after each M-step (m^2), >= 0 */
+    uint64_t seed;      /* k-means++ seed (SplitMix64 counter stream) */
+    int lloyd_iters;    /* Lloyd iterations after k-means++ (>= 0; stops early when no label changes) */
+    int init_mode;      /* gira_init_mode */
+} gira_fit_opts;
+
+/* Fill `opts` with the defaults: iters 100, tol 1e-3, reg_covar 1e-6, seed 0, lloyd_iters 10,
+ * init_mode GIRA_INIT_KMEANS. */
+void gira_fit_opts_default(gira_fit_opts *opts);
+
+/*
+ * gira_kmeans_init -- KInit seeding (Sec. V, Fig. "information flow").
+ *
+ * k-means++ (Arthur & Vassilvitskii 2007, one candidate per step): centre 0
+ * is point floor(u_0 N); centre j is the first point n whose running sum of
+ * D^2 (binary64 over binary32 squared distances to the nearest centre chosen
+ * so far) exceeds u_j * sum D^2, where u_j is draw j of the SplitMix64
+ * counter stream of `seed` (top 53 bits / 2^53).  Then Lloyd iterations:
+ * labels = argmin_b ||x - c_b||^2 (binary32, ties to the lowest b), centres
+ * = binary64 mean of their points rounded to binary32 (empty clusters keep
+ * their centre), until no label changes or `lloyd_iters` updates were made.
+ *
+ *   points       [host|device] N x 3 binary32 (read)
+ *   n, k         1 <= k <= n, k <= GIRA_MAX_K
+ *   centers      [host|device] K x 3 binary32 (written)
+ *   labels       [host|device] N int32 final labels (written), or NULL
+ *   iters_done   [host] number of Lloyd centre updates made, or NULL
+ */
+gira_status gira_kmeans_init(const float *points, int64_t n, int k, uint64_t seed, int lloyd_iters,
+                             float *centers, int32_t *labels, int *iters_done, void *stream);
+
+/*
+ * gira_gmm_fit -- EM fit of a K-component full-covariance GMM (Sec. V).
+ *
+ * Initialisation per opts->init_mode.  Iteration t = 1, 2, ...: the E-step
+ * with the current parameters gives the mean per-point log-likelihood l_t
+ * (stored in loglik_trace[t-1]) and the sufficient statistics of the
+ * responsibilities; the M-step then sets
+ *   N_b = sum_n r_nb + 10 eps64,  pi_b = N_b / sum_a N_a,
+ *   mu_b = sum_n r_nb x_n / N_b,
+ *   Sigma_b = sum_n r_nb (x_n - mu_b)(x_n - mu_b)^T / N_b + reg_covar I.
+ * The loop ends after opts->iters iterations, or after iteration t > 1 with
+ * |l_t - l_{t-1}| < opts->tol.
+ *
+ *   points        [host|device] N x 3 binary32 (read)
+ *   weights       [host|device] K binary32          (written; read first when GIRA_INIT_PARAMS)
+ *   means         [host|device] K x 3 binary32      (same)
+ *   covs          [host|device] K x 3 x 3 binary32  (same; symmetric positive definite when read)
+ *   loglik_trace  [host] opts->iters binary64, or NULL
+ *   iters_done    [host] iterations run, or NULL
+ *   final_loglik  [host] mean per-point log-likelihood of the returned parameters, or NULL
+ */
+gira_status gira_gmm_fit(const float *points, int64_t n, int k, const gira_fit_opts *opts, float *weights,
+                         float *means, float *covs, double *loglik_trace, int *iters_done,
+                         double *final_loglik, void *stream);
+
+/*
+ * gira_gmm_loglik -- per-point log-likelihood under a GMM: the log-sum-exp of
+ * Eq. logestep, ln sum_b pi_b N(x_n | mu_b, Sigma_b), with ln N from
+ * Eq. simplifiedGaussian.
+ *
+ *   points       [host|device] N x 3 binary32
+ *   weights      [host|device] K binary32, > 0 (used as given; not renormalised)
+ *   means        [host|device] K x 3 binary32
+ *   covs         [host|device] K x 3 x 3 binary32, symmetric positive definite
+ *   mean_loglik  [host] (1/N) sum_n ln p(x_n) (written), or NULL
+ *   per_point    [host|device] N binary32 ln p(x_n) (written), or NULL
+ */
+gira_status gira_gmm_loglik(const float *points, int64_t n, int k, const float *weights, const float *means,
+                            const float *covs, double *mean_loglik, float *per_point, void *stream);
+
+/*
+ * Profiling (off by default; process-wide).  When enabled, each call records
+ * CUDA events on its stream around its phases and around every launch of the
+ * fused E-step/statistics kernel, and accumulates the device times below when
+ * it synchronises.  Times are device times in milliseconds.
+ */
+typedef struct {
+    long long calls;            /* library calls accumulated */
+    long long kernel_launches;  /* kernels those calls launched (early-exiting ones included) */
+    long long estep_launches;   /* launches of the fused E-step/statistics kernel that did work */
+    double estep_ms;            /* summed duration of those launches */
+    long long em_iters;         /* EM iterations run */
+    double init_ms;             /* pack + KInit (k-means++, Lloyd, one-hot M-step) or parameter upload */
+    double em_ms;               /* the EM loop: E-step, reduction and FP64 finalize of every iteration */
+    double total_ms;            /* whole calls, first upload to last download */
+} gira_profile;
+
+/* Turn profiling on (on != 0) or off. */
+void gira_profile_enable(int on);
+
+/* Copy the accumulated profile to *out (may be NULL); reset it when reset != 0. */
+gira_status gira_profile_read(gira_profile *out, int reset);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *gira_last_error_message(void);
+
+/* Component index behind the last GIRA_ERR_NOT_PD on this thread, else -1. */
+int gira_last_error_component(void);
+
+/* Free the device workspace of every device (the next call re-allocates it). */
+gira_status gira_release_workspace(void);
+
+/* Library version string, e.g. "gira-gb300 0.1.0 sm_103a". */
+const char *gira_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIRA_H */

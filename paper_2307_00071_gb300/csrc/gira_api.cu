@@ -1,0 +1,597 @@
+// gira_api.cu -- the extern "C" entry points declared in include/gira.h.
+//
+// Host-side orchestration only: argument validation, the per-device workspace,
+// staging of host buffers, and the stream-ordered launch sequence
+//   pack -> KInit (k-means++, Lloyd, one-hot M-step) or caller parameters
+//        -> iters x [fused E-step/statistics -> reduce -> FP64 finalize]
+//        -> final log-likelihood -> model out.
+// Every arithmetic step of the method runs in the CUDA kernels; no loop waits
+// on the host between EM iterations (convergence is decided on the device).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gira_internal.cuh"
+
+using namespace gira;
+
+namespace {
+
+thread_local std::string t_msg;
+thread_local int t_bad = -1;
+
+gira_status fail(gira_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_msg = buf;
+    return s;
+}
+
+#define GIRA_CUDA(call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
+            return fail(GIRA_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+        }                                                                                     \
+    } while (0)
+
+// ---------------------------------------------------------------- workspace
+struct DeviceWs {
+    std::mutex mu;
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_table_mu;
+std::vector<DeviceWs*> g_ws;
+
+DeviceWs* ws_for(int dev) {
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1, nullptr);
+    if (!g_ws[dev]) g_ws[dev] = new DeviceWs();
+    return g_ws[dev];
+}
+
+// Bump allocator: run once with base == nullptr to size, then for real.
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += std::max<size_t>(count, 1) * sizeof(T);
+        return p;
+    }
+};
+
+gira_status ensure(DeviceWs* ws, size_t need, cudaStream_t s) {
+    if (ws->bytes >= need) return GIRA_OK;
+    GIRA_CUDA(cudaStreamSynchronize(s));
+    if (ws->ptr) GIRA_CUDA(cudaFree(ws->ptr));
+    ws->ptr = nullptr;
+    ws->bytes = 0;
+    size_t want = need + need / 4;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GIRA_ERR_OOM, "cannot allocate %zu bytes of device workspace: %s", need,
+                        cudaGetErrorString(e));
+        }
+        want = need;
+    }
+    ws->ptr = p;
+    ws->bytes = want;
+    return GIRA_OK;
+}
+
+// ---------------------------------------------------------------- pointers
+enum class Kind { Host, Device, Foreign };
+
+Kind kind_of(const void* p, int dev) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return Kind::Host;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == dev ? Kind::Device : Kind::Foreign;
+    return Kind::Host;
+}
+
+struct Ctx {
+    int dev = 0, sms = 1;
+    cudaStream_t s = nullptr;
+};
+
+void reset_error() {
+    t_msg.clear();
+    t_bad = -1;
+}
+
+gira_status begin(Ctx& c, void* stream) {
+    GIRA_CUDA(cudaGetDevice(&c.dev));
+    GIRA_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.dev));
+    c.s = reinterpret_cast<cudaStream_t>(stream);
+    return GIRA_OK;
+}
+
+gira_status check_ptr(const void* p, const char* name, int dev, Kind* k) {
+    *k = kind_of(p, dev);
+    if (*k == Kind::Foreign) return fail(GIRA_ERR_INVALID_ARG, "%s is device memory of another device", name);
+    return GIRA_OK;
+}
+
+gira_status device_status(const DeviceState& h) {
+    switch (h.error) {
+        case 0: return GIRA_OK;
+        case GIRA_ERR_NONFINITE_INPUT: return fail(GIRA_ERR_NONFINITE_INPUT, "NaN or Inf in the points or parameters");
+        case GIRA_ERR_NOT_PD:
+            t_bad = h.bad_component;
+            return fail(GIRA_ERR_NOT_PD, "covariance of component %d is not positive definite", h.bad_component);
+        case GIRA_ERR_INVALID_ARG: return fail(GIRA_ERR_INVALID_ARG, "a mixture weight is not positive");
+        case GIRA_ERR_NUMERIC:
+            return fail(GIRA_ERR_NUMERIC, "a point's likelihood underflows binary32 under every component");
+        default: return fail((gira_status)h.error, "device error %d", h.error);
+    }
+}
+
+gira_status check_nk(int64_t n, int k) {
+    if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "n = %lld < 1", (long long)n);
+    if (k < 1 || k > GIRA_MAX_K) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K);
+    if (k > n) return fail(GIRA_ERR_INVALID_ARG, "k = %d > n = %lld", k, (long long)n);
+    return GIRA_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        gira_status st_ = (x);          \
+        if (st_ != GIRA_OK) return st_; \
+    } while (0)
+
+#define LAUNCH(x) GIRA_CUDA(x)
+#define COUNTED(prof, n, x) \
+    do {                      \
+        LAUNCH(x);            \
+        (prof).launches += (n); \
+    } while (0)
+
+// ---------------------------------------------------------------- profiling
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+gira_profile g_prof{};
+
+// Events of one call: phase marks plus a pair per E-step launch.
+struct CallProfile {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaEvent_t t0 = nullptr, t_init = nullptr, t_em = nullptr, t_end = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> estep;
+    long long launches = 0;
+
+    cudaEvent_t mark() {
+        if (!on) return nullptr;
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+            pool.push_back(e);
+        }
+        cudaEvent_t e = pool[used++];
+        cudaEventRecord(e, s);
+        return e;
+    }
+    ~CallProfile() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+    static double ms(cudaEvent_t a, cudaEvent_t b) {
+        float v = 0.f;
+        if (!a || !b || cudaEventElapsedTime(&v, a, b) != cudaSuccess) { cudaGetLastError(); return 0.0; }
+        return v;
+    }
+    // after the stream has been synchronised
+    void commit(int em_iters, int estep_done) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.calls += 1;
+        g_prof.kernel_launches += launches;
+        if (!on) return;
+        for (int i = 0; i < (int)estep.size() && i < estep_done; ++i) g_prof.estep_ms += ms(estep[i].first, estep[i].second);
+        g_prof.estep_launches += std::min<long long>((long long)estep.size(), estep_done);
+        g_prof.em_iters += em_iters;
+        g_prof.init_ms += ms(t0, t_init);
+        g_prof.em_ms += ms(t_init, t_em);
+        g_prof.total_ms += ms(t0, t_end);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void gira_fit_opts_default(gira_fit_opts* o) {
+    if (!o) return;
+    o->iters = 100;
+    o->tol = 1e-3;
+    o->reg_covar = 1e-6;
+    o->seed = 0;
+    o->lloyd_iters = 10;
+    o->init_mode = GIRA_INIT_KMEANS;
+}
+
+void gira_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+gira_status gira_profile_read(gira_profile* out, int reset) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (out) *out = g_prof;
+    if (reset) g_prof = gira_profile{};
+    return GIRA_OK;
+}
+
+const char* gira_last_error_message(void) { return t_msg.c_str(); }
+int gira_last_error_component(void) { return t_bad; }
+const char* gira_version(void) { return "gira-gb300 0.1.0 sm_103a"; }
+
+gira_status gira_release_workspace(void) {
+    t_msg.clear();
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_ws.size(); ++d) {
+        if (!g_ws[d]) continue;
+        std::lock_guard<std::mutex> l2(g_ws[d]->mu);
+        if (g_ws[d]->ptr) {
+            cudaSetDevice((int)d);
+            cudaError_t e = cudaFree(g_ws[d]->ptr);
+            g_ws[d]->ptr = nullptr;
+            g_ws[d]->bytes = 0;
+            if (e != cudaSuccess) {
+                cudaSetDevice(cur);
+                return fail(GIRA_ERR_CUDA, "cudaFree failed: %s", cudaGetErrorString(e));
+            }
+        }
+    }
+    cudaSetDevice(cur);
+    return GIRA_OK;
+}
+
+// ================================================================ kmeans_init
+gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t seed, int lloyd_iters, float* centers,
+                             int32_t* labels, int* iters_done, void* stream) {
+    reset_error();
+    TRY(check_nk(n, k));
+    if (lloyd_iters < 0) return fail(GIRA_ERR_INVALID_ARG, "lloyd_iters < 0");
+    if (!points || !centers) return fail(GIRA_ERR_INVALID_ARG, "points and centers must not be NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kc, kl = Kind::Host;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(centers, "centers", c.dev, &kc));
+    if (labels) TRY(check_ptr(labels, "labels", c.dev, &kl));
+    const int nblk = kpp_num_blocks(n);
+
+    auto layout = [&](Carver& cv, DeviceState** st, float** pin, float4** p4, float4** c4, float** d2, double** bs,
+                      int64_t** ch, int32_t** lab, double** sums, unsigned long long** chg, float** cout) {
+        *st = cv.take<DeviceState>(1);
+        *pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
+        *p4 = cv.take<float4>(n);
+        *c4 = cv.take<float4>(k);
+        *d2 = cv.take<float>(n);
+        *bs = cv.take<double>(nblk);
+        *ch = cv.take<int64_t>(k);
+        *lab = cv.take<int32_t>((labels && kl == Kind::Device) ? 0 : n);
+        *sums = cv.take<double>(4 * (size_t)k);
+        *chg = cv.take<unsigned long long>(lloyd_iters + 1);
+        *cout = cv.take<float>(kc == Kind::Host ? 3 * (size_t)k : 0);
+    };
+    DeviceState* st;
+    float *pin, *d2, *cout;
+    float4 *p4, *c4;
+    double *bs, *sums;
+    int64_t* ch;
+    int32_t* lab;
+    unsigned long long* chg;
+    Carver sizer;
+    layout(sizer, &st, &pin, &p4, &c4, &d2, &bs, &ch, &lab, &sums, &chg, &cout);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv, &st, &pin, &p4, &c4, &d2, &bs, &ch, &lab, &sums, &chg, &cout);
+    if (labels && kl == Kind::Device) lab = labels;
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(pin, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c.s));
+        pts = pin;
+    }
+    COUNTED(prof, 1, launch_pack(pts, n, p4, st, c.s));
+    COUNTED(prof, 2 * k - 1, launch_kpp(p4, n, k, seed, c4, d2, bs, ch, st, c.s));
+    GIRA_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * k, c.s));
+    GIRA_CUDA(cudaMemsetAsync(chg, 0, sizeof(unsigned long long) * (lloyd_iters + 1), c.s));
+    COUNTED(prof, 1 + 2 * lloyd_iters, launch_lloyd(p4, n, k, lloyd_iters, c4, lab, sums, chg, st, c.s));
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    float* cdst = (kc == Kind::Device) ? centers : cout;
+    COUNTED(prof, 1, launch_centers_out(c4, k, cdst, c.s));
+    if (kc == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(centers, cout, sizeof(float) * 3 * k, cudaMemcpyDeviceToHost, c.s));
+    if (labels && kl == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    TRY(device_status(h));
+    if (iters_done) *iters_done = h.lloyd_done;
+    return GIRA_OK;
+}
+
+// ================================================================ gmm_fit
+gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_opts* opts, float* weights,
+                         float* means, float* covs, double* loglik_trace, int* iters_done, double* final_loglik,
+                         void* stream) {
+    reset_error();
+    if (!opts) return fail(GIRA_ERR_INVALID_ARG, "opts is NULL");
+    TRY(check_nk(n, k));
+    const gira_fit_opts o = *opts;
+    if (o.iters < 0) return fail(GIRA_ERR_INVALID_ARG, "iters < 0");
+    if (!(o.tol >= 0.0)) return fail(GIRA_ERR_INVALID_ARG, "tol must be >= 0");
+    if (!(o.reg_covar >= 0.0) || !std::isfinite(o.reg_covar)) return fail(GIRA_ERR_INVALID_ARG, "reg_covar must be finite and >= 0");
+    if (o.lloyd_iters < 0) return fail(GIRA_ERR_INVALID_ARG, "lloyd_iters < 0");
+    if (o.init_mode != GIRA_INIT_KMEANS && o.init_mode != GIRA_INIT_PARAMS)
+        return fail(GIRA_ERR_INVALID_ARG, "unknown init_mode %d", o.init_mode);
+    if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kw, km, kc;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    const bool model_host = kw == Kind::Host || km == Kind::Host || kc == Kind::Host;
+    const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
+    const int npairs = params_pairs_padded(k);
+    int64_t ppc = 0, ppc_ll = 0;
+    const int grid = estep_grid(n, k, true, c.sms, &ppc);
+    const int grid_ll = estep_grid(n, k, false, c.sms, &ppc_ll);
+    const int nblk = kpp_num_blocks(n);
+
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
+        float4 *p4, *shift4, *c4;
+        double *model64, *stats64, *llp, *trace, *bs, *sums;
+        int64_t* ch;
+        int32_t* lab;
+        unsigned long long* chg;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
+        b.p4 = cv.take<float4>(n);
+        b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
+        b.shift4 = cv.take<float4>(k);
+        b.model64 = cv.take<double>((size_t)k * MODEL);
+        b.stats64 = cv.take<double>((size_t)k * NSTAT);
+        b.partials = cv.take<float>((size_t)grid * k * NSTAT);
+        b.llp = cv.take<double>(std::max(grid, grid_ll));
+        b.trace = cv.take<double>(std::max(o.iters, 1));
+        b.mw = cv.take<float>(model_host ? k : 0);
+        b.mmu = cv.take<float>(model_host ? 3 * (size_t)k : 0);
+        b.mcov = cv.take<float>(model_host ? 9 * (size_t)k : 0);
+        if (kinit) {
+            b.c4 = cv.take<float4>(k);
+            b.d2 = cv.take<float>(n);
+            b.bs = cv.take<double>(nblk);
+            b.ch = cv.take<int64_t>(k);
+            b.lab = cv.take<int32_t>(n);
+            b.sums = cv.take<double>(4 * (size_t)k);
+            b.chg = cv.take<unsigned long long>(o.lloyd_iters + 1);
+        }
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.stop_after = o.iters;
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemsetAsync(b.trace, 0xff, sizeof(double) * std::max(o.iters, 1), c.s));   // NaN
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    COUNTED(prof, 1, launch_pack(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+
+    float* w_d = (kw == Kind::Device) ? weights : b.mw;
+    float* mu_d = (km == Kind::Device) ? means : b.mmu;
+    float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
+    if (kinit) {
+        COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 4 * k, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * (o.lloyd_iters + 1), c.s));
+        COUNTED(prof, 1 + 2 * o.lloyd_iters,
+                launch_lloyd(b.p4, n, k, o.lloyd_iters, b.c4, b.lab, b.sums, b.chg, b.st, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * k, c.s));
+        COUNTED(prof, 1, launch_label_stats(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
+        GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * k, cudaMemcpyDeviceToDevice, c.s));
+        COUNTED(prof, 1, launch_finalize(b.stats64, b.shift4, k, n, o.reg_covar, o.tol, b.model64, b.params,
+                                         b.trace, b.st, 0, false, c.s));
+    } else {
+        if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
+        if (km == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 3 * k, cudaMemcpyHostToDevice, c.s));
+        if (kc == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 9 * k, cudaMemcpyHostToDevice, c.s));
+        COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+    }
+    prof.t_init = prof.mark();
+
+    EStepLaunch a{b.p4, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
+    for (int t = 1; t <= o.iters; ++t) {
+        a.iter = t;
+        cudaEvent_t e0 = prof.mark();
+        COUNTED(prof, 1, launch_estep(a, true, grid, c.s));
+        cudaEvent_t e1 = prof.mark();
+        if (prof.on) prof.estep.emplace_back(e0, e1);
+        COUNTED(prof, 1, launch_em_reduce(b.partials, b.llp, grid, k, b.stats64, b.st, t, c.s));
+        COUNTED(prof, 1, launch_finalize(b.stats64, b.shift4, k, n, o.reg_covar, o.tol, b.model64, b.params,
+                                         b.trace, b.st, t, true, c.s));
+    }
+    prof.t_em = prof.mark();
+    if (final_loglik) {
+        EStepLaunch f = a;
+        f.iter = 0;
+        f.pts_per_cta = ppc_ll;
+        f.partials = nullptr;
+        COUNTED(prof, 1, launch_estep(f, false, grid_ll, c.s));
+        COUNTED(prof, 1, launch_em_reduce(nullptr, b.llp, grid_ll, k, nullptr, b.st, 0, c.s));
+    }
+    COUNTED(prof, 1, launch_model_out(b.model64, k, w_d, mu_d, cov_d, c.s));
+    if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
+    if (km == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(means, b.mmu, sizeof(float) * 3 * k, cudaMemcpyDeviceToHost, c.s));
+    if (kc == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(covs, b.mcov, sizeof(float) * 9 * k, cudaMemcpyDeviceToHost, c.s));
+    if (loglik_trace && o.iters > 0)
+        GIRA_CUDA(cudaMemcpyAsync(loglik_trace, b.trace, sizeof(double) * o.iters, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(h.iters_done, h.iters_done);
+    TRY(device_status(h));
+    if (iters_done) *iters_done = h.iters_done;
+    if (final_loglik) *final_loglik = h.ll_sum / (double)n;
+    return GIRA_OK;
+}
+
+// ================================================================ gmm_loglik
+gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* weights, const float* means,
+                            const float* covs, double* mean_loglik, float* per_point, void* stream) {
+    reset_error();
+    TRY(check_nk(n, k));
+    if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kw, km, kc, kpp = Kind::Host;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    if (per_point) TRY(check_ptr(per_point, "per_point", c.dev, &kpp));
+    const int npairs = params_pairs_padded(k);
+    int64_t ppc = 0;
+    const int grid = estep_grid(n, k, false, c.sms, &ppc);
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *params, *mw, *mmu, *mcov, *pp;
+        float4 *p4, *shift4;
+        double *model64, *llp;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
+        b.p4 = cv.take<float4>(n);
+        b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
+        b.shift4 = cv.take<float4>(k);
+        b.model64 = cv.take<double>((size_t)k * MODEL);
+        b.llp = cv.take<double>(grid);
+        b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
+        b.mmu = cv.take<float>(km == Kind::Host ? 3 * (size_t)k : 0);
+        b.mcov = cv.take<float>(kc == Kind::Host ? 9 * (size_t)k : 0);
+        b.pp = cv.take<float>((per_point && kpp == Kind::Host) ? n : 0);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.stop_after = 0;
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    const float* w_d = weights;
+    const float* mu_d = means;
+    const float* cov_d = covs;
+    if (kw == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
+        w_d = b.mw;
+    }
+    if (km == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 3 * k, cudaMemcpyHostToDevice, c.s));
+        mu_d = b.mmu;
+    }
+    if (kc == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 9 * k, cudaMemcpyHostToDevice, c.s));
+        cov_d = b.mcov;
+    }
+    COUNTED(prof, 1, launch_pack(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+    COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
+    EStepLaunch a{b.p4, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
+    COUNTED(prof, 1, launch_estep(a, false, grid, c.s));
+    COUNTED(prof, 1, launch_em_reduce(nullptr, b.llp, grid, k, nullptr, b.st, 0, c.s));
+    if (per_point && kpp == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(per_point, b.pp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    TRY(device_status(h));
+    if (mean_loglik) *mean_loglik = h.ll_sum / (double)n;
+    return GIRA_OK;
+}
+
+}  // extern "C"

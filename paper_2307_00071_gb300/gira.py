@@ -1,0 +1,214 @@
+"""Thin Python binding of libgira (the C ABI in ``include/gira.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+behind the C ABI.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays;
+CUDA tensors are passed as device pointers on torch's current stream, host
+arrays as host pointers (the library stages them).  Outputs are allocated on
+the same side as ``points``.  There is no CPU fallback: importing this module
+raises if the library cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_lib
+
+OK = 0
+ERR_INVALID_ARG, ERR_NONFINITE_INPUT, ERR_NOT_PD, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC = 1, 2, 3, 4, 5, 6, 7
+INIT_KMEANS, INIT_PARAMS = 0, 1
+MAX_K = 1024
+
+
+class GiraError(RuntimeError):
+    def __init__(self, status: int, message: str, component: int = -1):
+        self.status = status
+        self.component = component
+        super().__init__(f"gira error {status}: {message}")
+
+
+class FitOpts(C.Structure):
+    _fields_ = [("iters", C.c_int), ("tol", C.c_double), ("reg_covar", C.c_double), ("seed", C.c_uint64),
+                ("lloyd_iters", C.c_int), ("init_mode", C.c_int)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("calls", C.c_longlong), ("kernel_launches", C.c_longlong), ("estep_launches", C.c_longlong),
+                ("estep_ms", C.c_double), ("em_iters", C.c_longlong), ("init_ms", C.c_double), ("em_ms", C.c_double),
+                ("total_ms", C.c_double)]
+
+
+def _load():
+    path = build_lib.LIB
+    if not os.path.exists(path) or build_lib.is_stale():
+        path = build_lib.build()   # raises if nvcc fails: no fallback
+    lib = C.CDLL(path)
+    vp, i64, dp, ip = C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    lib.gira_fit_opts_default.argtypes = [C.POINTER(FitOpts)]
+    lib.gira_fit_opts_default.restype = None
+    lib.gira_kmeans_init.argtypes = [vp, i64, C.c_int, C.c_uint64, C.c_int, vp, vp, ip, vp]
+    lib.gira_gmm_fit.argtypes = [vp, i64, C.c_int, C.POINTER(FitOpts), vp, vp, vp, dp, ip, dp, vp]
+    lib.gira_gmm_loglik.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
+    for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
+        getattr(lib, f).restype = C.c_int
+    lib.gira_release_workspace.argtypes = []
+    lib.gira_profile_enable.argtypes = [C.c_int]
+    lib.gira_profile_enable.restype = None
+    lib.gira_profile_read.argtypes = [C.POINTER(Profile), C.c_int]
+    lib.gira_profile_read.restype = C.c_int
+    lib.gira_last_error_message.restype = C.c_char_p
+    lib.gira_last_error_component.restype = C.c_int
+    lib.gira_version.restype = C.c_char_p
+    return lib
+
+
+_lib = _load()
+LIB_PATH = build_lib.LIB
+
+
+def _check(status: int):
+    if status != OK:
+        msg = _lib.gira_last_error_message().decode(errors="replace")
+        raise GiraError(status, msg, _lib.gira_last_error_component())
+
+
+# ----------------------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, keepalive, stream) for a torch tensor or numpy array (contiguous float32/int32)."""
+    if x is None:
+        return None, None, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        stream = None
+        if x.is_cuda:
+            import torch
+            stream = torch.cuda.current_stream(x.device).cuda_stream
+        return x.data_ptr(), x, stream
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, a, None
+
+
+def _new(like, shape, dtype):
+    if _is_torch(like):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        return torch.empty(shape, dtype=tdt, device=like.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _check_points(points):
+    if points.ndim != 2 or points.shape[1] != 3:
+        raise ValueError("points must be N x 3")
+    dt = points.dtype
+    if (_is_torch(points) and str(dt) != "torch.float32") or (not _is_torch(points) and dt != np.float32):
+        raise ValueError("points must be float32")
+    return int(points.shape[0])
+
+
+def default_opts() -> FitOpts:
+    o = FitOpts()
+    _lib.gira_fit_opts_default(C.byref(o))
+    return o
+
+
+def version() -> str:
+    return _lib.gira_version().decode()
+
+
+def gira_profile_enable(on: bool = True):
+    """Record CUDA events around each call's phases and E-step launches (process-wide)."""
+    _lib.gira_profile_enable(1 if on else 0)
+
+
+def gira_profile_read(reset: bool = False) -> dict:
+    p = Profile()
+    _check(_lib.gira_profile_read(C.byref(p), 1 if reset else 0))
+    return {name: getattr(p, name) for name, _ in Profile._fields_}
+
+
+def gira_release_workspace():
+    _check(_lib.gira_release_workspace())
+
+
+# ----------------------------------------------------------------------------- entry points
+def gira_kmeans_init(points, k: int, seed: int = 0, lloyd_iters: int = 10, centers=None, labels=None,
+                     want_labels: bool = True):
+    """k-means++ + Lloyd (Sec. V KInit).  Returns (centers K x 3, labels N or None, lloyd iterations done)."""
+    n = _check_points(points)
+    centers = _new(points, (k, 3), np.float32) if centers is None else centers
+    if labels is None and want_labels:
+        labels = _new(points, (n,), np.int32)
+    pp, kp, s = _ptr(points)
+    cp, kc, _ = _ptr(centers)
+    lp, kl, _ = _ptr(labels)
+    done = C.c_int(0)
+    _check(_lib.gira_kmeans_init(pp, n, k, seed, lloyd_iters, cp, lp, C.byref(done), s))
+    return centers, labels, done.value
+
+
+def gira_gmm_fit(points, k: int, iters: int = 100, tol: float = 1e-3, reg_covar: float = 1e-6, seed: int = 0,
+                 lloyd_iters: int = 10, init=None, weights=None, means=None, covs=None, trace: bool = True,
+                 final_loglik: bool = True):
+    """EM fit (Sec. V).  ``init`` = (weights, means, covs) starts from given parameters.
+
+    Returns a dict: weights (K), means (K x 3), covs (K x 3 x 3), trace (iters_done,),
+    iters_done, final_loglik.
+    """
+    n = _check_points(points)
+    o = default_opts()
+    o.iters, o.tol, o.reg_covar, o.seed, o.lloyd_iters = iters, tol, reg_covar, seed, lloyd_iters
+    o.init_mode = INIT_KMEANS
+    if weights is None:
+        weights = _new(points, (k,), np.float32)
+    if means is None:
+        means = _new(points, (k, 3), np.float32)
+    if covs is None:
+        covs = _new(points, (k, 3, 3), np.float32)
+    if init is not None:
+        o.init_mode = INIT_PARAMS
+        for dst, src in zip((weights, means, covs), init):
+            if _is_torch(dst):
+                import torch
+                dst.copy_(torch.as_tensor(np.asarray(src, dtype=np.float32) if not _is_torch(src) else src))
+            else:
+                dst[...] = np.asarray(src, dtype=np.float32)
+    tr = np.full(max(iters, 1), np.nan) if trace else None
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(weights)
+    mp, km, _ = _ptr(means)
+    cp, kc, _ = _ptr(covs)
+    done, fll = C.c_int(0), C.c_double(np.nan)
+    _check(_lib.gira_gmm_fit(pp, n, k, C.byref(o), wp, mp, cp,
+                             tr.ctypes.data_as(C.POINTER(C.c_double)) if tr is not None else None,
+                             C.byref(done), C.byref(fll) if final_loglik else None, s))
+    return dict(weights=weights, means=means, covs=covs, trace=None if tr is None else tr[:done.value],
+                iters_done=done.value, final_loglik=fll.value if final_loglik else None)
+
+
+def gira_gmm_loglik(points, weights, means, covs, per_point: bool = False, out=None):
+    """Mean (and optionally per-point) log-likelihood ln sum_b pi_b N(x|b) (Eq. logestep)."""
+    n = _check_points(points)
+    k = int(weights.shape[0])
+    if per_point and out is None:
+        out = _new(points, (n,), np.float32)
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(weights)
+    mp, km, _ = _ptr(means)
+    cp, kc, _ = _ptr(covs)
+    op, ko, _ = _ptr(out if per_point else None)
+    mean = C.c_double(np.nan)
+    _check(_lib.gira_gmm_loglik(pp, n, k, wp, mp, cp, C.byref(mean), op, s))
+    return (mean.value, out) if per_point else mean.value
+
+
+# short aliases
+kmeans_init = gira_kmeans_init
+gmm_fit = gira_gmm_fit
+gmm_loglik = gira_gmm_loglik

@@ -1,0 +1,86 @@
+"""The C ABI library: builds for sm_103a, loads, exports every declared symbol,
+and rejects invalid arguments before touching a GPU (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "gira.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gira_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_00071_gb300 import build_lib
+    return C.CDLL(build_lib.build())
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert {"gira_gmm_fit", "gira_gmm_loglik", "gira_kmeans_init"} <= set(syms)
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_binary_targets_sm103a():
+    from paper_2307_00071_gb300 import build_lib
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build_lib.ARCH)
+
+
+def test_version_and_defaults():
+    from paper_2307_00071_gb300 import gira
+    assert "sm_103a" in gira.version()
+    o = gira.default_opts()
+    assert (o.iters, o.tol, o.reg_covar, o.lloyd_iters, o.init_mode) == (100, 1e-3, 1e-6, 10, gira.INIT_KMEANS)
+
+
+@pytest.mark.parametrize("n,k", [(0, 1), (5, 0), (5, 6), (5000, 1025)])
+def test_invalid_sizes_rejected_without_gpu(n, k):
+    from paper_2307_00071_gb300 import gira
+    pts = np.zeros((max(n, 1), 3), np.float32)
+    w, m, c = np.ones(max(k, 1), np.float32), np.zeros((max(k, 1), 3), np.float32), np.tile(np.eye(3, dtype=np.float32), (max(k, 1), 1, 1))
+    L = gira._lib
+    o = gira.default_opts()
+    st = L.gira_gmm_fit(pts.ctypes.data, n, k, C.byref(o), w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
+                        None, None)
+    assert st == gira.ERR_INVALID_ARG
+    assert L.gira_last_error_message()
+    assert L.gira_gmm_loglik(pts.ctypes.data, n, k, w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
+                             None) == gira.ERR_INVALID_ARG
+    assert L.gira_kmeans_init(pts.ctypes.data, n, k, 0, 1, m.ctypes.data, None, None, None) == gira.ERR_INVALID_ARG
+
+
+def test_invalid_options_rejected_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    pts = np.zeros((10, 3), np.float32)
+    w, m, c = np.ones(2, np.float32), np.zeros((2, 3), np.float32), np.tile(np.eye(3, dtype=np.float32), (2, 1, 1))
+    for field, val in (("iters", -1), ("tol", float("nan")), ("tol", -1.0), ("reg_covar", -1e-6),
+                       ("reg_covar", float("inf")), ("lloyd_iters", -2), ("init_mode", 7)):
+        o = gira.default_opts()
+        setattr(o, field, val)
+        st = L.gira_gmm_fit(pts.ctypes.data, 10, 2, C.byref(o), w.ctypes.data, m.ctypes.data, c.ctypes.data, None,
+                            None, None, None)
+        assert st == gira.ERR_INVALID_ARG, field
+    assert L.gira_gmm_fit(pts.ctypes.data, 10, 2, None, w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
+                          None, None) == gira.ERR_INVALID_ARG
+    o = gira.default_opts()
+    assert L.gira_gmm_fit(None, 10, 2, C.byref(o), w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None, None,
+                          None) == gira.ERR_INVALID_ARG
+    assert L.gira_kmeans_init(pts.ctypes.data, 10, 2, 0, -1, m.ctypes.data, None, None, None) == gira.ERR_INVALID_ARG
+
+
+def test_binding_raises_typed_error():
+    from paper_2307_00071_gb300 import gira
+    with pytest.raises(gira.GiraError) as e:
+        gira.gira_gmm_fit(np.zeros((3, 3), np.float32), 5)
+    assert e.value.status == gira.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        gira.gira_gmm_fit(np.zeros((3, 2), np.float32), 1)

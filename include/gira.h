@@ -157,6 +157,40 @@ void gira_profile_enable(int on);
 /* Copy the accumulated profile to *out (may be NULL); reset it when reset != 0. */
 gira_status gira_profile_read(gira_profile *out, int reset);
 
+/*
+ * gira_gmm_loglik_noalloc -- gira_gmm_loglik for callers that cannot allocate
+ * device memory.  (An engineering addition: the paper has no counterpart.)
+ *
+ * Who needs it: code that runs while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), real-time control loops that forbid allocation
+ * after start-up, and hosts whose device memory is owned by a pool they do not
+ * control.  It computes the same mean and per-point log-likelihoods as
+ * gira_gmm_loglik, with the same kernels, but never calls cudaMalloc,
+ * cudaFree or any allocating routine: its scratch (packed points, component
+ * parameters, per-CTA partial sums, status word) is one static device array of
+ * 17 MiB inside the library, which every GPU that loads the library keeps until
+ * the process exits.
+ *
+ *   points, weights, means, covs   device memory of the current device only
+ *                                  (same layouts as gira_gmm_loglik)
+ *   n                              1 <= n <= GIRA_NOALLOC_MAX_N, else GIRA_ERR_INVALID_ARG
+ *   k                              1 <= k <= min(n, GIRA_MAX_K)
+ *   mean_loglik                    [host] or NULL
+ *   per_point                      [device] N binary32, or NULL
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (the call re-initialises what it reads), so calls
+ * that overlap on the GPU -- on different streams, or from processes sharing a
+ * context -- race and must not be issued; calls from several host threads are
+ * serialised by a lock.  The call synchronises `stream` before returning.
+ */
+#define GIRA_NOALLOC_MAX_N 1048576
+gira_status gira_gmm_loglik_noalloc(const float *points, int64_t n, int k, const float *weights,
+                                    const float *means, const float *covs, double *mean_loglik,
+                                    float *per_point, void *stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *gira_last_error_message(void);
 

@@ -224,6 +224,11 @@ struct CallProfile {
 
 }  // namespace
 
+void gira::record_error(const char* msg, int component) {
+    if (msg) t_msg = msg;
+    t_bad = component;
+}
+
 extern "C" {
 
 void gira_fit_opts_default(gira_fit_opts* o) {

@@ -125,4 +125,8 @@ cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32
                                double* stats64, DeviceState* st, cudaStream_t s);
 cudaError_t launch_centers_out(const float4* centers4, int k, float* centers3, cudaStream_t s);
 
+// Set this thread's last-error message (msg may be nullptr to keep it) and
+// component (what gira_last_error_message / gira_last_error_component return).
+void record_error(const char* msg, int component);
+
 }  // namespace gira

@@ -51,6 +51,8 @@ def _load():
     lib.gira_kmeans_init.argtypes = [vp, i64, C.c_int, C.c_uint64, C.c_int, vp, vp, ip, vp]
     lib.gira_gmm_fit.argtypes = [vp, i64, C.c_int, C.POINTER(FitOpts), vp, vp, vp, dp, ip, dp, vp]
     lib.gira_gmm_loglik.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
+    lib.gira_gmm_loglik_noalloc.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
+    lib.gira_gmm_loglik_noalloc.restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
     lib.gira_release_workspace.argtypes = []
@@ -205,6 +207,26 @@ def gira_gmm_loglik(points, weights, means, covs, per_point: bool = False, out=N
     op, ko, _ = _ptr(out if per_point else None)
     mean = C.c_double(np.nan)
     _check(_lib.gira_gmm_loglik(pp, n, k, wp, mp, cp, C.byref(mean), op, s))
+    return (mean.value, out) if per_point else mean.value
+
+
+def gira_gmm_loglik_noalloc(points, weights, means, covs, per_point: bool = False, out=None):
+    """gira_gmm_loglik for callers that cannot allocate device memory (CUDA tensors only).
+
+    The library keeps this call's scratch in a static device array instead of
+    allocating it, for code inside CUDA-graph capture or allocation-free loops.
+    """
+    n = _check_points(points)
+    k = int(weights.shape[0])
+    if per_point and out is None:
+        out = _new(points, (n,), np.float32)
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(weights)
+    mp, km, _ = _ptr(means)
+    cp, kc, _ = _ptr(covs)
+    op, ko, _ = _ptr(out if per_point else None)
+    mean = C.c_double(np.nan)
+    _check(_lib.gira_gmm_loglik_noalloc(pp, n, k, wp, mp, cp, C.byref(mean), op, s))
     return (mean.value, out) if per_point else mean.value
 
 

@@ -63,6 +63,26 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate(local, world):
+    """Whole-job figures from per-rank (units, seconds, e2e_units, e2e_seconds).
+
+    Units add over ranks (each rank fits its own frame); time is the slowest
+    rank's.  Uses torch.distributed when world > 1 (any backend).
+    """
+    import torch
+    vals = torch.tensor(local, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl":
+            vals = vals.cuda()
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        dist.all_gather(gathered, vals)
+        g = torch.stack(gathered).cpu().numpy()
+    else:
+        g = vals.reshape(1, -1).cpu().numpy()
+    return float(g[:, 0].sum()), float(g[:, 1].max()), float(g[:, 2].sum()), float(g[:, 3].max())
+
+
 def workload_config(n_points):
     return {"workload": f"synthetic 640x480 depth frame (procedural scene, 5 mm noise, 10% dropout) -> "
                         f"{n_points} points; K={K} full-covariance GMM; k-means++ + {LLOYD} Lloyd + up to "
@@ -246,15 +266,7 @@ def run_gira(args):
     d2h = sum(a.nbytes for a in host_out.values()) + 8 * ITERS
 
     # aggregate over ranks
-    vals = torch.tensor([units, total_s, e2e_units, e2e_t], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        gathered = [torch.zeros_like(vals) for _ in range(world)]
-        dist.all_gather(gathered, vals)
-        g = torch.stack(gathered).cpu().numpy()
-        units_all, t_max, e2e_units_all, e2e_tmax = g[:, 0].sum(), g[:, 1].max(), g[:, 2].sum(), g[:, 3].max()
-    else:
-        units_all, t_max, e2e_units_all, e2e_tmax = units, total_s, e2e_units, e2e_t
+    units_all, t_max, e2e_units_all, e2e_tmax = aggregate([units, total_s, e2e_units, e2e_t], world)
 
     if rank == 0:
         sms = torch.cuda.get_device_properties(local).multi_processor_count

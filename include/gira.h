@@ -186,7 +186,7 @@ gira_status gira_profile_read(gira_profile *out, int reset);
  * context -- race and must not be issued; calls from several host threads are
  * serialised by a lock.  The call synchronises `stream` before returning.
  */
-#define GIRA_NOALLOC_MAX_N 1048576
+#define GIRA_NOALLOC_MAX_N 524288
 gira_status gira_gmm_loglik_noalloc(const float *points, int64_t n, int k, const float *weights,
                                     const float *means, const float *covs, double *mean_loglik,
                                     float *per_point, void *stream);

@@ -53,6 +53,9 @@ def lib():
         L.oracle_gmm_fit.argtypes = [fp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                      C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int), dp]
         L.oracle_last_bad_component.restype = C.c_int
+        u64p = C.POINTER(C.c_uint64)
+        L.oracle_fx48_parts.argtypes = [C.c_float, u64p, u64p]
+        L.oracle_fx_threshold.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, u64p, u64p]
         _lib = L
     return _lib
 
@@ -109,6 +112,19 @@ def log_gaussian(x, mu, cov) -> float:
     P = tri_inverse3(cholesky3(cov))
     x, mu = _f64(x).copy(), _f64(mu).copy()
     return float(lib().oracle_log_gaussian(_p(x, C.c_double), _p(mu, C.c_double), _p(P, C.c_double)))
+
+
+def fx48(d) -> int:
+    """floor(d * 2^48) of a binary32 d >= 0 (k-means++ weight), as a Python int."""
+    lo, hi = C.c_uint64(), C.c_uint64()
+    lib().oracle_fx48_parts(float(np.float32(d)), C.byref(lo), C.byref(hi))
+    return (hi.value << 64) | lo.value
+
+
+def fx_threshold(k53: int, total: int) -> int:
+    lo, hi = C.c_uint64(), C.c_uint64()
+    lib().oracle_fx_threshold(k53, total & ((1 << 64) - 1), total >> 64, C.byref(lo), C.byref(hi))
+    return (hi.value << 64) | lo.value
 
 
 def dist2_f32(x, c) -> np.float32:

@@ -30,6 +30,9 @@
  * that same precision.  k-means centres are rounded to binary32 after each
  * update, as the GPU stores them.
  *
+ * k-means++ draws are integer decisions taken in exact fixed point (see
+ * oracle_fx48): no floating-point rounding enters the choice of a centre.
+ *
  * Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
  * counter-based generator: draw j of seed s is the (j+1)-th output of the
  * SplitMix64 stream started at state s;  u_j = (r_j >> 11) * 2^-53.
@@ -220,6 +223,44 @@ static float dist2_f32(const float *x, const float *c) {
 }
 float oracle_dist2_f32(const float *x, const float *c) { return dist2_f32(x, c); }
 
+/* The k-means++ weights D^2 are taken in exact fixed point so that the draw is
+ * an integer decision with no rounding: fx(d) = floor(d * 2^48) for a binary32
+ * d >= 0 (d >= 2^47 saturates to 2^95 - 1), summed exactly in 128 bits.  With
+ * k_j = r_j >> 11 the 53-bit integer behind u_j and T the exact total, the
+ * threshold is t = floor(k_j * T / 2^53) and the drawn point is the first n whose
+ * running sum exceeds t.  (Points closer than 2^-24 m to a chosen centre get
+ * weight 0; nothing else differs from real-valued D^2 sampling.) */
+typedef unsigned __int128 u128;
+
+u128 oracle_fx48(float d) {
+    if (!(d > 0.0f)) return 0;
+    if (d >= 140737488355328.0f) return (((u128)1) << 95) - 1; /* 2^47 */
+    return (u128)floor(ldexp((double)d, 48)); /* exact: d has 24 bits, doubles 53 */
+}
+
+static u128 fx_threshold(uint64_t k53, u128 T) {
+    uint64_t tl = (uint64_t)T, th = (uint64_t)(T >> 64);
+    u128 a = (u128)k53 * tl, b = (u128)k53 * th; /* k*T = b*2^64 + a (192 bits) */
+    uint64_t w0 = (uint64_t)a;
+    uint64_t a_hi = (uint64_t)(a >> 64), b_lo = (uint64_t)b, b_hi = (uint64_t)(b >> 64);
+    uint64_t w1 = a_hi + b_lo;
+    uint64_t w2 = b_hi + (w1 < a_hi ? 1u : 0u);
+    uint64_t t_lo = (w0 >> 53) | (w1 << 11), t_hi = (w1 >> 53) | (w2 << 11);
+    return ((u128)t_hi << 64) | t_lo;
+}
+
+/* Exported for the pins: threshold t (as two 64-bit halves) for k53 and T. */
+void oracle_fx_threshold(uint64_t k53, uint64_t T_lo, uint64_t T_hi, uint64_t *t_lo, uint64_t *t_hi) {
+    u128 t = fx_threshold(k53, ((u128)T_hi << 64) | T_lo);
+    *t_lo = (uint64_t)t;
+    *t_hi = (uint64_t)(t >> 64);
+}
+void oracle_fx48_parts(float d, uint64_t *lo, uint64_t *hi) {
+    u128 v = oracle_fx48(d);
+    *lo = (uint64_t)v;
+    *hi = (uint64_t)(v >> 64);
+}
+
 /* k-means++ seeding (Arthur & Vassilvitskii 2007, one candidate per step).
  * centers: K x 3 float (out); chosen: K indices into pts (out, may be NULL). */
 int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *centers, int64_t *chosen) {
@@ -232,25 +273,22 @@ int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *ce
     for (int j = 0; j < K; ++j) {
         if (j > 0) {
             /* D^2(x) = min over the centres chosen so far */
-            double total = 0.0;
+            u128 total = 0;
             for (int64_t n = 0; n < N; ++n) {
                 float dn = dist2_f32(pts + 3 * n, centers + 3 * (j - 1));
                 if (j == 1 || dn < d2[n]) d2[n] = dn;
-                total += (double)d2[n];
+                total += oracle_fx48(d2[n]);
             }
-            double u = oracle_uniform(seed, (uint64_t)j);
-            if (total > 0.0) {
-                double t = u * total, prefix = 0.0;
-                idx = -1;
-                int64_t last_pos = -1;
+            if (total > 0) {
+                const u128 t = fx_threshold(oracle_splitmix64(seed, (uint64_t)j) >> 11, total);
+                u128 prefix = 0;
+                idx = N - 1; /* unreachable: t < total */
                 for (int64_t n = 0; n < N; ++n) {
-                    prefix += (double)d2[n];
-                    if (d2[n] > 0.0f) last_pos = n;
+                    prefix += oracle_fx48(d2[n]);
                     if (prefix > t) { idx = n; break; }
                 }
-                if (idx < 0) idx = last_pos;  /* t rounded up to the total */
             } else {
-                idx = (int64_t)floor(u * (double)N);  /* every point is a chosen centre */
+                idx = (int64_t)floor(oracle_uniform(seed, (uint64_t)j) * (double)N); /* all weights zero */
                 if (idx > N - 1) idx = N - 1;
             }
         }

@@ -149,6 +149,7 @@ gira_status device_status(const DeviceState& h) {
         case GIRA_ERR_INVALID_ARG: return fail(GIRA_ERR_INVALID_ARG, "a mixture weight is not positive");
         case GIRA_ERR_NUMERIC:
             return fail(GIRA_ERR_NUMERIC, "a point's likelihood underflows binary32 under every component");
+        case GIRA_ERR_TIMEOUT: return fail(GIRA_ERR_TIMEOUT, "a bounded device-side wait ran out (k-means++ seeding)");
         default: return fail((gira_status)h.error, "device error %d", h.error);
     }
 }
@@ -291,15 +292,21 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
     TRY(check_ptr(centers, "centers", c.dev, &kc));
     if (labels) TRY(check_ptr(labels, "labels", c.dev, &kl));
     const int nblk = kpp_num_blocks(n);
+    int kgrid = kpp_persistent_grid();
+    if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
+    int* ksync = nullptr;
+    u128* ksums = nullptr;
 
-    auto layout = [&](Carver& cv, DeviceState** st, float** pin, float4** p4, float4** c4, float** d2, double** bs,
+    auto layout = [&](Carver& cv, DeviceState** st, float** pin, float4** p4, float4** c4, float** d2, u128** bs,
                       int64_t** ch, int32_t** lab, double** sums, unsigned long long** chg, float** cout) {
+        ksync = cv.take<int>((size_t)k + 1);
+        ksums = cv.take<u128>(kpp_persistent_sum_words(std::max(kgrid, 1), k));
         *st = cv.take<DeviceState>(1);
         *pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
         *p4 = cv.take<float4>(n);
         *c4 = cv.take<float4>(k);
-        *d2 = cv.take<float>(n);
-        *bs = cv.take<double>(nblk);
+        *d2 = cv.take<float>(2 * (size_t)n);   // double-buffered by the persistent seeding
+        *bs = cv.take<u128>(nblk);
         *ch = cv.take<int64_t>(k);
         *lab = cv.take<int32_t>((labels && kl == Kind::Device) ? 0 : n);
         *sums = cv.take<double>(4 * (size_t)k);
@@ -309,7 +316,8 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
     DeviceState* st;
     float *pin, *d2, *cout;
     float4 *p4, *c4;
-    double *bs, *sums;
+    u128* bs;
+    double* sums;
     int64_t* ch;
     int32_t* lab;
     unsigned long long* chg;
@@ -335,8 +343,13 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
         GIRA_CUDA(cudaMemcpyAsync(pin, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c.s));
         pts = pin;
     }
-    COUNTED(prof, 1, launch_pack(pts, n, p4, st, c.s));
-    COUNTED(prof, 2 * k - 1, launch_kpp(p4, n, k, seed, c4, d2, bs, ch, st, c.s));
+    COUNTED(prof, 1, launch_pack(pts, n, p4, nullptr, st, c.s));
+    if (kgrid > 0) {
+        GIRA_CUDA(cudaMemsetAsync(ksync, 0, sizeof(int) * (k + 1), c.s));
+        COUNTED(prof, 1, launch_kpp_persistent(p4, n, k, seed, c4, d2, ch, ksync, ksums, kgrid, st, c.s));
+    } else {
+        COUNTED(prof, 2 * k - 1, launch_kpp(p4, n, k, seed, c4, d2, bs, ch, st, c.s));
+    }
     GIRA_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * k, c.s));
     GIRA_CUDA(cudaMemsetAsync(chg, 0, sizeof(unsigned long long) * (lloyd_iters + 1), c.s));
     COUNTED(prof, 1 + 2 * lloyd_iters, launch_lloyd(p4, n, k, lloyd_iters, c4, lab, sums, chg, st, c.s));
@@ -386,20 +399,25 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     const int grid = estep_grid(n, k, true, c.sms, &ppc);
     const int grid_ll = estep_grid(n, k, false, c.sms, &ppc_ll);
     const int nblk = kpp_num_blocks(n);
+    int kgrid = kinit ? kpp_persistent_grid() : 0;
+    if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
 
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
-        float4 *p4, *shift4, *c4;
-        double *model64, *stats64, *llp, *trace, *bs, *sums;
+        float4 *p4, *p8, *shift4, *c4;
+        double *model64, *stats64, *llp, *trace, *sums;
+        u128 *bs, *ksums;
         int64_t* ch;
         int32_t* lab;
+        int* ksync;
         unsigned long long* chg;
     } b{};
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
-        b.p4 = cv.take<float4>(n);
+        b.p4 = cv.take<float4>(kinit ? n : 0);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
         b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
         b.shift4 = cv.take<float4>(k);
         b.model64 = cv.take<double>((size_t)k * MODEL);
@@ -412,12 +430,14 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.mcov = cv.take<float>(model_host ? 9 * (size_t)k : 0);
         if (kinit) {
             b.c4 = cv.take<float4>(k);
-            b.d2 = cv.take<float>(n);
-            b.bs = cv.take<double>(nblk);
+            b.d2 = cv.take<float>(2 * (size_t)n);   // double-buffered by the persistent seeding
+            b.bs = cv.take<u128>(nblk);
             b.ch = cv.take<int64_t>(k);
             b.lab = cv.take<int32_t>(n);
             b.sums = cv.take<double>(4 * (size_t)k);
             b.chg = cv.take<unsigned long long>(o.lloyd_iters + 1);
+            b.ksync = cv.take<int>((size_t)k + 1);
+            b.ksums = cv.take<u128>(kpp_persistent_sum_words(std::max(kgrid, 1), k));
         }
     };
     Carver sizer;
@@ -443,14 +463,20 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c.s));
         pts = b.pin;
     }
-    COUNTED(prof, 1, launch_pack(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_pack(pts, n, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
     COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
 
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
     float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
     if (kinit) {
-        COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s));
+        if (kgrid > 0) {
+            GIRA_CUDA(cudaMemsetAsync(b.ksync, 0, sizeof(int) * (k + 1), c.s));
+            COUNTED(prof, 1, launch_kpp_persistent(b.p4, n, k, o.seed, b.c4, b.d2, b.ch, b.ksync, b.ksums, kgrid, b.st,
+                                                   c.s));
+        } else {
+            COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s));
+        }
         GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 4 * k, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * (o.lloyd_iters + 1), c.s));
         COUNTED(prof, 1 + 2 * o.lloyd_iters,
@@ -458,8 +484,8 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * k, c.s));
         COUNTED(prof, 1, launch_label_stats(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
         GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * k, cudaMemcpyDeviceToDevice, c.s));
-        COUNTED(prof, 1, launch_finalize(b.stats64, b.shift4, k, n, o.reg_covar, o.tol, b.model64, b.params,
-                                         b.trace, b.st, 0, false, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize(nullptr, 0, nullptr, b.stats64, b.shift4, k, n, o.reg_covar, o.tol,
+                                                b.model64, b.params, b.trace, b.st, 0, false, c.s));
     } else {
         if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
         if (km == Kind::Host)
@@ -470,16 +496,15 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     }
     prof.t_init = prof.mark();
 
-    EStepLaunch a{b.p4, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
+    EStepLaunch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
     for (int t = 1; t <= o.iters; ++t) {
         a.iter = t;
         cudaEvent_t e0 = prof.mark();
         COUNTED(prof, 1, launch_estep(a, true, grid, c.s));
         cudaEvent_t e1 = prof.mark();
         if (prof.on) prof.estep.emplace_back(e0, e1);
-        COUNTED(prof, 1, launch_em_reduce(b.partials, b.llp, grid, k, b.stats64, b.st, t, c.s));
-        COUNTED(prof, 1, launch_finalize(b.stats64, b.shift4, k, n, o.reg_covar, o.tol, b.model64, b.params,
-                                         b.trace, b.st, t, true, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize(b.partials, grid, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
+                                                o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s));
     }
     prof.t_em = prof.mark();
     if (final_loglik) {
@@ -488,9 +513,9 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         f.pts_per_cta = ppc_ll;
         f.partials = nullptr;
         COUNTED(prof, 1, launch_estep(f, false, grid_ll, c.s));
-        COUNTED(prof, 1, launch_em_reduce(nullptr, b.llp, grid_ll, k, nullptr, b.st, 0, c.s));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid_ll, b.st, c.s));
     }
-    COUNTED(prof, 1, launch_model_out(b.model64, k, w_d, mu_d, cov_d, c.s));
+    COUNTED(prof, 1, launch_model_out(b.model64, k, w_d, mu_d, cov_d, b.st, c.s));
     if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
     if (km == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(means, b.mmu, sizeof(float) * 3 * k, cudaMemcpyDeviceToHost, c.s));
     if (kc == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(covs, b.mcov, sizeof(float) * 9 * k, cudaMemcpyDeviceToHost, c.s));
@@ -526,13 +551,13 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *mw, *mmu, *mcov, *pp;
-        float4 *p4, *shift4;
+        float4 *p8, *shift4;
         double *model64, *llp;
     } b{};
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
-        b.p4 = cv.take<float4>(n);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
         b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
         b.shift4 = cv.take<float4>(k);
         b.model64 = cv.take<double>((size_t)k * MODEL);
@@ -579,15 +604,15 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
         GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 9 * k, cudaMemcpyHostToDevice, c.s));
         cov_d = b.mcov;
     }
-    COUNTED(prof, 1, launch_pack(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_pack(pts, n, nullptr, b.p8, b.st, c.s));
     COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
     COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
     prof.t_em = prof.t_init;
     float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
-    EStepLaunch a{b.p4, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
+    EStepLaunch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
     COUNTED(prof, 1, launch_estep(a, false, grid, c.s));
-    COUNTED(prof, 1, launch_em_reduce(nullptr, b.llp, grid, k, nullptr, b.st, 0, c.s));
+    COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
     if (per_point && kpp == Kind::Host)
         GIRA_CUDA(cudaMemcpyAsync(per_point, b.pp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));

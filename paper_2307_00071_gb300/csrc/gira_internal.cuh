@@ -7,7 +7,9 @@
 //   slot 6..8   b' = -P' mu
 //   slot 9      c  = log2 pi + sum_j log2 (L^{-1})_jj - (3/2) log2(2 pi)
 //   slot 10..12 -mu (binary32; mu is also the shift of the M-step statistics)
-//   slot 13..15 padding
+//   slot 13     the weight behind c: N_b after an M-step (c then uses log2 N_b and
+//               the E-step subtracts log2 sum_a N_a), or the caller's weight
+//   slot 14..15 padding
 // alpha = sqrt(log2(e) / 2), so that c - ||P' x + b'||^2 = log2(pi N(x|mu,Sigma))
 // (Eq. simplifiedGaussian scaled to base 2).  Padding components carry
 // c = -inf, P' = b' = mu = 0, so they contribute exactly zero.
@@ -21,9 +23,9 @@
 namespace gira {
 
 constexpr int PAIR_FLOATS = 32;
-constexpr int SLOT_P = 0, SLOT_B = 6, SLOT_C = 9, SLOT_NMU = 10;
+constexpr int SLOT_P = 0, SLOT_B = 6, SLOT_C = 9, SLOT_NMU = 10, SLOT_W = 13;
 constexpr int NSTAT = 10;   // S0, S1[3], S2[6] (00,01,02,11,12,22)
-constexpr int MODEL = 10;   // pi, mu[3], Sigma[6] (00,01,02,11,12,22), binary64
+constexpr int MODEL = 10;   // w, mu[3], Sigma[6] (00,01,02,11,12,22), binary64; w = N_b or caller weight
 constexpr int Q_BATCH = 8;  // points per E-step batch
 
 // Device-side state of one library call (zeroed by the host at call start).
@@ -33,7 +35,7 @@ struct DeviceState {
     int stop_after;        // EM: last iteration to run (set on convergence); host sets it to iters
     int iters_done;        // EM iterations completed
     int lloyd_done;        // Lloyd centre updates made
-    int pad0;
+    int w_raw;             // 1 once an M-step has run: weights are N_b, normalised by sum_a N_a on use
     double prev_ll;        // l_{t-1}
     double ll_sum;         // sum_n lse_n of the last E-step (natural log)
     int64_t chosen_last;   // k-means++: index chosen by the last select step
@@ -60,6 +62,56 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------- TMA bulk copy + mbarrier
+// (PTX ISA: cp.async.bulk, mbarrier; a plain launch is a cluster of one CTA, so
+// the CTA's own shared memory is addressed through the shared::cluster window.)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bytes: multiple of 16; src and dst 16-byte aligned.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity: false once `limit_ns` of
+// wall time has passed (try_wait itself may suspend between polls).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > (uint64_t)limit_ns) return false;
+    }
+}
+
 // binary32 squared distance in the fixed order d_i = x_i - c_i; (d0^2 + d1^2) + d2^2,
 // every operation rounded separately (no contraction): k-means decisions are taken
 // in exactly this arithmetic.
@@ -67,6 +119,76 @@ __device__ __forceinline__ float dist2_f32(float4 x, float4 c) {
     float d0 = __fsub_rn(x.x, c.x), d1 = __fsub_rn(x.y, c.y), d2 = __fsub_rn(x.z, c.z);
     float s = __fadd_rn(__fmul_rn(d0, d0), __fmul_rn(d1, d1));
     return __fadd_rn(s, __fmul_rn(d2, d2));
+}
+
+// ---------------------------------------------------------------- exact fixed-point weights
+// k-means++ weights: fx(d) = floor(d * 2^48) for a binary32 d >= 0 (saturating
+// at 2^95 - 1 for d >= 2^47), summed exactly in 128 bits; the draw threshold is
+// floor(k * T / 2^53) for the 53-bit integer k behind u and the total T.
+struct u128 {
+    unsigned long long lo, hi;
+};
+__host__ __device__ __forceinline__ u128 u128_add(u128 a, u128 b) {
+    u128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
+__host__ __device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {
+    u128 r;
+    r.lo = a.lo - b.lo;
+    r.hi = a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull);
+    return r;
+}
+__host__ __device__ __forceinline__ bool u128_gt(u128 a, u128 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__host__ __device__ __forceinline__ bool u128_zero(u128 a) { return (a.lo | a.hi) == 0ull; }
+__device__ __forceinline__ u128 u128_shfl_up(u128 v, int o) {
+    u128 r;
+    r.lo = __shfl_up_sync(0xffffffffu, v.lo, o);
+    r.hi = __shfl_up_sync(0xffffffffu, v.hi, o);
+    return r;
+}
+__device__ __forceinline__ u128 u128_shfl(u128 v, int src) {
+    u128 r;
+    r.lo = __shfl_sync(0xffffffffu, v.lo, src);
+    r.hi = __shfl_sync(0xffffffffu, v.hi, src);
+    return r;
+}
+// Inclusive warp scan (exact, so the order of the additions does not matter).
+__device__ __forceinline__ u128 u128_warp_incl_scan(u128 v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u128 u = u128_shfl_up(v, o);
+        if (lane >= o) v = u128_add(v, u);
+    }
+    return v;
+}
+__device__ __forceinline__ u128 fx48(float d) {
+    u128 r{0ull, 0ull};
+    if (!(d > 0.f)) return r;
+    if (d >= 140737488355328.0f) return u128{~0ull, (1ull << 31) - 1ull};   // 2^47 -> 2^95 - 1
+    const unsigned bits = __float_as_uint(d);
+    const int ex = (int)(bits >> 23);
+    const unsigned long long mant = (bits & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int sh = (ex ? ex : 1) - 150 + 48;   // d = mant * 2^(sh - 48)
+    if (sh >= 64) {
+        r.hi = mant << (sh - 64);
+    } else if (sh > 40) {
+        r.lo = mant << sh;
+        r.hi = mant >> (64 - sh);
+    } else if (sh >= 0) {
+        r.lo = mant << sh;
+    } else if (sh > -24) {
+        r.lo = mant >> (-sh);
+    }
+    return r;
+}
+__device__ __forceinline__ u128 fx_threshold(unsigned long long k53, u128 T) {
+    const unsigned long long a_lo = k53 * T.lo, a_hi = __umul64hi(k53, T.lo);
+    const unsigned long long b_lo = k53 * T.hi, b_hi = __umul64hi(k53, T.hi);
+    const unsigned long long w0 = a_lo, w1 = a_hi + b_lo;
+    const unsigned long long w2 = b_hi + (w1 < a_hi ? 1ull : 0ull);
+    return u128{(w0 >> 53) | (w1 << 11), (w1 >> 53) | (w2 << 11)};
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
@@ -84,7 +206,7 @@ __host__ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t j) 
 // ---------------------------------------------------------------- kernel entry points
 // (defined in em_kernels.cu / kmeans_kernels.cu, launched from gira_api.cu)
 struct EStepLaunch {
-    const float4* pts;
+    const float4* pts8;      // 2 float4 per point: (x,x,y,y) (z,z,0,0)
     int64_t n;
     int k;
     const float* params;     // pair-interleaved, npairs_pad * PAIR_FLOATS
@@ -104,21 +226,38 @@ int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta);
 // Pairs (padded) the parameter buffer must hold for k components.
 int params_pairs_padded(int k);
 
-cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, DeviceState* st, cudaStream_t s);
+// N x 3 -> pts4 (x,y,z,0) (nullable) and pts8 (x,x,y,y)(z,z,0,0); flags non-finite input.
+cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, float4* pts8, DeviceState* st, cudaStream_t s);
 cudaError_t launch_fill_padding(float* params, int k, int npairs_pad, cudaStream_t s);
-cudaError_t launch_em_reduce(const float* partials, const double* ll_partials, int grid, int k, double* stats64,
-                             DeviceState* st, int iter, cudaStream_t s);
-cudaError_t launch_finalize(const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
-                            double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
-                            cudaStream_t s);
+// Sum of the per-CTA log-likelihoods into st->ll_sum (fixed order).
+cudaError_t launch_ll_reduce(const double* ll_partials, int grid, DeviceState* st, cudaStream_t s);
+// M-step: reduce the per-CTA partials (or read binary64 stats64 when partials is
+// nullptr), then binary64 finalize of every component; EM iterations (em) also
+// reduce the log-likelihood, write the trace and decide convergence.
+cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
+                                   const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
+                                   double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
+                                   cudaStream_t s);
 cudaError_t launch_params_from_model(const float* w, const float* mu, const float* cov, int k, double* model64,
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
-cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, cudaStream_t s);
+cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
+                             cudaStream_t s);
 
 // k-means
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
-                       double* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s);
+                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s);
 int kpp_num_blocks(int64_t n);
+// Persistent k-means++ (one cooperative launch for all K centres).  Grid size, or
+// 0 when cooperative launch is unavailable (the per-centre launches are used).
+int kpp_persistent_grid();
+// sync_ints: k+1 zeroed ints (per-centre arrival counters, abort flag);
+// sums: kpp_persistent_sum_words(grid, k) 128-bit words; d2: 2n floats.  Valid for
+// n <= kpp_persistent_max_n(grid) (points held in registers).
+size_t kpp_persistent_sum_words(int grid, int k);
+int64_t kpp_persistent_max_n(int grid);
+cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
+                                  int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
+                                  cudaStream_t s);
 cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, float4* centers, int32_t* labels,
                          double* sums, unsigned long long* changed, DeviceState* st, cudaStream_t s);
 cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32_t* labels, const float4* shift4,

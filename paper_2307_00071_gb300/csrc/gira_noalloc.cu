@@ -118,7 +118,7 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
         return p;
     };
     DeviceState* st = reinterpret_cast<DeviceState*>(take(sizeof(DeviceState)));
-    float4* p4 = reinterpret_cast<float4*>(take(sizeof(float4) * (size_t)n));
+    float4* p8 = reinterpret_cast<float4*>(take(2 * sizeof(float4) * (size_t)n));
     float* params = reinterpret_cast<float*>(take(sizeof(float) * (size_t)npairs * PAIR_FLOATS));
     float4* shift4 = reinterpret_cast<float4*>(take(sizeof(float4) * (size_t)k));
     double* model64 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)k * MODEL));
@@ -132,12 +132,12 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
     h.stop_after = 0;
     h.bad_component = INT_MAX;
     NA_CUDA(cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, s));
-    NA_CUDA(launch_pack(points, n, p4, st, s));
+    NA_CUDA(launch_pack(points, n, nullptr, p8, st, s));
     NA_CUDA(launch_fill_padding(params, k, npairs, s));
     NA_CUDA(launch_params_from_model(weights, means, covs, k, model64, params, shift4, st, s));
-    EStepLaunch a{p4, n, k, params, ppc, nullptr, llp, per_point, st, 0};
+    EStepLaunch a{p8, n, k, params, ppc, nullptr, llp, per_point, st, 0};
     NA_CUDA(launch_estep(a, false, grid, s));
-    NA_CUDA(launch_em_reduce(nullptr, llp, grid, k, nullptr, st, 0, s));
+    NA_CUDA(launch_ll_reduce(llp, grid, st, s));
     NA_CUDA(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
     switch (h.error) {

@@ -25,68 +25,6 @@ constexpr int KPP_ITEMS = 8;
 constexpr int KPP_CHUNK = KPP_THREADS * KPP_ITEMS;   // points per update block
 constexpr int SEL_THREADS = 1024;
 
-// Deterministic block-wide binary64 sum (fixed tree); result valid in thread 0.
-template <int THREADS>
-__device__ double block_sum(double v, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < THREADS / 32; ++w) r += sh[w];
-    __syncthreads();
-    return r;
-}
-
-// Block-wide inclusive scan of one binary64 value per thread (fixed order).
-template <int THREADS>
-__device__ double block_incl_scan(double v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        double u = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v += u;
-    }
-    if (lane == 31) sh[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double w = (lane < THREADS / 32) ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            double u = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += u;
-        }
-        if (lane < THREADS / 32) sh[lane] = w;   // inclusive warp prefix
-    }
-    __syncthreads();
-    if (warp > 0) v += sh[warp - 1];
-    __syncthreads();
-    return v;
-}
-
-__device__ int block_min_int(int v, int* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int r = sh[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = min(r, sh[w]);
-    __syncthreads();
-    return r;
-}
-
-__device__ long long block_max_ll(long long v, long long* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, (long long)__shfl_xor_sync(FULL, v, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    long long r = sh[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = max(r, sh[w]);
-    __syncthreads();
-    return r;
-}
-
 // ---------------------------------------------------------------- k-means++
 __global__ void kpp_first_kernel(const float4* __restrict__ pts, int64_t n, uint64_t seed, float4* centers,
                                  int64_t* chosen, DeviceState* st) {
@@ -97,16 +35,16 @@ __global__ void kpp_first_kernel(const float4* __restrict__ pts, int64_t n, uint
     chosen[0] = idx;
 }
 
-// D^2(x) = min(D^2(x), ||x - c_{j-1}||^2) and the binary64 sum of each chunk.
+// D^2(x) = min(D^2(x), ||x - c_{j-1}||^2) and the exact fixed-point sum of each chunk.
 __global__ void __launch_bounds__(KPP_THREADS) kpp_update_kernel(const float4* __restrict__ pts, int64_t n,
                                                                  const float4* __restrict__ centers, int j,
-                                                                 float* __restrict__ d2, double* blocksums,
+                                                                 float* __restrict__ d2, u128* blocksums,
                                                                  DeviceState* st) {
-    __shared__ double sh[KPP_THREADS / 32];
+    __shared__ u128 sh[KPP_THREADS / 32];
     if (st->error) return;
     const float4 c = centers[j - 1];
     const int64_t base = (int64_t)blockIdx.x * KPP_CHUNK;
-    double acc = 0.0;
+    u128 acc{0ull, 0ull};
 #pragma unroll
     for (int it = 0; it < KPP_ITEMS; ++it) {
         const int64_t i = base + it * KPP_THREADS + threadIdx.x;
@@ -114,82 +52,93 @@ __global__ void __launch_bounds__(KPP_THREADS) kpp_update_kernel(const float4* _
             float d = dist2_f32(pts[i], c);
             if (j > 1) d = fminf(d2[i], d);
             d2[i] = d;
-            acc += (double)d;
+            acc = u128_add(acc, fx48(d));
         }
     }
-    const double tot = block_sum<KPP_THREADS>(acc, sh);
-    if (threadIdx.x == 0) blocksums[blockIdx.x] = tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    acc = u128_warp_incl_scan(acc, lane);
+    if (lane == 31) sh[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u128 tot{0ull, 0ull};
+        for (int w = 0; w < KPP_THREADS / 32; ++w) tot = u128_add(tot, sh[w]);
+        blocksums[blockIdx.x] = tot;
+    }
 }
 
-// Draw centre j: the first point whose running binary64 sum of D^2 exceeds
-// t = u_j * sum D^2 (u_j = draw j of the seed's SplitMix64 stream).  Every
-// prefix used below comes from one chain of sequential additions per thread
-// plus fixed-order scans, so the search is self-consistent.
+// Block-wide inclusive scan of one exact value per thread.
+template <int THREADS>
+__device__ u128 block_incl_scan128(u128 v, u128* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = u128_warp_incl_scan(v, lane);
+    if (lane == 31) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        u128 w = (lane < THREADS / 32) ? sh[lane] : u128{0ull, 0ull};
+        w = u128_warp_incl_scan(w, lane);
+        if (lane < THREADS / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v = u128_add(v, sh[warp - 1]);
+    __syncthreads();
+    return v;
+}
+
+// Draw centre j: the first point whose exact running sum of fx(D^2) exceeds
+// t = floor(k_j * T / 2^53).
 __global__ void __launch_bounds__(SEL_THREADS) kpp_select_kernel(const float4* __restrict__ pts, int64_t n,
                                                                  const float* __restrict__ d2,
-                                                                 const double* __restrict__ blocksums, int nblk,
+                                                                 const u128* __restrict__ blocksums, int nblk,
                                                                  uint64_t seed, int j, float4* centers,
                                                                  int64_t* chosen, DeviceState* st) {
-    __shared__ double sh[SEL_THREADS / 32];
-    __shared__ double sh_incl[SEL_THREADS];
-    __shared__ int shi[SEL_THREADS / 32];
-    __shared__ long long shl[SEL_THREADS / 32];
-    __shared__ double s_total, s_excl;
+    __shared__ u128 sh[SEL_THREADS / 32];
+    __shared__ u128 s_total, s_rel;
+    __shared__ int s_blk;
     if (st->error) return;
     const int per = (nblk + SEL_THREADS - 1) / SEL_THREADS;   // consecutive chunks per thread
     const int b0 = threadIdx.x * per;
-    double local = 0.0;
-    for (int i = 0; i < per && b0 + i < nblk; ++i) local += blocksums[b0 + i];
-    sh_incl[threadIdx.x] = block_incl_scan<SEL_THREADS>(local, sh);
+    u128 local{0ull, 0ull};
+    for (int i = 0; i < per && b0 + i < nblk; ++i) local = u128_add(local, blocksums[b0 + i]);
+    const u128 incl = block_incl_scan128<SEL_THREADS>(local, sh);
+    if (threadIdx.x == SEL_THREADS - 1) s_total = incl;
+    if (threadIdx.x == 0) s_blk = INT_MAX;
     __syncthreads();
-    const double thread_excl = threadIdx.x ? sh_incl[threadIdx.x - 1] : 0.0;
-    if (threadIdx.x == 0) s_total = sh_incl[SEL_THREADS - 1];
-    __syncthreads();
-    const double total = s_total;
-    const double u = uniform53(seed, (uint64_t)j);
-    int64_t idx = -1;
-    if (total > 0.0) {
-        const double t = u * total;
-        // first chunk whose inclusive prefix exceeds t; remember its exclusive prefix
-        double run = thread_excl, before = 0.0;
-        int cand = INT_MAX;
+    const u128 T = s_total;
+    int64_t idx;
+    if (!u128_zero(T)) {
+        const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
+        // the first chunk whose inclusive prefix exceeds t (exact: exactly one thread finds it)
+        u128 run = u128_sub(incl, local);
         for (int i = 0; i < per && b0 + i < nblk; ++i) {
-            before = run;
-            run += blocksums[b0 + i];
-            if (run > t) { cand = b0 + i; break; }
+            const u128 nxt = u128_add(run, blocksums[b0 + i]);
+            if (u128_gt(nxt, t)) {
+                s_blk = b0 + i;
+                s_rel = u128_sub(t, run);
+                break;
+            }
+            run = nxt;
         }
-        int kb = block_min_int(cand, shi);
-        if (kb != INT_MAX && cand == kb) s_excl = before;
         __syncthreads();
-        double excl = (kb != INT_MAX) ? s_excl : 0.0;
-        while (kb < nblk) {
-            const int64_t p0 = (int64_t)kb * KPP_CHUNK + 2 * threadIdx.x;
-            const double v0 = (p0 < n) ? (double)d2[p0] : 0.0;
-            const double v1 = (p0 + 1 < n) ? (double)d2[p0 + 1] : 0.0;
-            sh_incl[threadIdx.x] = block_incl_scan<SEL_THREADS>(v0 + v1, sh);
-            __syncthreads();
-            const double in_excl = threadIdx.x ? sh_incl[threadIdx.x - 1] : 0.0;
-            const double r0 = (excl + in_excl) + v0;
-            const double r1 = r0 + v1;
-            int c2 = INT_MAX;
-            if (p0 < n && r0 > t) c2 = 2 * threadIdx.x;
-            else if (p0 + 1 < n && r1 > t) c2 = 2 * threadIdx.x + 1;
-            const int w = block_min_int(c2, shi);
-            if (w != INT_MAX) { idx = (int64_t)kb * KPP_CHUNK + w; break; }
-            excl += blocksums[kb];   // rounding put t past this chunk: continue with the next
-            ++kb;
-        }
-        if (idx < 0) {   // t rounded up to the total: the last point with D^2 > 0
-            long long last = -1;
-            for (int64_t i = threadIdx.x; i < n; i += SEL_THREADS)
-                if (d2[i] > 0.f) last = i;
-            idx = block_max_ll(last, shl);
-            if (idx < 0) idx = 0;   // unreachable for finite D^2 (total > 0 implies a positive term)
-        }
-    } else {   // every point coincides with a chosen centre: uniform index
-        idx = (int64_t)floor(u * (double)n);
-        if (idx > n - 1) idx = n - 1;
+        const int kb = s_blk;
+        const u128 rel = s_rel;
+        const int64_t p0 = (int64_t)kb * KPP_CHUNK + 2 * threadIdx.x;
+        const u128 f0 = (p0 < n) ? fx48(d2[p0]) : u128{0ull, 0ull};
+        const u128 f1 = (p0 + 1 < n) ? fx48(d2[p0 + 1]) : u128{0ull, 0ull};
+        const u128 pin = block_incl_scan128<SEL_THREADS>(u128_add(f0, f1), sh);
+        const u128 r0 = u128_add(u128_sub(pin, u128_add(f0, f1)), f0);
+        if (threadIdx.x == 0) s_blk = INT_MAX;
+        __syncthreads();
+        int c2 = INT_MAX;
+        if (p0 < n && u128_gt(r0, rel)) c2 = 2 * threadIdx.x;
+        else if (p0 + 1 < n && u128_gt(pin, rel)) c2 = 2 * threadIdx.x + 1;
+        if (c2 != INT_MAX) atomicMin(&s_blk, c2);
+        __syncthreads();
+        idx = (int64_t)kb * KPP_CHUNK + (s_blk == INT_MAX ? 0 : s_blk);   // s_blk is always set: rel < chunk sum
+    } else {   // every weight is zero (duplicates of chosen centres): uniform index
+        idx = (int64_t)floor(uniform53(seed, (uint64_t)j) * (double)n);
     }
+    if (idx > n - 1) idx = n - 1;
+    if (idx < 0) idx = 0;
     if (threadIdx.x == 0) {
         centers[j] = pts[idx];
         chosen[j] = idx;
@@ -197,37 +146,334 @@ __global__ void __launch_bounds__(SEL_THREADS) kpp_select_kernel(const float4* _
     }
 }
 
+// ---------------------------------------------------------------- k-means++, persistent
+// One CTA per SM (cooperative launch, so every CTA is resident).  CTA c owns a
+// contiguous range of points, split into one contiguous segment per warp; D^2
+// stays with the warp that owns it.  Per centre j: every CTA updates D^2 and
+// publishes its binary64 sum; after all have arrived (bounded wait), every CTA
+// finds the winning CTA from the same fixed-order prefix; the winner locates the
+// point and publishes centre j (bounded wait for the others).  The prefix used
+// for the draw is exactly excl_c + (sequential warp sums), so the search always
+// lands inside the winning CTA.
+constexpr int KPPP_THREADS = 512;
+constexpr int KPPP_WARPS = KPPP_THREADS / 32;
+constexpr long long SPIN_LIMIT = 1ll << 22;   // polls of >= 100 ns: ~0.4 s or more
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Range of lane `lane` of warp `warp` of CTA `c` (contiguous sub-ranges, so the
+// running sum in point order is: CTA prefix, warp prefix, lane prefix, then the
+// lane's points in order).
+constexpr int KPP_LANE_MAX = 8;    // points per lane kept in registers by the search
+constexpr int KPP_SLICE_MAX = 8;   // CTA sums per lane in the search (grid <= 256)
+
+struct LaneRange {
+    int64_t lo, hi;
+};
+__device__ __forceinline__ LaneRange lane_range(int64_t n, int G, int c, int warp, int lane) {
+    const int64_t per = (n + G - 1) / G;
+    const int64_t clo = min(n, (int64_t)c * per), chi = min(n, clo + per);
+    const int64_t pw = (chi - clo + KPPP_WARPS - 1) / KPPP_WARPS;
+    const int64_t wlo = min(chi, clo + warp * pw), whi = min(chi, wlo + pw);
+    const int64_t pl = (whi - wlo + 31) / 32;
+    const int64_t llo = min(whi, wlo + lane * pl), lhi = min(whi, llo + pl);
+    return {llo, lhi};
+}
+
+
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Per centre j (one grid-wide wait; all sums exact, so every CTA agrees bit for bit):
+//  1. every lane updates D^2 of its <= KPP_LANE_MAX points (registers) and
+//     publishes them; the CTA publishes its exact fixed-point sum to sums[j][c];
+//  2. one thread per CTA arrives on the step's counter and waits (bounded) for
+//     all CTAs (many pollers on shared lines are far slower on this GPU); warp 0
+//     then loads the G sums in parallel and finds the CTA holding the threshold;
+//  3. every CTA loads that CTA's D^2 with the owner's lane layout and locates the
+//     point (no second wait: the arithmetic is exact, so all CTAs find the same one).
+__global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
+    const float4* __restrict__ pts, int64_t n, int k, uint64_t seed, float4* centers, float* d2pub, int64_t* chosen,
+    u128* sums, int* arrive, int* abort_flag, DeviceState* st) {
+    __shared__ u128 s_w[KPPP_WARPS];
+    __shared__ u128 s_rel, s_wrel;
+    __shared__ int s_ok, s_win, s_mode, s_ww;
+    __shared__ long long s_idx;
+    __shared__ float4 s_cen;
+    if (st->error) return;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const LaneRange mine = lane_range(n, G, c, warp, lane);
+    const int mcnt = (int)(mine.hi - mine.lo);
+    float4 P[KPP_LANE_MAX];
+    float D[KPP_LANE_MAX];
+#pragma unroll
+    for (int q = 0; q < KPP_LANE_MAX; ++q) {
+        P[q] = (q < mcnt) ? __ldg(pts + mine.lo + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        D[q] = 0.f;
+    }
+    int64_t idx = (int64_t)floor(uniform53(seed, 0) * (double)n);
+    if (idx > n - 1) idx = n - 1;
+    float4 cen = __ldg(pts + idx);
+    if (c == 0 && threadIdx.x == 0) {
+        centers[0] = cen;
+        chosen[0] = idx;
+    }
+    for (int j = 1; j < k; ++j) {
+        float* pub = d2pub + (size_t)(j & 1) * n;   // double-buffered: readers of step j-1 may lag
+        // ---- 1. update, publish, exact sums
+        u128 ls{0ull, 0ull};
+#pragma unroll
+        for (int q = 0; q < KPP_LANE_MAX; ++q) {
+            if (q < mcnt) {
+                float d = dist2_f32(P[q], cen);
+                if (j > 1) d = fminf(D[q], d);
+                D[q] = d;
+                pub[mine.lo + q] = d;
+                ls = u128_add(ls, fx48(d));
+            }
+        }
+        const u128 inc = u128_warp_incl_scan(ls, lane);
+        if (lane == 31) s_w[warp] = inc;
+        __threadfence();
+        __syncthreads();
+        if (warp == 0) {
+            u128 wv = (lane < KPPP_WARPS) ? s_w[lane] : u128{0ull, 0ull};
+            const u128 wi = u128_warp_incl_scan(wv, lane);
+            const u128 csum_me = u128_shfl(wi, KPPP_WARPS - 1);
+            // ---- 2. publish; one thread per CTA waits on the arrival counter
+            bool ok = true;
+            if (lane == 0) {
+                sums[(size_t)j * G + c] = csum_me;
+                red_release_add(&arrive[j], 1);
+                long long spins = 0;
+                while (ld_acquire(&arrive[j]) < G) {
+                    if (ld_acquire(abort_flag)) { ok = false; break; }
+                    if (++spins > SPIN_LIMIT) {
+                        set_error(st, GIRA_ERR_TIMEOUT);
+                        st_release(abort_flag, 1);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+            __syncwarp();
+            if (lane == 0) s_ok = ok;
+            if (ok) {
+                const u128* js = sums + (size_t)j * G;
+                const int sl = (G + 31) / 32;
+                const int a0 = min(G, lane * sl), a1 = min(G, a0 + sl);
+                u128 v[KPP_SLICE_MAX];
+#pragma unroll
+                for (int q = 0; q < KPP_SLICE_MAX; ++q) {
+                    v[q] = u128{0ull, 0ull};
+                    if (q < a1 - a0) {
+                        v[q].lo = __ldcg(&js[a0 + q].lo);
+                        v[q].hi = __ldcg(&js[a0 + q].hi);
+                    }
+                }
+                u128 loc{0ull, 0ull};
+#pragma unroll
+                for (int q = 0; q < KPP_SLICE_MAX; ++q) loc = u128_add(loc, v[q]);
+                const u128 cinc = u128_warp_incl_scan(loc, lane);
+                const u128 T = u128_shfl(cinc, 31);
+                if (!u128_zero(T)) {
+                    const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
+                    u128 run = u128_sub(cinc, loc);
+                    int cand = -1;
+                    u128 before{0ull, 0ull};
+#pragma unroll
+                    for (int q = 0; q < KPP_SLICE_MAX; ++q) {
+                        const u128 nxt = u128_add(run, v[q]);
+                        if (cand < 0 && q < a1 - a0 && u128_gt(nxt, t)) {
+                            cand = a0 + q;
+                            before = run;
+                        }
+                        run = nxt;
+                    }
+                    const unsigned hits = __ballot_sync(FULL, cand >= 0);   // exactly one lane (t < T)
+                    const int src = hits ? __ffs(hits) - 1 : 0;
+                    if (lane == src) {
+                        s_win = hits ? cand : 0;
+                        s_rel = u128_sub(t, before);
+                        s_mode = 0;
+                    }
+                } else if (lane == 0) {   // every weight is zero: uniform index
+                    long long id2 = (long long)floor(uniform53(seed, (uint64_t)j) * (double)n);
+                    if (id2 > n - 1) id2 = n - 1;
+                    s_idx = id2;
+                    s_mode = 2;
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (s_mode == 2) {
+            if (threadIdx.x == 0) s_cen = __ldg(pts + s_idx);
+        } else {
+            // ---- 3. locate the point inside the winning CTA, from its published D^2
+            const LaneRange lr = lane_range(n, G, s_win, warp, lane);
+            const int cnt = (int)(lr.hi - lr.lo);
+            float dv[KPP_LANE_MAX];
+            u128 lsum{0ull, 0ull};
+#pragma unroll
+            for (int q = 0; q < KPP_LANE_MAX; ++q) {
+                dv[q] = (q < cnt) ? __ldcg(pub + lr.lo + q) : 0.f;
+                lsum = u128_add(lsum, fx48(dv[q]));
+            }
+            const u128 linc = u128_warp_incl_scan(lsum, lane);
+            if (lane == 31) s_w[warp] = linc;
+            __syncthreads();
+            if (warp == 0) {
+                const u128 rel = s_rel;
+                const u128 wv = (lane < KPPP_WARPS) ? s_w[lane] : u128{0ull, 0ull};
+                const u128 wi = u128_warp_incl_scan(wv, lane);
+                const unsigned wh = __ballot_sync(FULL, lane < KPPP_WARPS && u128_gt(wi, rel));
+                const int ww = wh ? __ffs(wh) - 1 : 0;
+                const u128 wexcl = u128_sub(u128_shfl(wi, ww), u128_shfl(wv, ww));
+                if (lane == 0) {
+                    s_ww = ww;
+                    s_wrel = u128_sub(rel, wexcl);
+                }
+            }
+            __syncthreads();
+            if (warp == s_ww) {
+                const u128 wrel = s_wrel;
+                const unsigned lh = __ballot_sync(FULL, cnt > 0 && u128_gt(linc, wrel));
+                const int src = lh ? __ffs(lh) - 1 : 0;
+                if (lane == src) {
+                    u128 r = u128_sub(linc, lsum);
+                    long long found = lr.lo;
+                    bool got = false;
+#pragma unroll
+                    for (int q = 0; q < KPP_LANE_MAX; ++q) {
+                        if (q < cnt && !got) {
+                            r = u128_add(r, fx48(dv[q]));
+                            if (u128_gt(r, wrel)) {
+                                found = lr.lo + q;
+                                got = true;
+                            }
+                        }
+                    }
+                    if (found > n - 1) found = n - 1;   // unreachable clamp (exact search)
+                    s_idx = found;
+                    s_cen = __ldg(pts + found);
+                }
+            }
+        }
+        __syncthreads();
+        idx = s_idx;
+        cen = s_cen;
+        if (c == 0 && threadIdx.x == 0) {
+            centers[j] = cen;
+            chosen[j] = idx;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Lloyd
 // labels = argmin_b ||x - c_b||^2 (binary32, ties to the lowest b); binary64
 // sums of the raw coordinates and counts per label; changed[it] counts labels
-// that moved (every label for it == 0).
-__global__ void lloyd_assign_kernel(const float4* __restrict__ pts, int64_t n, int k, const float4* __restrict__ centers,
-                                    int32_t* labels, double* sums, unsigned long long* changed, int it,
-                                    DeviceState* st) {
-    extern __shared__ float4 sc[];
+// that moved (every label for it == 0).  Centres are processed two at a time
+// with packed FP32 (each lane of FADD2/FMUL2 rounds exactly like the scalar
+// operation, so the distances are those of dist2_f32).  Each thread owns
+// LL_PPT points; equal consecutive labels in a warp are summed before the
+// atomics (runs of raster-order points share labels).
+constexpr int LL_PPT = 4;
+constexpr int LL_THREADS = 256;
+
+struct CPair {
+    float2 x, y, z;   // negated coordinates of centres 2p and 2p+1
+};
+
+__global__ void __launch_bounds__(LL_THREADS) lloyd_assign_kernel(
+    const float4* __restrict__ pts, int64_t n, int k, const float4* __restrict__ centers, int32_t* labels,
+    double* sums, unsigned long long* changed, int it, DeviceState* st) {
+    extern __shared__ CPair sc[];
     if (st->error) return;
     if (it > 0 && changed[it - 1] == 0) return;
-    for (int b = threadIdx.x; b < k; b += blockDim.x) sc[b] = centers[b];
+    const int npair = (k + 1) / 2;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+        const float4 a = centers[2 * p];
+        const float4 b = (2 * p + 1 < k) ? centers[2 * p + 1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        sc[p] = CPair{f2(-a.x, -b.x), f2(-a.y, -b.y), f2(-a.z, -b.z)};
+    }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     unsigned long long cnt = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 x = pts[i];
-        int best = 0;
-        float bd = dist2_f32(x, sc[0]);
-        for (int b = 1; b < k; ++b) {
-            const float d = dist2_f32(x, sc[b]);
-            if (d < bd) { bd = d; best = b; }
+    const int64_t group = (int64_t)LL_THREADS * LL_PPT;
+    for (int64_t g0 = (int64_t)blockIdx.x * group; g0 < n; g0 += (int64_t)gridDim.x * group) {
+        // point r of this thread: g0 + warp_base + r * 32 + lane (coalesced per r)
+        const int64_t wb = g0 + (int64_t)(threadIdx.x >> 5) * 32 * LL_PPT;
+        float2 X[LL_PPT], Y[LL_PPT], Z[LL_PPT];
+        float bd[LL_PPT];
+        int best[LL_PPT];
+#pragma unroll
+        for (int r = 0; r < LL_PPT; ++r) {
+            const int64_t i = min(wb + r * 32 + lane, n - 1);
+            const float4 x = pts[i];
+            X[r] = dup(x.x);
+            Y[r] = dup(x.y);
+            Z[r] = dup(x.z);
+            bd[r] = INFINITY;
+            best[r] = 0;
         }
-        if (it == 0 || labels[i] != best) ++cnt;
-        labels[i] = best;
-        atomicAdd(&sums[4 * best + 0], (double)x.x);
-        atomicAdd(&sums[4 * best + 1], (double)x.y);
-        atomicAdd(&sums[4 * best + 2], (double)x.z);
-        atomicAdd(&sums[4 * best + 3], 1.0);
+        for (int p = 0; p < npair; ++p) {
+            const CPair c = sc[p];
+#pragma unroll
+            for (int r = 0; r < LL_PPT; ++r) {
+                const float2 dx = add2(X[r], c.x), dy = add2(Y[r], c.y), dz = add2(Z[r], c.z);
+                const float2 d = add2(add2(mul2(dx, dx), mul2(dy, dy)), mul2(dz, dz));
+                if (d.x < bd[r]) { bd[r] = d.x; best[r] = 2 * p; }
+                if (d.y < bd[r]) { bd[r] = d.y; best[r] = 2 * p + 1; }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < LL_PPT; ++r) {
+            const int64_t i = wb + r * 32 + lane;
+            const bool valid = i < n;
+            int key = -1;
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            if (valid) {
+                if (it == 0 || labels[i] != best[r]) ++cnt;
+                labels[i] = best[r];
+                key = best[r];
+                v[0] = (double)X[r].x;
+                v[1] = (double)Y[r].x;
+                v[2] = (double)Z[r].x;
+                v[3] = 1.0;
+            }
+            // segmented inclusive scan over runs of equal keys (fixed order)
+            const int prev = __shfl_up_sync(FULL, key, 1);
+            const bool head = (lane == 0) || (prev != key);
+            const unsigned heads = __ballot_sync(FULL, head);
+            const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double u = __shfl_up_sync(FULL, v[q], o);
+                    if (lane - o >= start) v[q] += u;
+                }
+            }
+            const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+            if (tail && key >= 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) atomicAdd(&sums[4 * key + q], v[q]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&changed[it], cnt);
+    if (lane == 0 && cnt) atomicAdd(&changed[it], cnt);
 }
 
 // centres = binary64 mean of their points, rounded to binary32; empty clusters
@@ -279,8 +525,36 @@ __global__ void centers_out_kernel(const float4* __restrict__ c4, int k, float* 
 
 int kpp_num_blocks(int64_t n) { return (int)((n + KPP_CHUNK - 1) / KPP_CHUNK); }
 
+int kpp_persistent_grid() {
+    int dev = 0, sms = 1, occ = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kpp_persistent_kernel, KPPP_THREADS, 0) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::min(sms, 256);   // the search keeps at most 8 CTA sums per lane
+}
+
+size_t kpp_persistent_sum_words(int grid, int k) { return (size_t)grid * (size_t)k; }
+
+int64_t kpp_persistent_max_n(int grid) { return (int64_t)grid * KPPP_WARPS * 32 * KPP_LANE_MAX; }
+
+cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
+                                  int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
+                                  cudaStream_t s) {
+    int* arrive = sync_ints;
+    int* abort_flag = sync_ints + k;
+    void* args[] = {(void*)&pts4, (void*)&n, (void*)&k, (void*)&seed, (void*)&centers, (void*)&d2, (void*)&chosen,
+                    (void*)&sums, (void*)&arrive, (void*)&abort_flag, (void*)&st};
+    return cudaLaunchCooperativeKernel((const void*)kpp_persistent_kernel, dim3(grid), dim3(KPPP_THREADS), args, 0, s);
+}
+
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
-                       double* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s) {
+                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s) {
     const int nblk = kpp_num_blocks(n);
     kpp_first_kernel<<<1, 1, 0, s>>>(pts4, n, seed, centers, chosen, st);
     for (int j = 1; j < k; ++j) {
@@ -295,10 +569,10 @@ cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, 
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(float4) * (size_t)k;
-    const int threads = 256;
-    const int64_t want = (n + threads - 1) / threads;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    const size_t smem = sizeof(CPair) * (size_t)((k + 1) / 2);
+    const int threads = LL_THREADS;
+    const int64_t want = (n + (int64_t)threads * LL_PPT - 1) / ((int64_t)threads * LL_PPT);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024)
         e = cudaFuncSetAttribute(lloyd_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -360,3 +360,50 @@ def test_invalid_arguments_and_nonfinite():
     with pytest.raises(oracle.OracleError) as e:
         oracle.estep(bad, [1.0], np.zeros((1, 3)), np.eye(3)[None])
     assert e.value.code == oracle.ERR_NONFINITE
+
+
+# ------------------------------------------------------------------------------- fixed-point draw
+def test_fx48_is_exact_floor():
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    vals = np.concatenate([rng.uniform(0, 100, 300), 10.0 ** rng.uniform(-20, 14, 300), [0.0, 1e-30, 2.0**-48,
+                                                                                           2.0**-49, 3.0]])
+    for d in vals.astype(np.float32):
+        want = int(Fraction(float(d)) * 2**48) if d < 2.0**47 else 2**95 - 1
+        assert oracle.fx48(d) == want, d
+    assert oracle.fx48(np.float32(2.0**47)) == 2**95 - 1
+
+
+def test_fx_threshold_is_exact_floor():
+    rng = np.random.default_rng(8)
+    for _ in range(300):
+        k = int(rng.integers(0, 2**53))
+        T = int(rng.integers(1, 2**63)) << int(rng.integers(0, 64)) | int(rng.integers(0, 2**63))
+        T &= (1 << 127) - 1
+        assert oracle.fx_threshold(k, T) == (k * T) >> 53
+    assert oracle.fx_threshold(2**53 - 1, 2**127 - 1) == ((2**53 - 1) * (2**127 - 1)) >> 53
+
+
+def _kmeanspp_fp64_cumsum(pts, K, seed):
+    """Independent k-means++: binary32 distances, binary64 cumsum, searchsorted."""
+    x = pts.astype(np.float32)
+    idx = min(int(np.floor(oracle.uniform(seed, 0) * len(x))), len(x) - 1)
+    chosen = [idx]
+    d2 = None
+    for j in range(1, K):
+        d = (x - x[chosen[-1]]).astype(np.float32)
+        p = (d * d).astype(np.float32)
+        dn = ((p[:, 0] + p[:, 1]).astype(np.float32) + p[:, 2]).astype(np.float32)
+        d2 = dn if d2 is None else np.minimum(d2, dn)
+        cs = np.cumsum(d2.astype(np.float64))
+        t = oracle.uniform(seed, j) * cs[-1]
+        chosen.append(int(np.searchsorted(cs, t, side="right")))
+    return np.array(chosen)
+
+
+def test_fixed_point_draw_matches_floating_point_sampling():
+    """Away from measure-zero near-ties the exact draw equals the binary64 cumsum draw."""
+    for seed in range(12):
+        pts = synth.gmm_cloud(3000, 6, seed=seed).points
+        _, ch = oracle.kmeanspp(pts, 25, seed)
+        assert np.array_equal(ch, _kmeanspp_fp64_cumsum(pts, 25, seed)), seed

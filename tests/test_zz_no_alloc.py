@@ -59,7 +59,7 @@ def test_noalloc_rejects_what_it_cannot_hold():
     from paper_2307_00071_gb300 import gira
     f = _noalloc(gira._lib)
     pts, w, mu, cov = _case(3, 100, 4)
-    too_many = 1048576 + 1
+    too_many = 524288 + 1
     assert f(pts.data_ptr(), too_many, 4, w.data_ptr(), mu.data_ptr(), cov.data_ptr(), None, None,
              None) == gira.ERR_INVALID_ARG
     host = np.zeros((100, 3), np.float32)

@@ -12,9 +12,9 @@
 // (kept in registers), the per-point sums are combined across lanes (shuffle
 // transpose-reduce) and warps (shared memory), and pass 2 accumulates the
 // per-component statistics S0 = sum r, S1 = sum r d, S2 = sum r d d^T with
-// d = x - mu_old (binary32, per-CTA partials).  Component pairs are processed
-// with packed FP32 (FFMA2/FADD2/FMUL2).  The responsibility matrix is never
-// stored.
+// d = x - mu_old (binary32, per-CTA partials).  Pass 1 processes component
+// pairs with packed FP32 (FFMA2/FADD2); pass 2 uses scalar FP32.  The
+// responsibility matrix is never stored.
 #include <float.h>
 #include <math.h>
 
@@ -99,12 +99,12 @@ constexpr int PPC_MAX = 2048;                         // points staged per CTA (
 
 // Fused E-step (+ statistics when STATS).  Component-stationary: one CTA holds
 // all K components, G warps x 32 lanes x NP packed pairs.  The CTA's points
-// arrive in one TMA bulk copy, laid out (x,x,y,y)(z,z,0,0) per point.  The
-// batch loop is software-pipelined: after the single CTA barrier of batch t a
-// warp finishes t's log-sum-exp (cross-warp combine), then computes the logits
-// and warp-level sums of batch t+1 while it accumulates the statistics of
-// batch t, so the shuffle / MUFU / barrier latency of one batch overlaps the
-// FMA-dense work of the other.
+// arrive in one TMA bulk copy, laid out (x,x,y,y)(z,z,0,0) per point.  Per batch
+// of Q points: pass 1 (logits, e, warp-level sums), one CTA barrier, the
+// cross-warp total and 1/total, pass 2 (statistics).  The per-point sums are
+// double-buffered by batch parity, so one barrier per batch suffices: a warp
+// can only overwrite a buffer after the next barrier, which every warp reaches
+// after reading it.
 template <int NP, int Q, int MAXT, int MINB, bool STATS>
 __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) {
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -183,12 +183,12 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
     for (int j = 0; j < NP; ++j) prm[j].c = f2(cmax - prm[j].c.x, cmax - prm[j].c.y);
     const float ref0 = s_norm ? cmax - __log2f(wsum) : cmax;
 
-    float2 S[NP][NSTAT];
+    float Sx[NP][NSTAT], Sy[NP][NSTAT];   // statistics of components 2p and 2p+1
     if (STATS) {
 #pragma unroll
         for (int j = 0; j < NP; ++j)
 #pragma unroll
-            for (int s = 0; s < NSTAT; ++s) S[j][s] = f2(0.f, 0.f);
+            for (int s = 0; s < NSTAT; ++s) Sx[j][s] = Sy[j][s] = 0.f;
     }
     double ll_acc = 0.0;
     const int myq = q_of_lane<Q>(lane);
@@ -228,24 +228,28 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
         for (int q = 0; q < Q; ++q) {
             float2 X0, X1, X2;
             load_pt((q < nvalid) ? lb + q : lb, X0, X1, X2);
-            const float2 R = dup(__shfl_sync(FULL, r, q * LPQ));
+            const float R = __shfl_sync(FULL, r, q * LPQ);
+            // scalar FP32: measured faster than the packed form for this
+            // accumulate-heavy pattern
+            auto acc1 = [&](float e, float m0, float m1, float m2, float (&T)[NSTAT]) {
+                const float g = e * R;
+                const float d0 = X0.x + m0, d1 = X1.x + m1, d2 = X2.x + m2;
+                const float g0 = g * d0, g1 = g * d1, g2 = g * d2;
+                T[0] += g;
+                T[1] += g0;
+                T[2] += g1;
+                T[3] += g2;
+                T[4] = fmaf(g0, d0, T[4]);
+                T[5] = fmaf(g0, d1, T[5]);
+                T[6] = fmaf(g0, d2, T[6]);
+                T[7] = fmaf(g1, d1, T[7]);
+                T[8] = fmaf(g1, d2, T[8]);
+                T[9] = fmaf(g2, d2, T[9]);
+            };
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const float2 g = mul2(E[j][q], R);
-                const float2 d0 = add2(X0, prm[j].nmu[0]);
-                const float2 d1 = add2(X1, prm[j].nmu[1]);
-                const float2 d2 = add2(X2, prm[j].nmu[2]);
-                const float2 g0 = mul2(g, d0), g1 = mul2(g, d1), g2 = mul2(g, d2);
-                S[j][0] = add2(S[j][0], g);
-                S[j][1] = add2(S[j][1], g0);
-                S[j][2] = add2(S[j][2], g1);
-                S[j][3] = add2(S[j][3], g2);
-                S[j][4] = fma2(g0, d0, S[j][4]);
-                S[j][5] = fma2(g0, d1, S[j][5]);
-                S[j][6] = fma2(g0, d2, S[j][6]);
-                S[j][7] = fma2(g1, d1, S[j][7]);
-                S[j][8] = fma2(g1, d2, S[j][8]);
-                S[j][9] = fma2(g2, d2, S[j][9]);
+                acc1(E[j][q].x, prm[j].nmu[0].x, prm[j].nmu[1].x, prm[j].nmu[2].x, Sx[j]);
+                acc1(E[j][q].y, prm[j].nmu[0].y, prm[j].nmu[1].y, prm[j].nmu[2].y, Sy[j]);
             }
         }
     };
@@ -310,18 +314,12 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
         }
         return ok ? __frcp_rn(tot) : 0.f;
     };
-    auto step = [&](int t, float2 (&Ecur)[NP][Q], float2 (&Enext)[NP][Q]) {
+    float2 E[NP][Q];
+    for (int t = 0; t < nb; ++t) {
+        pass1(t, E);
         __syncthreads();   // every warp's sums of batch t are in red_sum[t & 1]
-        const float r = finish(t, Ecur);
-        if (t + 1 < nb) pass1(t + 1, Enext);
-        if (STATS) pass2(t, Ecur, r);
-    };
-
-    float2 E0[NP][Q], E1[NP][Q];
-    pass1(0, E0);
-    for (int t = 0; t < nb; t += 2) {
-        step(t, E0, E1);
-        if (t + 1 < nb) step(t + 1, E1, E0);
+        const float r = finish(t, E);
+        if (STATS) pass2(t, E, r);
     }
 
     if (STATS) {
@@ -331,10 +329,10 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
             const int b0 = 2 * ((j * G + warp) * 32 + lane);
             if (b0 < a.k)
 #pragma unroll
-                for (int s = 0; s < NSTAT; ++s) dst[(size_t)b0 * NSTAT + s] = S[j][s].x;
+                for (int s = 0; s < NSTAT; ++s) dst[(size_t)b0 * NSTAT + s] = Sx[j][s];
             if (b0 + 1 < a.k)
 #pragma unroll
-                for (int s = 0; s < NSTAT; ++s) dst[(size_t)(b0 + 1) * NSTAT + s] = S[j][s].y;
+                for (int s = 0; s < NSTAT; ++s) dst[(size_t)(b0 + 1) * NSTAT + s] = Sy[j][s];
         }
     }
     if (warp == 0) {   // owner lanes hold the per-point log-likelihood sums; fixed order
@@ -347,13 +345,17 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
 
 // ------------------------------------------------------------------ launch policy
 // Shapes: K <= 64 -> one component pair per lane and one warp; otherwise two
-// pairs per lane and G = ceil(K / 128) warps.  Batches of Q = 4 points keep two
-// E buffers of the pipeline within the register budget of 3 CTAs per SM.
-// (Measured on GB300 for K = 512: one pair per lane with 8 warps, other
-// CTA-per-SM targets, and a producer/consumer warp-specialised variant were
-// all slower than this shape.)
+// pairs per lane and G = ceil(K / 128) warps; batches of Q = 8 points, one CTA
+// barrier per batch, statistics accumulated with scalar FP32 operations.
+// Measured on GB300 for K = 512 (276,348 points): Q = 8 171 us, Q = 4 192 us,
+// Q = 4 software-pipelined 203 us, scalar statistics 169 us; one pair per lane
+// with 8 warps, other CTA-per-SM targets and a producer/consumer
+// warp-specialised variant were slower.  Probes of the two passes alone show
+// the FP32 pipe at ~60 % (pass 1) and ~74 % (pass 2) of its peak: the limit is
+// register-file operand bandwidth (three distinct register operands per FFMA),
+// not occupancy (3, 4 or 5 CTAs per SM run pass 1 at the same speed).
 #ifndef GIRA_ESTEP_Q
-#define GIRA_ESTEP_Q 4
+#define GIRA_ESTEP_Q 8
 #endif
 constexpr int QB = GIRA_ESTEP_Q;
 

@@ -344,7 +344,10 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
         pts = pin;
     }
     COUNTED(prof, 1, launch_pack(pts, n, p4, nullptr, st, c.s));
-    if (kgrid > 0) {
+    const int kcs = kpp_cluster_size(n);
+    if (kcs > 0) {
+        COUNTED(prof, 1, launch_kpp_cluster(p4, n, k, seed, c4, ch, kcs, st, c.s));
+    } else if (kgrid > 0) {
         GIRA_CUDA(cudaMemsetAsync(ksync, 0, sizeof(int) * (k + 1), c.s));
         COUNTED(prof, 1, launch_kpp_persistent(p4, n, k, seed, c4, d2, ch, ksync, ksums, kgrid, st, c.s));
     } else {
@@ -470,7 +473,10 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
     float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
     if (kinit) {
-        if (kgrid > 0) {
+        const int kcs = kpp_cluster_size(n);
+        if (kcs > 0) {
+            COUNTED(prof, 1, launch_kpp_cluster(b.p4, n, k, o.seed, b.c4, b.ch, kcs, b.st, c.s));
+        } else if (kgrid > 0) {
             GIRA_CUDA(cudaMemsetAsync(b.ksync, 0, sizeof(int) * (k + 1), c.s));
             COUNTED(prof, 1, launch_kpp_persistent(b.p4, n, k, o.seed, b.c4, b.d2, b.ch, b.ksync, b.ksums, kgrid, b.st,
                                                    c.s));

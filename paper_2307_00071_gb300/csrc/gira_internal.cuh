@@ -258,6 +258,11 @@ int64_t kpp_persistent_max_n(int grid);
 cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
                                   int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
                                   cudaStream_t s);
+// One-cluster k-means++ (no global synchronisation): cluster size for n points,
+// or 0 when the one-cluster path does not apply.
+int kpp_cluster_size(int64_t n);
+cudaError_t launch_kpp_cluster(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, int64_t* chosen,
+                               int cs, DeviceState* st, cudaStream_t s);
 cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, float4* centers, int32_t* labels,
                          double* sums, unsigned long long* changed, DeviceState* st, cudaStream_t s);
 cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32_t* labels, const float4* shift4,

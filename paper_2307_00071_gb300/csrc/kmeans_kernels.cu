@@ -14,7 +14,11 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "gira_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gira {
 
@@ -380,6 +384,220 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
     }
 }
 
+// ---------------------------------------------------------------- k-means++ in one cluster
+// For N <= cs * 512 * KC_LMAX (cs = cluster size, 16 where the GPU allows it):
+// one thread-block cluster seeds all K centres with no global-memory
+// synchronisation at all.  Each of the cs CTAs (one per SM) keeps its points'
+// coordinates in shared memory and their D^2 in registers; each lane keeps the
+// exact fixed-point sum of its own D^2, recomputed only when a new centre
+// lowers one of them.  Per centre j:
+//  1. update D^2 and the lane sums; warp / CTA prefixes of the lane sums; each
+//     CTA writes its total into every CTA's shared memory (DSMEM);
+//  2. cluster barrier; every CTA evaluates the same prefix over the cs totals
+//     and finds the CTA holding the threshold;
+//  3. that CTA locates the point (warp, lane, then the lane's points in order)
+//     and writes it into every CTA's shared memory; cluster barrier.
+// The arithmetic is the exact fixed point of the other seeding kernels, so the
+// chosen indices are identical.
+constexpr int KC_THREADS = 512;
+constexpr int KC_WARPS = KC_THREADS / 32;
+constexpr int KC_PMAX = 18;               // point pairs per lane
+constexpr int KC_LMAX = 2 * KC_PMAX;      // points per lane
+constexpr int KC_MAX_CS = 16;
+
+struct KcShared {
+    u128 wtot[KC_WARPS], wincl[KC_WARPS];
+    u128 csum[KC_MAX_CS];   // written by every CTA of the cluster (DSMEM)
+    u128 rel;
+    float4 cen;             // written by the CTA holding the chosen point (DSMEM)
+    long long idx;
+    int win, mode;
+};
+
+size_t kc_smem_bytes() { return (size_t)3 * KC_PMAX * KC_THREADS * sizeof(float2) + sizeof(KcShared) + 16; }
+
+// fx48(d) for 0 <= d < 2^10 as a 64-bit integer (36 of them sum below 2^64);
+// raises `big` for larger d, whose callers take the 128-bit fx48.
+__device__ __forceinline__ unsigned long long fx48_small(float d, bool& big) {
+    const unsigned bits = __float_as_uint(d);
+    const int ex = (int)(bits >> 23);
+    big |= ex >= 137;
+    const unsigned long long mant = (bits & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int sh = (ex ? ex : 1) - 102;   // d * 2^48 = mant * 2^sh
+    return sh >= 0 ? mant << min(sh, 63) : mant >> min(-sh, 63);
+}
+
+__global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4* __restrict__ pts, int64_t n, int k,
+                                                                    uint64_t seed, float4* centers, int64_t* chosen,
+                                                                    DeviceState* st) {
+    extern __shared__ __align__(16) unsigned char kc_dsm[];
+    float2* xs = reinterpret_cast<float2*>(kc_dsm);   // [KC_PMAX][KC_THREADS] each: points 2p, 2p+1 of a lane
+    float2* ys = xs + KC_PMAX * KC_THREADS;
+    float2* zs = ys + KC_PMAX * KC_THREADS;
+    KcShared& sh = *reinterpret_cast<KcShared*>(zs + KC_PMAX * KC_THREADS);
+    cg::cluster_group cluster = cg::this_cluster();
+    if (st->error) return;   // set before the launch: every CTA leaves
+    const int cs = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // contiguous ranges: CTA, warp, lane (the running sum in point order is
+    // CTA prefix, warp prefix, lane prefix, then the lane's points in order)
+    const int64_t per = (n + cs - 1) / cs;
+    const int64_t clo = min(n, (int64_t)me * per), chi = min(n, clo + per);
+    const int64_t pw = (chi - clo + KC_WARPS - 1) / KC_WARPS;
+    const int64_t wlo = min(chi, clo + warp * pw), whi = min(chi, wlo + pw);
+    const int64_t pl = (whi - wlo + 31) / 32;
+    const int64_t llo = min(whi, wlo + lane * pl), lhi = min(whi, llo + pl);
+    const int mcnt = (int)min(lhi - llo, (int64_t)KC_LMAX);   // <= KC_LMAX by the host's size check
+#pragma unroll
+    for (int p = 0; p < KC_PMAX; ++p) {
+        const float4 v0 = (2 * p < mcnt) ? __ldg(pts + llo + 2 * p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v1 = (2 * p + 1 < mcnt) ? __ldg(pts + llo + 2 * p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xs[p * KC_THREADS + tid] = f2(v0.x, v1.x);
+        ys[p * KC_THREADS + tid] = f2(v0.y, v1.y);
+        zs[p * KC_THREADS + tid] = f2(v0.z, v1.z);
+    }
+    float2 D[KC_PMAX];   // D^2 of points 2p, 2p+1 (padding lanes: +inf, never chosen, fx48 0 not used)
+    u128 ls{0ull, 0ull};
+    int64_t idx = (int64_t)floor(uniform53(seed, 0) * (double)n);
+    if (idx > n - 1) idx = n - 1;
+    float4 cen = __ldg(pts + idx);
+    if (me == 0 && tid == 0) {
+        centers[0] = cen;
+        chosen[0] = idx;
+    }
+    cluster.sync();   // every CTA of the cluster has started before any DSMEM access
+    for (int j = 1; j < k; ++j) {
+        // ---- 1. D^2 (packed: each lane of FADD2/FMUL2 rounds like dist2_f32) and,
+        //         where any D^2 dropped, the lane's exact sum from scratch (raster-
+        //         order lanes see their points' D^2 drop together, so one pass over
+        //         the lane beats per-point differences)
+        const float2 ncx = dup(-cen.x), ncy = dup(-cen.y), ncz = dup(-cen.z);
+        bool changed = (j == 1);
+#pragma unroll
+        for (int p = 0; p < KC_PMAX; ++p) {
+            if (2 * p < mcnt) {
+                const float2 d0 = add2(xs[p * KC_THREADS + tid], ncx);
+                const float2 d1 = add2(ys[p * KC_THREADS + tid], ncy);
+                const float2 d2 = add2(zs[p * KC_THREADS + tid], ncz);
+                const float2 dd = add2(add2(mul2(d0, d0), mul2(d1, d1)), mul2(d2, d2));
+                if (j == 1) {
+                    D[p] = dd;
+                } else {
+                    changed |= (dd.x < D[p].x) || (dd.y < D[p].y);
+                    D[p] = f2(fminf(D[p].x, dd.x), fminf(D[p].y, dd.y));
+                }
+            }
+        }
+        if (changed) {
+            bool big = false;   // a weight >= 2^10: sum in 128 bits
+            unsigned long long s64 = 0ull;
+#pragma unroll
+            for (int p = 0; p < KC_PMAX; ++p) {
+                if (2 * p < mcnt) s64 += fx48_small(D[p].x, big);
+                if (2 * p + 1 < mcnt) s64 += fx48_small(D[p].y, big);
+            }
+            ls = u128{s64, 0ull};
+            if (big) {
+                ls = u128{0ull, 0ull};
+#pragma unroll
+                for (int p = 0; p < KC_PMAX; ++p) {
+                    if (2 * p < mcnt) ls = u128_add(ls, fx48(D[p].x));
+                    if (2 * p + 1 < mcnt) ls = u128_add(ls, fx48(D[p].y));
+                }
+            }
+        }
+        const u128 linc = u128_warp_incl_scan(ls, lane);
+        if (lane == 31) sh.wtot[warp] = linc;
+        __syncthreads();
+        if (warp == 0) {
+            const u128 wv = (lane < KC_WARPS) ? sh.wtot[lane] : u128{0ull, 0ull};
+            const u128 wi = u128_warp_incl_scan(wv, lane);
+            if (lane < KC_WARPS) sh.wincl[lane] = wi;
+            const u128 total = u128_shfl(wi, KC_WARPS - 1);
+            if (lane < cs) cluster.map_shared_rank(&sh, lane)->csum[me] = total;
+        }
+        cluster.sync();   // ---- 2. every CTA total is in every CTA's csum
+        if (warp == 0) {
+            const u128 v = (lane < cs) ? sh.csum[lane] : u128{0ull, 0ull};
+            const u128 inc = u128_warp_incl_scan(v, lane);
+            const u128 T = u128_shfl(inc, 31);
+            if (!u128_zero(T)) {
+                const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
+                const unsigned hits = __ballot_sync(FULL, lane < cs && u128_gt(inc, t));   // t < T: not empty
+                const int w = hits ? __ffs(hits) - 1 : 0;
+                if (lane == w) {
+                    sh.win = w;
+                    sh.rel = u128_sub(t, u128_sub(inc, v));
+                    sh.mode = 0;
+                }
+            } else if (lane == 0) {   // every weight is zero: uniform index
+                long long id2 = (long long)floor(uniform53(seed, (uint64_t)j) * (double)n);
+                if (id2 > n - 1) id2 = n - 1;
+                sh.idx = id2;
+                sh.cen = __ldg(pts + id2);
+                sh.mode = 2;
+                if (me == 0) {
+                    centers[j] = sh.cen;
+                    chosen[j] = id2;
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.mode == 0 && sh.win == me) {
+            // ---- 3. this CTA holds the point: warp, lane, then the lane's points
+            const u128 rel = sh.rel;
+            const u128 wi = (lane < KC_WARPS) ? sh.wincl[lane] : u128{0ull, 0ull};
+            const unsigned wh = __ballot_sync(FULL, lane < KC_WARPS && u128_gt(wi, rel));
+            const int ww = wh ? __ffs(wh) - 1 : 0;   // wh != 0: rel < this CTA's total
+            if (warp == ww) {
+                const u128 wrel = u128_sub(rel, u128_sub(sh.wincl[ww], sh.wtot[ww]));
+                const unsigned lh = __ballot_sync(FULL, mcnt > 0 && u128_gt(linc, wrel));
+                const int src = lh ? __ffs(lh) - 1 : 0;
+                // the src lane's points, spread over the warp: lane l takes points l and 32 + l
+                const u128 base = u128_sub(u128_shfl(linc, src), u128_shfl(ls, src));
+                const u128 rel2 = u128_sub(wrel, base);
+                const int cnt = __shfl_sync(FULL, mcnt, src);
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int p = 0; p < KC_PMAX; ++p) {
+                    const float vx = __shfl_sync(FULL, D[p].x, src), vy = __shfl_sync(FULL, D[p].y, src);
+                    if (lane == ((2 * p) & 31)) {
+                        if (2 * p < 32) a0 = vx; else a1 = vx;
+                    }
+                    if (lane == ((2 * p + 1) & 31)) {
+                        if (2 * p + 1 < 32) a0 = vy; else a1 = vy;
+                    }
+                }
+                const u128 u0 = (lane < cnt) ? fx48(a0) : u128{0ull, 0ull};
+                const u128 u1 = (32 + lane < cnt) ? fx48(a1) : u128{0ull, 0ull};
+                const u128 p0 = u128_warp_incl_scan(u0, lane);
+                const u128 p1 = u128_add(u128_warp_incl_scan(u1, lane), u128_shfl(p0, 31));
+                const unsigned h0 = __ballot_sync(FULL, lane < cnt && u128_gt(p0, rel2));
+                const unsigned h1 = __ballot_sync(FULL, 32 + lane < cnt && u128_gt(p1, rel2));
+                const int qf = h0 ? __ffs(h0) - 1 : (h1 ? 32 + __ffs(h1) - 1 : 0);   // some hit: exact search
+                const int ft = warp * 32 + src;   // the src lane's column in xs / ys / zs
+                const float2 px = xs[(qf >> 1) * KC_THREADS + ft], py = ys[(qf >> 1) * KC_THREADS + ft],
+                             pz = zs[(qf >> 1) * KC_THREADS + ft];
+                const float4 pf = (qf & 1) ? make_float4(px.y, py.y, pz.y, 0.f) : make_float4(px.x, py.x, pz.x, 0.f);
+                const long long lo_src = __shfl_sync(FULL, (long long)llo, src);
+                const long long found = min((long long)n - 1, lo_src + qf);   // clamp never taken
+                if (lane < cs) {
+                    KcShared* dst = cluster.map_shared_rank(&sh, lane);
+                    dst->cen = pf;
+                    dst->idx = found;
+                }
+                if (lane == 0) {
+                    centers[j] = pf;
+                    chosen[j] = found;
+                }
+            }
+        }
+        cluster.sync();   // the chosen centre is in every CTA's shared memory
+        cen = sh.cen;
+        idx = sh.idx;
+    }
+}
+
 // ---------------------------------------------------------------- Lloyd
 // labels = argmin_b ||x - c_b||^2 (binary32, ties to the lowest b); binary64
 // sums of the raw coordinates and counts per label; changed[it] counts labels
@@ -551,6 +769,60 @@ cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t
     void* args[] = {(void*)&pts4, (void*)&n, (void*)&k, (void*)&seed, (void*)&centers, (void*)&d2, (void*)&chosen,
                     (void*)&sums, (void*)&arrive, (void*)&abort_flag, (void*)&st};
     return cudaLaunchCooperativeKernel((const void*)kpp_persistent_kernel, dim3(grid), dim3(KPPP_THREADS), args, 0, s);
+}
+
+// Cluster size for the one-cluster seeding of n points, or 0 when it does not
+// apply (too many points, or no cluster of that size fits on this GPU).
+int kpp_cluster_size(int64_t n) {
+    static int cached = -1;   // largest usable cluster size on the current device
+    if (cached < 0) {
+        cached = 0;
+        const size_t smem = kc_smem_bytes();
+        if (cudaFuncSetAttribute(kpp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(kpp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            for (int cs : {KC_MAX_CS, 8}) {
+                cudaLaunchConfig_t cfg{};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = cs;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3(cs);
+                cfg.blockDim = dim3(KC_THREADS);
+                cfg.dynamicSmemBytes = smem;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, kpp_cluster_kernel, &cfg) == cudaSuccess &&
+                    nclusters >= 1) {
+                    cached = cs;
+                    break;
+                }
+            }
+        }
+        cudaGetLastError();
+    }
+    if (cached == 0 || n > (int64_t)cached * KC_THREADS * KC_LMAX) return 0;
+    return cached;
+}
+
+cudaError_t launch_kpp_cluster(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, int64_t* chosen,
+                               int cs, DeviceState* st, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(KC_THREADS);
+    cfg.dynamicSmemBytes = kc_smem_bytes();
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kpp_cluster_kernel, pts4, n, k, seed, centers, chosen, st);
 }
 
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,

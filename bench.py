@@ -22,6 +22,7 @@ on the data path; barriers only bracket the timed region).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -49,7 +50,7 @@ EM_SOURCE = os.path.join(ROOT, "paper_2307_00071_gb300", "csrc", "em_kernels.cu"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gira", "reference"], default="gira")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -118,19 +119,28 @@ def traffic_per_launch():
 
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle sampling during the timed region."""
+    """nvidia-smi SM clock / throttle sampling; started before the warm-up (the
+    tool takes a while to start), only samples inside [mark_start, mark_end]
+    are summarised."""
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_ms=25):
         self.path = tempfile.mktemp(suffix=".csv")
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
+        self.t0 = self.t1 = None
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(period_ms)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -140,11 +150,19 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 8:
-                rows.append(parts)
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if self.t0 is not None and self.t1 is not None and not (self.t0 <= ts <= self.t1):
+                continue
+            rows.append(parts[1:])
         os.unlink(self.path)
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples inside the timed region"],
+                    "samples": 0}
         mhz = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -227,6 +245,7 @@ def run_gira(args):
     def fit(p, **kw):
         return gira.gira_gmm_fit(p, K, iters=ITERS, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD, **kw)
 
+    clocks = ClockSampler(local)
     for _ in range(args.warmup):
         fit(pts, **out)
     gira.gira_profile_enable(True)
@@ -234,7 +253,7 @@ def run_gira(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     units, iters_seen = 0, []
     barrier()
-    clocks = ClockSampler(local)
+    clocks.mark_start()
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record()
@@ -243,6 +262,7 @@ def run_gira(args):
         units += n * K * r["iters_done"]
         iters_seen.append(r["iters_done"])
     barrier()
+    clocks.mark_end()
     clk = clocks.stop()
     prof = gira.gira_profile_read(reset=True)
     gira.gira_profile_enable(False)
@@ -287,7 +307,7 @@ def run_gira(args):
             "iters_done": iters_seen,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_units, "unit": UNIT,
                          "frac": achieved / peak_units, "traffic": tr,
-                         "kernel": "estep_kernel<2,128,3,true> (fused E-step + M-step statistics)",
+                         "kernel": "estep_kernel<2,8,128,3,true> (fused E-step + M-step statistics)",
                          "launch_ms": avg_estep_s * 1e3,
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {mhz:.0f} MHz ({mhz_src}) / "
                                        f"{FP32_OPS_PER_UNIT} FP32 ops per unit"},

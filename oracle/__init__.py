@@ -56,6 +56,7 @@ def lib():
         u64p = C.POINTER(C.c_uint64)
         L.oracle_fx48_parts.argtypes = [C.c_float, u64p, u64p]
         L.oracle_fx_threshold.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, u64p, u64p]
+        L.oracle_loglik_grad.argtypes = [fp, C.c_int64, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -225,3 +226,25 @@ def kinit(pts, K: int, seed: int, lloyd_iters: int, reg: float):
     centers, labels, done = lloyd(pts, centers, lloyd_iters)
     w, m, c = init_from_labels(pts, labels, K, reg)
     return dict(weights=w, means=m, covs=c, centers=centers, labels=labels, chosen=chosen, lloyd_done=done)
+
+
+def loglik_grad(pts, logits, means, chol, pose=None, want_points: bool = True):
+    """Summed log-likelihood of the moved scan R x + t and its gradient.
+
+    pose: (R (3,3), t (3,)) or None.  Returns a dict: loglik, grad_points (N,3)
+    or None, grad_twist (6,) = (omega, v), grad_logits (K,), grad_means (K,3),
+    grad_chol (K,3,3) lower triangular."""
+    pts = _f32(pts)
+    N, K = pts.shape[0], len(logits)
+    lg, m, ch = _f64(logits), _f64(means), _f64(chol).reshape(K, 9).copy()
+    p12 = None
+    if pose is not None:
+        p12 = np.concatenate([_f64(pose[0]).reshape(9), _f64(pose[1]).reshape(3)])
+    gp = np.empty((N, 3)) if want_points else None
+    gt, gl, gm, gc = np.empty(6), np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
+    ll = C.c_double()
+    st = lib().oracle_loglik_grad(_p(pts, C.c_float), N, K, _p(p12, C.c_double), _p(lg, C.c_double),
+                                  _p(m, C.c_double), _p(ch, C.c_double), C.byref(ll), _p(gp, C.c_double),
+                                  _p(gt, C.c_double), _p(gl, C.c_double), _p(gm, C.c_double), _p(gc, C.c_double))
+    _check(st, "loglik_grad")
+    return dict(loglik=ll.value, grad_points=gp, grad_twist=gt, grad_logits=gl, grad_means=gm, grad_chol=gc)

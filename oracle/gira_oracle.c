@@ -33,6 +33,18 @@
  * k-means++ draws are integer decisions taken in exact fixed point (see
  * oracle_fx48): no floating-point rounding enters the choice of a centre.
  *
+ * Differentiable log-likelihood (oracle_loglik_grad): not in the paper, which
+ * registers scans with its own distribution-to-distribution method; here the
+ * plain definition  L = sum_n ln sum_b pi_b N(R x_n + t | mu_b, L_b L_b^T),
+ * pi = softmax(alpha), and its gradient by ordinary calculus, term by term
+ * per point and component (gamma = responsibility, y = L_b^{-1}(x'-mu_b)):
+ *   dL/dx'_n   = -sum_b gamma_nb L_b^{-T} y_nb          (dL/dx_n = R^T dL/dx'_n)
+ *   dL/dmu_b   =  sum_n gamma_nb L_b^{-T} y_nb
+ *   dL/dL_b    =  sum_n gamma_nb (L_b^{-T} y y^T - diag(1/L_b,ii)), lower triangle
+ *   dL/dalpha_b = sum_n gamma_nb - N pi_b
+ *   twist xi = (omega, v), a left perturbation x' <- exp(xi^) x' (rotation
+ *   first):  dL/domega = sum_n x'_n x dL/dx'_n,  dL/dv = sum_n dL/dx'_n.
+ *
  * Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
  * counter-based generator: draw j of seed s is the (j+1)-th output of the
  * SplitMix64 stream started at state s;  u_j = (r_j >> 11) * 2^-53.
@@ -406,4 +418,108 @@ int oracle_gmm_fit(const float *pts, int64_t N, int K, int iters, double tol, do
     free(lab);
     if (st != OR_OK) return st;
     return oracle_em(pts, N, K, iters, tol, reg, weights, means, covs, trace, iters_done, final_ll);
+}
+
+/* ------------------------------------------------ differentiable loglik -- */
+/* L and its gradient (see the header).  pose12 = R (row-major 3x3) then t, or
+ * NULL for the identity.  chol: K x 9 row-major, lower triangle read, diagonal
+ * must be positive (else OR_ERR_NOT_PD).  Every gradient pointer may be NULL. */
+int oracle_loglik_grad(const float *pts, int64_t N, int K, const double *pose12, const double *logits,
+                       const double *means, const double *chol, double *loglik, double *grad_pts,
+                       double *grad_twist, double *grad_logits, double *grad_means, double *grad_chol) {
+    if (N < 1 || K < 1 || !pts || !logits || !means || !chol) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, 3 * N) || !all_finite_d(logits, K) || !all_finite_d(means, 3 * (int64_t)K) ||
+        !all_finite_d(chol, 9 * (int64_t)K) || (pose12 && !all_finite_d(pose12, 12)))
+        return OR_ERR_NONFINITE;
+    const double I12[12] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
+    const double *R = pose12 ? pose12 : I12, *t = (pose12 ? pose12 : I12) + 9;
+    double *logw = malloc(sizeof(double) * K), *gam = malloc(sizeof(double) * K);
+    double *lgam = malloc(sizeof(double) * K);
+    if (!logw || !gam || !lgam) {
+        free(logw); free(gam); free(lgam);
+        return OR_ERR_OOM;
+    }
+    /* log pi_b = alpha_b - ln sum_a exp(alpha_a) */
+    double amax = logits[0];
+    for (int b = 1; b < K; ++b) amax = logits[b] > amax ? logits[b] : amax;
+    double z = 0.0;
+    for (int b = 0; b < K; ++b) z += exp(logits[b] - amax);
+    const double lz = amax + log(z);
+    for (int b = 0; b < K; ++b) {
+        const double *Lb = chol + 9 * (size_t)b;
+        if (!(Lb[0] > 0.0 && Lb[4] > 0.0 && Lb[8] > 0.0)) {
+            g_last_bad_component = b;
+            free(logw); free(gam); free(lgam);
+            return OR_ERR_NOT_PD;
+        }
+        /* ln pi_b - sum_j ln L_jj - (3/2) ln 2 pi */
+        logw[b] = (logits[b] - lz) - (log(Lb[0]) + log(Lb[4]) + log(Lb[8])) - 1.5 * log(2.0 * M_PI);
+    }
+    if (grad_twist) memset(grad_twist, 0, sizeof(double) * 6);
+    if (grad_logits) memset(grad_logits, 0, sizeof(double) * K);
+    if (grad_means) memset(grad_means, 0, sizeof(double) * 3 * K);
+    if (grad_chol) memset(grad_chol, 0, sizeof(double) * 9 * K);
+    double total = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        const double x[3] = {pts[3 * n], pts[3 * n + 1], pts[3 * n + 2]};
+        double xp[3];
+        for (int i = 0; i < 3; ++i) xp[i] = R[3 * i] * x[0] + R[3 * i + 1] * x[1] + R[3 * i + 2] * x[2] + t[i];
+        double lmax = -INFINITY;
+        for (int b = 0; b < K; ++b) {
+            const double *Lb = chol + 9 * (size_t)b, *mu = means + 3 * (size_t)b;
+            const double d0 = xp[0] - mu[0], d1 = xp[1] - mu[1], d2 = xp[2] - mu[2];
+            /* y = L^{-1} d (forward substitution) */
+            const double y0 = d0 / Lb[0];
+            const double y1 = (d1 - Lb[3] * y0) / Lb[4];
+            const double y2 = (d2 - Lb[6] * y0 - Lb[7] * y1) / Lb[8];
+            lgam[b] = logw[b] - 0.5 * (y0 * y0 + y1 * y1 + y2 * y2);
+            lmax = lgam[b] > lmax ? lgam[b] : lmax;
+        }
+        double ssum = 0.0;
+        for (int b = 0; b < K; ++b) ssum += exp(lgam[b] - lmax);
+        const double lse = lmax + log(ssum);
+        total += lse;
+        for (int b = 0; b < K; ++b) gam[b] = exp(lgam[b] - lse);
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; b < K; ++b) {
+            const double *Lb = chol + 9 * (size_t)b, *mu = means + 3 * (size_t)b;
+            const double d0 = xp[0] - mu[0], d1 = xp[1] - mu[1], d2 = xp[2] - mu[2];
+            const double y0 = d0 / Lb[0];
+            const double y1 = (d1 - Lb[3] * y0) / Lb[4];
+            const double y2 = (d2 - Lb[6] * y0 - Lb[7] * y1) / Lb[8];
+            /* w = L^{-T} y (back substitution) = Sigma^{-1} d */
+            const double w2 = y2 / Lb[8];
+            const double w1 = (y1 - Lb[7] * w2) / Lb[4];
+            const double w0 = (y0 - Lb[3] * w1 - Lb[6] * w2) / Lb[0];
+            const double gb = gam[b];
+            g[0] -= gb * w0;
+            g[1] -= gb * w1;
+            g[2] -= gb * w2;
+            if (grad_means) {
+                grad_means[3 * b] += gb * w0;
+                grad_means[3 * b + 1] += gb * w1;
+                grad_means[3 * b + 2] += gb * w2;
+            }
+            if (grad_chol) {
+                const double w[3] = {w0, w1, w2}, y[3] = {y0, y1, y2};
+                double *G = grad_chol + 9 * (size_t)b;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j <= i; ++j) G[3 * i + j] += gb * (w[i] * y[j] - (i == j ? 1.0 / Lb[4 * i] : 0.0));
+            }
+            if (grad_logits) grad_logits[b] += gb;
+        }
+        if (grad_pts)
+            for (int i = 0; i < 3; ++i) grad_pts[3 * n + i] = R[i] * g[0] + R[3 + i] * g[1] + R[6 + i] * g[2];
+        if (grad_twist) {
+            grad_twist[0] += xp[1] * g[2] - xp[2] * g[1];
+            grad_twist[1] += xp[2] * g[0] - xp[0] * g[2];
+            grad_twist[2] += xp[0] * g[1] - xp[1] * g[0];
+            for (int i = 0; i < 3; ++i) grad_twist[3 + i] += g[i];
+        }
+    }
+    if (grad_logits)
+        for (int b = 0; b < K; ++b) grad_logits[b] -= (double)N * exp(logits[b] - lz);
+    if (loglik) *loglik = total;
+    free(logw); free(gam); free(lgam);
+    return OR_OK;
 }

@@ -135,6 +135,43 @@ gira_status gira_gmm_loglik(const float *points, int64_t n, int k, const float *
                             const float *covs, double *mean_loglik, float *per_point, void *stream);
 
 /*
+ * gira_gmm_loglik_grad -- the log-likelihood of a rigidly moved scan and its
+ * gradient (an extension beyond the paper, whose own registration is its
+ * distribution-to-distribution method): with x'_n = R x_n + t,
+ *   L = sum_n ln sum_b pi_b N(x'_n | mu_b, L_b L_b^T),  pi = softmax(logits),
+ * the per-component log-density of Eq. simplifiedGaussian with P = L_b^{-1}
+ * and the log-sum-exp of Eq. logestep.  Gradients (gamma = responsibility,
+ * y = L_b^{-1}(x' - mu_b)), all in one pass that recomputes gamma and never
+ * stores it:
+ *   dL/dx_n      = R^T dL/dx'_n,   dL/dx'_n = -sum_b gamma_nb Sigma_b^{-1}(x'_n - mu_b)
+ *   dL/dR, dL/dt = sum_n dL/dx'_n x_n^T,  sum_n dL/dx'_n
+ *   dL/dtwist    = (sum_n x'_n x dL/dx'_n, sum_n dL/dx'_n): twist (omega, v) of a
+ *                  left perturbation x' <- exp(twist^) x', rotation first
+ *   dL/dlogits_b = sum_n gamma_nb - N pi_b
+ *   dL/dmeans_b  = sum_n gamma_nb Sigma_b^{-1}(x'_n - mu_b)
+ *   dL/dchol_b   = lower triangle of sum_n gamma_nb (L_b^{-T} y y^T - diag(1/L_b,ii))
+ *
+ *   points       [host|device] N x 3 binary32 (the scan before the move)
+ *   pose12       [host|device] R row-major (9) then t (3), binary32, or NULL (identity)
+ *   logits       [host|device] K binary32
+ *   means        [host|device] K x 3 binary32
+ *   chol         [host|device] K x 3 x 3 binary32 row-major; the lower triangle is
+ *                read, the diagonal must be > 0 (else GIRA_ERR_NOT_PD)
+ *   loglik       [host] L (a sum over points, binary64), or NULL
+ *   grad_points  [host|device] N x 3 binary32, or NULL
+ *   grad_pose    [host|device] 12 binary64: dL/dR (row-major 3x3) then dL/dt, or NULL
+ *   grad_twist   [host|device] 6 binary64 (omega, v), or NULL
+ *   grad_logits  [host|device] K binary32, or NULL
+ *   grad_means   [host|device] K x 3 binary32, or NULL
+ *   grad_chol    [host|device] K x 3 x 3 binary32 (zeros above the diagonal), or NULL
+ * With every gradient pointer NULL only the log-likelihood pass runs.
+ */
+gira_status gira_gmm_loglik_grad(const float *points, int64_t n, int k, const float *pose12, const float *logits,
+                                 const float *means, const float *chol, double *loglik, float *grad_points,
+                                 double *grad_pose, double *grad_twist, float *grad_logits, float *grad_means,
+                                 float *grad_chol, void *stream);
+
+/*
  * Profiling (off by default; process-wide).  When enabled, each call records
  * CUDA events on its stream around its phases and around every launch of the
  * fused E-step/statistics kernel, and accumulates the device times below when

@@ -93,6 +93,18 @@ __device__ __forceinline__ float2 neg_logit2(const PairParams& P, float2 X0, flo
     const float2 y2 = fma2(P.p[3], X0, fma2(P.p[4], X1, fma2(P.p[5], X2, P.b[2])));
     return fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, P.c)));
 }
+// The same from d = x - mu (three more operations): P'x + b' cancels two
+// numbers of size |P'| |x| (a point metres from the origin against a
+// centimetre factor) and carries the binary32 rounding of b' as a fixed offset
+// of every y of the component; P'd does not.  Used where the log-likelihood
+// itself is the product (the differentiable path).
+__device__ __forceinline__ float2 neg_logit2_d(const PairParams& P, float2 X0, float2 X1, float2 X2) {
+    const float2 d0 = add2(X0, P.nmu[0]), d1 = add2(X1, P.nmu[1]), d2 = add2(X2, P.nmu[2]);
+    const float2 y0 = mul2(P.p[0], d0);
+    const float2 y1 = fma2(P.p[2], d1, mul2(P.p[1], d0));
+    const float2 y2 = fma2(P.p[5], d2, fma2(P.p[4], d1, mul2(P.p[3], d0)));
+    return fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, P.c)));
+}
 
 constexpr long long MBAR_POLL_LIMIT = 2000000000ll;   // bound on any mbarrier wait: 2 s of wall time
 constexpr int PPC_MAX = 2048;                         // points staged per CTA (64 KB)
@@ -105,11 +117,19 @@ constexpr int PPC_MAX = 2048;                         // points staged per CTA (
 // double-buffered by batch parity, so one barrier per batch suffices: a warp
 // can only overwrite a buffer after the next barrier, which every warp reaches
 // after reading it.
-template <int NP, int Q, int MAXT, int MINB, bool STATS>
+//
+// GRAD (the adjoint of the log-likelihood, with STATS): pass 2 also forms each
+// point's sum over components of gamma * Sigma_b^{-1} (x' - mu_b) (as
+// P'^T P' d, in the base-2 scaling of P'), reduced across lanes and warps (a
+// second barrier per batch) into dL/dx' = -(2 ln 2) * that sum; the owner lanes
+// write dL/dx = R^T dL/dx' and accumulate the pose sums (dL/dx' x'^T, dL/dx').
+// The statistics S0, S1, S2 give the parameter gradients (finalize).
+template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, bool DFORM = GRAD>
 __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar_tma;
     __shared__ float red_sum[2][32][Q];
+    __shared__ float red_g[GRAD ? 2 : 1][GRAD ? 32 : 1][Q][3];
     __shared__ float red_aux[2][32][Q];
     __shared__ float s_cmax[32], s_wsum[32];
     __shared__ int s_skip, s_norm, s_dead;
@@ -211,7 +231,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
             float2 acc = f2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const float2 nq = neg_logit2(prm[j], X0, X1, X2);
+                const float2 nq = DFORM ? neg_logit2_d(prm[j], X0, X1, X2) : neg_logit2(prm[j], X0, X1, X2);
                 const float2 e = f2(ex2_approx(-nq.x), ex2_approx(-nq.y));
                 E[j][q] = e;
                 acc = add2(acc, e);
@@ -224,16 +244,27 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
     // statistics of batch t from E and the reciprocal sums r (owned by lane q * LPQ)
     auto pass2 = [&](int t, const float2 (&E)[NP][Q], float r) {
         const int lb = t * Q, nvalid = min(Q, npts - lb);
+        float gq[Q][3];   // GRAD: this lane's share of sum_b gamma P'^T P' d, per point
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             float2 X0, X1, X2;
             load_pt((q < nvalid) ? lb + q : lb, X0, X1, X2);
             const float R = __shfl_sync(FULL, r, q * LPQ);
+            if (GRAD) gq[q][0] = gq[q][1] = gq[q][2] = 0.f;
             // scalar FP32: measured faster than the packed form for this
             // accumulate-heavy pattern
-            auto acc1 = [&](float e, float m0, float m1, float m2, float (&T)[NSTAT]) {
+            auto acc1 = [&](float e, float m0, float m1, float m2, float (&T)[NSTAT], const float2 (&pp)[6], int h) {
                 const float g = e * R;
                 const float d0 = X0.x + m0, d1 = X1.x + m1, d2 = X2.x + m2;
+                if (GRAD) {
+                    const float p0 = h ? pp[0].y : pp[0].x, p1 = h ? pp[1].y : pp[1].x, p2 = h ? pp[2].y : pp[2].x;
+                    const float p3 = h ? pp[3].y : pp[3].x, p4 = h ? pp[4].y : pp[4].x, p5 = h ? pp[5].y : pp[5].x;
+                    const float y0 = p0 * d0, y1 = fmaf(p2, d1, p1 * d0), y2 = fmaf(p5, d2, fmaf(p4, d1, p3 * d0));
+                    const float z0 = fmaf(p3, y2, fmaf(p1, y1, p0 * y0)), z1 = fmaf(p4, y2, p2 * y1), z2 = p5 * y2;
+                    gq[q][0] = fmaf(g, z0, gq[q][0]);
+                    gq[q][1] = fmaf(g, z1, gq[q][1]);
+                    gq[q][2] = fmaf(g, z2, gq[q][2]);
+                }
                 const float g0 = g * d0, g1 = g * d1, g2 = g * d2;
                 T[0] += g;
                 T[1] += g0;
@@ -248,8 +279,18 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
             };
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                acc1(E[j][q].x, prm[j].nmu[0].x, prm[j].nmu[1].x, prm[j].nmu[2].x, Sx[j]);
-                acc1(E[j][q].y, prm[j].nmu[0].y, prm[j].nmu[1].y, prm[j].nmu[2].y, Sy[j]);
+                acc1(E[j][q].x, prm[j].nmu[0].x, prm[j].nmu[1].x, prm[j].nmu[2].x, Sx[j], prm[j].p, 0);
+                acc1(E[j][q].y, prm[j].nmu[0].y, prm[j].nmu[1].y, prm[j].nmu[2].y, Sy[j], prm[j].p, 1);
+            }
+        }
+        if (GRAD) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float v[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) v[q] = gq[q][c];
+                const float w = warp_transpose_reduce<Q>(v, lane, AddOp());
+                if ((lane & (LPQ - 1)) == 0) red_g[t & 1][warp][myq][c] = w;
             }
         }
     };
@@ -272,7 +313,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
                 float mm = -INFINITY;
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    const float2 nq = neg_logit2(prm[j], X0, X1, X2);
+                    const float2 nq = DFORM ? neg_logit2_d(prm[j], X0, X1, X2) : neg_logit2(prm[j], X0, X1, X2);
                     const float2 l = f2(-nq.x, -nq.y);
                     E[j][q] = l;
                     mm = fmaxf(mm, fmaxf(l.x, l.y));
@@ -315,11 +356,47 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
         return ok ? __frcp_rn(tot) : 0.f;
     };
     float2 E[NP][Q];
+    float tw[12] = {};   // GRAD owner lanes: sum g x'^T (row-major), sum g
     for (int t = 0; t < nb; ++t) {
         pass1(t, E);
         __syncthreads();   // every warp's sums of batch t are in red_sum[t & 1]
         const float r = finish(t, E);
         if (STATS) pass2(t, E, r);
+        if (GRAD) {
+            __syncthreads();   // every warp's gradient sums of batch t are in red_g[t & 1]
+            const int lb = t * Q;
+            if (owner && myq < min(Q, npts - lb)) {
+                float g3[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = red_g[t & 1][0][myq][c];
+                    for (int w = 1; w < G; ++w) v += red_g[t & 1][w][myq][c];
+                    g3[c] = -1.38629436111989061883f * v;   // -(2 ln 2): P'^T P' = Sigma^{-1} log2(e) / 2
+                }
+                const float4 xy = spts[2 * (lb + myq)], zz = spts[2 * (lb + myq) + 1];
+                const float x0 = xy.x, x1 = xy.z, x2 = zz.x;
+                const float xq[3] = {x0, x1, x2};
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) tw[3 * i + j] = fmaf(g3[i], xq[j], tw[3 * i + j]);
+                    tw[9 + i] += g3[i];
+                }
+                if (a.grad_pts) {
+                    float* gp = a.grad_pts + 3 * (begin + lb + myq);
+                    if (a.rot) {
+                        const float* Rm = a.rot;
+                        gp[0] = fmaf(Rm[6], g3[2], fmaf(Rm[3], g3[1], Rm[0] * g3[0]));
+                        gp[1] = fmaf(Rm[7], g3[2], fmaf(Rm[4], g3[1], Rm[1] * g3[0]));
+                        gp[2] = fmaf(Rm[8], g3[2], fmaf(Rm[5], g3[1], Rm[2] * g3[0]));
+                    } else {
+                        gp[0] = g3[0];
+                        gp[1] = g3[1];
+                        gp[2] = g3[2];
+                    }
+                }
+            }
+        }
     }
 
     if (STATS) {
@@ -340,6 +417,15 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
 #pragma unroll
         for (int o = LPQ; o < 32; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
         if (lane == 0) a.ll_partials[blockIdx.x] = v * LN2;
+        if (GRAD) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                double u = owner ? (double)tw[i] : 0.0;
+#pragma unroll
+                for (int o = LPQ; o < 32; o <<= 1) u += __shfl_xor_sync(FULL, u, o);
+                if (lane == 0) a.pose_partials[(size_t)blockIdx.x * 12 + i] = u;
+            }
+        }
     }
 }
 
@@ -375,6 +461,18 @@ const void* kernel_for(const Shape& sh) {
     if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 3, STATS>;
     return (const void*)estep_kernel<2, QB, 256, 1, STATS>;
 }
+// Differentiable path: the adjoint kernel, or (forward only) the log-likelihood
+// with the same d-form logits.
+const void* grad_kernel_for(const Shape& sh, bool stats) {
+    if (!stats) {
+        if (sh.np == 1) return (const void*)estep_kernel<1, QB, 32, 16, false, false, true>;
+        if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 3, false, false, true>;
+        return (const void*)estep_kernel<2, QB, 256, 1, false, false, true>;
+    }
+    if (sh.np == 1) return (const void*)estep_kernel<1, QB, 32, 16, true, true>;
+    if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 2, true, true>;
+    return (const void*)estep_kernel<2, QB, 256, 1, true, true>;
+}
 
 size_t estep_smem(int64_t ppc) { return (size_t)ppc * 32; }
 
@@ -387,9 +485,9 @@ int params_pairs_padded(int k) {
 
 // Points per CTA and grid: as many CTAs as fit on the SMs (points of a CTA
 // staged in shared memory, at most PPC_MAX per CTA).
-int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta) {
+int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta, bool grad) {
     const Shape sh = shape_for(k);
-    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
     int occ = 1;
     // occupancy with the largest staging buffer the launch could use
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -407,10 +505,10 @@ int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta) 
     return (int)grid;
 }
 
-cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s) {
+cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad) {
     const Shape sh = shape_for(a.k);
     void* args[] = {(void*)&a};
-    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
     const size_t smem = estep_smem(a.pts_per_cta);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -526,6 +624,38 @@ __device__ bool build_component(int b, double w, const double mu[3], const doubl
     return true;
 }
 
+// The statistics of components b0 .. b0 + nout / NSTAT - 1 summed over the
+// per-CTA partials into S (binary64): FIN_SPLIT fixed slices of CTAs, binary32
+// groups of 8 within a slice, binary64 across groups and slices.  Call with
+// every thread of the block; ends with S valid after a barrier.
+__device__ void reduce_partials(const float* __restrict__ partials, int grid, int k, int b0, int nout,
+                                double (*part)[FIN_CPB * NSTAT], double* S) {
+    const int t = threadIdx.x;
+    const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
+    if (o < nout) {
+        const int c0 = q * grid / FIN_SPLIT, c1 = (q + 1) * grid / FIN_SPLIT;
+        const float* src = partials + (size_t)b0 * NSTAT + o;
+        const size_t stride = (size_t)k * NSTAT;
+        double acc = 0.0;
+        for (int c = c0; c < c1; c += 8) {   // eight independent loads in flight
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (c + u < c1) ? __ldcg(src + (size_t)(c + u) * stride) : 0.f;
+            float f = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) f += v[u];
+            acc += (double)f;
+        }
+        part[q][o] = acc;
+    }
+    __syncthreads();
+    if (t < nout) {
+        double v = 0.0;
+        for (int q2 = 0; q2 < FIN_SPLIT; ++q2) v += part[q2][t];
+        S[t] = v;
+    }
+}
+
 // M-step from the shifted statistics (d = x - s_b):
 //   N_b = S0 + 10 eps, mu = (S0 s + S1) / N_b, delta = mu - s,
 //   sum r (x-mu)(x-mu)^T = S2 - delta S1^T - S1 delta^T + S0 delta delta^T,
@@ -546,29 +676,7 @@ __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(
     const int nb = min(FIN_CPB, k - b0);
     const int nout = nb * NSTAT;
     if (partials) {
-        const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
-        if (o < nout) {
-            const int c0 = q * grid / FIN_SPLIT, c1 = (q + 1) * grid / FIN_SPLIT;
-            const float* src = partials + (size_t)b0 * NSTAT + o;
-            const size_t stride = (size_t)k * NSTAT;
-            double acc = 0.0;
-            for (int c = c0; c < c1; c += 8) {   // eight independent loads in flight
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (c + u < c1) ? __ldcg(src + (size_t)(c + u) * stride) : 0.f;
-                float f = 0.f;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) f += v[u];
-                acc += (double)f;
-            }
-            part[q][o] = acc;
-        }
-        __syncthreads();
-        if (t < nout) {
-            double v = 0.0;
-            for (int q2 = 0; q2 < FIN_SPLIT; ++q2) v += part[q2][t];
-            S[t] = v;
-        }
+        reduce_partials(partials, grid, k, b0, nout, part, S);
     } else if (t < nout) {
         S[t] = stats64[(size_t)b0 * NSTAT + t];
     }
@@ -649,6 +757,179 @@ __global__ void model_out_kernel(const double* __restrict__ model64, int k, floa
     const int idx[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
     for (int i = 0; i < 9; ++i) cov[9 * (size_t)b + i] = (float)m[4 + idx[i]];
 }
+
+// ------------------------------------------------------------------ differentiable log-likelihood
+// x' = R x + t in binary32 (fixed order), stored as (x,x,y,y)(z,z,0,0).
+__global__ void pack_pose_kernel(const float* __restrict__ p3, int64_t n, const float* __restrict__ pose,
+                                 float4* __restrict__ p8, DeviceState* st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = p3[3 * i], y = p3[3 * i + 1], z = p3[3 * i + 2];
+    float o[3] = {x, y, z};
+    if (pose) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[r] = fmaf(pose[3 * r + 2], z, fmaf(pose[3 * r + 1], y, pose[3 * r] * x)) + pose[9 + r];
+    }
+    if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) set_error(st, GIRA_ERR_NONFINITE_INPUT);
+    p8[2 * i] = make_float4(o[0], o[0], o[1], o[1]);
+    p8[2 * i + 1] = make_float4(o[2], o[2], 0.f, 0.f);
+}
+
+// One block: pi = softmax(logits) in binary64 (max, then fixed-order sums),
+// Sigma_b = L_b L_b^T, then the M-step's binary64 build of the E-step
+// parameters.  A non-positive diagonal entry of L_b is GIRA_ERR_NOT_PD.
+constexpr int PFC_THREADS = 256;
+__global__ void __launch_bounds__(PFC_THREADS) params_from_chol_kernel(const float* __restrict__ logits,
+                                                                       const float* __restrict__ mu,
+                                                                       const float* __restrict__ chol, int k,
+                                                                       double* model64, float* params,
+                                                                       float4* shift4, DeviceState* st) {
+    __shared__ double s_red[PFC_THREADS / 32];
+    __shared__ double s_max, s_lz;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    bool fin = true;
+    double m = -INFINITY;
+    for (int b = t; b < k; b += PFC_THREADS) {
+        fin = fin && isfinite(logits[b]);
+        m = fmax(m, (double)logits[b]);
+    }
+    if (!fin) set_error(st, GIRA_ERR_NONFINITE_INPUT);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+    if (lane == 0) s_red[warp] = m;
+    __syncthreads();
+    if (t == 0) {
+        double v = s_red[0];
+        for (int w = 1; w < PFC_THREADS / 32; ++w) v = fmax(v, s_red[w]);
+        s_max = v;
+    }
+    __syncthreads();
+    const double amax = s_max;
+    double z = 0.0;
+    for (int b = t; b < k; b += PFC_THREADS) z += exp((double)logits[b] - amax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = z;
+    __syncthreads();
+    if (t == 0) {
+        double v = 0.0;
+        for (int w = 0; w < PFC_THREADS / 32; ++w) v += s_red[w];
+        s_lz = amax + log(v);
+    }
+    __syncthreads();
+    const double lz = s_lz;
+    for (int b = t; b < k; b += PFC_THREADS) {
+        const float* L = chol + 9 * (size_t)b;
+        const double m3[3] = {mu[3 * b], mu[3 * b + 1], mu[3 * b + 2]};
+        bool ok = isfinite(m3[0]) && isfinite(m3[1]) && isfinite(m3[2]);
+        const double L00 = L[0], L10 = L[3], L11 = L[4], L20 = L[6], L21 = L[7], L22 = L[8];
+        ok = ok && isfinite(L00) && isfinite(L10) && isfinite(L11) && isfinite(L20) && isfinite(L21) && isfinite(L22);
+        if (!ok) {
+            set_error(st, GIRA_ERR_NONFINITE_INPUT);
+            continue;
+        }
+        if (!(L00 > 0.0 && L11 > 0.0 && L22 > 0.0)) {
+            atomicMin(&st->bad_component, b);
+            set_error(st, GIRA_ERR_NOT_PD);
+            continue;
+        }
+        const double c[6] = {L00 * L00, L00 * L10, L00 * L20, L10 * L10 + L11 * L11, L10 * L20 + L11 * L21,
+                             L20 * L20 + L21 * L21 + L22 * L22};
+        build_component(b, exp((double)logits[b] - lz), m3, c, params, shift4, model64, st);
+    }
+}
+
+// Parameter gradients from the statistics about mu_b (d = x' - mu_b):
+//   dL/dmu_b    = Sigma^{-1} S1 = P^T P S1
+//   dL/dL_b     = lower(P^T (P S2 P^T) - S0 diag(1/L_ii))
+//   dL/dalpha_b = S0 - N pi_b
+// with P = L_b^{-1}; block 0 also sums the log-likelihood and the twist.
+__global__ void __launch_bounds__(FIN_THREADS) grad_finalize_kernel(
+    const float* __restrict__ partials, int grid, const double* __restrict__ llp, const double* __restrict__ pp,
+    const float* __restrict__ pose, const float* __restrict__ chol, const double* __restrict__ model64, int k,
+    int64_t n, float* g_logits, float* g_means, float* g_chol, double* g_pose, double* g_twist, DeviceState* st) {
+    __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
+    __shared__ double S[FIN_CPB * NSTAT];
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = st->error != 0;
+    __syncthreads();
+    if (s_skip) return;
+    const int t = threadIdx.x;
+    const int b0 = blockIdx.x * FIN_CPB;
+    const int nb = min(FIN_CPB, k - b0);
+    reduce_partials(partials, grid, k, b0, nb * NSTAT, part, S);
+    __syncthreads();
+    if (t < nb) {
+        const int b = b0 + t;
+        const double* Sb = S + t * NSTAT;
+        const float* L = chol + 9 * (size_t)b;
+        const double L00 = L[0], L10 = L[3], L11 = L[4], L20 = L[6], L21 = L[7], L22 = L[8];
+        const double P00 = 1.0 / L00, P11 = 1.0 / L11, P22 = 1.0 / L22;
+        const double P10 = -L10 * P00 * P11, P21 = -L21 * P11 * P22, P20 = -(L20 * P00 + L21 * P10) * P22;
+        const double P[3][3] = {{P00, 0.0, 0.0}, {P10, P11, 0.0}, {P20, P21, P22}};
+        const double s0 = Sb[0];
+        const double s1[3] = {Sb[1], Sb[2], Sb[3]};
+        const double S2[3][3] = {{Sb[4], Sb[5], Sb[6]}, {Sb[5], Sb[7], Sb[8]}, {Sb[6], Sb[8], Sb[9]}};
+        double u[3], gm[3];
+        for (int i = 0; i < 3; ++i) u[i] = P[i][0] * s1[0] + P[i][1] * s1[1] + P[i][2] * s1[2];
+        for (int i = 0; i < 3; ++i) gm[i] = P[0][i] * u[0] + P[1][i] * u[1] + P[2][i] * u[2];
+        double A[3][3], M[3][3];   // A = P S2, M = A P^T
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) A[i][j] = P[i][0] * S2[0][j] + P[i][1] * S2[1][j] + P[i][2] * S2[2][j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = A[i][0] * P[j][0] + A[i][1] * P[j][1] + A[i][2] * P[j][2];
+        const double Ld[3] = {L00, L11, L22};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                double v = 0.0;
+                if (j <= i) {
+                    v = P[0][i] * M[0][j] + P[1][i] * M[1][j] + P[2][i] * M[2][j];
+                    if (i == j) v -= s0 / Ld[i];
+                }
+                if (g_chol) g_chol[9 * (size_t)b + 3 * i + j] = (float)v;
+            }
+            if (g_means) g_means[3 * (size_t)b + i] = (float)gm[i];
+        }
+        if (g_logits) g_logits[b] = (float)(s0 - (double)n * model64[(size_t)b * MODEL]);
+    }
+    if (blockIdx.x == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood and pose sums, fixed order
+        const int lane = t - 32;
+        double v[13] = {};
+        for (int c = lane; c < grid; c += 32) {
+            v[0] += llp[c];
+            for (int i = 0; i < 12; ++i) v[1 + i] += pp[(size_t)c * 12 + i];
+        }
+        for (int i = 0; i < 13; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(FULL, v[i], o);
+        }
+        if (lane == 0) {
+            st->ll_sum = v[0];
+            const double* M = v + 1;    // sum g x'^T
+            const double* G = v + 10;   // sum g
+            if (g_twist) {   // omega = sum x' x g, v = sum g
+                g_twist[0] = M[3 * 2 + 1] - M[3 * 1 + 2];
+                g_twist[1] = M[3 * 0 + 2] - M[3 * 2 + 0];
+                g_twist[2] = M[3 * 1 + 0] - M[3 * 0 + 1];
+                for (int i = 0; i < 3; ++i) g_twist[3 + i] = G[i];
+            }
+            if (g_pose) {    // x = R^T (x' - t): dL/dR = (sum g x'^T - G t^T) R, dL/dt = G
+                const double tt[3] = {pose ? pose[9] : 0.0, pose ? pose[10] : 0.0, pose ? pose[11] : 0.0};
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        double acc = 0.0;
+                        for (int m = 0; m < 3; ++m) {
+                            const double Rmj = pose ? (double)pose[3 * m + j] : (m == j ? 1.0 : 0.0);
+                            acc += (M[3 * i + m] - G[i] * tt[m]) * Rmj;
+                        }
+                        g_pose[3 * i + j] = acc;
+                    }
+                for (int i = 0; i < 3; ++i) g_pose[9 + i] = G[i];
+            }
+        }
+    }
+}
 }  // namespace
 
 cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
@@ -672,4 +953,28 @@ cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, 
     return cudaGetLastError();
 }
 
+}  // namespace gira
+
+namespace gira {
+cudaError_t launch_pack_pose(const float* pts3, int64_t n, const float* pose12, float4* pts8, DeviceState* st,
+                             cudaStream_t s) {
+    pack_pose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts3, n, pose12, pts8, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params_from_chol(const float* logits, const float* mu, const float* chol, int k, double* model64,
+                                    float* params, float4* shift4, DeviceState* st, cudaStream_t s) {
+    params_from_chol_kernel<<<1, PFC_THREADS, 0, s>>>(logits, mu, chol, k, model64, params, shift4, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize(const float* partials, int grid, const double* ll_partials,
+                                 const double* pose_partials, const float* pose12, const float* chol,
+                                 const double* model64, int k, int64_t n, float* g_logits, float* g_means,
+                                 float* g_chol, double* g_pose, double* g_twist, DeviceState* st, cudaStream_t s) {
+    grad_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(
+        partials, grid, ll_partials, pose_partials, pose12, chol, model64, k, n, g_logits, g_means, g_chol, g_pose,
+        g_twist, st);
+    return cudaGetLastError();
+}
 }  // namespace gira

@@ -630,4 +630,135 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
     return GIRA_OK;
 }
 
+// ================================================================ gmm_loglik_grad
+gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const float* pose12, const float* logits,
+                                 const float* means, const float* chol, double* loglik, float* grad_points,
+                                 double* grad_pose, double* grad_twist, float* grad_logits, float* grad_means,
+                                 float* grad_chol, void* stream) {
+    reset_error();
+    TRY(check_nk(n, k));
+    if (!points || !logits || !means || !chol) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kl, km, kc, kpose = Kind::Device, kgp = Kind::Device, kgo = Kind::Device, kgt = Kind::Device,
+                         kgl = Kind::Device, kgm = Kind::Device, kgc = Kind::Device;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(logits, "logits", c.dev, &kl));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(chol, "chol", c.dev, &kc));
+    if (pose12) TRY(check_ptr(pose12, "pose12", c.dev, &kpose));
+    if (grad_points) TRY(check_ptr(grad_points, "grad_points", c.dev, &kgp));
+    if (grad_pose) TRY(check_ptr(grad_pose, "grad_pose", c.dev, &kgo));
+    if (grad_twist) TRY(check_ptr(grad_twist, "grad_twist", c.dev, &kgt));
+    if (grad_logits) TRY(check_ptr(grad_logits, "grad_logits", c.dev, &kgl));
+    if (grad_means) TRY(check_ptr(grad_means, "grad_means", c.dev, &kgm));
+    if (grad_chol) TRY(check_ptr(grad_chol, "grad_chol", c.dev, &kgc));
+    const bool grad = grad_points || grad_pose || grad_twist || grad_logits || grad_means || grad_chol;
+    const int npairs = params_pairs_padded(k);
+    int64_t ppc = 0;
+    const int grid = estep_grid(n, k, grad, c.sms, &ppc, true);
+    auto host = [&](Kind kd, const void* ptr) { return ptr && kd == Kind::Host; };
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *pose, *lg, *mu, *ch, *params, *partials, *gp, *gl, *gm, *gc;
+        float4 *p8, *shift4;
+        double *model64, *llp, *ppart, *po64, *tw64;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(host(kp, points) ? 3 * (size_t)n : 0);
+        b.pose = cv.take<float>(host(kpose, pose12) ? 12 : 0);
+        b.lg = cv.take<float>(host(kl, logits) ? k : 0);
+        b.mu = cv.take<float>(host(km, means) ? 3 * (size_t)k : 0);
+        b.ch = cv.take<float>(host(kc, chol) ? 9 * (size_t)k : 0);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
+        b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
+        b.shift4 = cv.take<float4>(k);
+        b.model64 = cv.take<double>((size_t)k * MODEL);
+        b.llp = cv.take<double>(grid);
+        b.partials = cv.take<float>(grad ? (size_t)grid * k * NSTAT : 0);
+        b.ppart = cv.take<double>(grad ? (size_t)grid * 12 : 0);
+        b.po64 = cv.take<double>(12);
+        b.tw64 = cv.take<double>(6);
+        b.gp = cv.take<float>(host(kgp, grad_points) ? 3 * (size_t)n : 0);
+        b.gl = cv.take<float>(host(kgl, grad_logits) ? k : 0);
+        b.gm = cv.take<float>(host(kgm, grad_means) ? 3 * (size_t)k : 0);
+        b.gc = cv.take<float>(host(kgc, grad_chol) ? 9 * (size_t)k : 0);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.stop_after = 0;
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    // inputs: device pointers as given, host arrays staged
+    auto in = [&](const float* src, Kind kd, float* stage, size_t count) -> const float* {
+        if (!src || kd != Kind::Host) return src;
+        if (cudaMemcpyAsync(stage, src, sizeof(float) * count, cudaMemcpyHostToDevice, c.s) != cudaSuccess)
+            return nullptr;
+        return stage;
+    };
+    const float* pts_d = in(points, kp, b.pin, 3 * (size_t)n);
+    const float* pose_d = in(pose12, kpose, b.pose, 12);
+    const float* lg_d = in(logits, kl, b.lg, k);
+    const float* mu_d = in(means, km, b.mu, 3 * (size_t)k);
+    const float* ch_d = in(chol, kc, b.ch, 9 * (size_t)k);
+    if (!pts_d || (pose12 && !pose_d) || !lg_d || !mu_d || !ch_d) {
+        cudaGetLastError();
+        return fail(GIRA_ERR_CUDA, "host-to-device copy of an input failed");
+    }
+    float* gp_d = grad_points ? (kgp == Kind::Host ? b.gp : grad_points) : nullptr;
+    float* gl_d = grad_logits ? (kgl == Kind::Host ? b.gl : grad_logits) : nullptr;
+    float* gm_d = grad_means ? (kgm == Kind::Host ? b.gm : grad_means) : nullptr;
+    float* gc_d = grad_chol ? (kgc == Kind::Host ? b.gc : grad_chol) : nullptr;
+    double* po_d = grad_pose ? (kgo == Kind::Host ? b.po64 : grad_pose) : nullptr;
+    double* tw_d = grad_twist ? (kgt == Kind::Host ? b.tw64 : grad_twist) : nullptr;
+
+    COUNTED(prof, 1, launch_pack_pose(pts_d, n, pose_d, b.p8, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+    COUNTED(prof, 1, launch_params_from_chol(lg_d, mu_d, ch_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    EStepLaunch a{b.p8, n, k, b.params, ppc, grad ? b.partials : nullptr, b.llp, nullptr, b.st, 0};
+    if (grad) {
+        a.grad_pts = gp_d;
+        a.rot = pose_d;
+        a.pose_partials = b.ppart;
+        COUNTED(prof, 1, launch_estep(a, true, grid, c.s, true));
+        COUNTED(prof, 1, launch_grad_finalize(b.partials, grid, b.llp, b.ppart, pose_d, ch_d, b.model64, k, n, gl_d,
+                                              gm_d, gc_d, po_d, tw_d, b.st, c.s));
+    } else {
+        COUNTED(prof, 1, launch_estep(a, false, grid, c.s, true));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    }
+    auto out = [&](void* dst, Kind kd, const void* stage, size_t bytes) -> gira_status {
+        if (dst && kd == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, c.s));
+        return GIRA_OK;
+    };
+    TRY(out(grad_points, kgp, b.gp, sizeof(float) * 3 * (size_t)n));
+    TRY(out(grad_logits, kgl, b.gl, sizeof(float) * k));
+    TRY(out(grad_means, kgm, b.gm, sizeof(float) * 3 * (size_t)k));
+    TRY(out(grad_chol, kgc, b.gc, sizeof(float) * 9 * (size_t)k));
+    TRY(out(grad_pose, kgo, b.po64, sizeof(double) * 12));
+    TRY(out(grad_twist, kgt, b.tw64, sizeof(double) * 6));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    TRY(device_status(h));
+    if (loglik) *loglik = h.ll_sum;
+    return GIRA_OK;
+}
+
 }  // extern "C"

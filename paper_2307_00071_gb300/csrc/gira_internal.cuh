@@ -216,13 +216,18 @@ struct EStepLaunch {
     float* per_point;        // [n] natural-log lse, or nullptr
     DeviceState* st;
     int iter;                // iteration index (1-based); kernels skip if iter > st->stop_after
+    // adjoint launches (log-likelihood gradient) only
+    float* grad_pts = nullptr;           // [n][3] dL/dx (dL/dx' rotated back by R^T), or nullptr
+    const float* rot = nullptr;          // R, row-major 3x3, of x' = R x + t; nullptr = identity
+    double* pose_partials = nullptr;     // [grid][12]: per CTA sum dL/dx' x'^T (row-major), sum dL/dx'
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count
 // actually used in *grid_out (needed for the partials buffer size).
-cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s);
+// grad: the differentiable path's kernels (d-form logits; with stats, the adjoint).
+cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad = false);
 // Occupancy-derived grid size for (k, stats) with n points.
-int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta);
+int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta, bool grad = false);
 // Pairs (padded) the parameter buffer must hold for k components.
 int params_pairs_padded(int k);
 
@@ -242,6 +247,24 @@ cudaError_t launch_params_from_model(const float* w, const float* mu, const floa
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
 cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
                              cudaStream_t s);
+
+// Differentiable log-likelihood.  pose12 = R (row-major) then t, or nullptr.
+// N x 3 -> pts8 of x' = R x + t (binary32, fixed order); flags non-finite input.
+cudaError_t launch_pack_pose(const float* pts3, int64_t n, const float* pose12, float4* pts8, DeviceState* st,
+                             cudaStream_t s);
+// E-step parameters from (logits, means, Cholesky factors): pi = softmax in
+// binary64, Sigma = L L^T, then the same binary64 build as the M-step.
+cudaError_t launch_params_from_chol(const float* logits, const float* mu, const float* chol, int k, double* model64,
+                                    float* params, float4* shift4, DeviceState* st, cudaStream_t s);
+// Reduces the statistics, the log-likelihood and the pose partials of a
+// gradient launch, then writes dL/dlogits (k), dL/dmeans (k x 3), dL/dchol
+// (k x 3 x 3, lower) in binary32, and in binary64 dL/dpose (dL/dR row-major,
+// dL/dt) and dL/dtwist (omega, v); loglik goes to st->ll_sum.  Outputs nullable.
+cudaError_t launch_grad_finalize(const float* partials, int grid, const double* ll_partials,
+                                 const double* pose_partials, const float* pose12, const float* chol,
+                                 const double* model64, int k, int64_t n, float* g_logits, float* g_means,
+                                 float* g_chol, double* g_pose, double* g_twist,
+                                 DeviceState* st, cudaStream_t s);
 
 // k-means
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,

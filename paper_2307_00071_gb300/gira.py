@@ -53,6 +53,8 @@ def _load():
     lib.gira_gmm_loglik.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
     lib.gira_gmm_loglik_noalloc.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
     lib.gira_gmm_loglik_noalloc.restype = C.c_int
+    lib.gira_gmm_loglik_grad.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gira_gmm_loglik_grad.restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
     lib.gira_release_workspace.argtypes = []
@@ -100,7 +102,7 @@ def _ptr(x):
 def _new(like, shape, dtype):
     if _is_torch(like):
         import torch
-        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
         return torch.empty(shape, dtype=tdt, device=like.device)
     return np.empty(shape, dtype=dtype)
 
@@ -234,3 +236,53 @@ def gira_gmm_loglik_noalloc(points, weights, means, covs, per_point: bool = Fals
 kmeans_init = gira_kmeans_init
 gmm_fit = gira_gmm_fit
 gmm_loglik = gira_gmm_loglik
+
+
+GRADS = ("points", "pose", "twist", "logits", "means", "chol")
+
+
+def _f32_like(x, like):
+    """x as a contiguous float32 array/tensor on the same side (host/device) as `like`."""
+    if x is None:
+        return None
+    if _is_torch(like):
+        import torch
+        return torch.as_tensor(x, dtype=torch.float32, device=like.device).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def gira_gmm_loglik_grad(points, logits, means, chol, pose=None, want=GRADS):
+    """L = sum_n ln sum_b softmax(logits)_b N(R x_n + t | mu_b, L_b L_b^T) and its gradient.
+
+    pose: 12 values, R (row-major) then t, or None (identity).  chol: K x 3 x 3,
+    lower triangle read.  want: any of GRADS.  Returns a dict with "loglik"
+    (float) and "grad_<name>" for every requested gradient: points (N,3) f32,
+    pose (12,) f64 = dL/dR row-major then dL/dt, twist (6,) f64 = (omega, v),
+    logits (K,) f32, means (K,3) f32, chol (K,3,3) f32.  Arrays follow the
+    points (torch on the same device, or numpy)."""
+    n = _check_points(points)
+    k = int(logits.shape[0])
+    bad = set(want) - set(GRADS)
+    if bad:
+        raise ValueError(f"unknown gradient names {sorted(bad)}")
+    lg, mu, ch = _f32_like(logits, points), _f32_like(means, points), _f32_like(chol, points)
+    po = _f32_like(pose, points)
+    if po is not None and po.reshape(-1).shape[0] != 12:
+        raise ValueError("pose must hold 12 values: R row-major, then t")
+    shapes = {"points": ((n, 3), np.float32), "pose": ((12,), np.float64), "twist": ((6,), np.float64),
+              "logits": ((k,), np.float32), "means": ((k, 3), np.float32), "chol": ((k, 3, 3), np.float32)}
+    outs = {g: _new(points, *shapes[g]) for g in want}
+    pp, kp, s = _ptr(points)
+    keep = [kp]
+    ptrs = []
+    for x in (po, lg, mu, ch):
+        p_, k_, _ = _ptr(x)
+        ptrs.append(p_)
+        keep.append(k_)
+    optr = [(_ptr(outs[g])[0] if g in outs else None) for g in GRADS]
+    ll = C.c_double(np.nan)
+    _check(_lib.gira_gmm_loglik_grad(pp, n, k, ptrs[0], ptrs[1], ptrs[2], ptrs[3], C.byref(ll), *optr, s))
+    r = {"loglik": ll.value}
+    for g in want:
+        r["grad_" + g] = outs[g]
+    return r

@@ -84,3 +84,16 @@ def test_binding_raises_typed_error():
     assert e.value.status == gira.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         gira.gira_gmm_fit(np.zeros((3, 2), np.float32), 1)
+
+
+def test_loglik_grad_invalid_arguments_rejected_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    pts = np.zeros((4, 3), np.float32)
+    lg, mu, ch = np.zeros(2, np.float32), np.zeros((2, 3), np.float32), np.tile(np.eye(3, dtype=np.float32), (2, 1, 1))
+    args = lambda n, k, lgp: (pts.ctypes.data, n, k, None, lgp, mu.ctypes.data, ch.ctypes.data, None, None, None,
+                             None, None, None, None, None)
+    assert L.gira_gmm_loglik_grad(*args(0, 2, lg.ctypes.data)) == gira.ERR_INVALID_ARG
+    assert L.gira_gmm_loglik_grad(*args(4, 0, lg.ctypes.data)) == gira.ERR_INVALID_ARG
+    assert L.gira_gmm_loglik_grad(*args(4, 2, None)) == gira.ERR_INVALID_ARG
+    assert b"NULL" in L.gira_last_error_message()

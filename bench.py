@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gira", "reference"], default="gira")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the measurements of the paths beyond the fit")
     return p.parse_args()
 
 
@@ -206,6 +207,52 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- extras
+GRAD_K, GRAD_SCAN = 1024, 100_000
+GRAD_FP32_OPS = 44   # per unit: d-form logit 12 + exp-sum 1 + statistics 17 + P'^T P' d and its sums 14
+
+
+def bench_grad(gira, frame_pts, sms, mhz, reps=20):
+    """Differentiable log-likelihood on the registration workload: a K=1024 GMM of
+    the frame and a 100k-point scan of it under a rigid offset; one call returns
+    L and every gradient (points, pose, twist, logits, means, Cholesky factors)."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = torch.as_tensor(frame_pts, device="cuda")
+    fit = gira.gira_gmm_fit(x, GRAD_K, iters=20, tol=1e-4, seed=0, lloyd_iters=10)
+    logits = torch.log(fit["weights"])
+    chol = torch.linalg.cholesky(fit["covs"].double()).float()
+    sub = frame_pts[rng.choice(len(frame_pts), GRAD_SCAN, replace=False)].astype(np.float64)
+    th = np.radians(10.0)
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    scan = torch.as_tensor(((sub - 0.1) @ R).astype(np.float32), device="cuda")
+    pose = torch.as_tensor(np.concatenate([R.reshape(9), [0.1, 0.1, 0.1]]).astype(np.float32), device="cuda")
+    args = (scan, logits, fit["means"], chol, pose)
+    for _ in range(3):
+        gira.gira_gmm_loglik_grad(*args)
+    gira.gira_profile_enable(True)
+    gira.gira_profile_read(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        gira.gira_gmm_loglik_grad(*args)
+    ev1.record()
+    torch.cuda.synchronize()
+    prof = gira.gira_profile_read(reset=True)
+    gira.gira_profile_enable(False)
+    call_s = ev0.elapsed_time(ev1) / 1e3 / reps
+    kern_s = prof["estep_ms"] / max(prof["estep_launches"], 1) / 1e3
+    units = GRAD_SCAN * GRAD_K
+    peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / GRAD_FP32_OPS
+    return {"workload": f"L and all gradients: {GRAD_SCAN}-point scan, K={GRAD_K} GMM of the frame, 10 deg + 0.17 m offset",
+            "unit": UNIT, "value": units / call_s, "ms_per_call": call_s * 1e3,
+            "kernel": "estep_kernel<2,8,128,2,true,true> (fused log-likelihood adjoint)",
+            "kernel_ms": kern_s * 1e3, "kernel_units_per_s": units / kern_s if kern_s else None,
+            "frac_fp32": (units / kern_s) / peak if kern_s else None,
+            "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {GRAD_FP32_OPS} FP32 ops per unit"}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -316,6 +363,8 @@ def run_gira(args):
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk,
         }
+        if not args.no_extras:
+            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

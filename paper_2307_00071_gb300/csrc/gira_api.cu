@@ -735,7 +735,10 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
         a.grad_pts = gp_d;
         a.rot = pose_d;
         a.pose_partials = b.ppart;
+        cudaEvent_t e0 = prof.mark();
         COUNTED(prof, 1, launch_estep(a, true, grid, c.s, true));
+        cudaEvent_t e1 = prof.mark();
+        if (prof.on) prof.estep.emplace_back(e0, e1);
         COUNTED(prof, 1, launch_grad_finalize(b.partials, grid, b.llp, b.ppart, pose_d, ch_d, b.model64, k, n, gl_d,
                                               gm_d, gc_d, po_d, tw_d, b.st, c.s));
     } else {
@@ -755,7 +758,7 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
     prof.t_end = prof.mark();
     GIRA_CUDA(cudaStreamSynchronize(c.s));
-    prof.commit(0, 0);
+    prof.commit(0, grad ? 1 : 0);
     TRY(device_status(h));
     if (loglik) *loglik = h.ll_sum;
     return GIRA_OK;

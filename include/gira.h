@@ -120,6 +120,40 @@ gira_status gira_gmm_fit(const float *points, int64_t n, int k, const gira_fit_o
                          double *final_loglik, void *stream);
 
 /*
+ * gira_gmm_fit_batched -- gira_gmm_fit for many independent point clouds of
+ * uneven sizes and component counts in one call (an engineering extension:
+ * the paper fits one cloud at a time).  Every instance follows exactly the
+ * single fit's definition (KInit of Fig. "information flow", the E-step of
+ * Eq. estep / logestep / simplifiedGaussian, the M-step and stopping rule of
+ * gira_gmm_fit), with its own convergence: an instance that has converged
+ * stops updating while the others go on.  The EM iterations of all instances
+ * run as one CUDA graph: per iteration one E-step launch per block shape (the
+ * instances with the same ceil(K / 128)) and one binary64 finalize launch.
+ * Points per CTA are chosen by timing candidates on the first call for a
+ * shape and size, and cached for the process.
+ *
+ *   points          [host|device] sum_i N_i x 3 binary32, instance i at rows
+ *                   offsets[i] .. offsets[i+1]-1
+ *   offsets         [host] batch + 1 int64, offsets[0] = 0, strictly increasing
+ *   ks              [host] batch ints, 1 <= ks[i] <= min(N_i, GIRA_MAX_K)
+ *   opts            as gira_gmm_fit (the same for every instance)
+ *   weights, means, covs  [host|device] sum_i K_i, x 3, x 3 x 3 binary32:
+ *                   instance i at components sum_{j<i} K_j ..; output (and
+ *                   input with GIRA_INIT_PARAMS)
+ *   loglik_traces   [host] batch x opts->iters binary64 (row i: instance i;
+ *                   NaN after it stopped), or NULL
+ *   iters_done      [host] batch ints, or NULL
+ *   final_loglik    [host] batch binary64 mean log-likelihoods, or NULL
+ *   statuses        [host] batch gira_status values of the instances, or NULL
+ * Returns GIRA_OK when every instance succeeded, else the status of the first
+ * failing instance (the others' results are still written).
+ */
+gira_status gira_gmm_fit_batched(const float *points, const int64_t *offsets, int batch, const int *ks,
+                                 const gira_fit_opts *opts, float *weights, float *means, float *covs,
+                                 double *loglik_traces, int *iters_done, double *final_loglik, int *statuses,
+                                 void *stream);
+
+/*
  * gira_gmm_loglik -- per-point log-likelihood under a GMM: the log-sum-exp of
  * Eq. logestep, ln sum_b pi_b N(x_n | mu_b, Sigma_b), with ln N from
  * Eq. simplifiedGaussian.

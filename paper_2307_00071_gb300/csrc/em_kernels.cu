@@ -125,7 +125,7 @@ constexpr int PPC_MAX = 2048;                         // points staged per CTA (
 // write dL/dx = R^T dL/dx' and accumulate the pose sums (dL/dx' x'^T, dL/dx').
 // The statistics S0, S1, S2 give the parameter gradients (finalize).
 template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, bool DFORM = GRAD>
-__global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) {
+__global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_in) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar_tma;
     __shared__ float red_sum[2][32][Q];
@@ -135,9 +135,26 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
     __shared__ int s_skip, s_norm, s_dead;
     constexpr int LPQ = 32 / Q;   // lanes per batch index after the transpose-reduce
 
+    // batched launches: this CTA's instance and CTA index within it
+    int cta = blockIdx.x;
+    EStepLaunch a = a_in;
+    if (a_in.units) {
+        const BatchUnit u = a_in.units[blockIdx.x];
+        const BatchInst I = a_in.insts[u.inst];
+        cta = u.cta;
+        a.pts8 = a_in.pts8 + 2 * I.pt_off;
+        a.n = I.n;
+        a.k = I.k;
+        a.params = a_in.params + I.par_off;
+        a.pts_per_cta = I.ppc;
+        a.partials = a_in.partials ? a_in.partials + I.part_off : nullptr;
+        a.ll_partials = a_in.ll_partials + I.ll_off;
+        a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
+        a.st = a_in.states + u.inst;
+    }
     const int G = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t begin = (int64_t)blockIdx.x * a.pts_per_cta;
+    const int64_t begin = (int64_t)cta * a.pts_per_cta;
     const int64_t end = min(a.n, begin + a.pts_per_cta);
     const int npts = (int)(end - begin);
     const int nb = (npts + Q - 1) / Q;
@@ -400,7 +417,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
     }
 
     if (STATS) {
-        float* dst = a.partials + (size_t)blockIdx.x * a.k * NSTAT;
+        float* dst = a.partials + (size_t)cta * a.k * NSTAT;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             const int b0 = 2 * ((j * G + warp) * 32 + lane);
@@ -416,14 +433,14 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a) 
         double v = ll_acc;
 #pragma unroll
         for (int o = LPQ; o < 32; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (lane == 0) a.ll_partials[blockIdx.x] = v * LN2;
+        if (lane == 0) a.ll_partials[cta] = v * LN2;
         if (GRAD) {
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
                 double u = owner ? (double)tw[i] : 0.0;
 #pragma unroll
                 for (int o = LPQ; o < 32; o <<= 1) u += __shfl_xor_sync(FULL, u, o);
-                if (lane == 0) a.pose_partials[(size_t)blockIdx.x * 12 + i] = u;
+                if (lane == 0) a.pose_partials[(size_t)cta * 12 + i] = u;
             }
         }
     }
@@ -505,6 +522,41 @@ int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta, 
     return (int)grid;
 }
 
+void estep_shape(int k, int* np, int* g, int* threads) {
+    const Shape sh = shape_for(k);
+    *np = sh.np;
+    *g = sh.g;
+    *threads = sh.threads;
+}
+
+int estep_batch_q() { return QB; }
+
+int estep_ppc_max() { return PPC_MAX; }
+
+int estep_occupancy(int k, bool stats, int64_t ppc) {
+    const Shape sh = shape_for(k);
+    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estep_smem(PPC_MAX));
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, estep_smem(ppc)) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return occ;
+}
+
+cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int k_class, int64_t ppc_class,
+                               cudaStream_t s) {
+    const Shape sh = shape_for(k_class);
+    void* args[] = {(void*)&a};
+    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const size_t smem = estep_smem(ppc_class);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
+}
+
 cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad) {
     const Shape sh = shape_for(a.k);
     void* args[] = {(void*)&a};
@@ -530,6 +582,18 @@ __global__ void pack_kernel(const float* __restrict__ p3, int64_t n, float4* __r
     }
 }
 
+// One block per instance: the padding component slots k .. 2 * npairs - 1 of its block.
+__global__ void fill_padding_batched_kernel(float* params, const BatchInst* __restrict__ insts,
+                                            const int* __restrict__ npairs_of) {
+    const BatchInst I = insts[blockIdx.x];
+    const int slots = 2 * npairs_of[blockIdx.x];
+    for (int b = I.k + threadIdx.x; b < slots; b += blockDim.x) {
+        float* base = params + I.par_off + (size_t)(b >> 1) * PAIR_FLOATS + (b & 1);
+        for (int s = 0; s < PAIR_FLOATS / 2; ++s) base[2 * s] = 0.f;
+        base[2 * SLOT_C] = -INFINITY;
+    }
+}
+
 __global__ void fill_padding_kernel(float* params, int k, int npairs_pad) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;   // component slot
     if (b >= 2 * npairs_pad || b < k) return;
@@ -538,6 +602,34 @@ __global__ void fill_padding_kernel(float* params, int k, int npairs_pad) {
     base[2 * SLOT_C] = -INFINITY;
 }
 }  // namespace
+
+// Every point of a batch; the instance of point i (for the error flag) by binary
+// search over the offsets (batch + 1 entries).
+__global__ void pack_batched_kernel(const float* __restrict__ p3, int64_t n, const int64_t* __restrict__ offsets,
+                                    int batch, float4* __restrict__ p4, float4* __restrict__ p8, DeviceState* states) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = p3[3 * i], y = p3[3 * i + 1], z = p3[3 * i + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+        int lo = 0, hi = batch;   // offsets[lo] <= i < offsets[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offsets[mid] <= i) lo = mid; else hi = mid;
+        }
+        set_error(states + lo, GIRA_ERR_NONFINITE_INPUT);
+    }
+    if (p4) p4[i] = make_float4(x, y, z, 0.f);
+    if (p8) {
+        p8[2 * i] = make_float4(x, x, y, y);
+        p8[2 * i + 1] = make_float4(z, z, 0.f, 0.f);
+    }
+}
+
+cudaError_t launch_pack_batched(const float* pts3, int64_t n, const int64_t* offsets, int batch, float4* pts4,
+                                float4* pts8, DeviceState* states, cudaStream_t s) {
+    pack_batched_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts3, n, offsets, batch, pts4, pts8, states);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, float4* pts8, DeviceState* st, cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
@@ -553,6 +645,16 @@ cudaError_t launch_fill_padding(float* params, int k, int npairs_pad, cudaStream
 
 // ------------------------------------------------------------------ log-likelihood reduce
 namespace {
+__global__ void ll_reduce_batched_kernel(const double* __restrict__ llp, const BatchInst* __restrict__ insts,
+                                         DeviceState* states) {
+    const BatchInst I = insts[blockIdx.x];
+    double v = 0.0;
+    for (int c = threadIdx.x; c < I.ctas; c += 32) v += llp[I.ll_off + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) states[blockIdx.x].ll_sum = v;
+}
+
 __global__ void ll_reduce_kernel(const double* __restrict__ llp, int grid, DeviceState* st) {
     if (st->error) return;
     double v = 0.0;
@@ -661,30 +763,45 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
 //   sum r (x-mu)(x-mu)^T = S2 - delta S1^T - S1 delta^T + S0 delta delta^T,
 //   Sigma = that / N_b + reg I.  The weight N_b is normalised by sum_a N_a
 //   where it is used (E-step reference, model output).
-__global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(
-    const float* __restrict__ partials, int grid, const double* __restrict__ llp, const double* __restrict__ stats64,
-    float4* shift4, int k, int64_t n, double reg, double tol, double* model64, float* params, double* trace,
-    DeviceState* st, int iter, int em) {
+struct FinArgs {
+    const float* partials;     // [grid][k][NSTAT], or nullptr (then stats64)
+    int grid;
+    const double* llp;
+    const double* stats64;
+    float4* shift4;
+    int k;
+    int64_t n;
+    double reg, tol;
+    double* model64;
+    float* params;
+    double* trace;
+    DeviceState* st;
+    int iter, em;
+};
+
+// Components blk * FIN_CPB .. of one fit; block index blk == 0 also does the
+// log-likelihood, trace and convergence of an EM iteration.
+__device__ void reduce_finalize_body(const FinArgs& f, int blk) {
     __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
     __shared__ double S[FIN_CPB * NSTAT];
     __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = (em && iter > st->stop_after) || st->error != 0;
+    if (threadIdx.x == 0) s_skip = (f.em && f.iter > f.st->stop_after) || f.st->error != 0;
     __syncthreads();
     if (s_skip) return;
     const int t = threadIdx.x;
-    const int b0 = blockIdx.x * FIN_CPB;
-    const int nb = min(FIN_CPB, k - b0);
+    const int b0 = blk * FIN_CPB;
+    const int nb = min(FIN_CPB, f.k - b0);
     const int nout = nb * NSTAT;
-    if (partials) {
-        reduce_partials(partials, grid, k, b0, nout, part, S);
+    if (f.partials) {
+        reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
     } else if (t < nout) {
-        S[t] = stats64[(size_t)b0 * NSTAT + t];
+        S[t] = f.stats64[(size_t)b0 * NSTAT + t];
     }
     __syncthreads();
     if (t < nb) {
         const int b = b0 + t;
         const double* Sb = S + t * NSTAT;
-        const float4 sh = shift4[b];
+        const float4 sh = f.shift4[b];
         const double s[3] = {sh.x, sh.y, sh.z};
         const double s0 = Sb[0];
         const double nbw = s0 + 10.0 * DBL_EPSILON;
@@ -700,26 +817,54 @@ __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(
         for (int u = 0; u < 6; ++u) {
             const int i = ij[u][0], j = ij[u][1];
             const double v = Sb[4 + u] - dl[i] * Sb[1 + j] - Sb[1 + i] * dl[j] + s0 * dl[i] * dl[j];
-            c[u] = v * inv + ((i == j) ? reg : 0.0);
+            c[u] = v * inv + ((i == j) ? f.reg : 0.0);
         }
-        build_component(b, nbw, mu, c, params, shift4, model64, st);
-        if (b == 0) st->w_raw = 1;
+        build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st);
+        if (b == 0) f.st->w_raw = 1;
     }
-    if (em && blockIdx.x == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
+    if (f.em && blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
         const int lane = t - 32;
         double v = 0.0;
-        for (int c = lane; c < grid; c += 32) v += llp[c];
+        for (int c = lane; c < f.grid; c += 32) v += f.llp[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
         if (lane == 0) {
+            DeviceState* st = f.st;
             st->ll_sum = v;
-            const double ll = v / (double)n;
-            trace[iter - 1] = ll;
-            if (iter > 1 && fabs(ll - st->prev_ll) < tol) st->stop_after = iter;
+            const double ll = v / (double)f.n;
+            f.trace[f.iter - 1] = ll;
+            if (f.iter > 1 && fabs(ll - st->prev_ll) < f.tol) st->stop_after = f.iter;
             st->prev_ll = ll;
-            st->iters_done = iter;
+            st->iters_done = f.iter;
         }
     }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(const FinArgs f) {
+    reduce_finalize_body(f, blockIdx.x);
+}
+
+// Every instance of a batch: block (instance i, index j) finalizes components
+// j * FIN_CPB .. of instance i from its own partials, into its own state.
+__global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_batched_kernel(const FinArgs base,
+                                                                              const BatchInst* __restrict__ insts,
+                                                                              const int2* __restrict__ blocks,
+                                                                              DeviceState* states, int iters) {
+    const int2 bi = blocks[blockIdx.x];
+    const BatchInst I = insts[bi.x];
+    FinArgs f = base;
+    f.partials = base.partials ? base.partials + I.part_off : nullptr;
+    f.grid = I.ctas;
+    f.llp = base.llp ? base.llp + I.ll_off : nullptr;
+    f.stats64 = base.stats64 ? base.stats64 + (size_t)I.comp_off * NSTAT : nullptr;
+    f.shift4 = base.shift4 + I.comp_off;
+    f.k = I.k;
+    f.n = I.n;
+    f.model64 = base.model64 + (size_t)I.comp_off * MODEL;
+    f.params = base.params + I.par_off;
+    f.trace = base.trace + (size_t)bi.x * iters;
+    f.st = states + bi.x;
+    reduce_finalize_body(f, bi.y);
 }
 
 __global__ void params_from_model_kernel(const float* __restrict__ w, const float* __restrict__ mu,
@@ -736,6 +881,53 @@ __global__ void params_from_model_kernel(const float* __restrict__ w, const floa
     if (!fin) { set_error(st, GIRA_ERR_NONFINITE_INPUT); return; }
     if (!(pi > 0.0)) { set_error(st, GIRA_ERR_INVALID_ARG); return; }
     build_component(b, pi, m, c, params, shift4, model64, st);
+}
+
+// ------------------------------------------------------------------ batched helpers
+__global__ void params_from_model_batched_kernel(const float* __restrict__ w, const float* __restrict__ mu,
+                                                 const float* __restrict__ cov, int total_k,
+                                                 const int* __restrict__ comp_inst,
+                                                 const BatchInst* __restrict__ insts, double* model64, float* params,
+                                                 float4* shift4, DeviceState* states) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;   // global component
+    if (g >= total_k) return;
+    const int i = comp_inst[g];
+    const BatchInst I = insts[i];
+    const int b = g - I.comp_off;
+    DeviceState* st = states + i;
+    const double pi = w[g];
+    const double m[3] = {mu[3 * (size_t)g], mu[3 * (size_t)g + 1], mu[3 * (size_t)g + 2]};
+    const float* S = cov + 9 * (size_t)g;
+    const double c[6] = {S[0], S[3], S[6], S[4], S[7], S[8]};
+    bool fin = isfinite(pi) && isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]);
+    for (int q = 0; q < 9; ++q) fin = fin && isfinite(S[q]);
+    if (!fin) { set_error(st, GIRA_ERR_NONFINITE_INPUT); return; }
+    if (!(pi > 0.0)) { set_error(st, GIRA_ERR_INVALID_ARG); return; }
+    build_component(b, pi, m, c, params + I.par_off, shift4 + I.comp_off, model64 + (size_t)I.comp_off * MODEL, st);
+}
+
+__global__ void model_out_batched_kernel(const double* __restrict__ model64, const BatchInst* __restrict__ insts,
+                                         float* w, float* mu, float* cov, const DeviceState* states) {
+    __shared__ double s_part[2];
+    const BatchInst I = insts[blockIdx.x];
+    const DeviceState* st = states + blockIdx.x;
+    const double* M = model64 + (size_t)I.comp_off * MODEL;
+    double part = 0.0;
+    for (int a = threadIdx.x; a < I.k; a += blockDim.x) part += M[(size_t)a * MODEL];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    const double nsum = s_part[0] + s_part[1];
+    if (st->error) return;
+    for (int b = threadIdx.x; b < I.k; b += blockDim.x) {
+        const double* m = M + (size_t)b * MODEL;
+        const size_t g = (size_t)I.comp_off + b;
+        w[g] = (float)(st->w_raw ? m[0] / nsum : m[0]);
+        for (int q = 0; q < 3; ++q) mu[3 * g + q] = (float)m[1 + q];
+        const int idx[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+        for (int q = 0; q < 9; ++q) cov[9 * g + q] = (float)m[4 + idx[q]];
+    }
 }
 
 __global__ void model_out_kernel(const double* __restrict__ model64, int k, float* w, float* mu, float* cov,
@@ -936,8 +1128,47 @@ cudaError_t launch_reduce_finalize(const float* partials, int grid, const double
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
                                    cudaStream_t s) {
-    reduce_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(
-        partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter, em ? 1 : 0);
+    const FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
+                    em ? 1 : 0};
+    reduce_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+int fin_components_per_block() { return FIN_CPB; }
+
+cudaError_t launch_reduce_finalize_batched(const float* partials, const double* ll_partials, const double* stats64,
+                                           float4* shift4, const BatchInst* insts, const int2* blocks, int nblocks,
+                                           double reg, double tol, int iters, double* model64, float* params,
+                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s) {
+    const FinArgs f{partials, 0, ll_partials, stats64, shift4, 0, 0, reg, tol, model64, params, trace, nullptr,
+                    iter, em ? 1 : 0};
+    reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, states, std::max(iters, 1));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_padding_batched(float* params, const BatchInst* insts, int batch, int npairs_max,
+                                        const int* npairs_of, cudaStream_t s) {
+    fill_padding_batched_kernel<<<batch, 128, 0, s>>>(params, insts, npairs_of);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params_from_model_batched(const float* w, const float* mu, const float* cov, int total_k,
+                                             const int* comp_inst, const BatchInst* insts, double* model64,
+                                             float* params, float4* shift4, DeviceState* states, cudaStream_t s) {
+    params_from_model_batched_kernel<<<(total_k + 63) / 64, 64, 0, s>>>(w, mu, cov, total_k, comp_inst, insts, model64,
+                                                                       params, shift4, states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_model_out_batched(const double* model64, const BatchInst* insts, int batch, float* w, float* mu,
+                                     float* cov, const DeviceState* states, cudaStream_t s) {
+    model_out_batched_kernel<<<batch, 64, 0, s>>>(model64, insts, w, mu, cov, states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ll_reduce_batched(const double* ll_partials, const BatchInst* insts, int batch,
+                                     DeviceState* states, cudaStream_t s) {
+    ll_reduce_batched_kernel<<<batch, 32, 0, s>>>(ll_partials, insts, states);
     return cudaGetLastError();
 }
 

@@ -16,8 +16,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gira_internal.cuh"
@@ -53,7 +55,17 @@ struct DeviceWs {
     std::mutex mu;
     void* ptr = nullptr;
     size_t bytes = 0;
+    // the last batched-EM graph (valid for this workspace allocation only)
+    std::string graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
 };
+
+void drop_graph(DeviceWs* ws) {
+    if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
+    ws->graph_exec = nullptr;
+    ws->graph_key.clear();
+}
 std::mutex g_table_mu;
 std::vector<DeviceWs*> g_ws;
 
@@ -80,6 +92,7 @@ struct Carver {
 gira_status ensure(DeviceWs* ws, size_t need, cudaStream_t s) {
     if (ws->bytes >= need) return GIRA_OK;
     GIRA_CUDA(cudaStreamSynchronize(s));
+    drop_graph(ws);
     if (ws->ptr) GIRA_CUDA(cudaFree(ws->ptr));
     ws->ptr = nullptr;
     ws->bytes = 0;
@@ -161,6 +174,17 @@ gira_status check_nk(int64_t n, int k) {
     return GIRA_OK;
 }
 
+gira_status check_opts(const gira_fit_opts& o) {
+    if (o.iters < 0) return fail(GIRA_ERR_INVALID_ARG, "iters < 0");
+    if (!(o.tol >= 0.0)) return fail(GIRA_ERR_INVALID_ARG, "tol must be >= 0");
+    if (!(o.reg_covar >= 0.0) || !std::isfinite(o.reg_covar))
+        return fail(GIRA_ERR_INVALID_ARG, "reg_covar must be finite and >= 0");
+    if (o.lloyd_iters < 0) return fail(GIRA_ERR_INVALID_ARG, "lloyd_iters < 0");
+    if (o.init_mode != GIRA_INIT_KMEANS && o.init_mode != GIRA_INIT_PARAMS)
+        return fail(GIRA_ERR_INVALID_ARG, "unknown init_mode %d", o.init_mode);
+    return GIRA_OK;
+}
+
 #define TRY(x)                          \
     do {                                \
         gira_status st_ = (x);          \
@@ -230,6 +254,55 @@ void gira::record_error(const char* msg, int component) {
     t_bad = component;
 }
 
+
+// ---------------------------------------------------------------- batched EM helpers
+namespace {
+
+// Instances with the same E-step block shape run in one launch per iteration.
+struct BatchClass {
+    int np = 0, g = 0, threads = 0, kmax = 0;
+    std::vector<int> insts;
+    int64_t points = 0;
+    int64_t ppc = 0;
+    int unit_begin = 0, nunits = 0;
+};
+
+// Points per CTA chosen by measurement, per (device, shape, log2 of the class's points).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int64_t> g_tuned;
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << (r + 1)) <= v) ++r;
+    return r;
+}
+
+// Per-instance offsets and the unit list for the classes' current ppc values.
+// Returns the units, the partial floats and the log-likelihood slots used.
+void build_tables(std::vector<BatchInst>& hi, std::vector<BatchClass>& cls, std::vector<BatchUnit>& units,
+                  int64_t* part_floats, int64_t* ll_slots) {
+    int64_t part = 0, ll = 0;
+    units.clear();
+    for (auto& c : cls) {
+        c.unit_begin = (int)units.size();
+        for (int i : c.insts) {
+            BatchInst& I = hi[i];
+            I.ppc = c.ppc;
+            I.ctas = (int)((I.n + c.ppc - 1) / c.ppc);
+            I.part_off = part;
+            I.ll_off = ll;
+            part += (int64_t)I.ctas * I.k * NSTAT;
+            ll += I.ctas;
+            for (int t = 0; t < I.ctas; ++t) units.push_back(BatchUnit{i, t});
+        }
+        c.nunits = (int)units.size() - c.unit_begin;
+    }
+    *part_floats = part;
+    *ll_slots = ll;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gira_fit_opts_default(gira_fit_opts* o) {
@@ -263,6 +336,7 @@ gira_status gira_release_workspace(void) {
     for (size_t d = 0; d < g_ws.size(); ++d) {
         if (!g_ws[d]) continue;
         std::lock_guard<std::mutex> l2(g_ws[d]->mu);
+        drop_graph(g_ws[d]);
         if (g_ws[d]->ptr) {
             cudaSetDevice((int)d);
             cudaError_t e = cudaFree(g_ws[d]->ptr);
@@ -381,12 +455,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     if (!opts) return fail(GIRA_ERR_INVALID_ARG, "opts is NULL");
     TRY(check_nk(n, k));
     const gira_fit_opts o = *opts;
-    if (o.iters < 0) return fail(GIRA_ERR_INVALID_ARG, "iters < 0");
-    if (!(o.tol >= 0.0)) return fail(GIRA_ERR_INVALID_ARG, "tol must be >= 0");
-    if (!(o.reg_covar >= 0.0) || !std::isfinite(o.reg_covar)) return fail(GIRA_ERR_INVALID_ARG, "reg_covar must be finite and >= 0");
-    if (o.lloyd_iters < 0) return fail(GIRA_ERR_INVALID_ARG, "lloyd_iters < 0");
-    if (o.init_mode != GIRA_INIT_KMEANS && o.init_mode != GIRA_INIT_PARAMS)
-        return fail(GIRA_ERR_INVALID_ARG, "unknown init_mode %d", o.init_mode);
+    TRY(check_opts(o));
     if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
     Ctx c;
     TRY(begin(c, stream));
@@ -761,6 +830,374 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
     prof.commit(0, grad ? 1 : 0);
     TRY(device_status(h));
     if (loglik) *loglik = h.ll_sum;
+    return GIRA_OK;
+}
+
+// ================================================================ gmm_fit_batched
+gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, int batch, const int* ks,
+                                 const gira_fit_opts* opts, float* weights, float* means, float* covs,
+                                 double* loglik_traces, int* iters_done, double* final_loglik, int* statuses,
+                                 void* stream) {
+    reset_error();
+    if (!opts || !offsets || !ks) return fail(GIRA_ERR_INVALID_ARG, "opts, offsets and ks must not be NULL");
+    if (batch < 1) return fail(GIRA_ERR_INVALID_ARG, "batch = %d < 1", batch);
+    const gira_fit_opts o = *opts;
+    TRY(check_opts(o));
+    if (offsets[0] != 0) return fail(GIRA_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int i = 0; i < batch; ++i) {
+        const int64_t n = offsets[i + 1] - offsets[i];
+        if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "instance %d has %lld points", i, (long long)n);
+        if (ks[i] < 1 || ks[i] > GIRA_MAX_K || ks[i] > n)
+            return fail(GIRA_ERR_INVALID_ARG, "instance %d: k = %d outside [1, min(n, %d)]", i, ks[i], GIRA_MAX_K);
+    }
+    if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    const int64_t total_n = offsets[batch];
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kw, km, kc;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    const bool model_host = kw == Kind::Host || km == Kind::Host || kc == Kind::Host;
+    const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
+    const int Q = estep_batch_q();
+    const int iters = std::max(o.iters, 1);
+
+    // ---- host tables: instances, shape classes, finalize blocks
+    std::vector<BatchInst> hi(batch);
+    std::vector<int> npairs_of(batch);
+    int total_k = 0;
+    int64_t par_floats = 0;
+    std::map<std::pair<int, int>, int> class_of_shape;
+    std::vector<BatchClass> cls;
+    for (int i = 0; i < batch; ++i) {
+        BatchInst& I = hi[i];
+        I.pt_off = offsets[i];
+        I.n = offsets[i + 1] - offsets[i];
+        I.k = ks[i];
+        I.comp_off = total_k;
+        total_k += ks[i];
+        npairs_of[i] = params_pairs_padded(ks[i]);
+        I.par_off = par_floats;
+        par_floats += (int64_t)npairs_of[i] * PAIR_FLOATS;
+        int np, g, th;
+        estep_shape(ks[i], &np, &g, &th);
+        auto key = std::make_pair(np, g);
+        auto it = class_of_shape.find(key);
+        if (it == class_of_shape.end()) {
+            it = class_of_shape.emplace(key, (int)cls.size()).first;
+            cls.emplace_back();
+            cls.back().np = np;
+            cls.back().g = g;
+            cls.back().threads = th;
+        }
+        BatchClass& C = cls[it->second];
+        C.insts.push_back(i);
+        C.points += I.n;
+        C.kmax = std::max(C.kmax, ks[i]);
+    }
+    std::vector<int> comp_inst(total_k);
+    std::vector<int2> fin_blocks;
+    const int cpb = fin_components_per_block();
+    for (int i = 0; i < batch; ++i) {
+        for (int b = 0; b < ks[i]; ++b) comp_inst[hi[i].comp_off + b] = i;
+        for (int j = 0; j * cpb < ks[i]; ++j) fin_blocks.push_back(make_int2(i, j));
+    }
+    // points per CTA: measured per shape and size (first call), else at least two waves of CTAs
+    const int64_t cand[4] = {256, 512, 1024, 2048};
+    std::vector<bool> tune(cls.size(), false);
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+        BatchClass& C = cls[ci];
+        const int occ = estep_occupancy(C.kmax, true, 1024);
+        int64_t ppc = (C.points + 2LL * c.sms * occ - 1) / (2LL * c.sms * occ);
+        ppc = std::min<int64_t>(estep_ppc_max(), std::max<int64_t>(cand[0], (ppc + Q - 1) / Q * Q));
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(std::make_tuple(c.dev, C.np, C.g, ilog2(C.points)));
+        if (it != g_tuned.end()) {
+            ppc = it->second;
+        } else if (o.iters > 0) {   // (without iterations the E-step launches would exit at once)
+            tune[ci] = true;
+            ppc = cand[0];   // size the buffers for the smallest candidate
+        }
+        C.ppc = ppc;
+    }
+    std::vector<BatchUnit> units;
+    int64_t part_floats = 0, ll_slots = 0;
+    build_tables(hi, cls, units, &part_floats, &ll_slots);   // the largest sizes any candidate needs
+    const size_t max_units = units.size();
+
+    // per-instance KInit scratch
+    std::vector<int64_t> nblk_off(batch + 1, 0);
+    for (int i = 0; i < batch; ++i) nblk_off[i + 1] = nblk_off[i] + (kinit ? kpp_num_blocks(hi[i].n) : 0);
+
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *params, *partials, *mw, *mmu, *mcov, *d2;
+        float4 *p4, *p8, *shift4, *c4;
+        double *model64, *stats64, *llp, *trace, *sums;
+        BatchInst* insts;
+        BatchUnit* units;
+        int2* blocks;
+        int *comp_inst, *npairs;
+        int64_t *offs, *ch;
+        int32_t* lab;
+        u128* bs;
+        unsigned long long* chg;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(batch);
+        b.pin = cv.take<float>(kp == Kind::Host ? 3 * (size_t)total_n : 0);
+        b.p4 = cv.take<float4>(kinit ? (size_t)total_n : 0);
+        b.p8 = cv.take<float4>(2 * (size_t)total_n);
+        b.params = cv.take<float>((size_t)par_floats);
+        b.shift4 = cv.take<float4>(total_k);
+        b.model64 = cv.take<double>((size_t)total_k * MODEL);
+        b.stats64 = cv.take<double>((size_t)total_k * NSTAT);
+        b.partials = cv.take<float>((size_t)part_floats);
+        b.llp = cv.take<double>((size_t)ll_slots);
+        b.trace = cv.take<double>((size_t)batch * iters);
+        b.mw = cv.take<float>(model_host ? total_k : 0);
+        b.mmu = cv.take<float>(model_host ? 3 * (size_t)total_k : 0);
+        b.mcov = cv.take<float>(model_host ? 9 * (size_t)total_k : 0);
+        b.insts = cv.take<BatchInst>(batch);
+        b.units = cv.take<BatchUnit>(max_units);
+        b.blocks = cv.take<int2>(fin_blocks.size());
+        b.comp_inst = cv.take<int>(total_k);
+        b.npairs = cv.take<int>(batch);
+        b.offs = cv.take<int64_t>(batch + 1);
+        if (kinit) {
+            b.c4 = cv.take<float4>(total_k);
+            b.ch = cv.take<int64_t>(total_k);
+            b.lab = cv.take<int32_t>(total_n);
+            b.sums = cv.take<double>(4 * (size_t)total_k);
+            b.chg = cv.take<unsigned long long>((size_t)batch * (o.lloyd_iters + 1));
+            b.bs = cv.take<u128>((size_t)nblk_off[batch]);
+            b.d2 = cv.take<float>((size_t)total_n);
+        }
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    std::vector<DeviceState> hs(batch);
+    for (auto& h : hs) {
+        h = DeviceState{};
+        h.stop_after = o.iters;
+        h.bad_component = INT_MAX;
+    }
+    GIRA_CUDA(cudaMemcpyAsync(b.st, hs.data(), sizeof(DeviceState) * batch, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemsetAsync(b.trace, 0xff, sizeof(double) * batch * iters, c.s));   // NaN
+    GIRA_CUDA(cudaMemcpyAsync(b.offs, offsets, sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.blocks, fin_blocks.data(), sizeof(int2) * fin_blocks.size(), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.comp_inst, comp_inst.data(), sizeof(int) * total_k, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.npairs, npairs_of.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 3 * total_n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    COUNTED(prof, 1, launch_pack_batched(pts, total_n, b.offs, batch, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding_batched(b.params, b.insts, batch, 0, b.npairs, c.s));
+    float* w_d = (kw == Kind::Device) ? weights : b.mw;
+    float* mu_d = (km == Kind::Device) ? means : b.mmu;
+    float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
+    if (kinit) {
+        // KInit per instance (its own seeding launch, Lloyd, one-hot statistics)
+        GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 4 * total_k, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * batch * (o.lloyd_iters + 1), c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * total_k, c.s));
+        for (int i = 0; i < batch; ++i) {
+            const BatchInst& I = hi[i];
+            float4* p4 = b.p4 + I.pt_off;
+            float4* c4 = b.c4 + I.comp_off;
+            int64_t* ch = b.ch + I.comp_off;
+            DeviceState* st = b.st + i;
+            const int kcs = kpp_cluster_size(I.n);
+            if (kcs > 0) {
+                COUNTED(prof, 1, launch_kpp_cluster(p4, I.n, I.k, o.seed, c4, ch, kcs, st, c.s));
+            } else {
+                COUNTED(prof, 2 * I.k - 1,
+                        launch_kpp(p4, I.n, I.k, o.seed, c4, b.d2 + I.pt_off, b.bs + nblk_off[i], ch, st, c.s));
+            }
+            COUNTED(prof, 1 + 2 * o.lloyd_iters,
+                    launch_lloyd(p4, I.n, I.k, o.lloyd_iters, c4, b.lab + I.pt_off, b.sums + 4 * (size_t)I.comp_off,
+                                 b.chg + (size_t)i * (o.lloyd_iters + 1), st, c.s));
+            COUNTED(prof, 1, launch_label_stats(p4, I.n, I.k, b.lab + I.pt_off, c4,
+                                                b.stats64 + (size_t)I.comp_off * NSTAT, st, c.s));
+        }
+        GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * total_k, cudaMemcpyDeviceToDevice, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize_batched(nullptr, nullptr, b.stats64, b.shift4, b.insts, b.blocks,
+                                                        (int)fin_blocks.size(), o.reg_covar, o.tol, o.iters, b.model64,
+                                                        b.params, b.trace, b.st, 0, false, c.s));
+    } else {
+        if (kw == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * total_k, cudaMemcpyHostToDevice, c.s));
+        if (km == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 3 * total_k, cudaMemcpyHostToDevice, c.s));
+        if (kc == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 9 * total_k, cudaMemcpyHostToDevice, c.s));
+        COUNTED(prof, 1, launch_params_from_model_batched(w_d, mu_d, cov_d, total_k, b.comp_inst, b.insts, b.model64,
+                                                          b.params, b.shift4, b.st, c.s));
+    }
+    prof.t_init = prof.mark();
+
+    EStepLaunch base{b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
+    base.insts = b.insts;
+    base.units = b.units;
+    base.states = b.st;
+    auto estep_all = [&](bool stats, int iter, cudaStream_t s) -> cudaError_t {
+        EStepLaunch a = base;
+        a.iter = iter;
+        if (!stats) a.partials = nullptr;
+        for (const BatchClass& C : cls) {
+            if (!C.nunits) continue;
+            a.units = b.units + C.unit_begin;
+            cudaError_t e = launch_estep_units(a, stats, C.nunits, C.kmax, C.ppc, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+
+    // ---- autotune: time one E-step of each untuned class for every candidate
+    bool any_tune = false;
+    for (bool t : tune) any_tune = any_tune || t;
+    if (any_tune) {
+        cudaEvent_t e0, e1;
+        GIRA_CUDA(cudaEventCreate(&e0));
+        GIRA_CUDA(cudaEventCreate(&e1));
+        for (size_t ci = 0; ci < cls.size(); ++ci) {
+            if (!tune[ci]) continue;
+            double best = 1e30;
+            int64_t best_ppc = cand[0];
+            for (int64_t pc : cand) {
+                if (pc > estep_ppc_max()) continue;
+                cls[ci].ppc = pc;
+                build_tables(hi, cls, units, &part_floats, &ll_slots);
+                GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
+                GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(BatchUnit) * units.size(),
+                                          cudaMemcpyHostToDevice, c.s));
+                EStepLaunch a = base;
+                a.iter = 1;
+                a.units = b.units + cls[ci].unit_begin;
+                GIRA_CUDA(launch_estep_units(a, true, cls[ci].nunits, cls[ci].kmax, pc, c.s));   // warm
+                GIRA_CUDA(cudaEventRecord(e0, c.s));
+                for (int r = 0; r < 2; ++r) GIRA_CUDA(launch_estep_units(a, true, cls[ci].nunits, cls[ci].kmax, pc, c.s));
+                GIRA_CUDA(cudaEventRecord(e1, c.s));
+                GIRA_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                GIRA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_ppc = pc;
+                }
+            }
+            cls[ci].ppc = best_ppc;
+            std::lock_guard<std::mutex> lk2(g_tune_mu);
+            g_tuned[std::make_tuple(c.dev, cls[ci].np, cls[ci].g, ilog2(cls[ci].points))] = best_ppc;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    build_tables(hi, cls, units, &part_floats, &ll_slots);
+    GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, c.s));
+
+    // ---- the EM loop: one captured graph (E-step launch per shape class + one finalize per iteration)
+    std::string key = std::to_string((uintptr_t)ws->ptr) + "|" + std::to_string(sizer.off) + "|" +
+                      std::to_string(batch) + "|" + std::to_string(o.iters) + "|" + std::to_string(o.reg_covar) +
+                      "|" + std::to_string(o.tol) + "|" + std::to_string(o.lloyd_iters) + "|" +
+                      std::to_string((int)kinit) + std::to_string((int)(kp == Kind::Host)) +
+                      std::to_string((int)model_host);
+    for (int i = 0; i < batch; ++i) key += "|" + std::to_string(hi[i].n) + ":" + std::to_string(hi[i].k);
+    for (const auto& C : cls) key += "|p" + std::to_string(C.ppc);
+    if (o.iters > 0) {
+        if (ws->graph_key != key || !ws->graph_exec) {
+            drop_graph(ws);
+            if (!ws->capture_stream) GIRA_CUDA(cudaStreamCreateWithFlags(&ws->capture_stream, cudaStreamNonBlocking));
+            cudaStream_t cs = ws->capture_stream;
+            GIRA_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+            cudaError_t e = cudaSuccess;
+            for (int t = 1; t <= o.iters && e == cudaSuccess; ++t) {
+                e = estep_all(true, t, cs);
+                if (e == cudaSuccess)
+                    e = launch_reduce_finalize_batched(b.partials, b.llp, nullptr, b.shift4, b.insts, b.blocks,
+                                                       (int)fin_blocks.size(), o.reg_covar, o.tol, o.iters,
+                                                       b.model64, b.params, b.trace, b.st, t, true, cs);
+            }
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return fail(GIRA_ERR_CUDA, "capturing the batched EM graph failed: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(GIRA_ERR_CUDA, "instantiating the batched EM graph failed: %s", cudaGetErrorString(e));
+            }
+            ws->graph_exec = exec;
+            ws->graph_key = key;
+        }
+        prof.launches += (long long)o.iters * ((long long)cls.size() + 1);
+        GIRA_CUDA(cudaGraphLaunch(ws->graph_exec, c.s));
+    }
+    prof.t_em = prof.mark();
+    if (final_loglik) {
+        GIRA_CUDA(estep_all(false, 0, c.s));
+        prof.launches += (long long)cls.size();
+        COUNTED(prof, 1, launch_ll_reduce_batched(b.llp, b.insts, batch, b.st, c.s));
+    }
+    COUNTED(prof, 1, launch_model_out_batched(b.model64, b.insts, batch, w_d, mu_d, cov_d, b.st, c.s));
+    if (kw == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * total_k, cudaMemcpyDeviceToHost, c.s));
+    if (km == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(means, b.mmu, sizeof(float) * 3 * total_k, cudaMemcpyDeviceToHost, c.s));
+    if (kc == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(covs, b.mcov, sizeof(float) * 9 * total_k, cudaMemcpyDeviceToHost, c.s));
+    if (loglik_traces && o.iters > 0)
+        GIRA_CUDA(cudaMemcpyAsync(loglik_traces, b.trace, sizeof(double) * batch * o.iters, cudaMemcpyDeviceToHost,
+                                  c.s));
+    GIRA_CUDA(cudaMemcpyAsync(hs.data(), b.st, sizeof(DeviceState) * batch, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    long long em_iters = 0;
+    for (const auto& h : hs) em_iters += h.iters_done;
+    prof.commit((int)std::min<long long>(em_iters, INT_MAX), 0);
+    gira_status first = GIRA_OK;
+    int first_i = -1;
+    for (int i = 0; i < batch; ++i) {
+        gira_status si = GIRA_OK;
+        if (hs[i].error) {
+            si = device_status(hs[i]);
+            if (first == GIRA_OK) {
+                first = si;
+                first_i = i;
+            }
+        }
+        if (statuses) statuses[i] = (int)si;
+        if (iters_done) iters_done[i] = hs[i].iters_done;
+        if (final_loglik) final_loglik[i] = hs[i].ll_sum / (double)hi[i].n;
+    }
+    if (first != GIRA_OK) {
+        if (hs[first_i].error == GIRA_ERR_NOT_PD) t_bad = hs[first_i].bad_component;
+        const std::string m = t_msg;
+        return fail(first, "instance %d: %s", first_i, m.c_str());
+    }
     return GIRA_OK;
 }
 

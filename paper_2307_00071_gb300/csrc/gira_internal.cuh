@@ -205,6 +205,25 @@ __host__ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t j) 
 
 // ---------------------------------------------------------------- kernel entry points
 // (defined in em_kernels.cu / kmeans_kernels.cu, launched from gira_api.cu)
+
+// Batched fits: one entry per instance (device table).
+struct BatchInst {
+    int64_t pt_off;     // first point of the instance in the packed point arrays
+    int64_t n;          // its points
+    int64_t ppc;        // points per E-step CTA
+    int64_t par_off;    // float offset of its E-step parameters (its class's padded pair count)
+    int64_t part_off;   // float offset of its per-CTA statistic partials ([ctas][k][NSTAT])
+    int64_t ll_off;     // double offset of its per-CTA log-likelihood partials
+    int k;              // components
+    int comp_off;       // first component in the per-component arrays
+    int ctas;           // E-step CTAs of the instance
+    int pad_;
+};
+// One E-step CTA of a batched launch: instance and CTA index within it.
+struct BatchUnit {
+    int inst, cta;
+};
+
 struct EStepLaunch {
     const float4* pts8;      // 2 float4 per point: (x,x,y,y) (z,z,0,0)
     int64_t n;
@@ -220,6 +239,11 @@ struct EStepLaunch {
     float* grad_pts = nullptr;           // [n][3] dL/dx (dL/dx' rotated back by R^T), or nullptr
     const float* rot = nullptr;          // R, row-major 3x3, of x' = R x + t; nullptr = identity
     double* pose_partials = nullptr;     // [grid][12]: per CTA sum dL/dx' x'^T (row-major), sum dL/dx'
+    // batched launches: CTA b runs units[b]; pts8 / params / partials / ll_partials /
+    // per_point are then bases offset by the instance's table entry, st = states + inst
+    const BatchInst* insts = nullptr;
+    const BatchUnit* units = nullptr;
+    DeviceState* states = nullptr;
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count
@@ -247,6 +271,39 @@ cudaError_t launch_params_from_model(const float* w, const float* mu, const floa
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
 cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
                              cudaStream_t s);
+
+// Batched EM (per-instance tables on the device).
+// E-step block shape for k components (pairs per lane, warps, threads); the
+// batch size Q of the kernels; the largest points-per-CTA; CTAs per SM.
+void estep_shape(int k, int* np, int* g, int* threads);
+int estep_batch_q();
+int estep_ppc_max();
+int estep_occupancy(int k, bool stats, int64_t ppc);
+// One launch over nunits CTAs (a.units / a.insts / a.states set) of the class
+// whose shape is that of k_class; every instance of the class has ppc_class.
+cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int k_class, int64_t ppc_class,
+                               cudaStream_t s);
+cudaError_t launch_pack_batched(const float* pts3, int64_t n, const int64_t* offsets, int batch, float4* pts4,
+                                float4* pts8, DeviceState* states, cudaStream_t s);
+// Finalize blocks: (instance, block index within the instance), FIN_CPB components each.
+int fin_components_per_block();
+cudaError_t launch_reduce_finalize_batched(const float* partials, const double* ll_partials, const double* stats64,
+                                           float4* shift4, const BatchInst* insts, const int2* blocks, int nblocks,
+                                           double reg, double tol, int iters, double* model64, float* params,
+                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s);
+// Padding slots of every instance's parameter block (one block per instance).
+cudaError_t launch_fill_padding_batched(float* params, const BatchInst* insts, int batch, int npairs_max,
+                                        const int* npairs_of, cudaStream_t s);
+// E-step parameters of every instance from (w, mu, Sigma) (comp_inst: instance of each component).
+cudaError_t launch_params_from_model_batched(const float* w, const float* mu, const float* cov, int total_k,
+                                             const int* comp_inst, const BatchInst* insts, double* model64,
+                                             float* params, float4* shift4, DeviceState* states, cudaStream_t s);
+// Normalised model of every instance (one block per instance).
+cudaError_t launch_model_out_batched(const double* model64, const BatchInst* insts, int batch, float* w, float* mu,
+                                     float* cov, const DeviceState* states, cudaStream_t s);
+// Per-instance sums of the log-likelihood partials into states[i].ll_sum.
+cudaError_t launch_ll_reduce_batched(const double* ll_partials, const BatchInst* insts, int batch,
+                                     DeviceState* states, cudaStream_t s);
 
 // Differentiable log-likelihood.  pose12 = R (row-major) then t, or nullptr.
 // N x 3 -> pts8 of x' = R x + t (binary32, fixed order); flags non-finite input.

@@ -54,6 +54,8 @@ def _load():
     lib.gira_gmm_loglik_noalloc.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
     lib.gira_gmm_loglik_noalloc.restype = C.c_int
     lib.gira_gmm_loglik_grad.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gira_gmm_fit_batched.argtypes = [vp, vp, C.c_int, vp, C.POINTER(FitOpts), vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gira_gmm_fit_batched.restype = C.c_int
     lib.gira_gmm_loglik_grad.restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
@@ -286,3 +288,48 @@ def gira_gmm_loglik_grad(points, logits, means, chol, pose=None, want=GRADS):
     for g in want:
         r["grad_" + g] = outs[g]
     return r
+
+
+def gira_gmm_fit_batched(points, offsets, ks, iters: int = 100, tol: float = 1e-3, reg_covar: float = 1e-6,
+                         seed: int = 0, lloyd_iters: int = 10, init=None, final_loglik: bool = True,
+                         raise_on_error: bool = True):
+    """Fit one GMM per instance: instance i = points[offsets[i]:offsets[i+1]] with ks[i] components.
+
+    init: None (k-means++ / Lloyd per instance) or (weights, means, covs) stacked over
+    instances (sum K, (sum K,3), (sum K,3,3)).  Returns a dict: weights, means, covs
+    (stacked, like the points: torch on their device, or numpy), and per instance
+    iters_done, final_loglik, trace (batch x iters, NaN after stopping), status."""
+    total = _check_points(points)
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    B = len(kk)
+    if offs.shape != (B + 1,) or offs[-1] != total:
+        raise ValueError("offsets must hold batch + 1 entries ending at the number of points")
+    K = int(kk.sum())
+    o = default_opts()
+    o.iters, o.tol, o.reg_covar, o.seed, o.lloyd_iters = iters, tol, reg_covar, seed, lloyd_iters
+    if init is None:
+        w, m, c = _new(points, (K,), np.float32), _new(points, (K, 3), np.float32), _new(points, (K, 3, 3), np.float32)
+        o.init_mode = INIT_KMEANS
+    else:
+        w, m, c = (_f32_like(a, points) for a in init)
+        if _is_torch(points):
+            w, m, c = w.clone(), m.clone(), c.clone()
+        else:
+            w, m, c = w.copy(), m.copy(), c.copy()
+        o.init_mode = INIT_PARAMS
+    trace = np.full((B, max(iters, 1)), np.nan)
+    done = np.zeros(B, np.int32)
+    fll = np.full(B, np.nan)
+    stat = np.zeros(B, np.int32)
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(w)
+    mp, km, _ = _ptr(m)
+    cp, kc, _ = _ptr(c)
+    st = _lib.gira_gmm_fit_batched(pp, offs.ctypes.data, B, kk.ctypes.data, C.byref(o), wp, mp, cp,
+                                   trace.ctypes.data if iters > 0 else None, done.ctypes.data,
+                                   fll.ctypes.data if final_loglik else None, stat.ctypes.data, s)
+    if raise_on_error:
+        _check(st)
+    return dict(weights=w, means=m, covs=c, iters_done=done, final_loglik=fll, trace=trace[:, :iters],
+                status=stat)

@@ -97,3 +97,24 @@ def test_loglik_grad_invalid_arguments_rejected_without_gpu():
     assert L.gira_gmm_loglik_grad(*args(4, 0, lg.ctypes.data)) == gira.ERR_INVALID_ARG
     assert L.gira_gmm_loglik_grad(*args(4, 2, None)) == gira.ERR_INVALID_ARG
     assert b"NULL" in L.gira_last_error_message()
+
+
+def test_batched_invalid_arguments_rejected_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    pts = np.zeros((10, 3), np.float32)
+    w, m, c = np.ones(4, np.float32), np.zeros((4, 3), np.float32), np.tile(np.eye(3, dtype=np.float32), (4, 1, 1))
+    o = gira.default_opts()
+
+    def call(offs, ks, batch):
+        offs = np.asarray(offs, np.int64)
+        ks = np.asarray(ks, np.int32)
+        return L.gira_gmm_fit_batched(pts.ctypes.data, offs.ctypes.data, batch, ks.ctypes.data, C.byref(o),
+                                      w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None, None, None, None)
+
+    assert call([0, 5, 10], [2, 2], 0) == gira.ERR_INVALID_ARG        # empty batch
+    assert call([1, 5, 10], [2, 2], 2) == gira.ERR_INVALID_ARG        # offsets[0] != 0
+    assert call([0, 5, 5], [2, 2], 2) == gira.ERR_INVALID_ARG         # an empty instance
+    assert call([0, 5, 10], [2, 6], 2) == gira.ERR_INVALID_ARG        # k > n
+    assert call([0, 5, 10], [0, 2], 2) == gira.ERR_INVALID_ARG        # k < 1
+    assert b"instance" in L.gira_last_error_message()

@@ -253,6 +253,60 @@ def bench_grad(gira, frame_pts, sms, mhz, reps=20):
             "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {GRAD_FP32_OPS} FP32 ops per unit"}
 
 
+BATCH_B, BATCH_ITERS, BATCH_KS = 256, 25, (16, 32, 64, 128, 256, 512)
+
+
+def batch_workload(seed=7):
+    """256 clouds, N log-uniform in [2k, 200k], each drawn from a random K=8 GMM as in
+    the small configuration; K per instance drawn from {16, ..., 512}."""
+    from paper_2307_00071_gb300 import synth
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(2_000), np.log(200_000), size=BATCH_B)).astype(np.int64)
+    ks = rng.choice(BATCH_KS, size=BATCH_B).astype(np.int32)
+    clouds = [synth.gmm_cloud(int(n), 8, seed=1000 + i).points for i, n in enumerate(sizes)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return np.concatenate(clouds), offsets, ks
+
+
+def bench_batched(gira):
+    """Batched EM (one CUDA graph per call) against a loop of single fits, same
+    initial parameters, 25 EM iterations per instance, tol 0."""
+    import torch
+    pts, offs, ks = batch_workload()
+    x = torch.as_tensor(pts, device="cuda")
+    init = gira.gira_gmm_fit_batched(x, offs, ks, iters=0, tol=0.0, seed=0, lloyd_iters=10, final_loglik=False)
+    w0, m0, c0 = init["weights"], init["means"], init["covs"]
+    cks = np.concatenate([[0], np.cumsum(ks)])
+    units = float(np.sum((offs[1:] - offs[:-1]) * ks)) * BATCH_ITERS
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def batched():
+        return gira.gira_gmm_fit_batched(x, offs, ks, iters=BATCH_ITERS, tol=0.0, init=(w0, m0, c0),
+                                         final_loglik=False)
+
+    def loop():
+        for i in range(len(ks)):
+            sl, cl = slice(int(offs[i]), int(offs[i + 1])), slice(int(cks[i]), int(cks[i + 1]))
+            gira.gira_gmm_fit(x[sl], int(ks[i]), iters=BATCH_ITERS, tol=0.0,
+                              init=(w0[cl].clone(), m0[cl].clone(), c0[cl].clone()), final_loglik=False)
+
+    out = {}
+    for name, fn, reps in (("batched", batched, 3), ("loop", loop, 1)):
+        fn()   # warm (first batched call also tunes points per CTA)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        out[name] = ev0.elapsed_time(ev1) / reps
+    return {"workload": f"{BATCH_B} clouds, N log-uniform [2k, 200k] (sum {int(offs[-1])}), K in {list(BATCH_KS)}, "
+                        f"{BATCH_ITERS} EM iterations from the same k-means init, tol 0",
+            "unit": UNIT, "value": units / (out["batched"] / 1e3), "ms_batched": out["batched"],
+            "ms_per_instance_loop": out["loop"], "loop_units_per_s": units / (out["loop"] / 1e3),
+            "speedup_vs_loop": out["loop"] / out["batched"]}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -364,7 +418,7 @@ def run_gira(args):
             "clocks": clk,
         }
         if not args.no_extras:
-            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz)}
+            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

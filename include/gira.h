@@ -53,7 +53,9 @@ typedef enum {
 } gira_status;
 
 /* Largest number of mixture components one call accepts. */
-#define GIRA_MAX_K 1024
+#define GIRA_MAX_K 8192        /* gira_gmm_fit, gira_gmm_loglik, gira_kmeans_init */
+#define GIRA_MAX_K_BATCHED 1024 /* per instance of gira_gmm_fit_batched; gira_gmm_loglik_grad;
+                                   gira_gmm_loglik_noalloc */
 
 typedef enum {
     GIRA_INIT_KMEANS = 0,  /* k-means++ (seed) + Lloyd (lloyd_iters) + one-hot M-step */
@@ -135,7 +137,7 @@ gira_status gira_gmm_fit(const float *points, int64_t n, int k, const gira_fit_o
  *   points          [host|device] sum_i N_i x 3 binary32, instance i at rows
  *                   offsets[i] .. offsets[i+1]-1
  *   offsets         [host] batch + 1 int64, offsets[0] = 0, strictly increasing
- *   ks              [host] batch ints, 1 <= ks[i] <= min(N_i, GIRA_MAX_K)
+ *   ks              [host] batch ints, 1 <= ks[i] <= min(N_i, GIRA_MAX_K_BATCHED)
  *   opts            as gira_gmm_fit (the same for every instance)
  *   weights, means, covs  [host|device] sum_i K_i, x 3, x 3 x 3 binary32:
  *                   instance i at components sum_{j<i} K_j ..; output (and
@@ -245,7 +247,7 @@ gira_status gira_profile_read(gira_profile *out, int reset);
  *   points, weights, means, covs   device memory of the current device only
  *                                  (same layouts as gira_gmm_loglik)
  *   n                              1 <= n <= GIRA_NOALLOC_MAX_N, else GIRA_ERR_INVALID_ARG
- *   k                              1 <= k <= min(n, GIRA_MAX_K)
+ *   k                              1 <= k <= min(n, GIRA_MAX_K_BATCHED)
  *   mean_loglik                    [host] or NULL
  *   per_point                      [device] N binary32, or NULL
  *

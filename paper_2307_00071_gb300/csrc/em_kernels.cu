@@ -124,7 +124,12 @@ constexpr int PPC_MAX = 2048;                         // points staged per CTA (
 // second barrier per batch) into dL/dx' = -(2 ln 2) * that sum; the owner lanes
 // write dL/dx = R^T dL/dx' and accumulate the pose sums (dL/dx' x'^T, dL/dx').
 // The statistics S0, S1, S2 give the parameter gradients (finalize).
-template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, bool DFORM = GRAD>
+//
+// CH (K in chunks, each CTA one chunk of one tile; reference cmax over all K):
+// CH = 1 (pass A): pass 1 and the per-point sums of the chunk into psum, no
+// log-sum-exp; CH = 2 (pass B): e = 2^(shift_n - q') with (shift_n, 1 / total_n)
+// from pref, pass 2 only -- no cross-lane reduction and no barrier per batch.
+template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, bool DFORM = GRAD, int CH = 0>
 __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_in) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar_tma;
@@ -151,6 +156,10 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         a.ll_partials = a_in.ll_partials + I.ll_off;
         a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
         a.st = a_in.states + u.inst;
+        if (CH != 0) {   // chunks share the points and the state
+            a.st = a_in.states;
+            if (CH == 1) a.psum = a_in.psum + (size_t)u.inst * I.n;
+        }
     }
     const int G = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -216,9 +225,13 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         cmax = fmaxf(cmax, s_cmax[w]);
         wsum += s_wsum[w];
     }
+    float ref0 = s_norm ? cmax - __log2f(wsum) : cmax;
+    if (CH != 0) {   // one reference for every chunk
+        cmax = a.gref[0];
+        ref0 = a.gref[1];
+    }
 #pragma unroll
     for (int j = 0; j < NP; ++j) prm[j].c = f2(cmax - prm[j].c.x, cmax - prm[j].c.y);
-    const float ref0 = s_norm ? cmax - __log2f(wsum) : cmax;
 
     float Sx[NP][NSTAT], Sy[NP][NSTAT];   // statistics of components 2p and 2p+1
     if (STATS) {
@@ -237,10 +250,16 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         X1 = f2(xy.z, xy.w);
         X2 = f2(zz.x, zz.y);
     };
+    // pass B: (shift, 1 / total) of the batch's points
+    float2 pr[Q];
     // pass 1 of batch t: e for every (point, own component) into E, warp-level sums into red_sum[t & 1]
     auto pass1 = [&](int t, float2 (&E)[NP][Q]) {
         const int lb = t * Q, nvalid = min(Q, npts - lb);
         float part[Q];
+        if (CH == 2) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) pr[q] = (q < nvalid) ? a.pref[begin + lb + q] : f2(0.f, 0.f);
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             float2 X0, X1, X2;
@@ -249,14 +268,17 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 const float2 nq = DFORM ? neg_logit2_d(prm[j], X0, X1, X2) : neg_logit2(prm[j], X0, X1, X2);
-                const float2 e = f2(ex2_approx(-nq.x), ex2_approx(-nq.y));
+                const float sh = (CH == 2) ? pr[q].x : 0.f;
+                const float2 e = f2(ex2_approx(sh - nq.x), ex2_approx(sh - nq.y));
                 E[j][q] = e;
                 acc = add2(acc, e);
             }
             part[q] = acc.x + acc.y;
         }
-        const float wt = warp_transpose_reduce<Q>(part, lane, AddOp());
-        if ((lane & (LPQ - 1)) == 0) red_sum[t & 1][warp][myq] = wt;
+        if (CH != 2) {
+            const float wt = warp_transpose_reduce<Q>(part, lane, AddOp());
+            if ((lane & (LPQ - 1)) == 0) red_sum[t & 1][warp][myq] = wt;
+        }
     };
     // statistics of batch t from E and the reciprocal sums r (owned by lane q * LPQ)
     auto pass2 = [&](int t, const float2 (&E)[NP][Q], float r) {
@@ -266,7 +288,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         for (int q = 0; q < Q; ++q) {
             float2 X0, X1, X2;
             load_pt((q < nvalid) ? lb + q : lb, X0, X1, X2);
-            const float R = __shfl_sync(FULL, r, q * LPQ);
+            const float R = (CH == 2) ? pr[q].y : __shfl_sync(FULL, r, q * LPQ);
             if (GRAD) gq[q][0] = gq[q][1] = gq[q][2] = 0.f;
             // scalar FP32: measured faster than the packed form for this
             // accumulate-heavy pattern
@@ -376,7 +398,20 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
     float tw[12] = {};   // GRAD owner lanes: sum g x'^T (row-major), sum g
     for (int t = 0; t < nb; ++t) {
         pass1(t, E);
+        if (CH == 2) {
+            pass2(t, E, 0.f);
+            continue;
+        }
         __syncthreads();   // every warp's sums of batch t are in red_sum[t & 1]
+        if (CH == 1) {
+            const int lb = t * Q;
+            if (owner && myq < min(Q, npts - lb)) {
+                float tot = red_sum[t & 1][0][myq];
+                for (int w = 1; w < G; ++w) tot += red_sum[t & 1][w][myq];
+                a.psum[begin + lb + myq] = tot;
+            }
+            continue;
+        }
         const float r = finish(t, E);
         if (STATS) pass2(t, E, r);
         if (GRAD) {
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
                 for (int s = 0; s < NSTAT; ++s) dst[(size_t)(b0 + 1) * NSTAT + s] = Sy[j][s];
         }
     }
-    if (warp == 0) {   // owner lanes hold the per-point log-likelihood sums; fixed order
+    if (warp == 0 && CH == 0) {   // owner lanes hold the per-point log-likelihood sums; fixed order
         double v = ll_acc;
 #pragma unroll
         for (int o = LPQ; o < 32; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -557,6 +592,22 @@ cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int
     return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
 }
 
+constexpr int KCHUNK = 512;   // components per chunk: the 4-warp shape
+
+int chunk_components() { return KCHUNK; }
+
+int64_t chunk_param_floats() { return (int64_t)params_pairs_padded(KCHUNK) * PAIR_FLOATS; }
+
+cudaError_t launch_estep_chunks(const EStepLaunch& a, int pass, int nunits, int64_t ppc, cudaStream_t s) {
+    void* args[] = {(void*)&a};
+    const void* fn = (pass == 1) ? (const void*)estep_kernel<2, QB, 128, 3, false, false, false, 1>
+                                 : (const void*)estep_kernel<2, QB, 128, 3, true, false, false, 2>;
+    const size_t smem = estep_smem(ppc);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(nunits), dim3(128), args, smem, s);
+}
+
 cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad) {
     const Shape sh = shape_for(a.k);
     void* args[] = {(void*)&a};
@@ -645,6 +696,132 @@ cudaError_t launch_fill_padding(float* params, int k, int npairs_pad, cudaStream
 
 // ------------------------------------------------------------------ log-likelihood reduce
 namespace {
+// ------------------------------------------------------------------ large K (chunks)
+constexpr int CHUNK_K = 512;
+constexpr int COMBINE_BLOCKS = 608;
+constexpr int COMBINE_THREADS = 256;
+
+// component b of a chunked parameter buffer
+__device__ __forceinline__ const float* chunk_slot(const float* params, int b) {
+    const int c = b / CHUNK_K, l = b - c * CHUNK_K;
+    return params + (size_t)c * (CHUNK_K / 2) * PAIR_FLOATS + (size_t)(l >> 1) * PAIR_FLOATS + (l & 1);
+}
+
+// gref[0] = max_b c_b, gref[1] = the log-likelihood reference (cmax - log2 sum_a N_a
+// after an M-step, else cmax): the per-CTA kernel's prologue over all k components.
+__global__ void chunk_ref_kernel(const float* __restrict__ params, int k, const DeviceState* st, float* gref) {
+    __shared__ float s_m[8];
+    __shared__ double s_w[8];
+    float m = -INFINITY;
+    double w = 0.0;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+        const float* p = chunk_slot(params, b);
+        m = fmaxf(m, p[2 * SLOT_C]);
+        w += (double)p[2 * SLOT_W];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_m[threadIdx.x >> 5] = m;
+        s_w[threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = s_m[0];
+        double ww = s_w[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mm = fmaxf(mm, s_m[i]);
+            ww += s_w[i];
+        }
+        gref[0] = mm;
+        gref[1] = st->w_raw ? (float)((double)mm - log2(ww)) : mm;
+    }
+}
+
+// Per point: total over chunks (fixed order); (0, 1/total) and the natural-log
+// log-likelihood, or, if the total is below 2^-100, listed for the exact step.
+__global__ void __launch_bounds__(COMBINE_THREADS) chunk_combine_kernel(const float* __restrict__ psum, int chunks,
+                                                                        int64_t n, const float* __restrict__ gref,
+                                                                        float2* pref, double* llpt, int* flag_count,
+                                                                        int* flags) {
+    const float ref0 = gref[1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float tot = 0.f;
+        for (int c = 0; c < chunks; ++c) tot += psum[(size_t)c * n + i];
+        if (tot >= 0x1p-100f) {
+            pref[i] = make_float2(0.f, __frcp_rn(tot));
+            llpt[i] = (double)(lg2_approx(tot) + ref0) * 0.693147180559945309417232121458;
+        } else {
+            pref[i] = make_float2(0.f, 0.f);
+            llpt[i] = 0.0;
+            flags[atomicAdd(flag_count, 1)] = (int)i;
+        }
+    }
+}
+
+// One warp per listed point: exact maximum of the logits over all k components,
+// then (shift, 1/sum) relative to it (Eq. logestep's max-subtraction).
+__global__ void chunk_exact_kernel(const float4* __restrict__ pts8, const float* __restrict__ params, int k,
+                                   const float* __restrict__ gref, const int* __restrict__ flags,
+                                   const int* __restrict__ flag_count, float2* pref, double* llpt, DeviceState* st) {
+    const int count = *flag_count;
+    const float cmax = gref[0], ref0 = gref[1];
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int f = wg; f < count; f += nw) {
+        const int64_t i = flags[f];
+        const float4 xy = pts8[2 * i], zz = pts8[2 * i + 1];
+        const float x0 = xy.x, x1 = xy.z, x2 = zz.x;
+        auto nlog = [&](int b) {   // q' = |P'x + b'|^2 + (cmax - c_b), as the E-step forms it
+            const float* p = chunk_slot(params, b);
+            const float y0 = fmaf(p[2 * (SLOT_P + 0)], x0, p[2 * (SLOT_B + 0)]);
+            const float y1 = fmaf(p[2 * (SLOT_P + 1)], x0, fmaf(p[2 * (SLOT_P + 2)], x1, p[2 * (SLOT_B + 1)]));
+            const float y2 = fmaf(p[2 * (SLOT_P + 3)], x0,
+                                  fmaf(p[2 * (SLOT_P + 4)], x1, fmaf(p[2 * (SLOT_P + 5)], x2, p[2 * (SLOT_B + 2)])));
+            return fmaf(y2, y2, fmaf(y1, y1, fmaf(y0, y0, cmax - p[2 * SLOT_C])));
+        };
+        float mx = -INFINITY;
+        for (int b = lane; b < k; b += 32) mx = fmaxf(mx, -nlog(b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float sum = 0.f;
+        if (mx > -INFINITY)
+            for (int b = lane; b < k; b += 32) sum += ex2_approx(-nlog(b) - mx);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            if (!(mx > -INFINITY) || !(sum > 0.f)) {
+                set_error(st, GIRA_ERR_NUMERIC);
+                pref[i] = make_float2(0.f, 0.f);
+            } else {
+                pref[i] = make_float2(-mx, __frcp_rn(sum));
+                llpt[i] = (double)(lg2_approx(sum) + mx + ref0) * 0.693147180559945309417232121458;
+            }
+        }
+    }
+}
+
+// Fixed-order per-block sums of the per-point log-likelihoods.
+__global__ void __launch_bounds__(COMBINE_THREADS) points_ll_reduce_kernel(const double* __restrict__ llpt, int64_t n,
+                                                                           double* llp) {
+    __shared__ double s_w[COMBINE_THREADS / 32];
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += llpt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < COMBINE_THREADS / 32; ++w) t += s_w[w];
+        llp[blockIdx.x] = t;
+    }
+}
+
 __global__ void ll_reduce_batched_kernel(const double* __restrict__ llp, const BatchInst* __restrict__ insts,
                                          DeviceState* states) {
     const BatchInst I = insts[blockIdx.x];
@@ -777,6 +954,8 @@ struct FinArgs {
     double* trace;
     DeviceState* st;
     int iter, em;
+    int ll_count;   // log-likelihood partials to sum (grid when 0)
+    int do_ll;      // this launch's block 0 does the log-likelihood / convergence step
 };
 
 // Components blk * FIN_CPB .. of one fit; block index blk == 0 also does the
@@ -822,10 +1001,11 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
         build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st);
         if (b == 0) f.st->w_raw = 1;
     }
-    if (f.em && blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
+    if (f.em && f.do_ll && blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
         const int lane = t - 32;
         double v = 0.0;
-        for (int c = lane; c < f.grid; c += 32) v += f.llp[c];
+        const int nll = f.ll_count ? f.ll_count : f.grid;
+        for (int c = lane; c < nll; c += 32) v += f.llp[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
         if (lane == 0) {
@@ -846,15 +1026,30 @@ __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(const FinA
 
 // Every instance of a batch: block (instance i, index j) finalizes components
 // j * FIN_CPB .. of instance i from its own partials, into its own state.
+// shared: the entries are chunks of one fit (state, trace and log-likelihood
+// partials shared; the log-likelihood step runs in the block of (0, 0)).
 __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_batched_kernel(const FinArgs base,
                                                                               const BatchInst* __restrict__ insts,
                                                                               const int2* __restrict__ blocks,
-                                                                              DeviceState* states, int iters) {
+                                                                              DeviceState* states, int iters,
+                                                                              int shared) {
     const int2 bi = blocks[blockIdx.x];
     const BatchInst I = insts[bi.x];
     FinArgs f = base;
     f.partials = base.partials ? base.partials + I.part_off : nullptr;
     f.grid = I.ctas;
+    if (shared) {
+        f.stats64 = base.stats64 ? base.stats64 + (size_t)I.comp_off * NSTAT : nullptr;
+        f.shift4 = base.shift4 + I.comp_off;
+        f.k = I.k;
+        f.n = I.n;
+        f.model64 = base.model64 + (size_t)I.comp_off * MODEL;
+        f.params = base.params + I.par_off;
+        f.st = states;
+        f.do_ll = (bi.x == 0);
+        reduce_finalize_body(f, bi.y);
+        return;
+    }
     f.llp = base.llp ? base.llp + I.ll_off : nullptr;
     f.stats64 = base.stats64 ? base.stats64 + (size_t)I.comp_off * NSTAT : nullptr;
     f.shift4 = base.shift4 + I.comp_off;
@@ -1129,7 +1324,7 @@ cudaError_t launch_reduce_finalize(const float* partials, int grid, const double
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
                                    cudaStream_t s) {
     const FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
-                    em ? 1 : 0};
+                    em ? 1 : 0, 0, 1};
     reduce_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(f);
     return cudaGetLastError();
 }
@@ -1141,8 +1336,19 @@ cudaError_t launch_reduce_finalize_batched(const float* partials, const double* 
                                            double reg, double tol, int iters, double* model64, float* params,
                                            double* trace, DeviceState* states, int iter, bool em, cudaStream_t s) {
     const FinArgs f{partials, 0, ll_partials, stats64, shift4, 0, 0, reg, tol, model64, params, trace, nullptr,
-                    iter, em ? 1 : 0};
-    reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, states, std::max(iters, 1));
+                    iter, em ? 1 : 0, 0, 1};
+    reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, states, std::max(iters, 1), 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_finalize_chunks(const float* partials, const double* ll_partials, int ll_count,
+                                          const double* stats64, float4* shift4, const BatchInst* insts,
+                                          const int2* blocks, int nblocks, int64_t n, double reg, double tol,
+                                          double* model64, float* params, double* trace, DeviceState* st, int iter,
+                                          bool em, cudaStream_t s) {
+    const FinArgs f{partials, 0, ll_partials, stats64, shift4, 0, n, reg, tol, model64, params, trace, nullptr,
+                    iter, em ? 1 : 0, ll_count, 1};
+    reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, st, 1, 1);
     return cudaGetLastError();
 }
 
@@ -1206,6 +1412,49 @@ cudaError_t launch_grad_finalize(const float* partials, int grid, const double* 
     grad_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(
         partials, grid, ll_partials, pose_partials, pose12, chol, model64, k, n, g_logits, g_means, g_chol, g_pose,
         g_twist, st);
+    return cudaGetLastError();
+}
+}  // namespace gira
+
+namespace gira {
+int chunk_combine_grid() { return COMBINE_BLOCKS; }
+
+cudaError_t launch_chunk_ref(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s) {
+    chunk_ref_kernel<<<1, 256, 0, s>>>(params, k, st, gref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_combine(const float* psum, int chunks, int64_t n, const float* gref, float2* pref,
+                                 double* llpt, int* flag_count, int* flags, DeviceState* st, cudaStream_t s) {
+    (void)st;
+    chunk_combine_kernel<<<COMBINE_BLOCKS, COMBINE_THREADS, 0, s>>>(psum, chunks, n, gref, pref, llpt, flag_count,
+                                                                    flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_exact(const float4* pts8, const float* params, int k, const float* gref, const int* flags,
+                               const int* flag_count, float2* pref, double* llpt, DeviceState* st, cudaStream_t s) {
+    chunk_exact_kernel<<<152, 256, 0, s>>>(pts8, params, k, gref, flags, flag_count, pref, llpt, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points_ll_reduce(const double* llpt, int64_t n, double* llp, DeviceState* st, cudaStream_t s) {
+    points_ll_reduce_kernel<<<COMBINE_BLOCKS, COMBINE_THREADS, 0, s>>>(llpt, n, llp);
+    if (!st) return cudaGetLastError();
+    return launch_ll_reduce(llp, COMBINE_BLOCKS, st, s);
+}
+}  // namespace gira
+
+namespace gira {
+namespace {
+__global__ void double_to_float_kernel(const double* __restrict__ x, int64_t n, float* y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+}  // namespace
+
+cudaError_t launch_double_to_float(const double* x, int64_t n, float* y, cudaStream_t s) {
+    double_to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, y);
     return cudaGetLastError();
 }
 }  // namespace gira

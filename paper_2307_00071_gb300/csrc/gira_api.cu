@@ -303,6 +303,134 @@ void build_tables(std::vector<BatchInst>& hi, std::vector<BatchClass>& cls, std:
 
 }  // namespace
 
+
+// ---------------------------------------------------------------- large K (chunked E-step)
+namespace {
+
+// The chunk table of one fit over n points with k components, and its unit list.
+struct ChunkPlan {
+    int chunks = 0;
+    int64_t ppc = 0;
+    std::vector<BatchInst> hi;
+    std::vector<BatchUnit> units;
+    std::vector<int2> blocks;
+    std::vector<int> comp_inst, npairs;
+    int64_t part_floats = 0;
+};
+
+ChunkPlan plan_chunks(int64_t n, int k, int sms) {
+    ChunkPlan P;
+    const int KC = chunk_components();
+    P.chunks = (k + KC - 1) / KC;
+    const int Q = estep_batch_q();
+    const int occ = estep_occupancy(KC, true, 1024);
+    int64_t ppc = (n * P.chunks + 2LL * sms * occ - 1) / (2LL * sms * occ);
+    P.ppc = std::min<int64_t>(estep_ppc_max(), std::max<int64_t>(4 * Q, (ppc + Q - 1) / Q * Q));
+    const int ctas = (int)((n + P.ppc - 1) / P.ppc);
+    const int cpb = fin_components_per_block();
+    for (int c = 0; c < P.chunks; ++c) {
+        BatchInst I{};
+        I.pt_off = 0;
+        I.n = n;
+        I.ppc = P.ppc;
+        I.k = std::min(KC, k - c * KC);
+        I.comp_off = c * KC;
+        I.par_off = c * chunk_param_floats();
+        I.ctas = ctas;
+        I.part_off = P.part_floats;
+        I.ll_off = 0;
+        P.part_floats += (int64_t)ctas * I.k * NSTAT;
+        P.hi.push_back(I);
+        P.npairs.push_back((int)(chunk_param_floats() / PAIR_FLOATS));
+        for (int t = 0; t < ctas; ++t) P.units.push_back(BatchUnit{c, t});
+        for (int j = 0; j * cpb < I.k; ++j) P.blocks.push_back(make_int2(c, j));
+        for (int b = 0; b < I.k; ++b) P.comp_inst.push_back(c);
+    }
+    return P;
+}
+
+struct ChunkBufs {
+    float *params = nullptr, *partials = nullptr, *psum = nullptr, *gref = nullptr;
+    float2* pref = nullptr;
+    double *llpt = nullptr, *llp = nullptr;
+    int *flags = nullptr, *flag_count = nullptr, *comp_inst = nullptr, *npairs = nullptr;
+    BatchInst* insts = nullptr;
+    BatchUnit* units = nullptr;
+    int2* blocks = nullptr;
+};
+
+void carve_chunks(Carver& cv, const ChunkPlan& P, int64_t n, bool stats, ChunkBufs* b) {
+    b->params = cv.take<float>((size_t)P.chunks * chunk_param_floats());
+    b->partials = cv.take<float>(stats ? (size_t)P.part_floats : 0);
+    b->psum = cv.take<float>((size_t)P.chunks * n);
+    b->gref = cv.take<float>(2);
+    b->pref = cv.take<float2>(n);
+    b->llpt = cv.take<double>(n);
+    b->llp = cv.take<double>(chunk_combine_grid());
+    b->flags = cv.take<int>(n);
+    b->flag_count = cv.take<int>(1);
+    b->comp_inst = cv.take<int>(P.comp_inst.size());
+    b->npairs = cv.take<int>(P.chunks);
+    b->insts = cv.take<BatchInst>(P.chunks);
+    b->units = cv.take<BatchUnit>(P.units.size());
+    b->blocks = cv.take<int2>(P.blocks.size());
+}
+
+cudaError_t upload_chunks(const ChunkPlan& P, const ChunkBufs& b, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(b.insts, P.hi.data(), sizeof(BatchInst) * P.chunks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.units, P.units.data(), sizeof(BatchUnit) * P.units.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.blocks, P.blocks.data(), sizeof(int2) * P.blocks.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.comp_inst, P.comp_inst.data(), sizeof(int) * P.comp_inst.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.npairs, P.npairs.data(), sizeof(int) * P.chunks, cudaMemcpyHostToDevice, s);
+    return e;
+}
+
+// The two-level log-sum-exp: reference, pass A (chunk sums), combine, exact
+// points, per-point log-likelihood partials (and into st when ll_to_state).
+cudaError_t chunk_lse(const ChunkPlan& P, const ChunkBufs& b, const float4* p8, int64_t n, int k, DeviceState* st,
+                      int iter, bool ll_to_state, long long* launches, cudaStream_t s) {
+    cudaError_t e = launch_chunk_ref(b.params, k, st, b.gref, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.flag_count, 0, sizeof(int), s);
+    EStepLaunch a{p8, n, k, b.params, P.ppc, nullptr, nullptr, nullptr, nullptr, iter};
+    a.insts = b.insts;
+    a.units = b.units;
+    a.states = st;
+    a.gref = b.gref;
+    a.psum = b.psum;
+    if (e == cudaSuccess) e = launch_estep_chunks(a, 1, (int)P.units.size(), P.ppc, s);
+    if (e == cudaSuccess) e = launch_chunk_combine(b.psum, P.chunks, n, b.gref, b.pref, b.llpt, b.flag_count, b.flags, st, s);
+    if (e == cudaSuccess) e = launch_chunk_exact(p8, b.params, k, b.gref, b.flags, b.flag_count, b.pref, b.llpt, st, s);
+    if (e == cudaSuccess) e = launch_points_ll_reduce(b.llpt, n, b.llp, ll_to_state ? st : nullptr, s);
+    *launches += 5 + (ll_to_state ? 1 : 0);
+    return e;
+}
+
+cudaError_t chunk_em_iteration(const ChunkPlan& P, const ChunkBufs& b, const float4* p8, int64_t n, int k,
+                               float4* shift4, double* model64, double* trace, const gira_fit_opts& o,
+                               DeviceState* st, int iter, long long* launches, cudaStream_t s) {
+    cudaError_t e = chunk_lse(P, b, p8, n, k, st, iter, false, launches, s);
+    EStepLaunch a{p8, n, k, b.params, P.ppc, b.partials, nullptr, nullptr, nullptr, iter};
+    a.insts = b.insts;
+    a.units = b.units;
+    a.states = st;
+    a.gref = b.gref;
+    a.pref = b.pref;
+    if (e == cudaSuccess) e = launch_estep_chunks(a, 2, (int)P.units.size(), P.ppc, s);
+    if (e == cudaSuccess)
+        e = launch_reduce_finalize_chunks(b.partials, b.llp, chunk_combine_grid(), nullptr, shift4, b.insts,
+                                          b.blocks, (int)P.blocks.size(), n, o.reg_covar, o.tol, model64, b.params,
+                                          trace, st, iter, true, s);
+    *launches += 2;
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gira_fit_opts_default(gira_fit_opts* o) {
@@ -466,10 +594,13 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     TRY(check_ptr(covs, "covs", c.dev, &kc));
     const bool model_host = kw == Kind::Host || km == Kind::Host || kc == Kind::Host;
     const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
-    const int npairs = params_pairs_padded(k);
+    const bool chunked = k > MAX_K_DIRECT;   // two-level log-sum-exp over chunks of components
+    const ChunkPlan P = chunked ? plan_chunks(n, k, c.sms) : ChunkPlan{};
+    ChunkBufs cb;
+    const int npairs = chunked ? 0 : params_pairs_padded(k);
     int64_t ppc = 0, ppc_ll = 0;
-    const int grid = estep_grid(n, k, true, c.sms, &ppc);
-    const int grid_ll = estep_grid(n, k, false, c.sms, &ppc_ll);
+    const int grid = chunked ? 0 : estep_grid(n, k, true, c.sms, &ppc);
+    const int grid_ll = chunked ? 0 : estep_grid(n, k, false, c.sms, &ppc_ll);
     const int nblk = kpp_num_blocks(n);
     int kgrid = kinit ? kpp_persistent_grid() : 0;
     if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
@@ -497,6 +628,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.partials = cv.take<float>((size_t)grid * k * NSTAT);
         b.llp = cv.take<double>(std::max(grid, grid_ll));
         b.trace = cv.take<double>(std::max(o.iters, 1));
+        if (chunked) carve_chunks(cv, P, n, true, &cb);
         b.mw = cv.take<float>(model_host ? k : 0);
         b.mmu = cv.take<float>(model_host ? 3 * (size_t)k : 0);
         b.mcov = cv.take<float>(model_host ? 9 * (size_t)k : 0);
@@ -536,7 +668,13 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         pts = b.pin;
     }
     COUNTED(prof, 1, launch_pack(pts, n, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
-    COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+    if (chunked) {
+        GIRA_CUDA(upload_chunks(P, cb, c.s));
+        b.params = cb.params;
+        COUNTED(prof, 1, launch_fill_padding_batched(cb.params, cb.insts, P.chunks, 0, cb.npairs, c.s));
+    } else {
+        COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+    }
 
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
@@ -559,20 +697,38 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * k, c.s));
         COUNTED(prof, 1, launch_label_stats(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
         GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * k, cudaMemcpyDeviceToDevice, c.s));
-        COUNTED(prof, 1, launch_reduce_finalize(nullptr, 0, nullptr, b.stats64, b.shift4, k, n, o.reg_covar, o.tol,
-                                                b.model64, b.params, b.trace, b.st, 0, false, c.s));
+        if (chunked) {
+            COUNTED(prof, 1, launch_reduce_finalize_chunks(nullptr, nullptr, 0, b.stats64, b.shift4, cb.insts,
+                                                           cb.blocks, (int)P.blocks.size(), n, o.reg_covar, o.tol,
+                                                           b.model64, cb.params, b.trace, b.st, 0, false, c.s));
+        } else {
+            COUNTED(prof, 1, launch_reduce_finalize(nullptr, 0, nullptr, b.stats64, b.shift4, k, n, o.reg_covar,
+                                                    o.tol, b.model64, b.params, b.trace, b.st, 0, false, c.s));
+        }
     } else {
         if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
         if (km == Kind::Host)
             GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 3 * k, cudaMemcpyHostToDevice, c.s));
         if (kc == Kind::Host)
             GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 9 * k, cudaMemcpyHostToDevice, c.s));
-        COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+        if (chunked) {
+            COUNTED(prof, 1, launch_params_from_model_batched(w_d, mu_d, cov_d, k, cb.comp_inst, cb.insts, b.model64,
+                                                              cb.params, b.shift4, b.st, c.s));
+        } else {
+            COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+        }
     }
     prof.t_init = prof.mark();
 
+    if (chunked) {
+        for (int t = 1; t <= o.iters; ++t)
+            GIRA_CUDA(chunk_em_iteration(P, cb, b.p8, n, k, b.shift4, b.model64, b.trace, o, b.st, t, &prof.launches,
+                                         c.s));
+        prof.t_em = prof.mark();
+        if (final_loglik) GIRA_CUDA(chunk_lse(P, cb, b.p8, n, k, b.st, 0, true, &prof.launches, c.s));
+    }
     EStepLaunch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
-    for (int t = 1; t <= o.iters; ++t) {
+    for (int t = 1; t <= o.iters && !chunked; ++t) {
         a.iter = t;
         cudaEvent_t e0 = prof.mark();
         COUNTED(prof, 1, launch_estep(a, true, grid, c.s));
@@ -581,8 +737,8 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         COUNTED(prof, 1, launch_reduce_finalize(b.partials, grid, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
                                                 o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s));
     }
-    prof.t_em = prof.mark();
-    if (final_loglik) {
+    if (!chunked) prof.t_em = prof.mark();
+    if (final_loglik && !chunked) {
         EStepLaunch f = a;
         f.iter = 0;
         f.pts_per_cta = ppc_ll;
@@ -620,9 +776,12 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
     TRY(check_ptr(means, "means", c.dev, &km));
     TRY(check_ptr(covs, "covs", c.dev, &kc));
     if (per_point) TRY(check_ptr(per_point, "per_point", c.dev, &kpp));
-    const int npairs = params_pairs_padded(k);
+    const bool chunked = k > MAX_K_DIRECT;   // two-level log-sum-exp over chunks of components
+    const ChunkPlan P = chunked ? plan_chunks(n, k, c.sms) : ChunkPlan{};
+    ChunkBufs cb;
+    const int npairs = chunked ? 0 : params_pairs_padded(k);
     int64_t ppc = 0;
-    const int grid = estep_grid(n, k, false, c.sms, &ppc);
+    const int grid = chunked ? 0 : estep_grid(n, k, false, c.sms, &ppc);
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *mw, *mmu, *mcov, *pp;
@@ -641,6 +800,7 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
         b.mmu = cv.take<float>(km == Kind::Host ? 3 * (size_t)k : 0);
         b.mcov = cv.take<float>(kc == Kind::Host ? 9 * (size_t)k : 0);
         b.pp = cv.take<float>((per_point && kpp == Kind::Host) ? n : 0);
+        if (chunked) carve_chunks(cv, P, n, false, &cb);
     };
     Carver sizer;
     layout(sizer);
@@ -680,14 +840,25 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
         cov_d = b.mcov;
     }
     COUNTED(prof, 1, launch_pack(pts, n, nullptr, b.p8, b.st, c.s));
-    COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
-    COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
-    prof.t_init = prof.mark();
-    prof.t_em = prof.t_init;
     float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
-    EStepLaunch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
-    COUNTED(prof, 1, launch_estep(a, false, grid, c.s));
-    COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    if (chunked) {
+        GIRA_CUDA(upload_chunks(P, cb, c.s));
+        COUNTED(prof, 1, launch_fill_padding_batched(cb.params, cb.insts, P.chunks, 0, cb.npairs, c.s));
+        COUNTED(prof, 1, launch_params_from_model_batched(w_d, mu_d, cov_d, k, cb.comp_inst, cb.insts, b.model64,
+                                                          cb.params, b.shift4, b.st, c.s));
+        prof.t_init = prof.mark();
+        prof.t_em = prof.t_init;
+        GIRA_CUDA(chunk_lse(P, cb, b.p8, n, k, b.st, 0, true, &prof.launches, c.s));
+        if (ppd) COUNTED(prof, 1, launch_double_to_float(cb.llpt, n, ppd, c.s));
+    } else {
+        COUNTED(prof, 1, launch_fill_padding(b.params, k, npairs, c.s));
+        COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
+        prof.t_init = prof.mark();
+        prof.t_em = prof.t_init;
+        EStepLaunch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
+        COUNTED(prof, 1, launch_estep(a, false, grid, c.s));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    }
     if (per_point && kpp == Kind::Host)
         GIRA_CUDA(cudaMemcpyAsync(per_point, b.pp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
@@ -706,6 +877,7 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
                                  float* grad_chol, void* stream) {
     reset_error();
     TRY(check_nk(n, k));
+    if (k > GIRA_MAX_K_BATCHED) return fail(GIRA_ERR_INVALID_ARG, "k = %d > %d for the gradient", k, GIRA_MAX_K_BATCHED);
     if (!points || !logits || !means || !chol) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
     Ctx c;
     TRY(begin(c, stream));
@@ -847,8 +1019,8 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     for (int i = 0; i < batch; ++i) {
         const int64_t n = offsets[i + 1] - offsets[i];
         if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "instance %d has %lld points", i, (long long)n);
-        if (ks[i] < 1 || ks[i] > GIRA_MAX_K || ks[i] > n)
-            return fail(GIRA_ERR_INVALID_ARG, "instance %d: k = %d outside [1, min(n, %d)]", i, ks[i], GIRA_MAX_K);
+        if (ks[i] < 1 || ks[i] > GIRA_MAX_K_BATCHED || ks[i] > n)
+            return fail(GIRA_ERR_INVALID_ARG, "instance %d: k = %d outside [1, min(n, %d)]", i, ks[i], GIRA_MAX_K_BATCHED);
     }
     if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
     const int64_t total_n = offsets[batch];

@@ -203,6 +203,10 @@ __host__ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t j) 
     return (double)(splitmix64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// K above this runs the chunked (two-level log-sum-exp) path; the batched and
+// no-allocation entry points take K up to it only.
+constexpr int MAX_K_DIRECT = 1024;
+
 // ---------------------------------------------------------------- kernel entry points
 // (defined in em_kernels.cu / kmeans_kernels.cu, launched from gira_api.cu)
 
@@ -244,6 +248,12 @@ struct EStepLaunch {
     const BatchInst* insts = nullptr;
     const BatchUnit* units = nullptr;
     DeviceState* states = nullptr;
+    // K split into chunks (one table entry per chunk, all over the same points):
+    // pass A writes psum[chunk][n] = sum over the chunk of 2^(l - cmax); pass B
+    // takes pref[n] = (shift, 1 / total) from the combine step
+    const float* gref = nullptr;   // [0] cmax over all K, [1] log-likelihood reference (base 2)
+    float* psum = nullptr;
+    const float2* pref = nullptr;
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count
@@ -304,6 +314,36 @@ cudaError_t launch_model_out_batched(const double* model64, const BatchInst* ins
 // Per-instance sums of the log-likelihood partials into states[i].ll_sum.
 cudaError_t launch_ll_reduce_batched(const double* ll_partials, const BatchInst* insts, int batch,
                                      DeviceState* states, cudaStream_t s);
+
+// Large K: components in chunks of chunk_components() (one E-step shape),
+// each chunk an entry of a BatchInst table over the same points.
+int chunk_components();
+// gref = (max_b c_b over all k components, log-likelihood reference) from the
+// chunked parameter blocks (chunk c at c * chunk_param_floats()).
+int64_t chunk_param_floats();
+cudaError_t launch_chunk_ref(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s);
+// Pass A / pass B over all chunks (units: chunk-major); see EStepLaunch.
+cudaError_t launch_estep_chunks(const EStepLaunch& a, int pass, int nunits, int64_t ppc, cudaStream_t s);
+// Per point: total over chunks -> pref, per-point log-likelihood llpt (natural);
+// points whose total underflows (< 2^-100) are listed in flags for the exact step.
+int chunk_combine_grid();
+cudaError_t launch_chunk_combine(const float* psum, int chunks, int64_t n, const float* gref, float2* pref,
+                                 double* llpt, int* flag_count, int* flags, DeviceState* st, cudaStream_t s);
+// Listed points: exact per-point maximum over all k components (one warp each).
+cudaError_t launch_chunk_exact(const float4* pts8, const float* params, int k, const float* gref, const int* flags,
+                               const int* flag_count, float2* pref, double* llpt, DeviceState* st, cudaStream_t s);
+cudaError_t launch_double_to_float(const double* x, int64_t n, float* y, cudaStream_t s);
+// Fixed-order sums of llpt into chunk_combine_grid() partials, then (st != nullptr)
+// into st->ll_sum.
+cudaError_t launch_points_ll_reduce(const double* llpt, int64_t n, double* llp, DeviceState* st, cudaStream_t s);
+// The chunks' finalize: like the batched one, but every chunk shares state st
+// and trace; the log-likelihood / convergence step (em) runs once, from
+// ll_partials[0 .. ll_count).
+cudaError_t launch_reduce_finalize_chunks(const float* partials, const double* ll_partials, int ll_count,
+                                          const double* stats64, float4* shift4, const BatchInst* insts,
+                                          const int2* blocks, int nblocks, int64_t n, double reg, double tol,
+                                          double* model64, float* params, double* trace, DeviceState* st, int iter,
+                                          bool em, cudaStream_t s);
 
 // Differentiable log-likelihood.  pose12 = R (row-major) then t, or nullptr.
 // N x 3 -> pts8 of x' = R x + t (binary32, fixed order); flags non-finite input.

@@ -90,7 +90,7 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
     if (n < 1 || n > NOALLOC_MAX_N)
         return na_fail(GIRA_ERR_INVALID_ARG, "n = %lld outside [1, %lld] (the no-allocation limit)", (long long)n,
                        (long long)NOALLOC_MAX_N);
-    if (k < 1 || k > GIRA_MAX_K || k > n) return na_fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, min(n, %d)]", k, GIRA_MAX_K);
+    if (k < 1 || k > GIRA_MAX_K_BATCHED || k > n) return na_fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, min(n, %d)]", k, GIRA_MAX_K_BATCHED);
     if (!points || !weights || !means || !covs) return na_fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
     int dev = 0, sms = 1;
     NA_CUDA(cudaGetDevice(&dev));

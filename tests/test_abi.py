@@ -41,7 +41,7 @@ def test_version_and_defaults():
     assert (o.iters, o.tol, o.reg_covar, o.lloyd_iters, o.init_mode) == (100, 1e-3, 1e-6, 10, gira.INIT_KMEANS)
 
 
-@pytest.mark.parametrize("n,k", [(0, 1), (5, 0), (5, 6), (5000, 1025)])
+@pytest.mark.parametrize("n,k", [(0, 1), (5, 0), (5, 6), (9000, 8193)])
 def test_invalid_sizes_rejected_without_gpu(n, k):
     from paper_2307_00071_gb300 import gira
     pts = np.zeros((max(n, 1), 3), np.float32)

@@ -307,6 +307,43 @@ def bench_batched(gira):
             "speedup_vs_loop": out["loop"] / out["batched"]}
 
 
+MAP_FRAMES, MAP_N, MAP_K, MAP_ITERS = 16, 4_000_000, 8192, 20
+
+
+def bench_large_map(gira):
+    """16 depth frames under random poses (yaw, +-10 m), the first 4M points, K = 8192,
+    20 EM iterations (the chunked E-step) from means at random points."""
+    import torch
+    from paper_2307_00071_gb300 import synth
+    rng = np.random.default_rng(11)
+    parts = []
+    for i in range(MAP_FRAMES):
+        f = synth.depth_frame(seed=100 + i).points.astype(np.float64)
+        th = rng.uniform(0, 2 * np.pi)
+        R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+        parts.append(f @ R.T + np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), 0.0]))
+    pts = np.concatenate(parts)[:MAP_N].astype(np.float32)
+    x = torch.as_tensor(pts, device="cuda")
+    idx = rng.choice(len(pts), MAP_K, replace=False)
+    w0 = torch.full((MAP_K,), 1.0 / MAP_K, device="cuda")
+    m0 = x[torch.as_tensor(idx, device="cuda")].clone()
+    c0 = (torch.eye(3, device="cuda") * 0.05 ** 2).expand(MAP_K, 3, 3).contiguous()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gira.gira_gmm_fit(x, MAP_K, iters=1, tol=0.0, init=(w0.clone(), m0.clone(), c0.clone()), final_loglik=False)
+    torch.cuda.synchronize()
+    ev0.record()
+    r = gira.gira_gmm_fit(x, MAP_K, iters=MAP_ITERS, tol=0.0, init=(w0.clone(), m0.clone(), c0.clone()),
+                          final_loglik=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    units = float(len(pts)) * MAP_K * r["iters_done"]
+    return {"workload": f"{MAP_FRAMES} depth frames under random poses, N={len(pts)}, K={MAP_K}, "
+                        f"{MAP_ITERS} EM iterations (chunks of 512 components), tol 0",
+            "unit": UNIT, "value": units / (ms / 1e3), "ms": ms, "ms_per_iteration": ms / max(r["iters_done"], 1),
+            "trace_first_last": [float(r["trace"][0]), float(r["trace"][-1])]}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -418,7 +455,8 @@ def run_gira(args):
             "clocks": clk,
         }
         if not args.no_extras:
-            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira)}
+            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira),
+                              "large_map": bench_large_map(gira)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

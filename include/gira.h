@@ -208,6 +208,30 @@ gira_status gira_gmm_loglik_grad(const float *points, int64_t n, int k, const fl
                                  float *grad_chol, void *stream);
 
 /*
+ * gira_gmm_loglik_grad_batched -- gira_gmm_loglik_grad for a batch of scans,
+ * each with its own model and pose (e.g. many registrations advanced together);
+ * the whole evaluation (moving the scans, building the parameters, the adjoint
+ * E-step per block shape, the binary64 gradients) runs as one CUDA graph,
+ * cached per workspace and batch signature.
+ *
+ *   points, offsets, ks   as gira_gmm_fit_batched (ks[i] <= GIRA_MAX_K_BATCHED)
+ *   poses                 [host|device] batch x 12 binary32 (R row-major, t), or NULL
+ *   logits, means, chol   [host|device] stacked over instances (sum K, x 3, x 3 x 3)
+ *   logliks               [host] batch binary64 L_i, or NULL
+ *   grad_points           [host|device] sum N x 3 binary32, or NULL
+ *   grad_pose, grad_twist [host|device] batch x 12, batch x 6 binary64, or NULL
+ *   grad_logits, grad_means, grad_chol  [host|device] stacked, binary32, or NULL
+ *   statuses              [host] batch gira_status values, or NULL
+ * Every gradient is computed (NULL only skips its copy-out).  Returns the
+ * status of the first failing instance, else GIRA_OK.
+ */
+gira_status gira_gmm_loglik_grad_batched(const float *points, const int64_t *offsets, int batch, const int *ks,
+                                         const float *poses, const float *logits, const float *means,
+                                         const float *chol, double *logliks, float *grad_points, double *grad_pose,
+                                         double *grad_twist, float *grad_logits, float *grad_means,
+                                         float *grad_chol, int *statuses, void *stream);
+
+/*
  * Profiling (off by default; process-wide).  When enabled, each call records
  * CUDA events on its stream around its phases and around every launch of the
  * fused E-step/statistics kernel, and accumulates the device times below when

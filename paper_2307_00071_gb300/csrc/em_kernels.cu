@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
             a.st = a_in.states;
             if (CH == 1) a.psum = a_in.psum + (size_t)u.inst * I.n;
         }
+        if (GRAD) {   // per-instance scan gradient rows, pose and pose sums
+            a.grad_pts = a_in.grad_pts ? a_in.grad_pts + 3 * I.pt_off : nullptr;
+            a.rot = a_in.rot ? a_in.rot + 12 * (size_t)u.inst : nullptr;
+            a.pose_partials = a_in.pose_partials + 12 * I.ll_off;
+        }
     }
     const int G = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -590,6 +595,29 @@ cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
+}
+
+cudaError_t launch_estep_grad_units(const EStepLaunch& a, int nunits, int k_class, int64_t ppc_class, cudaStream_t s) {
+    const Shape sh = shape_for(k_class);
+    void* args[] = {(void*)&a};
+    const void* fn = grad_kernel_for(sh, true);
+    const size_t smem = estep_smem(ppc_class);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
+}
+
+int estep_grad_occupancy(int k, int64_t ppc) {
+    const Shape sh = shape_for(k);
+    const void* fn = grad_kernel_for(sh, true);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estep_smem(PPC_MAX));
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, estep_smem(ppc)) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return occ;
 }
 
 constexpr int KCHUNK = 512;   // components per chunk: the 4-warp shape
@@ -1162,15 +1190,56 @@ __global__ void pack_pose_kernel(const float* __restrict__ p3, int64_t n, const 
     p8[2 * i + 1] = make_float4(o[2], o[2], 0.f, 0.f);
 }
 
+// Every point of a batch of scans: x' = R_i x + t_i with the pose of its scan
+// (binary search over the offsets); flags non-finite input on its instance.
+__global__ void pack_pose_batched_kernel(const float* __restrict__ p3, int64_t n, const int64_t* __restrict__ offsets,
+                                         int batch, const float* __restrict__ poses, float4* __restrict__ p8,
+                                         DeviceState* states) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = batch;   // offsets[lo] <= i < offsets[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (offsets[mid] <= i) lo = mid; else hi = mid;
+    }
+    const float* pose = poses ? poses + 12 * (size_t)lo : nullptr;
+    const float x = p3[3 * i], y = p3[3 * i + 1], z = p3[3 * i + 2];
+    float o[3] = {x, y, z};
+    if (pose) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[r] = fmaf(pose[3 * r + 2], z, fmaf(pose[3 * r + 1], y, pose[3 * r] * x)) + pose[9 + r];
+    }
+    if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) set_error(states + lo, GIRA_ERR_NONFINITE_INPUT);
+    p8[2 * i] = make_float4(o[0], o[0], o[1], o[1]);
+    p8[2 * i + 1] = make_float4(o[2], o[2], 0.f, 0.f);
+}
+
 // One block: pi = softmax(logits) in binary64 (max, then fixed-order sums),
 // Sigma_b = L_b L_b^T, then the M-step's binary64 build of the E-step
 // parameters.  A non-positive diagonal entry of L_b is GIRA_ERR_NOT_PD.
 constexpr int PFC_THREADS = 256;
+__device__ void params_from_chol_body(const float* __restrict__ logits, const float* __restrict__ mu,
+                                      const float* __restrict__ chol, int k, double* model64, float* params,
+                                      float4* shift4, DeviceState* st);
 __global__ void __launch_bounds__(PFC_THREADS) params_from_chol_kernel(const float* __restrict__ logits,
                                                                        const float* __restrict__ mu,
                                                                        const float* __restrict__ chol, int k,
                                                                        double* model64, float* params,
                                                                        float4* shift4, DeviceState* st) {
+    params_from_chol_body(logits, mu, chol, k, model64, params, shift4, st);
+}
+// One block per instance of a batch.
+__global__ void __launch_bounds__(PFC_THREADS) params_from_chol_batched_kernel(
+    const float* __restrict__ logits, const float* __restrict__ mu, const float* __restrict__ chol,
+    const BatchInst* __restrict__ insts, double* model64, float* params, float4* shift4, DeviceState* states) {
+    const BatchInst I = insts[blockIdx.x];
+    const size_t c = I.comp_off;
+    params_from_chol_body(logits + c, mu + 3 * c, chol + 9 * c, I.k, model64 + c * MODEL, params + I.par_off,
+                          shift4 + c, states + blockIdx.x);
+}
+__device__ void params_from_chol_body(const float* __restrict__ logits, const float* __restrict__ mu,
+                                      const float* __restrict__ chol, int k, double* model64, float* params,
+                                      float4* shift4, DeviceState* st) {
     __shared__ double s_red[PFC_THREADS / 32];
     __shared__ double s_max, s_lz;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1232,18 +1301,74 @@ __global__ void __launch_bounds__(PFC_THREADS) params_from_chol_kernel(const flo
 //   dL/dL_b     = lower(P^T (P S2 P^T) - S0 diag(1/L_ii))
 //   dL/dalpha_b = S0 - N pi_b
 // with P = L_b^{-1}; block 0 also sums the log-likelihood and the twist.
-__global__ void __launch_bounds__(FIN_THREADS) grad_finalize_kernel(
-    const float* __restrict__ partials, int grid, const double* __restrict__ llp, const double* __restrict__ pp,
-    const float* __restrict__ pose, const float* __restrict__ chol, const double* __restrict__ model64, int k,
-    int64_t n, float* g_logits, float* g_means, float* g_chol, double* g_pose, double* g_twist, DeviceState* st) {
+struct GradFinArgs {
+    const float* partials;
+    int grid;
+    const double* llp;
+    const double* pp;
+    const float* pose;
+    const float* chol;
+    const double* model64;
+    int k;
+    int64_t n;
+    float *g_logits, *g_means, *g_chol;
+    double *g_pose, *g_twist;
+    DeviceState* st;
+};
+__device__ void grad_finalize_body(const GradFinArgs& f, int blk);
+__global__ void __launch_bounds__(FIN_THREADS) grad_finalize_kernel(const GradFinArgs f) {
+    grad_finalize_body(f, blockIdx.x);
+}
+// Block (instance i, index j) of a batch: components j * FIN_CPB .. of instance i.
+__global__ void __launch_bounds__(FIN_THREADS) grad_finalize_batched_kernel(const GradFinArgs base,
+                                                                           const BatchInst* __restrict__ insts,
+                                                                           const int2* __restrict__ blocks,
+                                                                           DeviceState* states) {
+    const int2 bi = blocks[blockIdx.x];
+    const BatchInst I = insts[bi.x];
+    const size_t c = I.comp_off;
+    GradFinArgs f = base;
+    f.partials = base.partials + I.part_off;
+    f.grid = I.ctas;
+    f.llp = base.llp + I.ll_off;
+    f.pp = base.pp + 12 * I.ll_off;
+    f.pose = base.pose ? base.pose + 12 * (size_t)bi.x : nullptr;
+    f.chol = base.chol + 9 * c;
+    f.model64 = base.model64 + c * MODEL;
+    f.k = I.k;
+    f.n = I.n;
+    f.g_logits = base.g_logits ? base.g_logits + c : nullptr;
+    f.g_means = base.g_means ? base.g_means + 3 * c : nullptr;
+    f.g_chol = base.g_chol ? base.g_chol + 9 * c : nullptr;
+    f.g_pose = base.g_pose ? base.g_pose + 12 * (size_t)bi.x : nullptr;
+    f.g_twist = base.g_twist ? base.g_twist + 6 * (size_t)bi.x : nullptr;
+    f.st = states + bi.x;
+    grad_finalize_body(f, bi.y);
+}
+__device__ void grad_finalize_body(const GradFinArgs& f, int blk) {
     __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
     __shared__ double S[FIN_CPB * NSTAT];
     __shared__ int s_skip;
+    const float* __restrict__ partials = f.partials;
+    const int grid = f.grid;
+    const double* __restrict__ llp = f.llp;
+    const double* __restrict__ pp = f.pp;
+    const float* __restrict__ pose = f.pose;
+    const float* __restrict__ chol = f.chol;
+    const double* __restrict__ model64 = f.model64;
+    const int k = f.k;
+    const int64_t n = f.n;
+    float* g_logits = f.g_logits;
+    float* g_means = f.g_means;
+    float* g_chol = f.g_chol;
+    double* g_pose = f.g_pose;
+    double* g_twist = f.g_twist;
+    DeviceState* st = f.st;
     if (threadIdx.x == 0) s_skip = st->error != 0;
     __syncthreads();
     if (s_skip) return;
     const int t = threadIdx.x;
-    const int b0 = blockIdx.x * FIN_CPB;
+    const int b0 = blk * FIN_CPB;
     const int nb = min(FIN_CPB, k - b0);
     reduce_partials(partials, grid, k, b0, nb * NSTAT, part, S);
     __syncthreads();
@@ -1280,7 +1405,7 @@ __global__ void __launch_bounds__(FIN_THREADS) grad_finalize_kernel(
         }
         if (g_logits) g_logits[b] = (float)(s0 - (double)n * model64[(size_t)b * MODEL]);
     }
-    if (blockIdx.x == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood and pose sums, fixed order
+    if (blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood and pose sums, fixed order
         const int lane = t - 32;
         double v[13] = {};
         for (int c = lane; c < grid; c += 32) {
@@ -1409,9 +1534,35 @@ cudaError_t launch_grad_finalize(const float* partials, int grid, const double* 
                                  const double* pose_partials, const float* pose12, const float* chol,
                                  const double* model64, int k, int64_t n, float* g_logits, float* g_means,
                                  float* g_chol, double* g_pose, double* g_twist, DeviceState* st, cudaStream_t s) {
-    grad_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(
-        partials, grid, ll_partials, pose_partials, pose12, chol, model64, k, n, g_logits, g_means, g_chol, g_pose,
-        g_twist, st);
+    const GradFinArgs f{partials, grid, ll_partials, pose_partials, pose12, chol, model64, k, n, g_logits, g_means,
+                        g_chol, g_pose, g_twist, st};
+    grad_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_pose_batched(const float* pts3, int64_t n, const int64_t* offsets, int batch,
+                                     const float* poses, float4* pts8, DeviceState* states, cudaStream_t s) {
+    pack_pose_batched_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts3, n, offsets, batch, poses, pts8,
+                                                                         states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params_from_chol_batched(const float* logits, const float* mu, const float* chol,
+                                            const BatchInst* insts, int batch, double* model64, float* params,
+                                            float4* shift4, DeviceState* states, cudaStream_t s) {
+    params_from_chol_batched_kernel<<<batch, PFC_THREADS, 0, s>>>(logits, mu, chol, insts, model64, params, shift4,
+                                                                  states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize_batched(const float* partials, const double* ll_partials,
+                                         const double* pose_partials, const float* poses, const float* chol,
+                                         const double* model64, const BatchInst* insts, const int2* blocks,
+                                         int nblocks, float* g_logits, float* g_means, float* g_chol, double* g_pose,
+                                         double* g_twist, DeviceState* states, cudaStream_t s) {
+    const GradFinArgs f{partials, 0, ll_partials, pose_partials, poses, chol, model64, 0, 0, g_logits, g_means,
+                        g_chol, g_pose, g_twist, nullptr};
+    grad_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, states);
     return cudaGetLastError();
 }
 }  // namespace gira

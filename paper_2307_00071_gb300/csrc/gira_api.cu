@@ -1373,4 +1373,250 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     return GIRA_OK;
 }
 
+// ================================================================ gmm_loglik_grad_batched
+gira_status gira_gmm_loglik_grad_batched(const float* points, const int64_t* offsets, int batch, const int* ks,
+                                         const float* poses, const float* logits, const float* means,
+                                         const float* chol, double* logliks, float* grad_points, double* grad_pose,
+                                         double* grad_twist, float* grad_logits, float* grad_means,
+                                         float* grad_chol, int* statuses, void* stream) {
+    reset_error();
+    if (!offsets || !ks) return fail(GIRA_ERR_INVALID_ARG, "offsets and ks must not be NULL");
+    if (batch < 1) return fail(GIRA_ERR_INVALID_ARG, "batch = %d < 1", batch);
+    if (offsets[0] != 0) return fail(GIRA_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int i = 0; i < batch; ++i) {
+        const int64_t n = offsets[i + 1] - offsets[i];
+        if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "instance %d has %lld points", i, (long long)n);
+        if (ks[i] < 1 || ks[i] > GIRA_MAX_K_BATCHED || ks[i] > n)
+            return fail(GIRA_ERR_INVALID_ARG, "instance %d: k = %d outside [1, min(n, %d)]", i, ks[i],
+                        GIRA_MAX_K_BATCHED);
+    }
+    if (!points || !logits || !means || !chol) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    const int64_t total_n = offsets[batch];
+    Ctx c;
+    TRY(begin(c, stream));
+    struct Arg {
+        const void* p;
+        const char* name;
+        Kind k = Kind::Device;
+    };
+    Arg in[5] = {{points, "points"}, {poses, "poses"}, {logits, "logits"}, {means, "means"}, {chol, "chol"}};
+    Arg out[7] = {{grad_points, "grad_points"}, {grad_pose, "grad_pose"}, {grad_twist, "grad_twist"},
+                  {grad_logits, "grad_logits"}, {grad_means, "grad_means"}, {grad_chol, "grad_chol"},
+                  {nullptr, ""}};
+    for (auto& a : in)
+        if (a.p) TRY(check_ptr(a.p, a.name, c.dev, &a.k));
+    for (auto& a : out)
+        if (a.p) TRY(check_ptr(a.p, a.name, c.dev, &a.k));
+    const int Q = estep_batch_q();
+
+    // ---- tables: instances, shape classes (points per CTA by a balance rule), finalize blocks
+    std::vector<BatchInst> hi(batch);
+    std::vector<int> npairs_of(batch);
+    int total_k = 0;
+    int64_t par_floats = 0;
+    std::map<std::pair<int, int>, int> class_of_shape;
+    std::vector<BatchClass> cls;
+    for (int i = 0; i < batch; ++i) {
+        BatchInst& I = hi[i];
+        I.pt_off = offsets[i];
+        I.n = offsets[i + 1] - offsets[i];
+        I.k = ks[i];
+        I.comp_off = total_k;
+        total_k += ks[i];
+        npairs_of[i] = params_pairs_padded(ks[i]);
+        I.par_off = par_floats;
+        par_floats += (int64_t)npairs_of[i] * PAIR_FLOATS;
+        int np, g, th;
+        estep_shape(ks[i], &np, &g, &th);
+        auto key = std::make_pair(np, g);
+        auto it = class_of_shape.find(key);
+        if (it == class_of_shape.end()) {
+            it = class_of_shape.emplace(key, (int)cls.size()).first;
+            cls.emplace_back();
+            cls.back().np = np;
+            cls.back().g = g;
+            cls.back().threads = th;
+        }
+        BatchClass& C = cls[it->second];
+        C.insts.push_back(i);
+        C.points += I.n;
+        C.kmax = std::max(C.kmax, ks[i]);
+    }
+    for (auto& C : cls) {
+        const int occ = estep_grad_occupancy(C.kmax, 1024);
+        int64_t ppc = (C.points + 2LL * c.sms * occ - 1) / (2LL * c.sms * occ);
+        C.ppc = std::min<int64_t>(estep_ppc_max(), std::max<int64_t>(4 * Q, (ppc + Q - 1) / Q * Q));
+    }
+    std::vector<BatchUnit> units;
+    int64_t part_floats = 0, ll_slots = 0;
+    build_tables(hi, cls, units, &part_floats, &ll_slots);
+    std::vector<int2> fin_blocks;
+    const int cpb = fin_components_per_block();
+    for (int i = 0; i < batch; ++i)
+        for (int j = 0; j * cpb < ks[i]; ++j) fin_blocks.push_back(make_int2(i, j));
+
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *poses, *lg, *mu, *ch, *params, *partials, *gp, *gl, *gm, *gc;
+        float4 *p8, *shift4;
+        double *model64, *llp, *ppart, *gpose, *gtwist;
+        BatchInst* insts;
+        BatchUnit* units;
+        int2* blocks;
+        int* npairs;
+        int64_t* offs;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(batch);
+        b.pin = cv.take<float>(3 * (size_t)total_n);
+        b.poses = cv.take<float>(12 * (size_t)batch);
+        b.lg = cv.take<float>(total_k);
+        b.mu = cv.take<float>(3 * (size_t)total_k);
+        b.ch = cv.take<float>(9 * (size_t)total_k);
+        b.p8 = cv.take<float4>(2 * (size_t)total_n);
+        b.params = cv.take<float>((size_t)par_floats);
+        b.shift4 = cv.take<float4>(total_k);
+        b.model64 = cv.take<double>((size_t)total_k * MODEL);
+        b.partials = cv.take<float>((size_t)part_floats);
+        b.llp = cv.take<double>((size_t)ll_slots);
+        b.ppart = cv.take<double>(12 * (size_t)ll_slots);
+        b.gp = cv.take<float>(3 * (size_t)total_n);
+        b.gl = cv.take<float>(total_k);
+        b.gm = cv.take<float>(3 * (size_t)total_k);
+        b.gc = cv.take<float>(9 * (size_t)total_k);
+        b.gpose = cv.take<double>(12 * (size_t)batch);
+        b.gtwist = cv.take<double>(6 * (size_t)batch);
+        b.insts = cv.take<BatchInst>(batch);
+        b.units = cv.take<BatchUnit>(units.size());
+        b.blocks = cv.take<int2>(fin_blocks.size());
+        b.npairs = cv.take<int>(batch);
+        b.offs = cv.take<int64_t>(batch + 1);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    std::vector<DeviceState> hs(batch);
+    for (auto& h : hs) {
+        h = DeviceState{};
+        h.bad_component = INT_MAX;
+    }
+    // every input staged into the workspace, so that the cached graph reads only workspace memory
+    auto stage = [&](void* dst, const Arg& a, size_t bytes) -> gira_status {
+        GIRA_CUDA(cudaMemcpyAsync(dst, a.p, bytes, a.k == Kind::Host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  c.s));
+        return GIRA_OK;
+    };
+    GIRA_CUDA(cudaMemcpyAsync(b.st, hs.data(), sizeof(DeviceState) * batch, cudaMemcpyHostToDevice, c.s));
+    TRY(stage(b.pin, in[0], sizeof(float) * 3 * total_n));
+    if (poses) {
+        TRY(stage(b.poses, in[1], sizeof(float) * 12 * batch));
+    } else {
+        std::vector<float> id(12 * (size_t)batch, 0.f);
+        for (int i = 0; i < batch; ++i) id[12 * i] = id[12 * i + 4] = id[12 * i + 8] = 1.f;
+        GIRA_CUDA(cudaMemcpyAsync(b.poses, id.data(), sizeof(float) * id.size(), cudaMemcpyHostToDevice, c.s));
+        GIRA_CUDA(cudaStreamSynchronize(c.s));   // id is a host temporary
+    }
+    TRY(stage(b.lg, in[2], sizeof(float) * total_k));
+    TRY(stage(b.mu, in[3], sizeof(float) * 3 * total_k));
+    TRY(stage(b.ch, in[4], sizeof(float) * 9 * total_k));
+    GIRA_CUDA(cudaMemcpyAsync(b.offs, offsets, sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.blocks, fin_blocks.data(), sizeof(int2) * fin_blocks.size(), cudaMemcpyHostToDevice,
+                              c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.npairs, npairs_of.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, c.s));
+    prof.t_init = prof.mark();
+
+    // ---- one graph: move the scans, build the parameters, the adjoint E-step per shape class, finalize
+    std::string key = "grad|" + std::to_string((uintptr_t)ws->ptr) + "|" + std::to_string(sizer.off) + "|" +
+                      std::to_string(batch);
+    for (int i = 0; i < batch; ++i) key += "|" + std::to_string(hi[i].n) + ":" + std::to_string(hi[i].k);
+    if (ws->graph_key != key || !ws->graph_exec) {
+        drop_graph(ws);
+        if (!ws->capture_stream) GIRA_CUDA(cudaStreamCreateWithFlags(&ws->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = ws->capture_stream;
+        GIRA_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = launch_pack_pose_batched(b.pin, total_n, b.offs, batch, b.poses, b.p8, b.st, cs);
+        if (e == cudaSuccess) e = launch_fill_padding_batched(b.params, b.insts, batch, 0, b.npairs, cs);
+        if (e == cudaSuccess)
+            e = launch_params_from_chol_batched(b.lg, b.mu, b.ch, b.insts, batch, b.model64, b.params, b.shift4, b.st,
+                                                cs);
+        EStepLaunch a{b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
+        a.insts = b.insts;
+        a.states = b.st;
+        a.grad_pts = b.gp;
+        a.rot = b.poses;
+        a.pose_partials = b.ppart;
+        for (const BatchClass& C : cls) {
+            if (e != cudaSuccess || !C.nunits) continue;
+            a.units = b.units + C.unit_begin;
+            e = launch_estep_grad_units(a, C.nunits, C.kmax, C.ppc, cs);
+        }
+        if (e == cudaSuccess)
+            e = launch_grad_finalize_batched(b.partials, b.llp, b.ppart, b.poses, b.ch, b.model64, b.insts, b.blocks,
+                                             (int)fin_blocks.size(), b.gl, b.gm, b.gc, b.gpose, b.gtwist, b.st, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(GIRA_ERR_CUDA, "capturing the batched gradient graph failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GIRA_ERR_CUDA, "instantiating the batched gradient graph failed: %s", cudaGetErrorString(e));
+        }
+        ws->graph_exec = exec;
+        ws->graph_key = key;
+    }
+    prof.launches += 4 + (long long)cls.size();
+    GIRA_CUDA(cudaGraphLaunch(ws->graph_exec, c.s));
+    prof.t_em = prof.mark();
+    const void* src[6] = {b.gp, b.gpose, b.gtwist, b.gl, b.gm, b.gc};
+    const size_t bytes[6] = {sizeof(float) * 3 * total_n, sizeof(double) * 12 * batch, sizeof(double) * 6 * batch,
+                             sizeof(float) * total_k, sizeof(float) * 3 * total_k, sizeof(float) * 9 * total_k};
+    for (int o = 0; o < 6; ++o)
+        if (out[o].p)
+            GIRA_CUDA(cudaMemcpyAsync(const_cast<void*>(out[o].p), src[o], bytes[o],
+                                      out[o].k == Kind::Host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(hs.data(), b.st, sizeof(DeviceState) * batch, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    gira_status first = GIRA_OK;
+    int first_i = -1;
+    for (int i = 0; i < batch; ++i) {
+        gira_status si = GIRA_OK;
+        if (hs[i].error) {
+            si = device_status(hs[i]);
+            if (first == GIRA_OK) {
+                first = si;
+                first_i = i;
+            }
+        }
+        if (statuses) statuses[i] = (int)si;
+        if (logliks) logliks[i] = hs[i].ll_sum;
+    }
+    if (first != GIRA_OK) {
+        if (hs[first_i].error == GIRA_ERR_NOT_PD) t_bad = hs[first_i].bad_component;
+        const std::string m = t_msg;
+        return fail(first, "instance %d: %s", first_i, m.c_str());
+    }
+    return GIRA_OK;
+}
+
 }  // extern "C"

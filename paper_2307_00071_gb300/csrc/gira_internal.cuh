@@ -345,6 +345,21 @@ cudaError_t launch_reduce_finalize_chunks(const float* partials, const double* l
                                           double* model64, float* params, double* trace, DeviceState* st, int iter,
                                           bool em, cudaStream_t s);
 
+// Batched differentiable log-likelihood (a batch table of scans, each with its
+// own model and pose; poses: batch x 12, or nullptr for identities).
+cudaError_t launch_pack_pose_batched(const float* pts3, int64_t n, const int64_t* offsets, int batch,
+                                     const float* poses, float4* pts8, DeviceState* states, cudaStream_t s);
+cudaError_t launch_params_from_chol_batched(const float* logits, const float* mu, const float* chol,
+                                            const BatchInst* insts, int batch, double* model64, float* params,
+                                            float4* shift4, DeviceState* states, cudaStream_t s);
+cudaError_t launch_estep_grad_units(const EStepLaunch& a, int nunits, int k_class, int64_t ppc_class, cudaStream_t s);
+int estep_grad_occupancy(int k, int64_t ppc);
+cudaError_t launch_grad_finalize_batched(const float* partials, const double* ll_partials,
+                                         const double* pose_partials, const float* poses, const float* chol,
+                                         const double* model64, const BatchInst* insts, const int2* blocks,
+                                         int nblocks, float* g_logits, float* g_means, float* g_chol, double* g_pose,
+                                         double* g_twist, DeviceState* states, cudaStream_t s);
+
 // Differentiable log-likelihood.  pose12 = R (row-major) then t, or nullptr.
 // N x 3 -> pts8 of x' = R x + t (binary32, fixed order); flags non-finite input.
 cudaError_t launch_pack_pose(const float* pts3, int64_t n, const float* pose12, float4* pts8, DeviceState* st,

@@ -56,6 +56,9 @@ def _load():
     lib.gira_gmm_loglik_grad.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, dp, vp, vp, vp, vp, vp, vp, vp]
     lib.gira_gmm_fit_batched.argtypes = [vp, vp, C.c_int, vp, C.POINTER(FitOpts), vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gira_gmm_fit_batched.restype = C.c_int
+    lib.gira_gmm_loglik_grad_batched.argtypes = [vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                                 vp]
+    lib.gira_gmm_loglik_grad_batched.restype = C.c_int
     lib.gira_gmm_loglik_grad.restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
@@ -333,3 +336,42 @@ def gira_gmm_fit_batched(points, offsets, ks, iters: int = 100, tol: float = 1e-
         _check(st)
     return dict(weights=w, means=m, covs=c, iters_done=done, final_loglik=fll, trace=trace[:, :iters],
                 status=stat)
+
+
+def gira_gmm_loglik_grad_batched(points, offsets, ks, logits, means, chol, poses=None, want=GRADS,
+                                 raise_on_error: bool = True):
+    """gira_gmm_loglik_grad for a batch of scans (instance i = points[offsets[i]:offsets[i+1]]
+    with its own model of ks[i] components, stacked, and pose poses[i] (12 values) or
+    identity).  Returns a dict: loglik (batch,), status (batch,) and grad_<name> for each
+    name in want: points (sum N,3), pose (batch,12), twist (batch,6), logits (sum K,),
+    means (sum K,3), chol (sum K,3,3), on the points' side (torch device or numpy)."""
+    total = _check_points(points)
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    B = len(kk)
+    if offs.shape != (B + 1,) or offs[-1] != total:
+        raise ValueError("offsets must hold batch + 1 entries ending at the number of points")
+    K = int(kk.sum())
+    lg, mu, ch = _f32_like(logits, points), _f32_like(means, points), _f32_like(chol, points)
+    po = _f32_like(poses, points)
+    shapes = {"points": ((total, 3), np.float32), "pose": ((B, 12), np.float64), "twist": ((B, 6), np.float64),
+              "logits": ((K,), np.float32), "means": ((K, 3), np.float32), "chol": ((K, 3, 3), np.float32)}
+    outs = {g: _new(points, *shapes[g]) for g in want}
+    ll = np.full(B, np.nan)
+    stat = np.zeros(B, np.int32)
+    pp, kp, s = _ptr(points)
+    keep = [kp]
+    ptrs = []
+    for x in (po, lg, mu, ch):
+        p_, k_, _ = _ptr(x)
+        ptrs.append(p_)
+        keep.append(k_)
+    optr = [(_ptr(outs[g])[0] if g in outs else None) for g in GRADS]
+    st = _lib.gira_gmm_loglik_grad_batched(pp, offs.ctypes.data, B, kk.ctypes.data, ptrs[0], ptrs[1], ptrs[2],
+                                           ptrs[3], ll.ctypes.data, *optr, stat.ctypes.data, s)
+    if raise_on_error:
+        _check(st)
+    r = {"loglik": ll, "status": stat}
+    for g in want:
+        r["grad_" + g] = outs[g]
+    return r

@@ -261,3 +261,54 @@ def test_registration_recovers_pose(gira):
     ang = math.degrees(math.acos(np.clip((np.trace(dR) - 1) / 2, -1, 1)))
     dt = np.linalg.norm(t_est - R_off.T @ (c_scan - t_off))
     assert ang < 1.0 and dt < 0.03, (ang, dt)
+
+
+def test_batched_grad_matches_oracle_per_instance(gira):
+    """Five registrations of uneven size and K (three block shapes) in one call."""
+    import torch
+    rng = np.random.default_rng(21)
+    sizes, kk = [3_000, 8_000, 2_500, 6_000, 4_000], [6, 40, 130, 9, 300]
+    scans, models, poses = [], [], []
+    for i, (n, k) in enumerate(zip(sizes, kk)):
+        cl = synth.gmm_cloud(n, min(k, 12), seed=200 + i)
+        if k > 12:   # more components than the generating mixture: centred on points
+            idx = rng.choice(n, k, replace=False)
+            mu = (cl.points[idx] + rng.normal(scale=0.01, size=(k, 3))).astype(np.float32)
+            ch = np.stack([np.eye(3) * rng.uniform(0.02, 0.1) for _ in range(k)]).astype(np.float32)
+            lg = rng.normal(scale=0.2, size=k).astype(np.float32)
+        else:
+            lg, mu, ch = model_from_mixture(cl, rng)
+        R, t = small_pose(rng)
+        scans.append(((cl.points.astype(np.float64) - t) @ np.float64(R)).astype(np.float32))
+        models.append((lg, mu, ch))
+        poses.append(pose12(R, t))
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    r = gira.gira_gmm_loglik_grad_batched(dev(np.concatenate(scans)), offs, kk,
+                                          dev(np.concatenate([m[0] for m in models])),
+                                          dev(np.concatenate([m[1] for m in models])),
+                                          dev(np.concatenate([m[2] for m in models])), dev(np.stack(poses)))
+    assert np.all(r["status"] == 0)
+    ck = np.concatenate([[0], np.cumsum(kk)])
+    for i in range(len(kk)):
+        R, t = poses[i][:9].reshape(3, 3), poses[i][9:]
+        ref = ref_grads(scans[i], *models[i], R, t)
+        got = {"loglik": r["loglik"][i],
+               "grad_points": to_np(r["grad_points"])[offs[i]:offs[i + 1]],
+               "grad_pose": to_np(r["grad_pose"])[i], "grad_twist": to_np(r["grad_twist"])[i],
+               "grad_logits": to_np(r["grad_logits"])[ck[i]:ck[i + 1]],
+               "grad_means": to_np(r["grad_means"])[ck[i]:ck[i + 1]],
+               "grad_chol": to_np(r["grad_chol"])[ck[i]:ck[i + 1]]}
+        check_all(got, ref, sizes[i])
+    # a second call with new poses reuses the cached graph and follows the new inputs
+    poses2 = [pose12(*small_pose(rng)) for _ in kk]
+    r2 = gira.gira_gmm_loglik_grad_batched(dev(np.concatenate(scans)), offs, kk,
+                                           dev(np.concatenate([m[0] for m in models])),
+                                           dev(np.concatenate([m[1] for m in models])),
+                                           dev(np.concatenate([m[2] for m in models])), dev(np.stack(poses2)),
+                                           want=("twist",))
+    for i in (0, 4):
+        R, t = poses2[i][:9].reshape(3, 3), poses2[i][9:]
+        ref = ref_grads(scans[i], *models[i], R, t)
+        assert abs(r2["loglik"][i] - ref["loglik"]) <= ll_tol(ref["loglik"], sizes[i])
+        assert_group(to_np(r2["grad_twist"])[i], ref["grad_twist"], "twist")

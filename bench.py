@@ -307,6 +307,60 @@ def bench_batched(gira):
             "speedup_vs_loop": out["loop"] / out["batched"]}
 
 
+REG_B, REG_N, REG_K = 64, 100_000, 1024
+
+
+def bench_batched_registrations(gira, frame_pts):
+    """64 registrations (100k-point scans of the frame under random poses, one K=1024 GMM of
+    the frame each): one batched call (one CUDA graph) against 64 single calls, L and every
+    gradient."""
+    import torch
+    rng = np.random.default_rng(17)
+    x = torch.as_tensor(frame_pts, device="cuda")
+    fit = gira.gira_gmm_fit(x, REG_K, iters=20, tol=1e-4, seed=0, lloyd_iters=10)
+    logits = torch.log(fit["weights"])
+    chol = torch.linalg.cholesky(fit["covs"].double()).float()
+    scans, poses = [], []
+    for _ in range(REG_B):
+        sub = frame_pts[rng.choice(len(frame_pts), REG_N, replace=False)].astype(np.float64)
+        th = np.radians(rng.uniform(-10, 10))
+        R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+        t = rng.uniform(-0.2, 0.2, size=3)
+        scans.append(((sub - t) @ R).astype(np.float32))
+        poses.append(np.concatenate([R.reshape(9), t]).astype(np.float32))
+    S = torch.as_tensor(np.concatenate(scans), device="cuda")
+    P = torch.as_tensor(np.stack(poses), device="cuda")
+    offs = np.arange(REG_B + 1, dtype=np.int64) * REG_N
+    ks = np.full(REG_B, REG_K, np.int32)
+    L = logits.repeat(REG_B).contiguous()
+    M = fit["means"].repeat(REG_B, 1).contiguous()
+    C = chol.repeat(REG_B, 1, 1).contiguous()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def batched():
+        gira.gira_gmm_loglik_grad_batched(S, offs, ks, L, M, C, P)
+
+    def loop():
+        for i in range(REG_B):
+            gira.gira_gmm_loglik_grad(S[i * REG_N:(i + 1) * REG_N], logits, fit["means"], chol, P[i])
+
+    out = {}
+    for name, fn, reps in (("batched", batched, 5), ("loop", loop, 2)):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        out[name] = ev0.elapsed_time(ev1) / reps
+    units = float(REG_B) * REG_N * REG_K
+    return {"workload": f"{REG_B} registrations: {REG_N}-point scans of the frame under random poses, "
+                        f"K={REG_K} GMM of the frame; L and every gradient",
+            "unit": UNIT, "value": units / (out["batched"] / 1e3), "ms_batched": out["batched"],
+            "ms_per_instance_loop": out["loop"], "speedup_vs_loop": out["loop"] / out["batched"]}
+
+
 MAP_FRAMES, MAP_N, MAP_K, MAP_ITERS = 16, 4_000_000, 8192, 20
 
 
@@ -456,7 +510,8 @@ def run_gira(args):
         }
         if not args.no_extras:
             line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira),
-                              "large_map": bench_large_map(gira)}
+                              "large_map": bench_large_map(gira),
+                              "batched_registrations": bench_batched_registrations(gira, frame.points)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

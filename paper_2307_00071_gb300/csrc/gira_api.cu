@@ -1116,7 +1116,35 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         int32_t* lab;
         u128* bs;
         unsigned long long* chg;
+        KppInst *ktab, *kseed;
+        BatchUnit* lunits;
     } b{};
+    // KInit tables: every instance; the seeding clusters grouped by cluster size
+    // (instances beyond one 16-CTA cluster are seeded alone); Lloyd tiles
+    std::vector<KppInst> ktab(batch);
+    std::vector<BatchUnit> lloyd_units;
+    std::vector<KppInst> kseed;
+    std::vector<std::pair<int, int>> seed_class;   // (cluster size, count), in kseed order
+    std::vector<int> seed_alone;
+    if (kinit) {
+        const int cs_max = kpp_cluster_size(1);   // the largest cluster this GPU runs (0: none)
+        std::map<int, std::vector<int>> by_cs;
+        for (int i = 0; i < batch; ++i) {
+            ktab[i] = KppInst{hi[i].pt_off, hi[i].n, hi[i].k, hi[i].comp_off, i, 0};
+            for (int t = 0; (int64_t)t * lloyd_tile() < hi[i].n; ++t) lloyd_units.push_back(BatchUnit{i, t});
+            int cs = 0;
+            for (int c2 = 1; c2 <= cs_max; c2 *= 2)
+                if (hi[i].n <= kpp_cluster_capacity(c2)) {
+                    cs = c2;
+                    break;
+                }
+            if (cs) by_cs[cs].push_back(i); else seed_alone.push_back(i);
+        }
+        for (auto& kv : by_cs) {
+            seed_class.emplace_back(kv.first, (int)kv.second.size());
+            for (int i : kv.second) kseed.push_back(ktab[i]);
+        }
+    }
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(batch);
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * (size_t)total_n : 0);
@@ -1146,6 +1174,9 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
             b.chg = cv.take<unsigned long long>((size_t)batch * (o.lloyd_iters + 1));
             b.bs = cv.take<u128>((size_t)nblk_off[batch]);
             b.d2 = cv.take<float>((size_t)total_n);
+            b.ktab = cv.take<KppInst>(batch);
+            b.kseed = cv.take<KppInst>(batch);
+            b.lunits = cv.take<BatchUnit>(lloyd_units.size());
         }
     };
     Carver sizer;
@@ -1185,29 +1216,35 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
     float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
     if (kinit) {
-        // KInit per instance (its own seeding launch, Lloyd, one-hot statistics)
+        // KInit of every instance: batched seeding launches (one cluster per
+        // instance, one launch per cluster size), batched Lloyd, batched one-hot
+        // statistics
         GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 4 * total_k, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * batch * (o.lloyd_iters + 1), c.s));
         GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * total_k, c.s));
-        for (int i = 0; i < batch; ++i) {
-            const BatchInst& I = hi[i];
-            float4* p4 = b.p4 + I.pt_off;
-            float4* c4 = b.c4 + I.comp_off;
-            int64_t* ch = b.ch + I.comp_off;
-            DeviceState* st = b.st + i;
-            const int kcs = kpp_cluster_size(I.n);
-            if (kcs > 0) {
-                COUNTED(prof, 1, launch_kpp_cluster(p4, I.n, I.k, o.seed, c4, ch, kcs, st, c.s));
-            } else {
-                COUNTED(prof, 2 * I.k - 1,
-                        launch_kpp(p4, I.n, I.k, o.seed, c4, b.d2 + I.pt_off, b.bs + nblk_off[i], ch, st, c.s));
-            }
-            COUNTED(prof, 1 + 2 * o.lloyd_iters,
-                    launch_lloyd(p4, I.n, I.k, o.lloyd_iters, c4, b.lab + I.pt_off, b.sums + 4 * (size_t)I.comp_off,
-                                 b.chg + (size_t)i * (o.lloyd_iters + 1), st, c.s));
-            COUNTED(prof, 1, launch_label_stats(p4, I.n, I.k, b.lab + I.pt_off, c4,
-                                                b.stats64 + (size_t)I.comp_off * NSTAT, st, c.s));
+        GIRA_CUDA(cudaMemcpyAsync(b.ktab, ktab.data(), sizeof(KppInst) * batch, cudaMemcpyHostToDevice, c.s));
+        if (!kseed.empty())
+            GIRA_CUDA(cudaMemcpyAsync(b.kseed, kseed.data(), sizeof(KppInst) * kseed.size(), cudaMemcpyHostToDevice,
+                                      c.s));
+        GIRA_CUDA(cudaMemcpyAsync(b.lunits, lloyd_units.data(), sizeof(BatchUnit) * lloyd_units.size(),
+                                  cudaMemcpyHostToDevice, c.s));
+        int seed_off = 0;
+        for (const auto& sc : seed_class) {
+            COUNTED(prof, 1, launch_kpp_cluster_batched(b.p4, b.kseed + seed_off, sc.second, o.seed, b.c4, b.ch,
+                                                        sc.first, b.st, c.s));
+            seed_off += sc.second;
         }
+        for (int i : seed_alone) {   // beyond one 16-CTA cluster: two launches per centre
+            const BatchInst& I = hi[i];
+            COUNTED(prof, 2 * I.k - 1, launch_kpp(b.p4 + I.pt_off, I.n, I.k, o.seed, b.c4 + I.comp_off,
+                                                  b.d2 + I.pt_off, b.bs + nblk_off[i], b.ch + I.comp_off, b.st + i,
+                                                  c.s));
+        }
+        COUNTED(prof, 1 + 2 * o.lloyd_iters,
+                launch_lloyd_batched(b.p4, b.ktab, b.lunits, (int)lloyd_units.size(), total_k, b.comp_inst,
+                                     o.lloyd_iters, b.c4, b.lab, b.sums, b.chg, b.st, c.s));
+        COUNTED(prof, 1, launch_label_stats_batched(b.p4, total_n, b.offs, batch, b.ktab, b.lab, b.c4, b.stats64,
+                                                    b.st, c.s));
         GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * total_k, cudaMemcpyDeviceToDevice, c.s));
         COUNTED(prof, 1, launch_reduce_finalize_batched(nullptr, nullptr, b.stats64, b.shift4, b.insts, b.blocks,
                                                         (int)fin_blocks.size(), o.reg_covar, o.tol, o.iters, b.model64,

@@ -393,6 +393,27 @@ int64_t kpp_persistent_max_n(int grid);
 cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
                                   int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
                                   cudaStream_t s);
+// Batched KInit: one entry per instance.
+struct KppInst {
+    int64_t pt_off, n;
+    int k, comp_off, inst, pad_;
+};
+// Batched seeding: cluster c of the launch (cs CTAs each) seeds instance
+// table[c]; every instance needs n <= kpp_cluster_capacity(cs).
+cudaError_t launch_kpp_cluster_batched(const float4* pts4, const KppInst* table, int clusters, uint64_t seed,
+                                       float4* centers, int64_t* chosen, int cs, DeviceState* states,
+                                       cudaStream_t s);
+int kpp_cluster_capacity(int cs);
+// Batched Lloyd: units (instance, tile of lloyd_tile() points); per-instance
+// label / sum / changed slabs (changed: lloyd_iters + 1 counters per instance).
+int lloyd_tile();
+cudaError_t launch_lloyd_batched(const float4* pts4, const KppInst* table, const BatchUnit* units, int nunits,
+                                 int total_k, const int* comp_inst, int lloyd_iters, float4* centers, int32_t* labels,
+                                 double* sums, unsigned long long* changed, DeviceState* states, cudaStream_t s);
+// One-hot statistics of every instance (instance of point i by binary search over offsets).
+cudaError_t launch_label_stats_batched(const float4* pts4, int64_t n, const int64_t* offsets, int batch,
+                                       const KppInst* table, const int32_t* labels, const float4* shift4,
+                                       double* stats64, DeviceState* states, cudaStream_t s);
 // One-cluster k-means++ (no global synchronisation): cluster size for n points,
 // or 0 when the one-cluster path does not apply.
 int kpp_cluster_size(int64_t n);

@@ -427,17 +427,35 @@ __device__ __forceinline__ unsigned long long fx48_small(float d, bool& big) {
     return sh >= 0 ? mant << min(sh, 63) : mant >> min(-sh, 63);
 }
 
-__global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4* __restrict__ pts, int64_t n, int k,
-                                                                    uint64_t seed, float4* centers, int64_t* chosen,
-                                                                    DeviceState* st) {
+// table (batched seeding): cluster c of the launch seeds instance table[c]; the
+// pointers are then bases offset by its entry.
+__global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4* __restrict__ pts0, int64_t n0,
+                                                                    int k0, uint64_t seed, float4* centers0,
+                                                                    int64_t* chosen0, DeviceState* st0,
+                                                                    const KppInst* __restrict__ table) {
     extern __shared__ __align__(16) unsigned char kc_dsm[];
     float2* xs = reinterpret_cast<float2*>(kc_dsm);   // [KC_PMAX][KC_THREADS] each: points 2p, 2p+1 of a lane
     float2* ys = xs + KC_PMAX * KC_THREADS;
     float2* zs = ys + KC_PMAX * KC_THREADS;
     KcShared& sh = *reinterpret_cast<KcShared*>(zs + KC_PMAX * KC_THREADS);
     cg::cluster_group cluster = cg::this_cluster();
-    if (st->error) return;   // set before the launch: every CTA leaves
     const int cs = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+    const float4* pts = pts0;
+    int64_t n = n0;
+    int k = k0;
+    float4* centers = centers0;
+    int64_t* chosen = chosen0;
+    DeviceState* st = st0;
+    if (table) {
+        const KppInst e = table[blockIdx.x / cs];
+        pts = pts0 + e.pt_off;
+        n = e.n;
+        k = e.k;
+        centers = centers0 + e.comp_off;
+        chosen = chosen0 + e.comp_off;
+        st = st0 + e.inst;
+    }
+    if (st->error) return;   // set before the launch: every CTA of the cluster leaves
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // contiguous ranges: CTA, warp, lane (the running sum in point order is
     // CTA prefix, warp prefix, lane prefix, then the lane's points in order)
@@ -613,6 +631,12 @@ struct CPair {
     float2 x, y, z;   // negated coordinates of centres 2p and 2p+1
 };
 
+// The points of groups g0 = first, first + stride, ... (LL_THREADS * LL_PPT points
+// each) against the k centres in shared memory.
+__device__ void lloyd_assign_groups(const float4* __restrict__ pts, int64_t n, int npair, const CPair* sc,
+                                    int32_t* labels, double* sums, unsigned long long* changed, int it,
+                                    int64_t first, int64_t stride);
+
 __global__ void __launch_bounds__(LL_THREADS) lloyd_assign_kernel(
     const float4* __restrict__ pts, int64_t n, int k, const float4* __restrict__ centers, int32_t* labels,
     double* sums, unsigned long long* changed, int it, DeviceState* st) {
@@ -626,10 +650,41 @@ __global__ void __launch_bounds__(LL_THREADS) lloyd_assign_kernel(
         sc[p] = CPair{f2(-a.x, -b.x), f2(-a.y, -b.y), f2(-a.z, -b.z)};
     }
     __syncthreads();
+    const int64_t group = (int64_t)LL_THREADS * LL_PPT;
+    lloyd_assign_groups(pts, n, npair, sc, labels, sums, changed, it, (int64_t)blockIdx.x * group,
+                        (int64_t)gridDim.x * group);
+}
+
+// Batched: CTA u assigns tile units[u].cta of instance units[u].inst.
+__global__ void __launch_bounds__(LL_THREADS) lloyd_assign_batched_kernel(
+    const float4* __restrict__ pts, const KppInst* __restrict__ table, const BatchUnit* __restrict__ units,
+    const float4* __restrict__ centers, int32_t* labels, double* sums, unsigned long long* changed, int iters1,
+    int it, DeviceState* states) {
+    extern __shared__ CPair sc[];
+    const BatchUnit u = units[blockIdx.x];
+    const KppInst e = table[u.inst];
+    if (states[e.inst].error) return;
+    unsigned long long* chg = changed + (size_t)e.inst * iters1;
+    if (it > 0 && chg[it - 1] == 0) return;
+    const int k = e.k, npair = (k + 1) / 2;
+    const float4* c = centers + e.comp_off;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+        const float4 a = c[2 * p];
+        const float4 b = (2 * p + 1 < k) ? c[2 * p + 1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        sc[p] = CPair{f2(-a.x, -b.x), f2(-a.y, -b.y), f2(-a.z, -b.z)};
+    }
+    __syncthreads();
+    const int64_t group = (int64_t)LL_THREADS * LL_PPT;
+    lloyd_assign_groups(pts + e.pt_off, e.n, npair, sc, labels + e.pt_off, sums + 4 * (size_t)e.comp_off, chg, it,
+                        (int64_t)u.cta * group, INT64_MAX / 2);
+}
+
+__device__ void lloyd_assign_groups(const float4* __restrict__ pts, int64_t n, int npair, const CPair* sc,
+                                    int32_t* labels, double* sums, unsigned long long* changed, int it,
+                                    int64_t first, int64_t stride) {
     const int lane = threadIdx.x & 31;
     unsigned long long cnt = 0;
-    const int64_t group = (int64_t)LL_THREADS * LL_PPT;
-    for (int64_t g0 = (int64_t)blockIdx.x * group; g0 < n; g0 += (int64_t)gridDim.x * group) {
+    for (int64_t g0 = first; g0 < n; g0 += stride) {
         // point r of this thread: g0 + warp_base + r * 32 + lane (coalesced per r)
         const int64_t wb = g0 + (int64_t)(threadIdx.x >> 5) * 32 * LL_PPT;
         float2 X[LL_PPT], Y[LL_PPT], Z[LL_PPT];
@@ -710,6 +765,23 @@ __global__ void lloyd_update_kernel(int k, double* sums, float4* centers, const 
     if (b == 0) st->lloyd_done = it;
 }
 
+// Batched: global component g of instance comp_inst[g].
+__global__ void lloyd_update_batched_kernel(int total_k, const int* __restrict__ comp_inst,
+                                            const KppInst* __restrict__ table, double* sums, float4* centers,
+                                            const unsigned long long* changed, int iters1, int it,
+                                            DeviceState* states) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_k) return;
+    const KppInst e = table[comp_inst[g]];
+    if (states[e.inst].error || changed[(size_t)e.inst * iters1 + it - 1] == 0) return;
+    const double cnt = sums[4 * (size_t)g + 3];
+    if (cnt > 0.0)
+        centers[g] = make_float4((float)(sums[4 * (size_t)g] / cnt), (float)(sums[4 * (size_t)g + 1] / cnt),
+                                 (float)(sums[4 * (size_t)g + 2] / cnt), 0.f);
+    for (int i = 0; i < 4; ++i) sums[4 * (size_t)g + i] = 0.0;
+    if (g == e.comp_off) states[e.inst].lloyd_done = it;
+}
+
 // One-hot statistics about the shift s_b (the final centre): S0 = count,
 // S1 = sum (x - s), S2 = sum (x - s)(x - s)^T, binary64.
 __global__ void label_stats_kernel(const float4* __restrict__ pts, int64_t n, int k, const int32_t* __restrict__ labels,
@@ -717,6 +789,33 @@ __global__ void label_stats_kernel(const float4* __restrict__ pts, int64_t n, in
     if (st->error) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int b = labels[i];
+        const float4 x = pts[i], s = shift4[b];
+        const double d[3] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z};
+        double* S = stats64 + (size_t)b * NSTAT;
+        atomicAdd(&S[0], 1.0);
+        for (int t = 0; t < 3; ++t) atomicAdd(&S[1 + t], d[t]);
+        atomicAdd(&S[4], d[0] * d[0]);
+        atomicAdd(&S[5], d[0] * d[1]);
+        atomicAdd(&S[6], d[0] * d[2]);
+        atomicAdd(&S[7], d[1] * d[1]);
+        atomicAdd(&S[8], d[1] * d[2]);
+        atomicAdd(&S[9], d[2] * d[2]);
+    }
+}
+
+// Batched: the instance of point i by binary search over the offsets.
+__global__ void label_stats_batched_kernel(const float4* __restrict__ pts, int64_t n, const int64_t* __restrict__ offsets,
+                                           int batch, const KppInst* __restrict__ table,
+                                           const int32_t* __restrict__ labels, const float4* __restrict__ shift4,
+                                           double* stats64, DeviceState* states) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = batch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offsets[mid] <= i) lo = mid; else hi = mid;
+        }
+        if (states[lo].error) continue;
+        const int b = table[lo].comp_off + labels[i];
         const float4 x = pts[i], s = shift4[b];
         const double d[3] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z};
         double* S = stats64 + (size_t)b * NSTAT;
@@ -808,6 +907,26 @@ int kpp_cluster_size(int64_t n) {
     return cached;
 }
 
+cudaError_t launch_kpp_cluster_batched(const float4* pts4, const KppInst* table, int clusters, uint64_t seed,
+                                       float4* centers, int64_t* chosen, int cs, DeviceState* states,
+                                       cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs * clusters);
+    cfg.blockDim = dim3(KC_THREADS);
+    cfg.dynamicSmemBytes = kc_smem_bytes();
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kpp_cluster_kernel, pts4, (int64_t)0, 0, seed, centers, chosen, states, table);
+}
+
+int kpp_cluster_capacity(int cs) { return cs * KC_THREADS * KC_LMAX; }
+
 cudaError_t launch_kpp_cluster(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, int64_t* chosen,
                                int cs, DeviceState* st, cudaStream_t s) {
     cudaLaunchConfig_t cfg{};
@@ -822,7 +941,7 @@ cudaError_t launch_kpp_cluster(const float4* pts4, int64_t n, int k, uint64_t se
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kpp_cluster_kernel, pts4, n, k, seed, centers, chosen, st);
+    return cudaLaunchKernelEx(&cfg, kpp_cluster_kernel, pts4, n, k, seed, centers, chosen, st, (const KppInst*)nullptr);
 }
 
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
@@ -854,6 +973,40 @@ cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, 
         lloyd_update_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, sums, centers, changed, it, st);
         lloyd_assign_kernel<<<grid, threads, smem, s>>>(pts4, n, k, centers, labels, sums, changed, it, st);
     }
+    return cudaGetLastError();
+}
+
+int lloyd_tile() { return LL_THREADS * LL_PPT; }
+
+cudaError_t launch_lloyd_batched(const float4* pts4, const KppInst* table, const BatchUnit* units, int nunits,
+                                 int total_k, const int* comp_inst, int lloyd_iters, float4* centers, int32_t* labels,
+                                 double* sums, unsigned long long* changed, DeviceState* states, cudaStream_t s) {
+    const size_t smem = sizeof(CPair) * (size_t)((GIRA_MAX_K_BATCHED + 1) / 2);
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024)
+        e = cudaFuncSetAttribute(lloyd_assign_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int iters1 = lloyd_iters + 1;
+    lloyd_assign_batched_kernel<<<nunits, LL_THREADS, smem, s>>>(pts4, table, units, centers, labels, sums, changed,
+                                                                 iters1, 0, states);
+    for (int it = 1; it <= lloyd_iters; ++it) {
+        lloyd_update_batched_kernel<<<(total_k + 127) / 128, 128, 0, s>>>(total_k, comp_inst, table, sums, centers,
+                                                                          changed, iters1, it, states);
+        lloyd_assign_batched_kernel<<<nunits, LL_THREADS, smem, s>>>(pts4, table, units, centers, labels, sums,
+                                                                     changed, iters1, it, states);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_label_stats_batched(const float4* pts4, int64_t n, const int64_t* offsets, int batch,
+                                       const KppInst* table, const int32_t* labels, const float4* shift4,
+                                       double* stats64, DeviceState* states, cudaStream_t s) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    label_stats_batched_kernel<<<grid, 256, 0, s>>>(pts4, n, offsets, batch, table, labels, shift4, stats64, states);
     return cudaGetLastError();
 }
 

@@ -57,7 +57,8 @@ def test_batched_from_given_init_matches_oracle(gira):
 
 
 def test_batched_kmeans_init_matches_oracle_fit(gira):
-    sizes, kk = [3_000, 6_000, 2_500, 9_000], [4, 16, 33, 64]
+    # 40k points need a 4-CTA seeding cluster, the others one CTA: two seeding launches
+    sizes, kk = [3_000, 6_000, 2_500, 40_000], [4, 16, 33, 64]
     clouds, pts, offs, ks = make_batch(sizes, kk, seed=20)
     r = gira.gira_gmm_fit_batched(pts, offs, ks, iters=10, tol=0.0, seed=3, lloyd_iters=6)
     assert np.all(r["status"] == 0)

@@ -290,8 +290,19 @@ def bench_batched(gira):
             gira.gira_gmm_fit(x[sl], int(ks[i]), iters=BATCH_ITERS, tol=0.0,
                               init=(w0[cl].clone(), m0[cl].clone(), c0[cl].clone()), final_loglik=False)
 
+    def batched_full():
+        return gira.gira_gmm_fit_batched(x, offs, ks, iters=BATCH_ITERS, tol=0.0, seed=0, lloyd_iters=10,
+                                         final_loglik=False)
+
+    def loop_full():
+        for i in range(len(ks)):
+            sl = slice(int(offs[i]), int(offs[i + 1]))
+            gira.gira_gmm_fit(x[sl], int(ks[i]), iters=BATCH_ITERS, tol=0.0, seed=0, lloyd_iters=10,
+                              final_loglik=False)
+
     out = {}
-    for name, fn, reps in (("batched", batched, 3), ("loop", loop, 1)):
+    for name, fn, reps in (("batched", batched, 3), ("loop", loop, 1), ("batched_full", batched_full, 2),
+                           ("loop_full", loop_full, 1)):
         fn()   # warm (first batched call also tunes points per CTA)
         torch.cuda.synchronize()
         ev0.record()
@@ -304,7 +315,9 @@ def bench_batched(gira):
                         f"{BATCH_ITERS} EM iterations from the same k-means init, tol 0",
             "unit": UNIT, "value": units / (out["batched"] / 1e3), "ms_batched": out["batched"],
             "ms_per_instance_loop": out["loop"], "loop_units_per_s": units / (out["loop"] / 1e3),
-            "speedup_vs_loop": out["loop"] / out["batched"]}
+            "speedup_vs_loop": out["loop"] / out["batched"],
+            "with_kinit": {"ms_batched": out["batched_full"], "ms_per_instance_loop": out["loop_full"],
+                           "speedup_vs_loop": out["loop_full"] / out["batched_full"]}}
 
 
 REG_B, REG_N, REG_K = 64, 100_000, 1024

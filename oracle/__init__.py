@@ -57,6 +57,24 @@ def lib():
         L.oracle_fx48_parts.argtypes = [C.c_float, u64p, u64p]
         L.oracle_fx_threshold.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, u64p, u64p]
         L.oracle_loglik_grad.argtypes = [fp, C.c_int64, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        ci = C.c_int
+        L.oracle_cholesky_d.argtypes = [dp, dp, ci]
+        L.oracle_tri_inverse_d.argtypes = [dp, dp, ci]
+        L.oracle_log_gaussian_d.restype = C.c_double
+        L.oracle_log_gaussian_d.argtypes = [dp, dp, dp, ci]
+        L.oracle_estep_d.argtypes = [fp, C.c_int64, ci, ci, dp, dp, dp, dp, dp, dp]
+        L.oracle_mstep_d.argtypes = [fp, C.c_int64, ci, ci, dp, C.c_double, dp, dp, dp]
+        L.oracle_dist2_f32_d.restype = C.c_float
+        L.oracle_dist2_f32_d.argtypes = [fp, fp, ci]
+        L.oracle_kmeanspp_d.argtypes = [fp, C.c_int64, ci, ci, C.c_uint64, fp, i64p]
+        L.oracle_lloyd_d.argtypes = [fp, C.c_int64, ci, ci, fp, ci, i32p, C.POINTER(ci)]
+        L.oracle_init_from_labels_d.argtypes = [fp, C.c_int64, ci, ci, i32p, C.c_double, dp, dp, dp]
+        L.oracle_em_d.argtypes = [fp, C.c_int64, ci, ci, ci, C.c_double, C.c_double, dp, dp, dp, dp, C.POINTER(ci),
+                                  dp]
+        L.oracle_gmm_fit_d.argtypes = [fp, C.c_int64, ci, ci, ci, C.c_double, C.c_double, C.c_uint64, ci, dp, dp, dp,
+                                       dp, C.POINTER(ci), dp]
+        L.oracle_conditional4.argtypes = [fp, C.c_int64, ci, dp, dp, dp, dp, dp]
+        L.oracle_sample_d.argtypes = [C.c_int64, ci, ci, dp, dp, dp, C.c_uint64, fp, i32p]
         _lib = L
     return _lib
 
@@ -92,19 +110,24 @@ def uniform(seed: int, j: int) -> float:
 
 
 # ----------------------------------------------------------------------------- algebra
+# The dimension d (3, or 4 for xyz + intensity) is taken from the arrays.
 def cholesky3(S):
-    S = _f64(S).reshape(3, 3).copy()
-    L = np.zeros((3, 3))
-    st = lib().oracle_cholesky3(_p(S, C.c_double), _p(L, C.c_double))
+    S = _f64(S)
+    d = int(round(np.sqrt(S.size)))
+    S = S.reshape(d, d).copy()
+    L = np.zeros((d, d))
+    st = lib().oracle_cholesky_d(_p(S, C.c_double), _p(L, C.c_double), d)
     if st != 0:
-        raise OracleError(ERR_NOT_PD, "cholesky3")
+        raise OracleError(ERR_NOT_PD, "cholesky")
     return L
 
 
 def tri_inverse3(L):
-    L = _f64(L).reshape(3, 3).copy()
-    P = np.zeros((3, 3))
-    lib().oracle_tri_inverse3(_p(L, C.c_double), _p(P, C.c_double))
+    L = _f64(L)
+    d = int(round(np.sqrt(L.size)))
+    L = L.reshape(d, d).copy()
+    P = np.zeros((d, d))
+    lib().oracle_tri_inverse_d(_p(L, C.c_double), _p(P, C.c_double), d)
     return P
 
 
@@ -112,7 +135,7 @@ def log_gaussian(x, mu, cov) -> float:
     """Eq. (simplifiedGaussian) at one point."""
     P = tri_inverse3(cholesky3(cov))
     x, mu = _f64(x).copy(), _f64(mu).copy()
-    return float(lib().oracle_log_gaussian(_p(x, C.c_double), _p(mu, C.c_double), _p(P, C.c_double)))
+    return float(lib().oracle_log_gaussian_d(_p(x, C.c_double), _p(mu, C.c_double), _p(P, C.c_double), len(x)))
 
 
 def fx48(d) -> int:
@@ -130,65 +153,76 @@ def fx_threshold(k53: int, total: int) -> int:
 
 def dist2_f32(x, c) -> np.float32:
     x, c = _f32(x).copy(), _f32(c).copy()
-    return np.float32(lib().oracle_dist2_f32(_p(x, C.c_float), _p(c, C.c_float)))
+    return np.float32(lib().oracle_dist2_f32_d(_p(x, C.c_float), _p(c, C.c_float), len(x)))
+
+
+def _dim(pts):
+    if pts.ndim != 2 or pts.shape[1] not in (3, 4):
+        raise ValueError("points must be N x 3 or N x 4")
+    return pts.shape[1]
 
 
 # ----------------------------------------------------------------------------- EM steps
 def estep(pts, weights, means, covs, want_resp: bool = True, want_lse: bool = False):
     """Returns (mean_ll, resp or None, lse or None)."""
     pts = _f32(pts)
+    d = _dim(pts)
     N, K = pts.shape[0], len(weights)
     w, m, c = _f64(weights), _f64(means), _f64(covs)
     resp = np.empty((N, K)) if want_resp else None
     lse = np.empty(N) if want_lse else None
     ll = C.c_double()
-    st = lib().oracle_estep(_p(pts, C.c_float), N, K, _p(w, C.c_double), _p(m, C.c_double), _p(c, C.c_double),
-                            _p(resp, C.c_double), _p(lse, C.c_double), C.byref(ll))
+    st = lib().oracle_estep_d(_p(pts, C.c_float), N, K, d, _p(w, C.c_double), _p(m, C.c_double),
+                              _p(c, C.c_double), _p(resp, C.c_double), _p(lse, C.c_double), C.byref(ll))
     _check(st, "estep")
     return ll.value, resp, lse
 
 
 def mstep(pts, resp, reg: float):
     pts, resp = _f32(pts), _f64(resp)
+    d = _dim(pts)
     N, K = resp.shape
-    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
-    st = lib().oracle_mstep(_p(pts, C.c_float), N, K, _p(resp, C.c_double), reg, _p(w, C.c_double),
-                            _p(m, C.c_double), _p(c, C.c_double))
+    w, m, c = np.empty(K), np.empty((K, d)), np.empty((K, d, d))
+    st = lib().oracle_mstep_d(_p(pts, C.c_float), N, K, d, _p(resp, C.c_double), reg, _p(w, C.c_double),
+                              _p(m, C.c_double), _p(c, C.c_double))
     _check(st, "mstep")
     return w, m, c
 
 
 def kmeanspp(pts, K: int, seed: int):
-    """Returns (centers (K,3) float32, chosen indices (K,) int64)."""
+    """Returns (centers (K,d) float32, chosen indices (K,) int64)."""
     pts = _f32(pts)
+    d = _dim(pts)
     N = pts.shape[0]
-    centers = np.empty((K, 3), np.float32)
+    centers = np.empty((K, d), np.float32)
     chosen = np.empty(K, np.int64)
-    st = lib().oracle_kmeanspp(_p(pts, C.c_float), N, K, seed, _p(centers, C.c_float), _p(chosen, C.c_int64))
+    st = lib().oracle_kmeanspp_d(_p(pts, C.c_float), N, K, d, seed, _p(centers, C.c_float), _p(chosen, C.c_int64))
     _check(st, "kmeanspp")
     return centers, chosen
 
 
 def lloyd(pts, centers, lloyd_iters: int):
-    """Returns (centers (K,3) float32, labels (N,) int32, iterations done)."""
+    """Returns (centers (K,d) float32, labels (N,) int32, iterations done)."""
     pts = _f32(pts)
+    d = _dim(pts)
     centers = _f32(centers).copy()
     N, K = pts.shape[0], centers.shape[0]
     labels = np.empty(N, np.int32)
     done = C.c_int()
-    st = lib().oracle_lloyd(_p(pts, C.c_float), N, K, _p(centers, C.c_float), lloyd_iters,
-                            _p(labels, C.c_int32), C.byref(done))
+    st = lib().oracle_lloyd_d(_p(pts, C.c_float), N, K, d, _p(centers, C.c_float), lloyd_iters,
+                              _p(labels, C.c_int32), C.byref(done))
     _check(st, "lloyd")
     return centers, labels, done.value
 
 
 def init_from_labels(pts, labels, K: int, reg: float):
     pts = _f32(pts)
+    d = _dim(pts)
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     N = pts.shape[0]
-    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
-    st = lib().oracle_init_from_labels(_p(pts, C.c_float), N, K, _p(labels, C.c_int32), reg, _p(w, C.c_double),
-                                       _p(m, C.c_double), _p(c, C.c_double))
+    w, m, c = np.empty(K), np.empty((K, d)), np.empty((K, d, d))
+    st = lib().oracle_init_from_labels_d(_p(pts, C.c_float), N, K, d, _p(labels, C.c_int32), reg,
+                                         _p(w, C.c_double), _p(m, C.c_double), _p(c, C.c_double))
     _check(st, "init_from_labels")
     return w, m, c
 
@@ -196,26 +230,28 @@ def init_from_labels(pts, labels, K: int, reg: float):
 def em(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-6):
     """EM from explicit parameters.  Returns a dict (weights, means, covs, trace, iters_done, final_ll)."""
     pts = _f32(pts)
+    d = _dim(pts)
     N = pts.shape[0]
     w, m, c = _f64(weights).copy(), _f64(means).copy(), _f64(covs).copy()
     K = w.shape[0]
     trace = np.full(max(iters, 1), np.nan)
     done, fll = C.c_int(), C.c_double()
-    st = lib().oracle_em(_p(pts, C.c_float), N, K, iters, tol, reg, _p(w, C.c_double), _p(m, C.c_double),
-                         _p(c, C.c_double), _p(trace, C.c_double), C.byref(done), C.byref(fll))
+    st = lib().oracle_em_d(_p(pts, C.c_float), N, K, d, iters, tol, reg, _p(w, C.c_double), _p(m, C.c_double),
+                           _p(c, C.c_double), _p(trace, C.c_double), C.byref(done), C.byref(fll))
     _check(st, "em")
     return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
 
 
 def gmm_fit(pts, K: int, iters: int, tol: float = 0.0, reg: float = 1e-6, seed: int = 0, lloyd_iters: int = 10):
     pts = _f32(pts)
+    d = _dim(pts)
     N = pts.shape[0]
-    w, m, c = np.empty(K), np.empty((K, 3)), np.empty((K, 3, 3))
+    w, m, c = np.empty(K), np.empty((K, d)), np.empty((K, d, d))
     trace = np.full(max(iters, 1), np.nan)
     done, fll = C.c_int(), C.c_double()
-    st = lib().oracle_gmm_fit(_p(pts, C.c_float), N, K, iters, tol, reg, seed, lloyd_iters, _p(w, C.c_double),
-                              _p(m, C.c_double), _p(c, C.c_double), _p(trace, C.c_double), C.byref(done),
-                              C.byref(fll))
+    st = lib().oracle_gmm_fit_d(_p(pts, C.c_float), N, K, d, iters, tol, reg, seed, lloyd_iters,
+                                _p(w, C.c_double), _p(m, C.c_double), _p(c, C.c_double), _p(trace, C.c_double),
+                                C.byref(done), C.byref(fll))
     _check(st, "gmm_fit")
     return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
 
@@ -226,6 +262,30 @@ def kinit(pts, K: int, seed: int, lloyd_iters: int, reg: float):
     centers, labels, done = lloyd(pts, centers, lloyd_iters)
     w, m, c = init_from_labels(pts, labels, K, reg)
     return dict(weights=w, means=m, covs=c, centers=centers, labels=labels, chosen=chosen, lloyd_done=done)
+
+
+def conditional4(locs, weights, means, covs):
+    """E[I | xyz] and V[I | xyz] of a D = 4 mixture at locs (M x 3): Gaussian-mixture regression."""
+    locs = _f32(locs)
+    M, K = locs.shape[0], len(weights)
+    w, m, c = _f64(weights), _f64(means).reshape(K, 4), _f64(covs).reshape(K, 16)
+    e, v = np.empty(M), np.empty(M)
+    st = lib().oracle_conditional4(_p(locs, C.c_float), M, K, _p(w, C.c_double), _p(m, C.c_double),
+                                   _p(c, C.c_double), _p(e, C.c_double), _p(v, C.c_double))
+    _check(st, "conditional4")
+    return e, v
+
+
+def sample(M: int, weights, means, covs, seed: int):
+    """M draws from the mixture (d from means): (points (M,d) float32, components (M,) int32)."""
+    w, m, c = _f64(weights), _f64(means), _f64(covs)
+    K, d = m.shape
+    out = np.empty((M, d), np.float32)
+    comp = np.empty(M, np.int32)
+    st = lib().oracle_sample_d(M, K, d, _p(w, C.c_double), _p(m, C.c_double), _p(c, C.c_double), seed,
+                               _p(out, C.c_float), _p(comp, C.c_int32))
+    _check(st, "sample")
+    return out, comp
 
 
 def loglik_grad(pts, logits, means, chol, pose=None, want_points: bool = True):

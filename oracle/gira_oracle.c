@@ -55,7 +55,6 @@
 #include <string.h>
 #include <float.h>
 
-#define D 3
 
 /* binary32 expressions must be evaluated in binary32 (no excess precision) */
 #if defined(__FLT_EVAL_METHOD__) && __FLT_EVAL_METHOD__ != 0
@@ -83,47 +82,53 @@ double oracle_uniform(uint64_t seed, uint64_t j) {
     return (double)(oracle_splitmix64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
 }
 
-/* ------------------------------------------------------ 3x3 algebra --- */
-/* Cholesky Sigma = L L^T (row-major, L lower).  Returns 0, or -1 if a pivot
- * is not strictly positive (Sigma not positive definite). */
-int oracle_cholesky3(const double *S, double *L) {
-    memset(L, 0, 9 * sizeof(double));
-    for (int j = 0; j < D; ++j) {
-        double s = S[j * D + j];
-        for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
+/* ----------------------------------------------- d x d algebra (d <= 4) -- */
+#define DMAX 4
+/* Cholesky Sigma = L L^T (row-major d x d, L lower).  Returns 0, or -1 if a
+ * pivot is not strictly positive (Sigma not positive definite). */
+int oracle_cholesky_d(const double *S, double *L, int d) {
+    memset(L, 0, (size_t)d * d * sizeof(double));
+    for (int j = 0; j < d; ++j) {
+        double s = S[j * d + j];
+        for (int k = 0; k < j; ++k) s -= L[j * d + k] * L[j * d + k];
         if (!(s > 0.0)) return -1;
-        L[j * D + j] = sqrt(s);
-        for (int i = j + 1; i < D; ++i) {
-            double t = S[i * D + j];
-            for (int k = 0; k < j; ++k) t -= L[i * D + k] * L[j * D + k];
-            L[i * D + j] = t / L[j * D + j];
+        L[j * d + j] = sqrt(s);
+        for (int i = j + 1; i < d; ++i) {
+            double t = S[i * d + j];
+            for (int k = 0; k < j; ++k) t -= L[i * d + k] * L[j * d + k];
+            L[i * d + j] = t / L[j * d + j];
         }
     }
     return 0;
 }
+int oracle_cholesky3(const double *S, double *L) { return oracle_cholesky_d(S, L, 3); }
 
 /* P = L^{-1} for lower-triangular L (forward substitution on the identity). */
-void oracle_tri_inverse3(const double *L, double *P) {
-    memset(P, 0, 9 * sizeof(double));
-    for (int c = 0; c < D; ++c) {
-        for (int i = c; i < D; ++i) {
+void oracle_tri_inverse_d(const double *L, double *P, int d) {
+    memset(P, 0, (size_t)d * d * sizeof(double));
+    for (int c = 0; c < d; ++c) {
+        for (int i = c; i < d; ++i) {
             double t = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) t -= L[i * D + k] * P[k * D + c];
-            P[i * D + c] = t / L[i * D + i];
+            for (int k = c; k < i; ++k) t -= L[i * d + k] * P[k * d + c];
+            P[i * d + c] = t / L[i * d + i];
         }
     }
 }
+void oracle_tri_inverse3(const double *L, double *P) { oracle_tri_inverse_d(L, P, 3); }
 
-/* Eq. (simplifiedGaussian): ln N(x | mu, Sigma) with P = L^{-1}. */
-double oracle_log_gaussian(const double *x, const double *mu, const double *P) {
+/* Eq. (simplifiedGaussian): ln N(x | mu, Sigma) with P = L^{-1}, dimension d. */
+double oracle_log_gaussian_d(const double *x, const double *mu, const double *P, int d) {
     double q = 0.0, logdet = 0.0;
-    for (int i = 0; i < D; ++i) {
+    for (int i = 0; i < d; ++i) {
         double y = 0.0;
-        for (int j = 0; j <= i; ++j) y += P[i * D + j] * (x[j] - mu[j]);
+        for (int j = 0; j <= i; ++j) y += P[i * d + j] * (x[j] - mu[j]);
         q += y * y;
-        logdet += log(P[i * D + i]);
+        logdet += log(P[i * d + i]);
     }
-    return -0.5 * (D * log(2.0 * M_PI) + q) + logdet;
+    return -0.5 * (d * log(2.0 * M_PI) + q) + logdet;
+}
+double oracle_log_gaussian(const double *x, const double *mu, const double *P) {
+    return oracle_log_gaussian_d(x, mu, P, 3);
 }
 
 static int all_finite_f(const float *a, int64_t n) {
@@ -138,36 +143,42 @@ static int all_finite_d(const double *a, int64_t n) {
 }
 
 /* Precision factors of every component: P_b = chol(Sigma_b)^{-1}. */
-static int precision_factors(int K, const double *covs, double *P) {
+static int precision_factors(int K, const double *covs, double *P, int d) {
+    const int dd = d * d;
     for (int b = 0; b < K; ++b) {
-        double L[9];
-        if (oracle_cholesky3(covs + 9 * b, L) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
-        oracle_tri_inverse3(L, P + 9 * b);
+        double L[DMAX * DMAX];
+        if (oracle_cholesky_d(covs + (size_t)dd * b, L, d) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
+        oracle_tri_inverse_d(L, P + (size_t)dd * b, d);
     }
     return OR_OK;
 }
 
+static int valid_dim(int d) { return d == 3 || d == 4; }
+
 /* ------------------------------------------------------------ E-step -- */
-/* Eq. (estep) in the form of Eq. (logestep).  Writes resp (N x K, row-major;
- * may be NULL) and lse_n = ln sum_a pi_a N(x_n|a) (may be NULL); returns the
- * mean per-point log-likelihood (1/N) sum_n lse_n in *mean_ll. */
-int oracle_estep(const float *pts, int64_t N, int K, const double *weights, const double *means,
-                 const double *covs, double *resp, double *lse, double *mean_ll) {
-    if (N < 1 || K < 1 || !pts || !weights || !means || !covs) return OR_ERR_INVALID_ARG;
-    if (!all_finite_f(pts, 3 * N)) return OR_ERR_NONFINITE;
-    if (!all_finite_d(weights, K) || !all_finite_d(means, 3 * K) || !all_finite_d(covs, 9 * K))
+/* Eq. (estep) in the form of Eq. (logestep), points of dimension d.  Writes
+ * resp (N x K, row-major; may be NULL) and lse_n = ln sum_a pi_a N(x_n|a) (may
+ * be NULL); returns the mean per-point log-likelihood (1/N) sum_n lse_n in
+ * *mean_ll. */
+int oracle_estep_d(const float *pts, int64_t N, int K, int d, const double *weights, const double *means,
+                   const double *covs, double *resp, double *lse, double *mean_ll) {
+    if (N < 1 || K < 1 || !valid_dim(d) || !pts || !weights || !means || !covs) return OR_ERR_INVALID_ARG;
+    const int dd = d * d;
+    if (!all_finite_f(pts, (int64_t)d * N)) return OR_ERR_NONFINITE;
+    if (!all_finite_d(weights, K) || !all_finite_d(means, (int64_t)d * K) || !all_finite_d(covs, (int64_t)dd * K))
         return OR_ERR_NONFINITE;
-    double *P = (double *)malloc(sizeof(double) * 9 * K);
+    double *P = (double *)malloc(sizeof(double) * dd * K);
     double *a = (double *)malloc(sizeof(double) * K);
     if (!P || !a) { free(P); free(a); return OR_ERR_OOM; }
-    int st = precision_factors(K, covs, P);
+    int st = precision_factors(K, covs, P, d);
     if (st != OR_OK) { free(P); free(a); return st; }
     double total = 0.0;
     for (int64_t n = 0; n < N; ++n) {
-        double x[3] = {pts[3 * n], pts[3 * n + 1], pts[3 * n + 2]};
+        double x[DMAX];
+        for (int i = 0; i < d; ++i) x[i] = pts[(size_t)d * n + i];
         double m = -INFINITY;
         for (int b = 0; b < K; ++b) {
-            a[b] = log(weights[b]) + oracle_log_gaussian(x, means + 3 * b, P + 9 * b);
+            a[b] = log(weights[b]) + oracle_log_gaussian_d(x, means + (size_t)d * b, P + (size_t)dd * b, d);
             if (a[b] > m) m = a[b];
         }
         double s = 0.0;
@@ -183,57 +194,71 @@ int oracle_estep(const float *pts, int64_t N, int K, const double *weights, cons
     free(a);
     return OR_OK;
 }
+int oracle_estep(const float *pts, int64_t N, int K, const double *weights, const double *means,
+                 const double *covs, double *resp, double *lse, double *mean_ll) {
+    return oracle_estep_d(pts, N, K, 3, weights, means, covs, resp, lse, mean_ll);
+}
 
 /* ------------------------------------------------------------ M-step -- */
-int oracle_mstep(const float *pts, int64_t N, int K, const double *resp, double reg, double *weights,
-                 double *means, double *covs) {
-    if (N < 1 || K < 1 || !pts || !resp || !weights || !means || !covs || !(reg >= 0.0))
+int oracle_mstep_d(const float *pts, int64_t N, int K, int d, const double *resp, double reg, double *weights,
+                   double *means, double *covs) {
+    if (N < 1 || K < 1 || !valid_dim(d) || !pts || !resp || !weights || !means || !covs || !(reg >= 0.0))
         return OR_ERR_INVALID_ARG;
+    const int dd = d * d;
     const double tiny = 10.0 * DBL_EPSILON;
     double nsum = 0.0;
     for (int b = 0; b < K; ++b) {
-        double nb = 0.0, sx[3] = {0, 0, 0};
+        double nb = 0.0, sx[DMAX] = {0, 0, 0, 0};
         for (int64_t n = 0; n < N; ++n) {
             double r = resp[n * K + b];
             nb += r;
-            for (int i = 0; i < 3; ++i) sx[i] += r * (double)pts[3 * n + i];
+            for (int i = 0; i < d; ++i) sx[i] += r * (double)pts[(size_t)d * n + i];
         }
         nb += tiny;
-        double mu[3];
-        for (int i = 0; i < 3; ++i) mu[i] = sx[i] / nb;
-        double c[9] = {0};
+        double mu[DMAX];
+        for (int i = 0; i < d; ++i) mu[i] = sx[i] / nb;
+        double c[DMAX * DMAX] = {0};
         for (int64_t n = 0; n < N; ++n) {
             double r = resp[n * K + b];
-            double d[3];
-            for (int i = 0; i < 3; ++i) d[i] = (double)pts[3 * n + i] - mu[i];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) c[i * 3 + j] += r * d[i] * d[j];
+            double dv[DMAX];
+            for (int i = 0; i < d; ++i) dv[i] = (double)pts[(size_t)d * n + i] - mu[i];
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) c[i * d + j] += r * dv[i] * dv[j];
         }
-        for (int i = 0; i < 9; ++i) c[i] /= nb;
-        for (int i = 0; i < 3; ++i) c[i * 3 + i] += reg;
+        for (int i = 0; i < dd; ++i) c[i] /= nb;
+        for (int i = 0; i < d; ++i) c[i * d + i] += reg;
         weights[b] = nb;
         nsum += nb;
-        memcpy(means + 3 * b, mu, sizeof mu);
-        memcpy(covs + 9 * b, c, sizeof c);
+        memcpy(means + (size_t)d * b, mu, sizeof(double) * d);
+        memcpy(covs + (size_t)dd * b, c, sizeof(double) * dd);
     }
     for (int b = 0; b < K; ++b) weights[b] /= nsum;
     /* the new covariances must admit a Cholesky factor for the next E-step */
     for (int b = 0; b < K; ++b) {
-        double L[9];
-        if (oracle_cholesky3(covs + 9 * b, L) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
+        double L[DMAX * DMAX];
+        if (oracle_cholesky_d(covs + (size_t)dd * b, L, d) != 0) { g_last_bad_component = b; return OR_ERR_NOT_PD; }
     }
     return OR_OK;
 }
+int oracle_mstep(const float *pts, int64_t N, int K, const double *resp, double reg, double *weights,
+                 double *means, double *covs) {
+    return oracle_mstep_d(pts, N, K, 3, resp, reg, weights, means, covs);
+}
 
 /* ------------------------------------------------------------ k-means -- */
-/* squared distance in binary32, fixed order, no FMA (see header) */
-static float dist2_f32(const float *x, const float *c) {
-    float d0 = x[0] - c[0], d1 = x[1] - c[1], d2 = x[2] - c[2];
-    float p0 = d0 * d0, p1 = d1 * d1, p2 = d2 * d2;
-    float s = p0 + p1;
-    return s + p2;
+/* squared distance in binary32, fixed order ((d0^2 + d1^2) + d2^2) + d3^2, no
+ * FMA (see header) */
+static float dist2_f32(const float *x, const float *c, int d) {
+    float s = 0.0f;
+    for (int i = 0; i < d; ++i) {
+        const float di = x[i] - c[i];
+        const float p = di * di;
+        s = (i == 0) ? p : s + p;
+    }
+    return s;
 }
-float oracle_dist2_f32(const float *x, const float *c) { return dist2_f32(x, c); }
+float oracle_dist2_f32(const float *x, const float *c) { return dist2_f32(x, c, 3); }
+float oracle_dist2_f32_d(const float *x, const float *c, int d) { return dist2_f32(x, c, d); }
 
 /* The k-means++ weights D^2 are taken in exact fixed point so that the draw is
  * an integer decision with no rounding: fx(d) = floor(d * 2^48) for a binary32
@@ -274,10 +299,10 @@ void oracle_fx48_parts(float d, uint64_t *lo, uint64_t *hi) {
 }
 
 /* k-means++ seeding (Arthur & Vassilvitskii 2007, one candidate per step).
- * centers: K x 3 float (out); chosen: K indices into pts (out, may be NULL). */
-int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *centers, int64_t *chosen) {
-    if (N < 1 || K < 1 || K > N || !pts || !centers) return OR_ERR_INVALID_ARG;
-    if (!all_finite_f(pts, 3 * N)) return OR_ERR_NONFINITE;
+ * centers: K x d float (out); chosen: K indices into pts (out, may be NULL). */
+int oracle_kmeanspp_d(const float *pts, int64_t N, int K, int d, uint64_t seed, float *centers, int64_t *chosen) {
+    if (N < 1 || K < 1 || K > N || !valid_dim(d) || !pts || !centers) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, (int64_t)d * N)) return OR_ERR_NONFINITE;
     float *d2 = (float *)malloc(sizeof(float) * N);
     if (!d2) return OR_ERR_OOM;
     int64_t idx = (int64_t)floor(oracle_uniform(seed, 0) * (double)N);
@@ -287,7 +312,7 @@ int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *ce
             /* D^2(x) = min over the centres chosen so far */
             u128 total = 0;
             for (int64_t n = 0; n < N; ++n) {
-                float dn = dist2_f32(pts + 3 * n, centers + 3 * (j - 1));
+                float dn = dist2_f32(pts + (size_t)d * n, centers + (size_t)d * (j - 1), d);
                 if (j == 1 || dn < d2[n]) d2[n] = dn;
                 total += oracle_fx48(d2[n]);
             }
@@ -304,22 +329,25 @@ int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *ce
                 if (idx > N - 1) idx = N - 1;
             }
         }
-        for (int i = 0; i < 3; ++i) centers[3 * j + i] = pts[3 * idx + i];
+        for (int i = 0; i < d; ++i) centers[(size_t)d * j + i] = pts[(size_t)d * idx + i];
         if (chosen) chosen[j] = idx;
     }
     free(d2);
     return OR_OK;
 }
+int oracle_kmeanspp(const float *pts, int64_t N, int K, uint64_t seed, float *centers, int64_t *chosen) {
+    return oracle_kmeanspp_d(pts, N, K, 3, seed, centers, chosen);
+}
 
 /* labels_n = argmin_b ||x_n - c_b||^2 in binary32, ties to the lowest b. */
-static int64_t assign_labels(const float *pts, int64_t N, int K, const float *centers, int32_t *labels) {
+static int64_t assign_labels(const float *pts, int64_t N, int K, int d, const float *centers, int32_t *labels) {
     int64_t changed = 0;
     for (int64_t n = 0; n < N; ++n) {
         int best = 0;
-        float bd = dist2_f32(pts + 3 * n, centers);
+        float bd = dist2_f32(pts + (size_t)d * n, centers, d);
         for (int b = 1; b < K; ++b) {
-            float d = dist2_f32(pts + 3 * n, centers + 3 * b);
-            if (d < bd) { bd = d; best = b; }
+            float dv = dist2_f32(pts + (size_t)d * n, centers + (size_t)d * b, d);
+            if (dv < bd) { bd = dv; best = b; }
         }
         if (labels[n] != best) ++changed;
         labels[n] = best;
@@ -331,36 +359,43 @@ static int64_t assign_labels(const float *pts, int64_t N, int K, const float *ce
  * = FP64 mean of their points (rounded to binary32; an empty cluster keeps its
  * centre), then re-assign; stop after lloyd_iters or when no label changed.
  * labels (out, N) hold the final assignment. */
-int oracle_lloyd(const float *pts, int64_t N, int K, float *centers, int lloyd_iters, int32_t *labels,
-                 int *iters_done) {
-    if (N < 1 || K < 1 || K > N || lloyd_iters < 0 || !pts || !centers || !labels) return OR_ERR_INVALID_ARG;
-    if (!all_finite_f(pts, 3 * N) || !all_finite_f(centers, 3 * K)) return OR_ERR_NONFINITE;
+int oracle_lloyd_d(const float *pts, int64_t N, int K, int d, float *centers, int lloyd_iters, int32_t *labels,
+                   int *iters_done) {
+    if (N < 1 || K < 1 || K > N || !valid_dim(d) || lloyd_iters < 0 || !pts || !centers || !labels)
+        return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, (int64_t)d * N) || !all_finite_f(centers, (int64_t)d * K)) return OR_ERR_NONFINITE;
     for (int64_t n = 0; n < N; ++n) labels[n] = -1;
-    assign_labels(pts, N, K, centers, labels);
-    double *sum = (double *)malloc(sizeof(double) * 4 * K);
+    assign_labels(pts, N, K, d, centers, labels);
+    const int w = d + 1;   /* coordinate sums, then the count */
+    double *sum = (double *)malloc(sizeof(double) * w * K);
     if (!sum) return OR_ERR_OOM;
     int it = 0;
     while (it < lloyd_iters) {
-        memset(sum, 0, sizeof(double) * 4 * K);
+        memset(sum, 0, sizeof(double) * w * K);
         for (int64_t n = 0; n < N; ++n) {
             int b = labels[n];
-            for (int i = 0; i < 3; ++i) sum[4 * b + i] += (double)pts[3 * n + i];
-            sum[4 * b + 3] += 1.0;
+            for (int i = 0; i < d; ++i) sum[(size_t)w * b + i] += (double)pts[(size_t)d * n + i];
+            sum[(size_t)w * b + d] += 1.0;
         }
         for (int b = 0; b < K; ++b)
-            if (sum[4 * b + 3] > 0.0)
-                for (int i = 0; i < 3; ++i) centers[3 * b + i] = (float)(sum[4 * b + i] / sum[4 * b + 3]);
+            if (sum[(size_t)w * b + d] > 0.0)
+                for (int i = 0; i < d; ++i)
+                    centers[(size_t)d * b + i] = (float)(sum[(size_t)w * b + i] / sum[(size_t)w * b + d]);
         ++it;
-        if (assign_labels(pts, N, K, centers, labels) == 0) break;
+        if (assign_labels(pts, N, K, d, centers, labels) == 0) break;
     }
     if (iters_done) *iters_done = it;
     free(sum);
     return OR_OK;
 }
+int oracle_lloyd(const float *pts, int64_t N, int K, float *centers, int lloyd_iters, int32_t *labels,
+                 int *iters_done) {
+    return oracle_lloyd_d(pts, N, K, 3, centers, lloyd_iters, labels, iters_done);
+}
 
 /* One-hot responsibilities from labels, then the M-step. */
-int oracle_init_from_labels(const float *pts, int64_t N, int K, const int32_t *labels, double reg,
-                            double *weights, double *means, double *covs) {
+int oracle_init_from_labels_d(const float *pts, int64_t N, int K, int d, const int32_t *labels, double reg,
+                              double *weights, double *means, double *covs) {
     if (N < 1 || K < 1 || !labels) return OR_ERR_INVALID_ARG;
     double *resp = (double *)calloc((size_t)N * (size_t)K, sizeof(double));
     if (!resp) return OR_ERR_OOM;
@@ -368,9 +403,13 @@ int oracle_init_from_labels(const float *pts, int64_t N, int K, const int32_t *l
         if (labels[n] < 0 || labels[n] >= K) { free(resp); return OR_ERR_INVALID_ARG; }
         resp[n * K + labels[n]] = 1.0;
     }
-    int st = oracle_mstep(pts, N, K, resp, reg, weights, means, covs);
+    int st = oracle_mstep_d(pts, N, K, d, resp, reg, weights, means, covs);
     free(resp);
     return st;
+}
+int oracle_init_from_labels(const float *pts, int64_t N, int K, const int32_t *labels, double reg,
+                            double *weights, double *means, double *covs) {
+    return oracle_init_from_labels_d(pts, N, K, 3, labels, reg, weights, means, covs);
 }
 
 /* ------------------------------------------------------------ EM fit -- */
@@ -379,18 +418,18 @@ int oracle_init_from_labels(const float *pts, int64_t N, int K, const int32_t *l
  * trace[t-1]), then the M-step.  Stops after `iters` iterations or when
  * t > 1 and |ll_t - ll_{t-1}| < tol.  final_ll (may be NULL) is the mean
  * log-likelihood of the returned parameters. */
-int oracle_em(const float *pts, int64_t N, int K, int iters, double tol, double reg, double *weights,
-              double *means, double *covs, double *trace, int *iters_done, double *final_ll) {
-    if (N < 1 || K < 1 || iters < 0 || !(tol >= 0.0) || !(reg >= 0.0)) return OR_ERR_INVALID_ARG;
+int oracle_em_d(const float *pts, int64_t N, int K, int d, int iters, double tol, double reg, double *weights,
+                double *means, double *covs, double *trace, int *iters_done, double *final_ll) {
+    if (N < 1 || K < 1 || !valid_dim(d) || iters < 0 || !(tol >= 0.0) || !(reg >= 0.0)) return OR_ERR_INVALID_ARG;
     double *resp = (double *)malloc(sizeof(double) * (size_t)N * (size_t)K);
     if (!resp) return OR_ERR_OOM;
     double prev = -INFINITY;
     int t = 0, st = OR_OK;
     while (t < iters) {
         double ll;
-        st = oracle_estep(pts, N, K, weights, means, covs, resp, NULL, &ll);
+        st = oracle_estep_d(pts, N, K, d, weights, means, covs, resp, NULL, &ll);
         if (st != OR_OK) break;
-        st = oracle_mstep(pts, N, K, resp, reg, weights, means, covs);
+        st = oracle_mstep_d(pts, N, K, d, resp, reg, weights, means, covs);
         if (st != OR_OK) break;
         if (trace) trace[t] = ll;
         ++t;
@@ -398,26 +437,36 @@ int oracle_em(const float *pts, int64_t N, int K, int iters, double tol, double 
         prev = ll;
     }
     if (iters_done) *iters_done = t;
-    if (st == OR_OK && final_ll) st = oracle_estep(pts, N, K, weights, means, covs, NULL, NULL, final_ll);
+    if (st == OR_OK && final_ll) st = oracle_estep_d(pts, N, K, d, weights, means, covs, NULL, NULL, final_ll);
     free(resp);
     return st;
 }
+int oracle_em(const float *pts, int64_t N, int K, int iters, double tol, double reg, double *weights,
+              double *means, double *covs, double *trace, int *iters_done, double *final_ll) {
+    return oracle_em_d(pts, N, K, 3, iters, tol, reg, weights, means, covs, trace, iters_done, final_ll);
+}
 
 /* Full fit: k-means++ (seed) + Lloyd (lloyd_iters) + init M-step, then EM. */
-int oracle_gmm_fit(const float *pts, int64_t N, int K, int iters, double tol, double reg, uint64_t seed,
-                   int lloyd_iters, double *weights, double *means, double *covs, double *trace,
-                   int *iters_done, double *final_ll) {
-    if (N < 1 || K < 1 || K > N) return OR_ERR_INVALID_ARG;
-    float *c = (float *)malloc(sizeof(float) * 3 * K);
+int oracle_gmm_fit_d(const float *pts, int64_t N, int K, int d, int iters, double tol, double reg, uint64_t seed,
+                     int lloyd_iters, double *weights, double *means, double *covs, double *trace,
+                     int *iters_done, double *final_ll) {
+    if (N < 1 || K < 1 || K > N || !valid_dim(d)) return OR_ERR_INVALID_ARG;
+    float *c = (float *)malloc(sizeof(float) * d * K);
     int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * N);
     if (!c || !lab) { free(c); free(lab); return OR_ERR_OOM; }
-    int st = oracle_kmeanspp(pts, N, K, seed, c, NULL);
-    if (st == OR_OK) st = oracle_lloyd(pts, N, K, c, lloyd_iters, lab, NULL);
-    if (st == OR_OK) st = oracle_init_from_labels(pts, N, K, lab, reg, weights, means, covs);
+    int st = oracle_kmeanspp_d(pts, N, K, d, seed, c, NULL);
+    if (st == OR_OK) st = oracle_lloyd_d(pts, N, K, d, c, lloyd_iters, lab, NULL);
+    if (st == OR_OK) st = oracle_init_from_labels_d(pts, N, K, d, lab, reg, weights, means, covs);
     free(c);
     free(lab);
     if (st != OR_OK) return st;
-    return oracle_em(pts, N, K, iters, tol, reg, weights, means, covs, trace, iters_done, final_ll);
+    return oracle_em_d(pts, N, K, d, iters, tol, reg, weights, means, covs, trace, iters_done, final_ll);
+}
+int oracle_gmm_fit(const float *pts, int64_t N, int K, int iters, double tol, double reg, uint64_t seed,
+                   int lloyd_iters, double *weights, double *means, double *covs, double *trace,
+                   int *iters_done, double *final_ll) {
+    return oracle_gmm_fit_d(pts, N, K, 3, iters, tol, reg, seed, lloyd_iters, weights, means, covs, trace,
+                            iters_done, final_ll);
 }
 
 /* ------------------------------------------------ differentiable loglik -- */
@@ -521,5 +570,111 @@ int oracle_loglik_grad(const float *pts, int64_t N, int K, const double *pose12,
         for (int b = 0; b < K; ++b) grad_logits[b] -= (double)N * exp(logits[b] - lz);
     if (loglik) *loglik = total;
     free(logw); free(gam); free(lgam);
+    return OR_OK;
+}
+
+/* --------------------------------------- 4D mixtures: conditional, sampling -- */
+/* Gaussian-mixture regression of the last coordinate on the first three for a
+ * D = 4 mixture (xyz + intensity): with mu_b = (mu_x, mu_I) and Sigma_b split
+ * as [[S_xx, S_xI], [S_Ix, S_II]], the conditional of I given x under component
+ * b is normal with mean m_b = mu_I + S_Ix S_xx^{-1} (x - mu_x) and variance
+ * v_b = S_II - S_Ix S_xx^{-1} S_xI; the mixture weight of b given x is
+ * w_b ∝ pi_b N(x | mu_x, S_xx).  E[I|x] = sum_b w_b m_b,
+ * V[I|x] = sum_b w_b (v_b + m_b^2) - E[I|x]^2.  locs: M x 3. */
+int oracle_conditional4(const float *locs, int64_t M, int K, const double *weights, const double *means,
+                        const double *covs, double *cmean, double *cvar) {
+    if (M < 1 || K < 1 || !locs || !weights || !means || !covs || !cmean || !cvar) return OR_ERR_INVALID_ARG;
+    double *P = (double *)malloc(sizeof(double) * 9 * K), *g = (double *)malloc(sizeof(double) * 3 * K);
+    double *v = (double *)malloc(sizeof(double) * K), *a = (double *)malloc(sizeof(double) * K);
+    if (!P || !g || !v || !a) { free(P); free(g); free(v); free(a); return OR_ERR_OOM; }
+    for (int b = 0; b < K; ++b) {
+        const double *S = covs + 16 * (size_t)b;
+        const double Sxx[9] = {S[0], S[1], S[2], S[4], S[5], S[6], S[8], S[9], S[10]};
+        const double SxI[3] = {S[3], S[7], S[11]};
+        double L[9];
+        if (oracle_cholesky_d(Sxx, L, 3) != 0) {
+            g_last_bad_component = b;
+            free(P); free(g); free(v); free(a);
+            return OR_ERR_NOT_PD;
+        }
+        oracle_tri_inverse_d(L, P + 9 * (size_t)b, 3);
+        /* g_b = S_xx^{-1} S_xI = P^T P S_xI */
+        const double *Pb = P + 9 * (size_t)b;
+        double u[3];
+        for (int i = 0; i < 3; ++i) u[i] = Pb[3 * i] * SxI[0] + Pb[3 * i + 1] * SxI[1] + Pb[3 * i + 2] * SxI[2];
+        for (int i = 0; i < 3; ++i) g[3 * b + i] = Pb[i] * u[0] + Pb[3 + i] * u[1] + Pb[6 + i] * u[2];
+        v[b] = S[15] - (SxI[0] * g[3 * b] + SxI[1] * g[3 * b + 1] + SxI[2] * g[3 * b + 2]);
+    }
+    for (int64_t n = 0; n < M; ++n) {
+        const double x[3] = {locs[3 * n], locs[3 * n + 1], locs[3 * n + 2]};
+        double m = -INFINITY;
+        for (int b = 0; b < K; ++b) {
+            const double *mu = means + 4 * (size_t)b;
+            a[b] = log(weights[b]) + oracle_log_gaussian_d(x, mu, P + 9 * (size_t)b, 3);
+            if (a[b] > m) m = a[b];
+        }
+        double s = 0.0;
+        for (int b = 0; b < K; ++b) s += exp(a[b] - m);
+        double e1 = 0.0, e2 = 0.0;
+        for (int b = 0; b < K; ++b) {
+            const double *mu = means + 4 * (size_t)b;
+            const double w = exp(a[b] - m) / s;
+            const double mb = mu[3] + g[3 * b] * (x[0] - mu[0]) + g[3 * b + 1] * (x[1] - mu[1]) +
+                              g[3 * b + 2] * (x[2] - mu[2]);
+            e1 += w * mb;
+            e2 += w * (v[b] + mb * mb);
+        }
+        cmean[n] = e1;
+        cvar[n] = e2 - e1 * e1;
+    }
+    free(P); free(g); free(v); free(a);
+    return OR_OK;
+}
+
+/* Draw M points from a d-dimensional mixture.  Sample i takes the uniforms of
+ * draws 5i .. 5i+4 of `seed`: the first picks the component (the first b whose
+ * running binary64 weight sum exceeds u * sum_a pi_a), the other four give four
+ * standard normals by the Box-Muller transform, z = sqrt(-2 ln(1 - u1)) *
+ * (cos, sin)(2 pi u2) for the pairs (u1, u2) = (5i+1, 5i+2) and (5i+3, 5i+4);
+ * x = mu_b + L_b z (L_b = chol Sigma_b), rounded to binary32.  comp (may be
+ * NULL) receives the component of each sample. */
+int oracle_sample_d(int64_t M, int K, int d, const double *weights, const double *means, const double *covs,
+                    uint64_t seed, float *out, int32_t *comp) {
+    if (M < 1 || K < 1 || !valid_dim(d) || !weights || !means || !covs || !out) return OR_ERR_INVALID_ARG;
+    const int dd = d * d;
+    double *L = (double *)malloc(sizeof(double) * dd * K), *cum = (double *)malloc(sizeof(double) * K);
+    if (!L || !cum) { free(L); free(cum); return OR_ERR_OOM; }
+    double tot = 0.0;
+    for (int b = 0; b < K; ++b) {
+        if (oracle_cholesky_d(covs + (size_t)dd * b, L + (size_t)dd * b, d) != 0 || !(weights[b] >= 0.0)) {
+            g_last_bad_component = b;
+            free(L); free(cum);
+            return OR_ERR_NOT_PD;
+        }
+        tot += weights[b];
+        cum[b] = tot;
+    }
+    for (int64_t i = 0; i < M; ++i) {
+        const double u0 = oracle_uniform(seed, 5 * (uint64_t)i) * tot;
+        int b = K - 1;
+        for (int a = 0; a < K; ++a)
+            if (cum[a] > u0) { b = a; break; }
+        double z[4];
+        for (int p = 0; p < 2; ++p) {
+            const double u1 = oracle_uniform(seed, 5 * (uint64_t)i + 1 + 2 * p);
+            const double u2 = oracle_uniform(seed, 5 * (uint64_t)i + 2 + 2 * p);
+            const double r = sqrt(-2.0 * log(1.0 - u1));
+            z[2 * p] = r * cos(2.0 * M_PI * u2);
+            z[2 * p + 1] = r * sin(2.0 * M_PI * u2);
+        }
+        const double *Lb = L + (size_t)dd * b, *mu = means + (size_t)d * b;
+        for (int r = 0; r < d; ++r) {
+            double x = mu[r];
+            for (int c = 0; c <= r; ++c) x += Lb[r * d + c] * z[c];
+            out[(size_t)d * i + r] = (float)x;
+        }
+        if (comp) comp[i] = b;
+    }
+    free(L); free(cum);
     return OR_OK;
 }

@@ -170,6 +170,51 @@ def depth_frame(seed: int = 1, n_objects: int = 20, noise_sigma: float = 0.005, 
     return DepthFrame(pts.astype(np.float32), depth, float(np.rad2deg(pitch)))
 
 
+def gmm_cloud4(n: int = 20_000, k: int = 8, seed: int = 0, lam_lo: float = 1e-4, lam_hi: float = 1e-2,
+               box: float = 2.0) -> GMMCloud:
+    """xyz + intensity: ``n`` points from a random K-component full-covariance 4D GMM
+    (means uniform in [-box, box]^3 x [0, 1], Haar-rotated covariances with
+    eigenvalues log-uniform in [lam_lo, lam_hi], so intensity correlates with
+    position inside each component)."""
+    rng = np.random.default_rng(seed)
+    means = np.concatenate([rng.uniform(-box, box, size=(k, 3)), rng.uniform(0, 1, size=(k, 1))], axis=1)
+    covs = np.empty((k, 4, 4))
+    factors = np.empty((k, 4, 4))
+    for b in range(k):
+        q, r = np.linalg.qr(rng.standard_normal((4, 4)))
+        rot = q * np.sign(np.diag(r))[None, :]
+        lam = np.exp(rng.uniform(np.log(lam_lo), np.log(lam_hi), size=4))
+        covs[b] = (rot * lam[None, :]) @ rot.T
+        factors[b] = rot * np.sqrt(lam)[None, :]
+    weights = rng.dirichlet(np.ones(k))
+    counts = rng.multinomial(n, weights)
+    pts = np.empty((n, 4))
+    labels = np.empty(n, dtype=np.int32)
+    at = 0
+    for b in range(k):
+        c = int(counts[b])
+        pts[at:at + c] = means[b] + rng.standard_normal((c, 4)) @ factors[b].T
+        labels[at:at + c] = b
+        at += c
+    perm = rng.permutation(n)
+    return GMMCloud(pts[perm].astype(np.float32), weights, means, covs, labels[perm])
+
+
+def frame_intensity(pts: np.ndarray, seed: int = 1, noise_sigma: float = 0.01) -> np.ndarray:
+    """An intensity channel for a depth frame (the paper fits xyz + intensity): a smooth
+    procedural texture of the 3D position plus N(0, noise_sigma), in [0, 1]."""
+    rng = np.random.default_rng(seed + 7919)
+    x, y, z = pts[:, 0].astype(np.float64), pts[:, 1].astype(np.float64), pts[:, 2].astype(np.float64)
+    tex = 0.5 + 0.25 * np.sin(3.0 * x) * np.cos(2.0 * y) + 0.15 * np.sin(1.3 * z + 0.5 * x) - 0.02 * z
+    return np.clip(tex + rng.normal(0.0, noise_sigma, size=len(pts)), 0.0, 1.0).astype(np.float32)
+
+
+def depth_frame4(seed: int = 1) -> np.ndarray:
+    """The depth frame's points with an intensity channel: N x 4 float32."""
+    pts = depth_frame(seed=seed).points
+    return np.concatenate([pts, frame_intensity(pts, seed)[:, None]], axis=1)
+
+
 def uniform_cloud(n: int, seed: int = 0, scale: float = 1.0) -> np.ndarray:
     """Plain uniform points in a cube (edge cases, ragged sizes)."""
     rng = np.random.default_rng(seed)

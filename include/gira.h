@@ -232,6 +232,62 @@ gira_status gira_gmm_loglik_grad_batched(const float *points, const int64_t *off
                                          float *grad_chol, int *statuses, void *stream);
 
 /*
+ * Four dimensions: position and intensity (the paper's (1,K,D) / (1,K,D,D)
+ * model layout with D = 4, as in its SOGMM intensity data).
+ *
+ * gira_gmm_fit4 -- gira_gmm_fit for N x 4 binary32 points (x, y, z, intensity),
+ * rows contiguous.  The same KInit (k-means++ and Lloyd with squared distances
+ * over all four coordinates, binary32 in the order ((d0^2 + d1^2) + d2^2) + d3^2),
+ * the same E-step (Eq. estep / logestep with the log-density of
+ * Eq. simplifiedGaussian for D = 4) and M-step, the same opts and stopping rule.
+ * k <= GIRA_MAX_K4.
+ *   weights [host|device] K binary32, means K x 4, covs K x 4 x 4 (row-major;
+ *   the lower triangle is read when GIRA_INIT_PARAMS), written on return.
+ */
+#define GIRA_MAX_K4 1024
+gira_status gira_gmm_fit4(const float *points, int64_t n, int k, const gira_fit_opts *opts, float *weights,
+                          float *means, float *covs, double *loglik_trace, int *iters_done, double *final_loglik,
+                          void *stream);
+
+/* gira_gmm_loglik4 -- gira_gmm_loglik for N x 4 points and a D = 4 mixture (k <= GIRA_MAX_K4). */
+gira_status gira_gmm_loglik4(const float *points, int64_t n, int k, const float *weights, const float *means,
+                             const float *covs, double *mean_loglik, float *per_point, void *stream);
+
+/*
+ * gira_gmm_conditional4 -- Gaussian-mixture regression of the 4th coordinate
+ * (intensity) on the first three at M query positions (Sec. IV: intensity
+ * inferred from the joint model at any resolution).  With the blocks
+ * Sigma_b = [[S_xx, S_xI], [S_Ix, S_II]]:
+ *   w_b(x)  proportional to pi_b N(x | mu_b,xyz, S_xx)          (normalised over b)
+ *   m_b(x)  = mu_b,I + S_Ix S_xx^{-1} (x - mu_b,xyz),  v_b = S_II - S_Ix S_xx^{-1} S_xI
+ *   mean(x) = sum_b w_b m_b,  var(x) = sum_b w_b (v_b + m_b^2) - mean(x)^2.
+ *
+ *   locs         [host|device] M x 3 binary32
+ *   weights      [host|device] K binary32 (> 0), means K x 4, covs K x 4 x 4 (lower triangle read)
+ *   cond_mean    [host|device] M binary32 (written)
+ *   cond_var     [host|device] M binary32 (written), or NULL
+ */
+gira_status gira_gmm_conditional4(const float *locs, int64_t m, int k, const float *weights, const float *means,
+                                  const float *covs, float *cond_mean, float *cond_var, void *stream);
+
+/*
+ * gira_gmm_sample -- M draws from a d-dimensional mixture (d = 3 or 4; Sec. IV:
+ * resampling a point cloud from the model).  Sample i takes draws 5i .. 5i+4 of
+ * the SplitMix64 counter stream of `seed` (top 53 bits / 2^53): the first picks
+ * the component, the first b whose running binary64 sum of weights exceeds
+ * u * sum_a pi_a; the others give four standard normals by the Box-Muller
+ * transform, z = sqrt(-2 ln(1 - u1)) (cos, sin)(2 pi u2) for (u1, u2) = draws
+ * (5i+1, 5i+2) and (5i+3, 5i+4); x = mu_b + L_b z with L_b the binary64
+ * Cholesky factor of Sigma_b, rounded to binary32.
+ *
+ *   weights      [host|device] K binary32 (>= 0, not all zero), means K x d, covs K x d x d
+ *   out          [host|device] M x d binary32 (written)
+ *   components   [host|device] M int32 (written), or NULL
+ */
+gira_status gira_gmm_sample(int64_t m, int k, int d, const float *weights, const float *means, const float *covs,
+                            uint64_t seed, float *out, int32_t *components, void *stream);
+
+/*
  * Profiling (off by default; process-wide).  When enabled, each call records
  * CUDA events on its stream around its phases and around every launch of the
  * fused E-step/statistics kernel, and accumulates the device times below when

@@ -30,56 +30,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float LN2F = 0.693147180559945309f;
 constexpr double LN2 = 0.693147180559945309417232121458;
 
-struct AddOp {
-    __device__ __forceinline__ float operator()(float a, float b) const { return a + b; }
-};
-struct MaxOp {
-    __device__ __forceinline__ float operator()(float a, float b) const { return fmaxf(a, b); }
-};
-
-// Per-lane batch index owned after the transpose-reduce: Q = 8 -> bits 4..2 of
-// the lane, Q = 4 -> bits 4..3.  The owner of index q is lane q * (32 / Q).
-template <int Q>
-__device__ __forceinline__ int q_of_lane(int lane) {
-    return Q == 8 ? (lane >> 2) & 7 : (lane >> 3) & 3;
-}
-
-// Combine Q per-lane values over the 32 lanes of a warp.  On return, lane l
-// holds the combination for index q_of_lane<Q>(l); the order of combination is
-// fixed, and the lanes sharing an index hold bit-identical results.
-template <int Q, class Op>
-__device__ __forceinline__ float warp_transpose_reduce(const float (&v)[Q], int lane, Op op) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float w[Q / 2];
-#pragma unroll
-    for (int i = 0; i < Q / 2; ++i) {
-        const float send = b4 ? v[i] : v[i + Q / 2];
-        const float keep = b4 ? v[i + Q / 2] : v[i];
-        w[i] = op(keep, __shfl_xor_sync(FULL, send, 16));
-    }
-    float t;
-    if (Q == 8) {
-        float z[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = b3 ? w[i] : w[i + 2];
-            const float keep = b3 ? w[i + 2] : w[i];
-            z[i] = op(keep, __shfl_xor_sync(FULL, send, 8));
-        }
-        const float send = b2 ? z[0] : z[1];
-        const float keep = b2 ? z[1] : z[0];
-        t = op(keep, __shfl_xor_sync(FULL, send, 4));
-    } else {
-        const float send = b3 ? w[0] : w[1];
-        const float keep = b3 ? w[1] : w[0];
-        t = op(keep, __shfl_xor_sync(FULL, send, 8));
-        t = op(t, __shfl_xor_sync(FULL, t, 4));
-    }
-    t = op(t, __shfl_xor_sync(FULL, t, 2));
-    t = op(t, __shfl_xor_sync(FULL, t, 1));
-    return t;
-}
-
 // Log-density in base 2 for a component pair and one point (pairs packed).
 struct PairParams {
     float2 p[6], b[3], c, nmu[3], w;

@@ -1656,4 +1656,387 @@ gira_status gira_gmm_loglik_grad_batched(const float* points, const int64_t* off
     return GIRA_OK;
 }
 
+
+// ================================================================ four dimensions
+namespace {
+gira_status check_nk4(int64_t n, int k) {
+    if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "n = %lld < 1", (long long)n);
+    if (k < 1 || k > GIRA_MAX_K4) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K4);
+    if (k > n) return fail(GIRA_ERR_INVALID_ARG, "k = %d > n = %lld", k, (long long)n);
+    return GIRA_OK;
+}
+}  // namespace
+
+gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_opts* opts, float* weights,
+                          float* means, float* covs, double* loglik_trace, int* iters_done, double* final_loglik,
+                          void* stream) {
+    reset_error();
+    if (!opts) return fail(GIRA_ERR_INVALID_ARG, "opts is NULL");
+    TRY(check_nk4(n, k));
+    const gira_fit_opts o = *opts;
+    TRY(check_opts(o));
+    if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kw, km, kc;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
+    const int kpad = estep4_threads(k);
+    int64_t ppc = 0;
+    const int grid = estep4_grid(n, k, c.sms, &ppc);
+    const int nblk = kpp_num_blocks(n);
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
+        float4 *p4, *c4;
+        double *model64, *stats64, *llp, *trace, *sums;
+        u128* bs;
+        int64_t* ch;
+        int32_t* lab;
+        unsigned long long* chg;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(kp == Kind::Host ? 4 * n : 0);
+        b.p4 = cv.take<float4>(n);
+        b.params = cv.take<float>((size_t)kpad * COMP4_FLOATS);
+        b.model64 = cv.take<double>((size_t)k * MODEL4);
+        b.stats64 = cv.take<double>((size_t)k * NSTAT4);
+        b.partials = cv.take<float>((size_t)grid * k * NSTAT4);
+        b.llp = cv.take<double>(grid);
+        b.trace = cv.take<double>(std::max(o.iters, 1));
+        b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
+        b.mmu = cv.take<float>(km == Kind::Host ? 4 * (size_t)k : 0);
+        b.mcov = cv.take<float>(kc == Kind::Host ? 16 * (size_t)k : 0);
+        if (kinit) {
+            b.c4 = cv.take<float4>(k);
+            b.d2 = cv.take<float>(n);
+            b.bs = cv.take<u128>(nblk);
+            b.ch = cv.take<int64_t>(k);
+            b.lab = cv.take<int32_t>(n);
+            b.sums = cv.take<double>(5 * (size_t)k);
+            b.chg = cv.take<unsigned long long>(o.lloyd_iters + 1);
+        }
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.stop_after = o.iters;
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemsetAsync(b.trace, 0xff, sizeof(double) * std::max(o.iters, 1), c.s));   // NaN
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    COUNTED(prof, 1, launch_pack4(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding4(b.params, k, c.s));
+    float* w_d = (kw == Kind::Device) ? weights : b.mw;
+    float* mu_d = (km == Kind::Device) ? means : b.mmu;
+    float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
+    if (kinit) {
+        COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s, 4));
+        GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 5 * k, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * (o.lloyd_iters + 1), c.s));
+        COUNTED(prof, 1 + 2 * o.lloyd_iters, launch_lloyd4(b.p4, n, k, o.lloyd_iters, b.c4, b.lab, b.sums, b.chg,
+                                                          b.st, c.s));
+        GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT4 * k, c.s));
+        COUNTED(prof, 1, launch_label_stats4(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize4(nullptr, 0, nullptr, b.stats64, b.c4, k, n, o.reg_covar, o.tol,
+                                                 b.model64, b.params, b.trace, b.st, 0, false, c.s));
+    } else {
+        if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
+        if (km == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 4 * k, cudaMemcpyHostToDevice, c.s));
+        if (kc == Kind::Host)
+            GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 16 * k, cudaMemcpyHostToDevice, c.s));
+        COUNTED(prof, 1, launch_params_from_model4(w_d, mu_d, cov_d, k, b.model64, b.params, b.st, c.s));
+    }
+    prof.t_init = prof.mark();
+    EStep4Launch a{b.p4, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
+    for (int t = 1; t <= o.iters; ++t) {
+        a.iter = t;
+        cudaEvent_t e0 = prof.mark();
+        COUNTED(prof, 1, launch_estep4(a, true, grid, c.s));
+        cudaEvent_t e1 = prof.mark();
+        if (prof.on) prof.estep.emplace_back(e0, e1);
+        COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, b.llp, nullptr, nullptr, k, n, o.reg_covar, o.tol,
+                                                 b.model64, b.params, b.trace, b.st, t, true, c.s));
+    }
+    prof.t_em = prof.mark();
+    if (final_loglik) {
+        EStep4Launch f = a;
+        f.iter = 0;
+        f.partials = nullptr;
+        COUNTED(prof, 1, launch_estep4(f, false, grid, c.s));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    }
+    COUNTED(prof, 1, launch_model_out4(b.model64, k, w_d, mu_d, cov_d, b.st, c.s));
+    if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
+    if (km == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(means, b.mmu, sizeof(float) * 4 * k, cudaMemcpyDeviceToHost, c.s));
+    if (kc == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(covs, b.mcov, sizeof(float) * 16 * k, cudaMemcpyDeviceToHost, c.s));
+    if (loglik_trace && o.iters > 0)
+        GIRA_CUDA(cudaMemcpyAsync(loglik_trace, b.trace, sizeof(double) * o.iters, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(h.iters_done, h.iters_done);
+    TRY(device_status(h));
+    if (iters_done) *iters_done = h.iters_done;
+    if (final_loglik) *final_loglik = h.ll_sum / (double)n;
+    return GIRA_OK;
+}
+
+gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float* weights, const float* means,
+                             const float* covs, double* mean_loglik, float* per_point, void* stream) {
+    reset_error();
+    TRY(check_nk4(n, k));
+    if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, kw, km, kc, kpp = Kind::Host;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    if (per_point) TRY(check_ptr(per_point, "per_point", c.dev, &kpp));
+    const int kpad = estep4_threads(k);
+    int64_t ppc = 0;
+    const int grid = estep4_grid(n, k, c.sms, &ppc);
+    struct Bufs {
+        DeviceState* st;
+        float *pin, *params, *mw, *mmu, *mcov, *pp;
+        float4* p4;
+        double *model64, *llp;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(kp == Kind::Host ? 4 * n : 0);
+        b.p4 = cv.take<float4>(n);
+        b.params = cv.take<float>((size_t)kpad * COMP4_FLOATS);
+        b.model64 = cv.take<double>((size_t)k * MODEL4);
+        b.llp = cv.take<double>(grid);
+        b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
+        b.mmu = cv.take<float>(km == Kind::Host ? 4 * (size_t)k : 0);
+        b.mcov = cv.take<float>(kc == Kind::Host ? 16 * (size_t)k : 0);
+        b.pp = cv.take<float>((per_point && kpp == Kind::Host) ? n : 0);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.stop_after = 0;
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    const float* w_d = weights;
+    const float* mu_d = means;
+    const float* cov_d = covs;
+    if (kw == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
+        w_d = b.mw;
+    }
+    if (km == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * 4 * k, cudaMemcpyHostToDevice, c.s));
+        mu_d = b.mmu;
+    }
+    if (kc == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 16 * k, cudaMemcpyHostToDevice, c.s));
+        cov_d = b.mcov;
+    }
+    COUNTED(prof, 1, launch_pack4(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_fill_padding4(b.params, k, c.s));
+    COUNTED(prof, 1, launch_params_from_model4(w_d, mu_d, cov_d, k, b.model64, b.params, b.st, c.s));
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
+    EStep4Launch a{b.p4, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
+    COUNTED(prof, 1, launch_estep4(a, false, grid, c.s));
+    COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    if (per_point && kpp == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(per_point, b.pp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    TRY(device_status(h));
+    if (mean_loglik) *mean_loglik = h.ll_sum / (double)n;
+    return GIRA_OK;
+}
+
+gira_status gira_gmm_conditional4(const float* locs, int64_t m, int k, const float* weights, const float* means,
+                                  const float* covs, float* cond_mean, float* cond_var, void* stream) {
+    reset_error();
+    if (m < 1) return fail(GIRA_ERR_INVALID_ARG, "m = %lld < 1", (long long)m);
+    if (k < 1 || k > GIRA_MAX_K4) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K4);
+    if (!locs || !weights || !means || !covs || !cond_mean)
+        return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kl, kw, km, kc, ke, kv = Kind::Host;
+    TRY(check_ptr(locs, "locs", c.dev, &kl));
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    TRY(check_ptr(cond_mean, "cond_mean", c.dev, &ke));
+    if (cond_var) TRY(check_ptr(cond_var, "cond_var", c.dev, &kv));
+    struct Bufs {
+        DeviceState* st;
+        float *lin, *mw, *mmu, *mcov, *prep, *e, *v;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.lin = cv.take<float>(kl == Kind::Host ? 3 * m : 0);
+        b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
+        b.mmu = cv.take<float>(km == Kind::Host ? 4 * (size_t)k : 0);
+        b.mcov = cv.take<float>(kc == Kind::Host ? 16 * (size_t)k : 0);
+        b.prep = cv.take<float>((size_t)k * cond_floats());
+        b.e = cv.take<float>(ke == Kind::Host ? m : 0);
+        b.v = cv.take<float>((kv == Kind::Host || !cond_var) ? m : 0);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    auto stage = [&](const float* src, Kind kd, float* buf, size_t count) -> const float* {
+        if (kd != Kind::Host) return src;
+        if (cudaMemcpyAsync(buf, src, sizeof(float) * count, cudaMemcpyHostToDevice, c.s) != cudaSuccess) return nullptr;
+        return buf;
+    };
+    const float* l_d = stage(locs, kl, b.lin, 3 * (size_t)m);
+    const float* w_d = stage(weights, kw, b.mw, k);
+    const float* mu_d = stage(means, km, b.mmu, 4 * (size_t)k);
+    const float* cov_d = stage(covs, kc, b.mcov, 16 * (size_t)k);
+    if (!l_d || !w_d || !mu_d || !cov_d) GIRA_CUDA(cudaGetLastError());
+    float* e_d = (ke == Kind::Device) ? cond_mean : b.e;
+    float* v_d = (cond_var && kv == Kind::Device) ? cond_var : b.v;
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    COUNTED(prof, 2, launch_conditional4(l_d, m, k, w_d, mu_d, cov_d, b.prep, e_d, v_d, b.st, c.s));
+    if (ke == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(cond_mean, b.e, sizeof(float) * m, cudaMemcpyDeviceToHost, c.s));
+    if (cond_var && kv == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(cond_var, b.v, sizeof(float) * m, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    return device_status(h);
+}
+
+gira_status gira_gmm_sample(int64_t m, int k, int d, const float* weights, const float* means, const float* covs,
+                            uint64_t seed, float* out, int32_t* components, void* stream) {
+    reset_error();
+    if (m < 1) return fail(GIRA_ERR_INVALID_ARG, "m = %lld < 1", (long long)m);
+    if (d != 3 && d != 4) return fail(GIRA_ERR_INVALID_ARG, "d = %d is neither 3 nor 4", d);
+    if (k < 1 || k > GIRA_MAX_K) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K);
+    if (!weights || !means || !covs || !out) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kw, km, kc, ko, kq = Kind::Host;
+    TRY(check_ptr(weights, "weights", c.dev, &kw));
+    TRY(check_ptr(means, "means", c.dev, &km));
+    TRY(check_ptr(covs, "covs", c.dev, &kc));
+    TRY(check_ptr(out, "out", c.dev, &ko));
+    if (components) TRY(check_ptr(components, "components", c.dev, &kq));
+    struct Bufs {
+        DeviceState* st;
+        float *mw, *mmu, *mcov, *o;
+        double *cum, *chol;
+        int32_t* q;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
+        b.mmu = cv.take<float>(km == Kind::Host ? (size_t)d * k : 0);
+        b.mcov = cv.take<float>(kc == Kind::Host ? (size_t)d * d * k : 0);
+        b.cum = cv.take<double>(k);
+        b.chol = cv.take<double>(16 * (size_t)k);
+        b.o = cv.take<float>(ko == Kind::Host ? (size_t)d * m : 0);
+        b.q = cv.take<int32_t>((components && kq == Kind::Host) ? m : 0);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    const float* w_d = weights;
+    const float* mu_d = means;
+    const float* cov_d = covs;
+    if (kw == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
+        w_d = b.mw;
+    }
+    if (km == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mmu, means, sizeof(float) * d * k, cudaMemcpyHostToDevice, c.s));
+        mu_d = b.mmu;
+    }
+    if (kc == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * d * d * k, cudaMemcpyHostToDevice, c.s));
+        cov_d = b.mcov;
+    }
+    float* o_d = (ko == Kind::Device) ? out : b.o;
+    int32_t* q_d = components ? ((kq == Kind::Device) ? components : b.q) : nullptr;
+    prof.t_init = prof.mark();
+    prof.t_em = prof.t_init;
+    COUNTED(prof, 2, launch_sample(m, k, d, w_d, mu_d, cov_d, seed, b.cum, b.chol, o_d, q_d, b.st, c.s));
+    if (ko == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(out, b.o, sizeof(float) * d * m, cudaMemcpyDeviceToHost, c.s));
+    if (components && kq == Kind::Host)
+        GIRA_CUDA(cudaMemcpyAsync(components, b.q, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_end = prof.mark();
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    return device_status(h);
+}
+
 }  // extern "C"

@@ -62,6 +62,58 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------- warp reductions
+struct AddOp {
+    __device__ __forceinline__ float operator()(float a, float b) const { return a + b; }
+};
+struct MaxOp {
+    __device__ __forceinline__ float operator()(float a, float b) const { return fmaxf(a, b); }
+};
+
+// Per-lane batch index owned after the transpose-reduce: Q = 8 -> bits 4..2 of
+// the lane, Q = 4 -> bits 4..3.  The owner of index q is lane q * (32 / Q).
+template <int Q>
+__device__ __forceinline__ int q_of_lane(int lane) {
+    return Q == 8 ? (lane >> 2) & 7 : (lane >> 3) & 3;
+}
+
+// Combine Q per-lane values over the 32 lanes of a warp.  On return, lane l
+// holds the combination for index q_of_lane<Q>(l); the order of combination is
+// fixed, and the lanes sharing an index hold bit-identical results.
+template <int Q, class Op>
+__device__ __forceinline__ float warp_transpose_reduce(const float (&v)[Q], int lane, Op op) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[Q / 2];
+#pragma unroll
+    for (int i = 0; i < Q / 2; ++i) {
+        const float send = b4 ? v[i] : v[i + Q / 2];
+        const float keep = b4 ? v[i + Q / 2] : v[i];
+        w[i] = op(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+    }
+    float t;
+    if (Q == 8) {
+        float z[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = b3 ? w[i] : w[i + 2];
+            const float keep = b3 ? w[i + 2] : w[i];
+            z[i] = op(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+        }
+        const float send = b2 ? z[0] : z[1];
+        const float keep = b2 ? z[1] : z[0];
+        t = op(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+    } else {
+        const float send = b3 ? w[0] : w[1];
+        const float keep = b3 ? w[1] : w[0];
+        t = op(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+        t = op(t, __shfl_xor_sync(0xffffffffu, t, 4));
+    }
+    t = op(t, __shfl_xor_sync(0xffffffffu, t, 2));
+    t = op(t, __shfl_xor_sync(0xffffffffu, t, 1));
+    return t;
+}
+
+
 // ---------------------------------------------------------------- TMA bulk copy + mbarrier
 // (PTX ISA: cp.async.bulk, mbarrier; a plain launch is a cluster of one CTA, so
 // the CTA's own shared memory is addressed through the shared::cluster window.)
@@ -119,6 +171,11 @@ __device__ __forceinline__ float dist2_f32(float4 x, float4 c) {
     float d0 = __fsub_rn(x.x, c.x), d1 = __fsub_rn(x.y, c.y), d2 = __fsub_rn(x.z, c.z);
     float s = __fadd_rn(__fmul_rn(d0, d0), __fmul_rn(d1, d1));
     return __fadd_rn(s, __fmul_rn(d2, d2));
+}
+// Four dimensions: ((d0^2 + d1^2) + d2^2) + d3^2, same rules.
+__device__ __forceinline__ float dist2_f32_4(float4 x, float4 c) {
+    const float d3 = __fsub_rn(x.w, c.w);
+    return __fadd_rn(dist2_f32(x, c), __fmul_rn(d3, d3));
 }
 
 // ---------------------------------------------------------------- exact fixed-point weights
@@ -379,8 +436,9 @@ cudaError_t launch_grad_finalize(const float* partials, int grid, const double* 
                                  DeviceState* st, cudaStream_t s);
 
 // k-means
+// dim: 3 (distances over x, y, z) or 4 (also the fourth coordinate)
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
-                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s);
+                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s, int dim = 3);
 int kpp_num_blocks(int64_t n);
 // Persistent k-means++ (one cooperative launch for all K centres).  Grid size, or
 // 0 when cooperative launch is unavailable (the per-centre launches are used).
@@ -424,6 +482,68 @@ cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, 
 cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32_t* labels, const float4* shift4,
                                double* stats64, DeviceState* st, cudaStream_t s);
 cudaError_t launch_centers_out(const float4* centers4, int k, float* centers3, cudaStream_t s);
+
+// ---------------------------------------------------------------- four dimensions (xyz + intensity)
+// E-step parameters of one component (COMP4_FLOATS floats, 16-byte aligned):
+//   0..9   P' = alpha * L^{-1}, lower triangle (00,10,11,20,21,22,30,31,32,33)
+//   10..13 unused (zero)
+//   14     c = log2 w + sum_j log2 (L^{-1})_jj - (4/2) log2(2 pi)
+//   15..18 -mu (binary32; also the shift of the M-step statistics)
+//   19     w (N_b after an M-step, or the caller's weight)
+//   20..23 unused
+// Statistics (NSTAT4): S0, S1[4], S2[10] in the order 00,01,02,03,11,12,13,22,23,33;
+// binary64 model (MODEL4): w, mu[4], Sigma[10] in the same order.
+constexpr int COMP4_FLOATS = 24;
+constexpr int SLOT4_P = 0, SLOT4_B = 10, SLOT4_C = 14, SLOT4_NMU = 15, SLOT4_W = 19;
+constexpr int NSTAT4 = 15;
+constexpr int MODEL4 = 15;
+constexpr int MAX_K4 = 1024;
+// index of (i, j), i <= j, in the upper-triangle order 00,01,02,03,11,12,13,22,23,33
+__host__ __device__ constexpr int sym4(int i, int j) { return i * (7 - i) / 2 + j; }
+
+struct EStep4Launch {
+    const float4* pts4;    // (x, y, z, intensity) per point
+    int64_t n;
+    int k;
+    const float* params;   // estep4_threads(k) * COMP4_FLOATS (padding components: c = -inf)
+    int64_t pts_per_cta;   // multiple of 8
+    float* partials;       // [grid][k][NSTAT4] (stats launches)
+    double* ll_partials;   // [grid]
+    float* per_point;      // [n] natural-log lse, or nullptr
+    DeviceState* st;
+    int iter;              // 1-based EM iteration; skipped when iter > st->stop_after
+};
+
+// Components (with padding) the E-step block holds for k.
+int estep4_threads(int k);
+int estep4_grid(int64_t n, int k, int num_sms, int64_t* pts_per_cta);
+cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s);
+// N x 4 -> float4; flags non-finite input.
+cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, DeviceState* st, cudaStream_t s);
+cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s);
+// M-step from the per-CTA partials (or binary64 stats64 when partials is nullptr),
+// about the shift shift4 (nullptr: the means held in params); em as in launch_reduce_finalize.
+cudaError_t launch_reduce_finalize4(const float* partials, int grid, const double* ll_partials,
+                                    const double* stats64, const float4* shift4, int k, int64_t n, double reg,
+                                    double tol, double* model64, float* params, double* trace, DeviceState* st,
+                                    int iter, bool em, cudaStream_t s);
+cudaError_t launch_params_from_model4(const float* w, const float* mu, const float* cov, int k, double* model64,
+                                      float* params, DeviceState* st, cudaStream_t s);
+cudaError_t launch_model_out4(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
+                              cudaStream_t s);
+// Lloyd in four dimensions and the one-hot statistics about the final centres.
+cudaError_t launch_lloyd4(const float4* pts4, int64_t n, int k, int lloyd_iters, float4* centers, int32_t* labels,
+                          double* sums, unsigned long long* changed, DeviceState* st, cudaStream_t s);
+cudaError_t launch_label_stats4(const float4* pts4, int64_t n, int k, const int32_t* labels, const float4* shift4,
+                                double* stats64, DeviceState* st, cudaStream_t s);
+// Gaussian-mixture regression of the 4th coordinate on the first three.
+int cond_floats();
+cudaError_t launch_conditional4(const float* locs, int64_t m, int k, const float* w, const float* mu,
+                                const float* cov, float* prep, float* cmean, float* cvar, DeviceState* st,
+                                cudaStream_t s);
+// m draws from a d-dimensional mixture (d = 3 or 4); cum: k doubles, chol: 16 k doubles.
+cudaError_t launch_sample(int64_t m, int k, int d, const float* w, const float* mu, const float* cov, uint64_t seed,
+                          double* cum, double* chol, float* out, int32_t* comp, DeviceState* st, cudaStream_t s);
 
 // Set this thread's last-error message (msg may be nullptr to keep it) and
 // component (what gira_last_error_message / gira_last_error_component return).

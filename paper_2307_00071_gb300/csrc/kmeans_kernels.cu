@@ -39,7 +39,9 @@ __global__ void kpp_first_kernel(const float4* __restrict__ pts, int64_t n, uint
     chosen[0] = idx;
 }
 
-// D^2(x) = min(D^2(x), ||x - c_{j-1}||^2) and the exact fixed-point sum of each chunk.
+// D^2(x) = min(D^2(x), ||x - c_{j-1}||^2) and the exact fixed-point sum of each chunk
+// (DIM 3: distances over x, y, z; DIM 4: also over the fourth coordinate).
+template <int DIM>
 __global__ void __launch_bounds__(KPP_THREADS) kpp_update_kernel(const float4* __restrict__ pts, int64_t n,
                                                                  const float4* __restrict__ centers, int j,
                                                                  float* __restrict__ d2, u128* blocksums,
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(KPP_THREADS) kpp_update_kernel(const float4* _
     for (int it = 0; it < KPP_ITEMS; ++it) {
         const int64_t i = base + it * KPP_THREADS + threadIdx.x;
         if (i < n) {
-            float d = dist2_f32(pts[i], c);
+            float d = (DIM == 4) ? dist2_f32_4(pts[i], c) : dist2_f32(pts[i], c);
             if (j > 1) d = fminf(d2[i], d);
             d2[i] = d;
             acc = u128_add(acc, fx48(d));
@@ -945,11 +947,14 @@ cudaError_t launch_kpp_cluster(const float4* pts4, int64_t n, int k, uint64_t se
 }
 
 cudaError_t launch_kpp(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
-                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s) {
+                       u128* blocksums, int64_t* chosen, DeviceState* st, cudaStream_t s, int dim) {
     const int nblk = kpp_num_blocks(n);
     kpp_first_kernel<<<1, 1, 0, s>>>(pts4, n, seed, centers, chosen, st);
     for (int j = 1; j < k; ++j) {
-        kpp_update_kernel<<<nblk, KPP_THREADS, 0, s>>>(pts4, n, centers, j, d2, blocksums, st);
+        if (dim == 4)
+            kpp_update_kernel<4><<<nblk, KPP_THREADS, 0, s>>>(pts4, n, centers, j, d2, blocksums, st);
+        else
+            kpp_update_kernel<3><<<nblk, KPP_THREADS, 0, s>>>(pts4, n, centers, j, d2, blocksums, st);
         kpp_select_kernel<<<1, SEL_THREADS, 0, s>>>(pts4, n, d2, blocksums, nblk, seed, j, centers, chosen, st);
     }
     return cudaGetLastError();

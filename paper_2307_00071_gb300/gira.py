@@ -19,7 +19,7 @@ from . import build_lib
 OK = 0
 ERR_INVALID_ARG, ERR_NONFINITE_INPUT, ERR_NOT_PD, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC = 1, 2, 3, 4, 5, 6, 7
 INIT_KMEANS, INIT_PARAMS = 0, 1
-MAX_K, MAX_K_BATCHED = 8192, 1024
+MAX_K, MAX_K_BATCHED, MAX_K4 = 8192, 1024, 1024
 
 
 class GiraError(RuntimeError):
@@ -60,6 +60,12 @@ def _load():
                                                  vp]
     lib.gira_gmm_loglik_grad_batched.restype = C.c_int
     lib.gira_gmm_loglik_grad.restype = C.c_int
+    lib.gira_gmm_fit4.argtypes = [vp, i64, C.c_int, C.POINTER(FitOpts), vp, vp, vp, dp, ip, dp, vp]
+    lib.gira_gmm_loglik4.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
+    lib.gira_gmm_conditional4.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, vp, vp]
+    lib.gira_gmm_sample.argtypes = [i64, C.c_int, C.c_int, vp, vp, vp, C.c_uint64, vp, vp, vp]
+    for f in ("gira_gmm_fit4", "gira_gmm_loglik4", "gira_gmm_conditional4", "gira_gmm_sample"):
+        getattr(lib, f).restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
     lib.gira_release_workspace.argtypes = []
@@ -112,9 +118,9 @@ def _new(like, shape, dtype):
     return np.empty(shape, dtype=dtype)
 
 
-def _check_points(points):
-    if points.ndim != 2 or points.shape[1] != 3:
-        raise ValueError("points must be N x 3")
+def _check_points(points, d: int = 3):
+    if points.ndim != 2 or points.shape[1] != d:
+        raise ValueError(f"points must be N x {d}")
     dt = points.dtype
     if (_is_torch(points) and str(dt) != "torch.float32") or (not _is_torch(points) and dt != np.float32):
         raise ValueError("points must be float32")
@@ -375,3 +381,91 @@ def gira_gmm_loglik_grad_batched(points, offsets, ks, logits, means, chol, poses
     for g in want:
         r["grad_" + g] = outs[g]
     return r
+
+
+# ----------------------------------------------------------------------------- four dimensions
+def gira_gmm_fit4(points, k: int, iters: int = 100, tol: float = 1e-3, reg_covar: float = 1e-6, seed: int = 0,
+                  lloyd_iters: int = 10, init=None, final_loglik: bool = True):
+    """EM fit of a D = 4 mixture to N x 4 points (x, y, z, intensity).  ``init`` =
+    (weights, means K x 4, covs K x 4 x 4) starts from given parameters.  Returns a
+    dict like gira_gmm_fit: weights, means, covs, trace, iters_done, final_loglik."""
+    n = _check_points(points, 4)
+    o = default_opts()
+    o.iters, o.tol, o.reg_covar, o.seed, o.lloyd_iters = iters, tol, reg_covar, seed, lloyd_iters
+    o.init_mode = INIT_KMEANS
+    if init is None:
+        w, m, c = _new(points, (k,), np.float32), _new(points, (k, 4), np.float32), _new(points, (k, 4, 4), np.float32)
+    else:
+        w, m, c = (_f32_like(a, points) for a in init)
+        w, m, c = (a.clone() if _is_torch(a) else a.copy() for a in (w, m, c))
+        o.init_mode = INIT_PARAMS
+    tr = np.full(max(iters, 1), np.nan)
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(w)
+    mp, km, _ = _ptr(m)
+    cp, kc, _ = _ptr(c)
+    done, fll = C.c_int(0), C.c_double(np.nan)
+    _check(_lib.gira_gmm_fit4(pp, n, k, C.byref(o), wp, mp, cp, tr.ctypes.data_as(C.POINTER(C.c_double)),
+                              C.byref(done), C.byref(fll) if final_loglik else None, s))
+    return dict(weights=w, means=m, covs=c, trace=tr[:done.value], iters_done=done.value,
+                final_loglik=fll.value if final_loglik else None)
+
+
+def gira_gmm_loglik4(points, weights, means, covs, per_point: bool = False):
+    """Mean (and optionally per-point) log-likelihood of N x 4 points under a D = 4 mixture."""
+    n = _check_points(points, 4)
+    k = int(weights.shape[0])
+    w, m, c = (_f32_like(a, points) for a in (weights, means, covs))
+    out = _new(points, (n,), np.float32) if per_point else None
+    pp, kp, s = _ptr(points)
+    wp, kw, _ = _ptr(w)
+    mp, km, _ = _ptr(m)
+    cp, kc, _ = _ptr(c)
+    op, ko, _ = _ptr(out)
+    mean = C.c_double(np.nan)
+    _check(_lib.gira_gmm_loglik4(pp, n, k, wp, mp, cp, C.byref(mean), op, s))
+    return (mean.value, out) if per_point else mean.value
+
+
+def gira_gmm_conditional4(locs, weights, means, covs, want_var: bool = True):
+    """Intensity regression (Sec. IV): E[I | xyz] and V[I | xyz] at M x 3 locations under a
+    D = 4 mixture.  Returns (mean (M,), var (M,) or None) on the side of ``locs``."""
+    m_ = _check_points(locs, 3)
+    k = int(weights.shape[0])
+    w, m, c = (_f32_like(a, locs) for a in (weights, means, covs))
+    e = _new(locs, (m_,), np.float32)
+    v = _new(locs, (m_,), np.float32) if want_var else None
+    lp, kl, s = _ptr(locs)
+    wp, kw, _ = _ptr(w)
+    mp, km, _ = _ptr(m)
+    cp, kc, _ = _ptr(c)
+    ep, ke, _ = _ptr(e)
+    vp_, kv, _ = _ptr(v)
+    _check(_lib.gira_gmm_conditional4(lp, m_, k, wp, mp, cp, ep, vp_, s))
+    return e, v
+
+
+def gira_gmm_sample(m: int, weights, means, covs, seed: int = 0, device=None, want_components: bool = True):
+    """m draws from a d-dimensional mixture (d = means.shape[1], 3 or 4).  Outputs live on
+    ``device`` (a torch device) or, when None, on the side of ``means``.  Returns
+    (points (m, d) float32, components (m,) int32 or None)."""
+    like = means
+    if device is not None:
+        import torch
+        like = torch.empty(0, device=device)
+    d = int(means.shape[1])
+    k = int(weights.shape[0])
+    w, mu, c = (_f32_like(a, like) for a in (weights, means, covs))
+    out = _new(like, (m, d), np.float32)
+    comp = _new(like, (m,), np.int32) if want_components else None
+    s = None
+    if _is_torch(like) and like.is_cuda:
+        import torch
+        s = torch.cuda.current_stream(like.device).cuda_stream
+    wp, kw, _ = _ptr(w)
+    mp, km, _ = _ptr(mu)
+    cp, kc, _ = _ptr(c)
+    op, ko, _ = _ptr(out)
+    qp, kq, _ = _ptr(comp)
+    _check(_lib.gira_gmm_sample(m, k, d, wp, mp, cp, seed, op, qp, s))
+    return out, comp

@@ -118,3 +118,31 @@ def test_batched_invalid_arguments_rejected_without_gpu():
     assert call([0, 5, 10], [2, 6], 2) == gira.ERR_INVALID_ARG        # k > n
     assert call([0, 5, 10], [0, 2], 2) == gira.ERR_INVALID_ARG        # k < 1
     assert b"instance" in L.gira_last_error_message()
+
+
+def test_d4_invalid_arguments_rejected_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    pts = np.zeros((10, 4), np.float32)
+    w, m, c = np.ones(2, np.float32), np.zeros((2, 4), np.float32), np.tile(np.eye(4, dtype=np.float32), (2, 1, 1))
+    o = gira.default_opts()
+    fit = lambda n, k: L.gira_gmm_fit4(pts.ctypes.data, n, k, C.byref(o), w.ctypes.data, m.ctypes.data,
+                                       c.ctypes.data, None, None, None, None)
+    assert fit(0, 1) == gira.ERR_INVALID_ARG
+    assert fit(10, 11) == gira.ERR_INVALID_ARG
+    assert fit(5000, 1025) == gira.ERR_INVALID_ARG                     # above GIRA_MAX_K4
+    assert L.gira_gmm_loglik4(pts.ctypes.data, 10, 0, w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
+                              None) == gira.ERR_INVALID_ARG
+    loc = np.zeros((3, 3), np.float32)
+    out = np.zeros(3, np.float32)
+    assert L.gira_gmm_conditional4(loc.ctypes.data, 0, 2, w.ctypes.data, m.ctypes.data, c.ctypes.data,
+                                   out.ctypes.data, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gmm_conditional4(loc.ctypes.data, 3, 2, w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
+                                   None) == gira.ERR_INVALID_ARG
+    so = np.zeros((4, 4), np.float32)
+    assert L.gira_gmm_sample(4, 2, 5, w.ctypes.data, m.ctypes.data, c.ctypes.data, 0, so.ctypes.data, None,
+                             None) == gira.ERR_INVALID_ARG                 # d not 3 or 4
+    assert L.gira_gmm_sample(0, 2, 4, w.ctypes.data, m.ctypes.data, c.ctypes.data, 0, so.ctypes.data, None,
+                             None) == gira.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        gira.gira_gmm_fit4(np.zeros((5, 3), np.float32), 1)

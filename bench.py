@@ -411,6 +411,73 @@ def bench_large_map(gira):
             "trace_first_last": [float(r["trace"][0]), float(r["trace"][-1])]}
 
 
+D4_K = 512
+# per unit, the fewest FP32 operations the 4D step needs: logit P'x + b' and its squares 14,
+# sum 1, statistics 20 (gamma, S0, gamma d, S1, S2); the kernel issues 8 more (d = x - mu
+# in both passes) and one MUFU ex2
+D4_FP32_OPS = 35
+
+
+def bench_d4(gira, frame_pts, sms, mhz, reps=5):
+    """The frame with an intensity channel (N x 4: xyz + I, the paper's SOGMM data),
+    K = 512, the main fit's settings; plus intensity regression at every point of the
+    frame and resampling of a frame-sized cloud from the fitted model."""
+    import torch
+    from paper_2307_00071_gb300 import synth
+    pts4 = np.concatenate([frame_pts, synth.frame_intensity(frame_pts, 1)[:, None]], axis=1)
+    x = torch.as_tensor(pts4, device="cuda")
+    n = len(pts4)
+
+    def fit():
+        return gira.gira_gmm_fit4(x, D4_K, iters=ITERS, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD)
+
+    for _ in range(2):
+        r = fit()
+    gira.gira_profile_enable(True)
+    gira.gira_profile_read(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    iters = 0
+    for _ in range(reps):
+        r = fit()
+        iters += r["iters_done"]
+    ev1.record()
+    torch.cuda.synchronize()
+    prof = gira.gira_profile_read(reset=True)
+    gira.gira_profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / reps
+    kern_s = prof["estep_ms"] / max(prof["estep_launches"], 1) / 1e3
+    peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / D4_FP32_OPS
+    locs = x[:, :3].contiguous()
+    w, m, c = r["weights"], r["means"], r["covs"]
+    gira.gira_gmm_conditional4(locs, w, m, c)
+    gira.gira_gmm_sample(n, w, m, c, seed=1)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        gira.gira_gmm_conditional4(locs, w, m, c)
+    ev1.record()
+    torch.cuda.synchronize()
+    cond_ms = ev0.elapsed_time(ev1) / reps
+    ev0.record()
+    for _ in range(reps):
+        gira.gira_gmm_sample(n, w, m, c, seed=1)
+    ev1.record()
+    torch.cuda.synchronize()
+    samp_ms = ev0.elapsed_time(ev1) / reps
+    return {"workload": f"depth frame with intensity (N={n} x 4), K={D4_K}, tol {TOL}, KInit as the main fit",
+            "unit": UNIT, "value": float(n) * D4_K * iters / reps / (ms / 1e3), "ms_per_frame": ms,
+            "em_ms_per_frame": prof["em_ms"] / reps, "init_ms_per_frame": prof["init_ms"] / reps,
+            "iters_done": r["iters_done"], "final_loglik": r["final_loglik"],
+            "kernel": "estep4_kernel<true> (4D fused E-step + statistics)", "kernel_ms": kern_s * 1e3,
+            "kernel_units_per_s": n * D4_K / kern_s if kern_s else None,
+            "frac_fp32": (n * D4_K / kern_s) / peak if kern_s else None,
+            "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {D4_FP32_OPS} FP32 ops per unit",
+            "conditional_ms": cond_ms, "conditional_points_per_s": n / (cond_ms / 1e3),
+            "sample_ms": samp_ms, "sample_points_per_s": n / (samp_ms / 1e3)}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -524,7 +591,8 @@ def run_gira(args):
         if not args.no_extras:
             line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira),
                               "large_map": bench_large_map(gira),
-                              "batched_registrations": bench_batched_registrations(gira, frame.points)}
+                              "batched_registrations": bench_batched_registrations(gira, frame.points),
+                              "xyz_intensity": bench_d4(gira, frame.points, sms, mhz)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

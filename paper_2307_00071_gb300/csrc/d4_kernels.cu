@@ -464,49 +464,80 @@ __global__ void cond_prepare_kernel(const float* __restrict__ w, const float* __
     for (int i = 0; i < 4; ++i) o[11 + i] = mu[4 * (size_t)b + i];
 }
 
-// One thread per location, all K components in order: two passes (maximum of
-// the log-weights, then the weighted moments), binary32 with binary64 moments.
-__global__ void conditional4_kernel(const float* __restrict__ locs, int64_t m, int k, const float* __restrict__ prep,
-                                    float* cmean, float* cvar, DeviceState* st) {
+// One thread per location, all K components in order, the prepared components
+// staged through shared memory in tiles: pass 1 takes the maximum log-weight
+// and, as a reference, the regression mean m_ref of that component; pass 2 sums
+// w_b = exp(lw_b - max), w_b (m_b - m_ref) and w_b (v_b + (m_b - m_ref)^2) in
+// binary32 (the shift keeps the variance free of cancellation).
+constexpr int COND_THREADS = 256;
+constexpr int COND_TILE = 256;
+
+__global__ void __launch_bounds__(COND_THREADS) conditional4_kernel(const float* __restrict__ locs, int64_t m, int k,
+                                                                    const float* __restrict__ prep, float* cmean,
+                                                                    float* cvar, DeviceState* st) {
+    __shared__ float sp[COND_TILE * COND_FLOATS];
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = st->error;
+    __syncthreads();
+    if (s_err) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m || st->error) return;
-    const float x0 = locs[3 * i], x1 = locs[3 * i + 1], x2 = locs[3 * i + 2];
-    if (!(isfinite(x0) && isfinite(x1) && isfinite(x2))) {
-        set_error(st, GIRA_ERR_NONFINITE_INPUT);
-        return;
+    const bool valid = i < m;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (valid) {
+        x0 = locs[3 * i];
+        x1 = locs[3 * i + 1];
+        x2 = locs[3 * i + 2];
+        if (!(isfinite(x0) && isfinite(x1) && isfinite(x2))) set_error(st, GIRA_ERR_NONFINITE_INPUT);
     }
-    auto logw = [&](const float* o, float& d0, float& d1, float& d2) {
-        d0 = x0 - o[11];
-        d1 = x1 - o[12];
-        d2 = x2 - o[13];
+    // log-weight and regression mean of component o at this location
+    auto eval = [&](const float* o, float& mb) {
+        const float d0 = x0 - o[11], d1 = x1 - o[12], d2 = x2 - o[13];
         const float y0 = o[0] * d0;
         const float y1 = fmaf(o[2], d1, o[1] * d0);
         const float y2 = fmaf(o[5], d2, fmaf(o[4], d1, o[3] * d0));
-        return o[10] - 0.5f * fmaf(y2, y2, fmaf(y1, y1, y0 * y0));
+        mb = fmaf(o[8], d2, fmaf(o[7], d1, fmaf(o[6], d0, o[14])));
+        return fmaf(-0.5f, fmaf(y2, y2, fmaf(y1, y1, y0 * y0)), o[10]);
     };
-    float mx = -INFINITY;
-    for (int b = 0; b < k; ++b) {
-        float d0, d1, d2;
-        mx = fmaxf(mx, logw(prep + (size_t)b * COND_FLOATS, d0, d1, d2));
+    auto load_tile = [&](int b0, int nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * COND_FLOATS; t += blockDim.x) sp[t] = prep[(size_t)b0 * COND_FLOATS + t];
+        __syncthreads();
+    };
+    float mx = -INFINITY, mref = 0.f;
+    for (int b0 = 0; b0 < k; b0 += COND_TILE) {
+        const int nb = min(COND_TILE, k - b0);
+        load_tile(b0, nb);
+        for (int b = 0; b < nb; ++b) {
+            float mb;
+            const float lw = eval(sp + b * COND_FLOATS, mb);
+            if (lw > mx) {
+                mx = lw;
+                mref = mb;
+            }
+        }
     }
-    double s = 0.0, e1 = 0.0, e2 = 0.0;
-    for (int b = 0; b < k; ++b) {
-        const float* o = prep + (size_t)b * COND_FLOATS;
-        float d0, d1, d2;
-        const float lw = logw(o, d0, d1, d2);
-        const double wgt = (double)__expf(lw - mx);
-        const double mb = (double)o[14] + (double)o[6] * d0 + (double)o[7] * d1 + (double)o[8] * d2;
-        s += wgt;
-        e1 += wgt * mb;
-        e2 += wgt * ((double)o[9] + mb * mb);
+    float s = 0.f, e1 = 0.f, e2 = 0.f;
+    for (int b0 = 0; b0 < k; b0 += COND_TILE) {
+        const int nb = min(COND_TILE, k - b0);
+        load_tile(b0, nb);
+        for (int b = 0; b < nb; ++b) {
+            const float* o = sp + b * COND_FLOATS;
+            float mb;
+            const float w = __expf(eval(o, mb) - mx);
+            const float dm = mb - mref;
+            s += w;
+            e1 = fmaf(w, dm, e1);
+            e2 = fmaf(w, fmaf(dm, dm, o[9]), e2);
+        }
     }
-    if (!(s > 0.0)) {
+    if (!valid) return;
+    if (!(s > 0.f)) {
         set_error(st, GIRA_ERR_NUMERIC);
         return;
     }
-    const double em = e1 / s;
-    cmean[i] = (float)em;
-    cvar[i] = (float)(e2 / s - em * em);
+    const float r = 1.f / s, a = e1 * r;
+    cmean[i] = mref + a;
+    if (cvar) cvar[i] = fmaf(-a, a, e2 * r);
 }
 
 // ------------------------------------------------------------------ sampling
@@ -769,7 +800,8 @@ cudaError_t launch_conditional4(const float* locs, int64_t m, int k, const float
                                 const float* cov, float* prep, float* cmean, float* cvar, DeviceState* st,
                                 cudaStream_t s) {
     cond_prepare_kernel<<<(k + 63) / 64, 64, 0, s>>>(w, mu, cov, k, prep, st);
-    conditional4_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(locs, m, k, prep, cmean, cvar, st);
+    conditional4_kernel<<<(unsigned)((m + COND_THREADS - 1) / COND_THREADS), COND_THREADS, 0, s>>>(locs, m, k, prep,
+                                                                                                 cmean, cvar, st);
     return cudaGetLastError();
 }
 

@@ -1688,14 +1688,17 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
     int64_t ppc = 0;
     const int grid = estep4_grid(n, k, c.sms, &ppc);
     const int nblk = kpp_num_blocks(n);
+    int kgrid = kinit ? kpp_persistent_grid() : 0;
+    if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
         float4 *p4, *c4;
         double *model64, *stats64, *llp, *trace, *sums;
-        u128* bs;
+        u128 *bs, *ksums;
         int64_t* ch;
         int32_t* lab;
+        int* ksync;
         unsigned long long* chg;
     } b{};
     auto layout = [&](Carver& cv) {
@@ -1713,12 +1716,14 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         b.mcov = cv.take<float>(kc == Kind::Host ? 16 * (size_t)k : 0);
         if (kinit) {
             b.c4 = cv.take<float4>(k);
-            b.d2 = cv.take<float>(n);
+            b.d2 = cv.take<float>(2 * (size_t)n);   // double-buffered by the persistent seeding
             b.bs = cv.take<u128>(nblk);
             b.ch = cv.take<int64_t>(k);
             b.lab = cv.take<int32_t>(n);
             b.sums = cv.take<double>(5 * (size_t)k);
             b.chg = cv.take<unsigned long long>(o.lloyd_iters + 1);
+            b.ksync = cv.take<int>((size_t)k + 1);
+            b.ksums = cv.take<u128>(kpp_persistent_sum_words(std::max(kgrid, 1), k));
         }
     };
     Carver sizer;
@@ -1750,7 +1755,13 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
     float* cov_d = (kc == Kind::Device) ? covs : b.mcov;
     if (kinit) {
-        COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s, 4));
+        if (kgrid > 0) {
+            GIRA_CUDA(cudaMemsetAsync(b.ksync, 0, sizeof(int) * (k + 1), c.s));
+            COUNTED(prof, 1, launch_kpp_persistent(b.p4, n, k, o.seed, b.c4, b.d2, b.ch, b.ksync, b.ksums, kgrid, b.st,
+                                                   c.s, 4));
+        } else {
+            COUNTED(prof, 2 * k - 1, launch_kpp(b.p4, n, k, o.seed, b.c4, b.d2, b.bs, b.ch, b.st, c.s, 4));
+        }
         GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 5 * k, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * (o.lloyd_iters + 1), c.s));
         COUNTED(prof, 1 + 2 * o.lloyd_iters, launch_lloyd4(b.p4, n, k, o.lloyd_iters, b.c4, b.lab, b.sums, b.chg,

@@ -450,7 +450,7 @@ size_t kpp_persistent_sum_words(int grid, int k);
 int64_t kpp_persistent_max_n(int grid);
 cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
                                   int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int dim = 3);
 // Batched KInit: one entry per instance.
 struct KppInst {
     int64_t pt_off, n;

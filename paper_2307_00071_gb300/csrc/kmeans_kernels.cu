@@ -113,11 +113,12 @@ __global__ void __launch_bounds__(SEL_THREADS) kpp_select_kernel(const float4* _
     int64_t idx;
     if (!u128_zero(T)) {
         const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
-        // the first chunk whose inclusive prefix exceeds t (exact: exactly one thread finds it)
+        // the chunk with exclusive prefix <= t < inclusive prefix (exact and monotone:
+        // exactly one thread finds it)
         u128 run = u128_sub(incl, local);
         for (int i = 0; i < per && b0 + i < nblk; ++i) {
             const u128 nxt = u128_add(run, blocksums[b0 + i]);
-            if (u128_gt(nxt, t)) {
+            if (!u128_gt(run, t) && u128_gt(nxt, t)) {
                 s_blk = b0 + i;
                 s_rel = u128_sub(t, run);
                 break;
@@ -205,6 +206,7 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 //     then loads the G sums in parallel and finds the CTA holding the threshold;
 //  3. every CTA loads that CTA's D^2 with the owner's lane layout and locates the
 //     point (no second wait: the arithmetic is exact, so all CTAs find the same one).
+template <int DIM>
 __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
     const float4* __restrict__ pts, int64_t n, int k, uint64_t seed, float4* centers, float* d2pub, int64_t* chosen,
     u128* sums, int* arrive, int* abort_flag, DeviceState* st) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
 #pragma unroll
         for (int q = 0; q < KPP_LANE_MAX; ++q) {
             if (q < mcnt) {
-                float d = dist2_f32(P[q], cen);
+                float d = (DIM == 4) ? dist2_f32_4(P[q], cen) : dist2_f32(P[q], cen);
                 if (j > 1) d = fminf(D[q], d);
                 D[q] = d;
                 pub[mine.lo + q] = d;
@@ -850,8 +852,10 @@ int kpp_persistent_grid() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kpp_persistent_kernel, KPPP_THREADS, 0) != cudaSuccess ||
-        occ < 1) {
+    int occ4 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kpp_persistent_kernel<3>, KPPP_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, kpp_persistent_kernel<4>, KPPP_THREADS, 0) != cudaSuccess ||
+        occ < 1 || occ4 < 1) {
         cudaGetLastError();
         return 0;
     }
@@ -864,12 +868,13 @@ int64_t kpp_persistent_max_n(int grid) { return (int64_t)grid * KPPP_WARPS * 32 
 
 cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t seed, float4* centers, float* d2,
                                   int64_t* chosen, int* sync_ints, u128* sums, int grid, DeviceState* st,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int dim) {
     int* arrive = sync_ints;
     int* abort_flag = sync_ints + k;
     void* args[] = {(void*)&pts4, (void*)&n, (void*)&k, (void*)&seed, (void*)&centers, (void*)&d2, (void*)&chosen,
                     (void*)&sums, (void*)&arrive, (void*)&abort_flag, (void*)&st};
-    return cudaLaunchCooperativeKernel((const void*)kpp_persistent_kernel, dim3(grid), dim3(KPPP_THREADS), args, 0, s);
+    const void* fn = (dim == 4) ? (const void*)kpp_persistent_kernel<4> : (const void*)kpp_persistent_kernel<3>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(KPPP_THREADS), args, 0, s);
 }
 
 // Cluster size for the one-cluster seeding of n points, or 0 when it does not

@@ -64,6 +64,19 @@ def test_fit4_on_depth_frame_with_intensity(gira, frame4):
     assert_model_close((r["weights"], r["means"], r["covs"]), (ref["weights"], ref["means"], ref["covs"]))
 
 
+@pytest.mark.parametrize("n", [400_000, 700_000])   # persistent and per-centre seeding kernels
+def test_fit4_kinit_on_large_clouds_matches_oracle(gira, n):
+    f = np.concatenate([synth.depth_frame(seed=s).points for s in (1, 2, 3)])[:n]
+    pts = np.ascontiguousarray(np.concatenate([f, synth.frame_intensity(f, 1)[:, None]], axis=1), np.float32)
+    r = gira.gira_gmm_fit4(pts, 48, iters=0, seed=5, lloyd_iters=0)
+    c0, _ = oracle.kmeanspp(pts, 48, 5)
+    _, lab, _ = oracle.lloyd(pts, c0, 0)
+    w, m, c = oracle.init_from_labels(pts, lab, 48, 1e-6)
+    ll, _, _ = oracle.estep(pts, w, m, c, want_resp=False)
+    assert abs(r["final_loglik"] - ll) <= LL_ABS
+    assert_model_close((r["weights"], r["means"], r["covs"]), (w, m, c))
+
+
 def test_fit4_device_tensors_and_convergence(gira):
     import torch
     cl = synth.gmm_cloud4(12_000, 6, seed=9)

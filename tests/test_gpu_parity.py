@@ -152,6 +152,22 @@ def test_kmeans_duplicates_fallback(gira):
     assert np.array_equal(to_np(c), ref_c)
 
 
+def scan_cloud(n):
+    """n points of three depth frames laid one after the other (N x 3)."""
+    return np.ascontiguousarray(np.concatenate([synth.depth_frame(seed=s).points for s in (1, 2, 3)])[:n])
+
+
+# On a 152-SM GPU that runs 16-CTA clusters these sizes take the three seeding
+# kernels: one thread-block cluster (N <= 294,912), the persistent cooperative
+# kernel (N <= 622,592), and one update + one select launch per centre.
+@pytest.mark.parametrize("n", [200_000, 400_000, 700_000])
+def test_kmeanspp_bit_exact_on_every_seeding_path(gira, n):
+    pts = scan_cloud(n)
+    ref_c, _ = oracle.kmeanspp(pts, 48, 5)
+    c, _, _ = gira.gira_kmeans_init(dev(pts), 48, seed=5, lloyd_iters=0, want_labels=False)
+    assert np.array_equal(to_np(c), ref_c)
+
+
 def test_full_fit_with_kmeans_init_matches_oracle(gira):
     cl = synth.gmm_cloud(20_000, 8, seed=0)
     ref = oracle.gmm_fit(cl.points, 8, iters=20, tol=0.0, reg=1e-6, seed=0, lloyd_iters=10)

@@ -75,6 +75,7 @@ def lib():
                                        dp, C.POINTER(ci), dp]
         L.oracle_conditional4.argtypes = [fp, C.c_int64, ci, dp, dp, dp, dp, dp]
         L.oracle_sample_d.argtypes = [C.c_int64, ci, ci, dp, dp, dp, C.c_uint64, fp, i32p]
+        L.oracle_gbms_d.argtypes = [fp, C.c_int64, ci, C.c_double, ci, C.POINTER(ci), dp, i32p]
         _lib = L
     return _lib
 
@@ -308,3 +309,18 @@ def loglik_grad(pts, logits, means, chol, pose=None, want_points: bool = True):
                                   _p(gt, C.c_double), _p(gl, C.c_double), _p(gm, C.c_double), _p(gc, C.c_double))
     _check(st, "loglik_grad")
     return dict(loglik=ll.value, grad_points=gp, grad_twist=gt, grad_logits=gl, grad_means=gm, grad_chol=gc)
+
+
+def gbms(pts, bandwidth: float, max_iter: int = 300):
+    """Mode seeking that sets K (Sec. V GBMS): (modes (K,d) float64 in rank order,
+    counts (K,) int32).  d from the points (3 or 4)."""
+    pts = _f32(pts)
+    d = _dim(pts)
+    N = pts.shape[0]
+    modes = np.empty((N, d))
+    counts = np.empty(N, np.int32)
+    k = C.c_int(0)
+    st = lib().oracle_gbms_d(_p(pts, C.c_float), N, d, float(bandwidth), max_iter, C.byref(k),
+                             _p(modes, C.c_double), _p(counts, C.c_int32))
+    _check(st, "gbms")
+    return modes[:k.value].copy(), counts[:k.value].copy()

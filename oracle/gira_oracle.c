@@ -678,3 +678,135 @@ int oracle_sample_d(int64_t M, int K, int d, const double *weights, const double
     free(L); free(cum);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------ GBMS -- */
+/* Mode seeking that sets the number of components K (Sec. V, paragraph
+ * "Gaussian Blurring Mean Shift", and Fig. "information flow"): seeds from a
+ * binned estimator (Comaniciu & Meer 2002), each seed moved to the average of
+ * the points within the bandwidth h of it until it stops moving or an iteration
+ * limit is reached; the distinct end points are the modes.  Written out:
+ *
+ *   cells   c_i(x) = floor(x_i / h + 0.5)  (binary64);  one seed per occupied
+ *           cell, at c h; seeds in ascending order of the cell key
+ *           sum_i (c_i + 2^15) 2^(16 i)  (the last coordinate most significant).
+ *   ball    x is within h of m when  s <= (float)(h*h),  s the binary32 squared
+ *           distance between x and m rounded to binary32, in the order
+ *           ((d0^2 + d1^2) + d2^2) [+ d3^2], each operation rounded (no FMA).
+ *   mean    exact sums of q(x_i) = rint(x_i 2^24) in 64-bit integers;
+ *           m_i = ((double)S_i / count) 2^-24.
+ *   moves   m_0 = seed; m_t = mean of the ball of m_{t-1}; stop after the first
+ *           t with ||m_t - m_{t-1}||^2 <= (1e-3 h)^2 (binary64) or t = max_iter;
+ *           the mode is m_t with count = the size of that last ball.  A seed
+ *           whose ball is empty is dropped.
+ *   merge   modes ranked by count (descending), ties by seed order; in rank
+ *           order a mode is kept unless a kept mode lies within h of it
+ *           (binary64 squared distance <= h*h, coordinate order, no FMA).
+ *
+ * The fixed point makes the mean independent of the order of summation, so an
+ * implementation that gathers the ball in another order reaches the same bits.
+ * Requires |x_i| < 2^12 and |c_i| < 2^15 (else OR_ERR_INVALID_ARG).
+ * Outputs: *K, modes (K x d binary64, rank order; capacity N x d), counts (K),
+ * all may be NULL except K. */
+static int cell_of(double v, double h, int32_t *c) {
+    const double f = floor(v / h + 0.5);
+    if (!(f > -32768.0 && f < 32768.0)) return 0;
+    *c = (int32_t)f;
+    return 1;
+}
+static uint64_t cell_key(const int32_t *c, int d) {
+    uint64_t k = 0;
+    for (int i = 0; i < d; ++i) k |= (uint64_t)(uint32_t)(c[i] + 32768) << (16 * i);
+    return k;
+}
+static int cmp_u64(const void *a, const void *b) {
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+typedef struct { int32_t count; int32_t seed; } ModeRank;
+static int cmp_rank(const void *a, const void *b) {
+    const ModeRank *x = (const ModeRank *)a, *y = (const ModeRank *)b;
+    if (x->count != y->count) return x->count > y->count ? -1 : 1;
+    return (x->seed > y->seed) - (x->seed < y->seed);
+}
+
+int oracle_gbms_d(const float *pts, int64_t N, int d, double h, int max_iter, int *K, double *modes_out,
+                  int32_t *counts_out) {
+    if (N < 1 || !valid_dim(d) || !pts || !K || !(h > 0.0) || !isfinite(h) || max_iter < 1) return OR_ERR_INVALID_ARG;
+    if (!all_finite_f(pts, (int64_t)d * N)) return OR_ERR_NONFINITE;
+    const float h2f = (float)(h * h);
+    const double thr2 = (1e-3 * h) * (1e-3 * h);
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    int64_t *q = (int64_t *)malloc(sizeof(int64_t) * d * N);
+    if (!keys || !q) { free(keys); free(q); return OR_ERR_OOM; }
+    for (int64_t n = 0; n < N; ++n) {
+        int32_t c[DMAX];
+        for (int i = 0; i < d; ++i) {
+            const float x = pts[(size_t)d * n + i];
+            if (!(fabsf(x) < 4096.0f) || !cell_of((double)x, h, &c[i])) { free(keys); free(q); return OR_ERR_INVALID_ARG; }
+            q[(size_t)d * n + i] = llrint(ldexp((double)x, 24));
+        }
+        keys[n] = cell_key(c, d);
+    }
+    qsort(keys, (size_t)N, sizeof(uint64_t), cmp_u64);
+    int64_t S = 0;   /* distinct cells, compacted in place */
+    for (int64_t n = 0; n < N; ++n)
+        if (n == 0 || keys[n] != keys[n - 1]) keys[S++] = keys[n];
+    double *modes = (double *)malloc(sizeof(double) * d * S);
+    ModeRank *rank = (ModeRank *)malloc(sizeof(ModeRank) * S);
+    if (!modes || !rank) { free(keys); free(q); free(modes); free(rank); return OR_ERR_OOM; }
+    int64_t live = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        double m[DMAX];
+        for (int i = 0; i < d; ++i) m[i] = (double)((int32_t)((keys[s] >> (16 * i)) & 0xFFFF) - 32768) * h;
+        int32_t count = 0;
+        for (int t = 1; t <= max_iter; ++t) {
+            float mf[DMAX];
+            for (int i = 0; i < d; ++i) mf[i] = (float)m[i];
+            int64_t sum[DMAX] = {0, 0, 0, 0};
+            count = 0;
+            for (int64_t n = 0; n < N; ++n)
+                if (dist2_f32(pts + (size_t)d * n, mf, d) <= h2f) {
+                    ++count;
+                    for (int i = 0; i < d; ++i) sum[i] += q[(size_t)d * n + i];
+                }
+            if (count == 0) break;
+            double mv = 0.0;
+            for (int i = 0; i < d; ++i) {
+                const double v = ldexp((double)sum[i] / (double)count, -24);
+                const double dv = v - m[i];
+                mv = (i == 0) ? dv * dv : mv + dv * dv;
+                m[i] = v;
+            }
+            if (mv <= thr2) break;
+        }
+        if (count == 0) continue;   /* dropped */
+        memcpy(modes + (size_t)d * live, m, sizeof(double) * d);
+        rank[live].count = count;
+        rank[live].seed = (int32_t)live;   /* live modes keep the seed order */
+        ++live;
+    }
+    qsort(rank, (size_t)live, sizeof(ModeRank), cmp_rank);
+    int kept = 0;
+    int32_t *keep_idx = (int32_t *)malloc(sizeof(int32_t) * (live > 0 ? live : 1));
+    if (!keep_idx) { free(keys); free(q); free(modes); free(rank); return OR_ERR_OOM; }
+    for (int64_t r = 0; r < live; ++r) {
+        const double *a = modes + (size_t)d * rank[r].seed;
+        int near = 0;
+        for (int j = 0; j < kept && !near; ++j) {
+            const double *b = modes + (size_t)d * keep_idx[j];
+            double s2 = 0.0;
+            for (int i = 0; i < d; ++i) {
+                const double dv = a[i] - b[i];
+                s2 = (i == 0) ? dv * dv : s2 + dv * dv;
+            }
+            near = s2 <= h * h;
+        }
+        if (near) continue;
+        if (modes_out) memcpy(modes_out + (size_t)d * kept, a, sizeof(double) * d);
+        if (counts_out) counts_out[kept] = rank[r].count;
+        keep_idx[kept++] = rank[r].seed;
+    }
+    *K = kept;
+    free(keys); free(q); free(modes); free(rank); free(keep_idx);
+    return OR_OK;
+}

@@ -478,6 +478,30 @@ def bench_d4(gira, frame_pts, sms, mhz, reps=5):
             "sample_ms": samp_ms, "sample_points_per_s": n / (samp_ms / 1e3)}
 
 
+GBMS_H = 0.05
+
+
+def bench_gbms(gira, frame_pts, reps=5):
+    """Mode seeking that sets K on the frame with intensity (N x 4), bandwidth 0.05:
+    binned seeds, flat-kernel moves to <= 1e-3 h or 300 iterations, merge."""
+    import torch
+    from paper_2307_00071_gb300 import synth
+    pts4 = np.concatenate([frame_pts, synth.frame_intensity(frame_pts, 1)[:, None]], axis=1)
+    x = torch.as_tensor(pts4, device="cuda")
+    gira.gira_gbms(x, GBMS_H)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        m, c = gira.gira_gbms(x, GBMS_H)
+    ev1.record()
+    torch.cuda.synchronize()
+    seeds = len(np.unique(np.floor(pts4.astype(np.float64) / GBMS_H + 0.5), axis=0))
+    return {"workload": f"frame with intensity (N={len(pts4)} x 4), bandwidth {GBMS_H}, max_iter 300",
+            "ms_per_call": ev0.elapsed_time(ev1) / reps, "K": int(len(m)), "seeds": int(seeds),
+            "largest_mode_count": int(c[0])}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -592,7 +616,8 @@ def run_gira(args):
             line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira),
                               "large_map": bench_large_map(gira),
                               "batched_registrations": bench_batched_registrations(gira, frame.points),
-                              "xyz_intensity": bench_d4(gira, frame.points, sms, mhz)}
+                              "xyz_intensity": bench_d4(gira, frame.points, sms, mhz),
+                              "gbms": bench_gbms(gira, frame.points)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

@@ -288,6 +288,36 @@ gira_status gira_gmm_sample(int64_t m, int k, int d, const float *weights, const
                             uint64_t seed, float *out, int32_t *components, void *stream);
 
 /*
+ * gira_gbms -- the number of components from a bandwidth (Sec. V, paragraph
+ * "Gaussian Blurring Mean Shift", and Fig. "information flow": the step before
+ * KInit).  Seeds from a binned estimator, each moved to the average of the
+ * points within the bandwidth h of it until it stops; the distinct end points
+ * (modes) give K.  Exactly:
+ *   cells   c_i(x) = floor(x_i / h + 0.5) (binary64); one seed per occupied
+ *           cell, at c h, in ascending order of sum_i (c_i + 2^15) 2^(16 i)
+ *   ball    points whose binary32 squared distance to m (rounded to binary32),
+ *           ((d0^2 + d1^2) + d2^2) [+ d3^2] without FMA, is <= (float)(h*h)
+ *   mean    ((double)S_i / count) * 2^-24 with S_i the exact 64-bit sum of
+ *           rint(x_i * 2^24) over the ball (independent of summation order)
+ *   stop    after the first move with ||m_t - m_{t-1}||^2 <= (1e-3 h)^2
+ *           (binary64) or after max_iter moves; a seed whose ball empties is
+ *           dropped; count = the size of its last ball
+ *   merge   modes ranked by count (descending), ties by seed order; a mode is
+ *           kept unless a kept mode of lower rank is within h (binary64
+ *           squared distance <= h*h)
+ *
+ *   points     [host|device] N x d binary32, d = 3 (xyz) or 4 (xyz + intensity);
+ *              |x_i| < 4096 and |c_i| < 32768 (else GIRA_ERR_INVALID_ARG)
+ *   bandwidth  h > 0
+ *   max_iter   >= 1 (moves per seed)
+ *   k          [host] number of modes K (written)
+ *   modes      [host|device] capacity N x d binary64: the K modes in rank order, or NULL
+ *   counts     [host|device] capacity N int32: each mode's count, or NULL
+ */
+gira_status gira_gbms(const float *points, int64_t n, int d, double bandwidth, int max_iter, int *k,
+                      double *modes, int32_t *counts, void *stream);
+
+/*
  * Profiling (off by default; process-wide).  When enabled, each call records
  * CUDA events on its stream around its phases and around every launch of the
  * fused E-step/statistics kernel, and accumulates the device times below when

@@ -2050,4 +2050,135 @@ gira_status gira_gmm_sample(int64_t m, int k, int d, const float* weights, const
     return device_status(h);
 }
 
+
+// ================================================================ gbms (K from a bandwidth)
+gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, int max_iter, int* k_out,
+                      double* modes, int32_t* counts, void* stream) {
+    reset_error();
+    if (n < 1 || n > (int64_t)INT_MAX / 2) return fail(GIRA_ERR_INVALID_ARG, "n = %lld outside [1, 2^30]", (long long)n);
+    if (d != 3 && d != 4) return fail(GIRA_ERR_INVALID_ARG, "d = %d is neither 3 nor 4", d);
+    if (!(bandwidth > 0.0) || !std::isfinite(bandwidth)) return fail(GIRA_ERR_INVALID_ARG, "bandwidth must be > 0");
+    if (max_iter < 1) return fail(GIRA_ERR_INVALID_ARG, "max_iter < 1");
+    if (!points || !k_out) return fail(GIRA_ERR_INVALID_ARG, "points and k must not be NULL");
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, km = Kind::Host, kq = Kind::Host;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    if (modes) TRY(check_ptr(modes, "modes", c.dev, &km));
+    if (counts) TRY(check_ptr(counts, "counts", c.dev, &kq));
+    const size_t tb = gbms_temp_bytes(n, d);
+    struct Bufs {
+        DeviceState* st;
+        float* pin;
+        float4 *p4, *spts;
+        uint64_t *keys, *keys2, *ukeys, *rkeys, *rkeys2, *mkeys, *mkeys2, *mukeys;
+        int *idx, *idx2, *ulen, *ustart, *ints, *mcount, *rcount, *midx, *midx2, *mulen, *mustart, *state, *flags,
+            *pos, *cout;
+        double4 *modes64, *rmodes;
+        double* mout;
+        void* temp;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.pin = cv.take<float>(kp == Kind::Host ? (size_t)d * n : 0);
+        b.p4 = cv.take<float4>(n);
+        b.spts = cv.take<float4>(n);
+        for (uint64_t** p : {&b.keys, &b.keys2, &b.ukeys, &b.rkeys, &b.rkeys2, &b.mkeys, &b.mkeys2, &b.mukeys})
+            *p = cv.take<uint64_t>(n);
+        for (int** p : {&b.idx, &b.idx2, &b.ulen, &b.ustart, &b.mcount, &b.rcount, &b.midx, &b.midx2, &b.mulen,
+                        &b.mustart, &b.state, &b.flags, &b.pos})
+            *p = cv.take<int>(n);
+        b.ints = cv.take<int>(4);   // cells, live modes, mode cells, undecided
+        b.modes64 = cv.take<double4>(n);
+        b.rmodes = cv.take<double4>(n);
+        b.mout = cv.take<double>((modes && km == Kind::Host) ? (size_t)d * n : 0);
+        b.cout = cv.take<int>((counts && kq == Kind::Host) ? n : 0);
+        b.temp = cv.take<unsigned char>(tb);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+    int* ncells = b.ints;
+    int* nlive = b.ints + 1;
+    int* mncells = b.ints + 2;
+    int* undecided = b.ints + 3;
+
+    CallProfile prof;
+    prof.on = g_prof_on.load() != 0;
+    prof.s = c.s;
+    prof.t0 = prof.mark();
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemsetAsync(b.ints, 0, sizeof(int) * 4, c.s));
+    const float* pts = points;
+    if (kp == Kind::Host) {
+        GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * d * n, cudaMemcpyHostToDevice, c.s));
+        pts = b.pin;
+    }
+    COUNTED(prof, 1, launch_gbms_keys(pts, n, d, bandwidth, b.p4, b.keys, b.idx, b.st, c.s));
+    COUNTED(prof, 3, gbms_sort_cells(b.temp, tb, b.keys, b.keys2, b.idx, b.idx2, n, d, b.ukeys, b.ulen, b.ustart,
+                                     ncells, c.s));
+    int hints[4];
+    GIRA_CUDA(cudaMemcpyAsync(hints, b.ints, sizeof hints, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    TRY(device_status(h));
+    const int S = hints[0];
+    prof.t_init = prof.mark();
+    COUNTED(prof, 1, launch_gbms_gather(b.p4, b.idx2, n, b.spts, c.s));
+    COUNTED(prof, 1, launch_gbms_shift(b.spts, b.ukeys, b.ustart, b.ulen, S, d, bandwidth, max_iter, b.modes64,
+                                       b.mcount, b.st, c.s));
+    COUNTED(prof, 2, launch_gbms_rank(b.temp, tb, b.mcount, S, b.rkeys, b.rkeys2, nlive, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(hints, b.ints, sizeof hints, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    const int L = hints[1];
+    int K = 0;
+    if (L > 0) {
+        COUNTED(prof, 1, launch_gbms_rank_modes(b.rkeys2, nlive, L, b.modes64, b.mcount, d, bandwidth, b.rmodes,
+                                                b.rcount, b.mkeys, b.midx, b.state, b.st, c.s));
+        COUNTED(prof, 3, gbms_sort_cells(b.temp, tb, b.mkeys, b.mkeys2, b.midx, b.midx2, L, d, b.mukeys, b.mulen,
+                                         b.mustart, mncells, c.s));
+        // every round decides at least the lowest undecided rank: at most L rounds
+        for (int round = 0; round < L; round += 2) {
+            GIRA_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), c.s));
+            COUNTED(prof, 1, launch_gbms_merge_round(b.rmodes, nlive, L, b.mukeys, b.mustart, b.mulen, mncells,
+                                                     b.midx2, d, bandwidth, b.state, undecided, c.s));
+            GIRA_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), c.s));
+            COUNTED(prof, 1, launch_gbms_merge_round(b.rmodes, nlive, L, b.mukeys, b.mustart, b.mulen, mncells,
+                                                     b.midx2, d, bandwidth, b.state, undecided, c.s));
+            int open = 0;
+            GIRA_CUDA(cudaMemcpyAsync(&open, undecided, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+            GIRA_CUDA(cudaStreamSynchronize(c.s));
+            if (open == 0) break;
+        }
+        double* m_d = modes ? ((km == Kind::Device) ? modes : b.mout) : nullptr;
+        int* q_d = counts ? ((kq == Kind::Device) ? counts : b.cout) : nullptr;
+        COUNTED(prof, 3, launch_gbms_output(b.temp, tb, b.state, nlive, L, b.rmodes, b.rcount, d, b.flags, b.pos,
+                                            m_d, q_d, c.s));
+        int last[2];
+        GIRA_CUDA(cudaMemcpyAsync(&last[0], b.pos + (L - 1), sizeof(int), cudaMemcpyDeviceToHost, c.s));
+        GIRA_CUDA(cudaMemcpyAsync(&last[1], b.flags + (L - 1), sizeof(int), cudaMemcpyDeviceToHost, c.s));
+        GIRA_CUDA(cudaStreamSynchronize(c.s));
+        K = last[0] + last[1];
+        if (modes && km == Kind::Host && K > 0)
+            GIRA_CUDA(cudaMemcpyAsync(modes, b.mout, sizeof(double) * d * K, cudaMemcpyDeviceToHost, c.s));
+        if (counts && kq == Kind::Host && K > 0)
+            GIRA_CUDA(cudaMemcpyAsync(counts, b.cout, sizeof(int) * K, cudaMemcpyDeviceToHost, c.s));
+    }
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    prof.t_em = prof.mark();
+    prof.t_end = prof.t_em;
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    prof.commit(0, 0);
+    TRY(device_status(h));
+    *k_out = K;
+    return GIRA_OK;
+}
+
 }  // extern "C"

@@ -545,6 +545,42 @@ cudaError_t launch_conditional4(const float* locs, int64_t m, int k, const float
 cudaError_t launch_sample(int64_t m, int k, int d, const float* w, const float* mu, const float* cov, uint64_t seed,
                           double* cum, double* chol, float* out, int32_t* comp, DeviceState* st, cudaStream_t s);
 
+// ---------------------------------------------------------------- mode seeking (K from a bandwidth)
+// Temporary bytes the sorts / scans of one gira_gbms call need for n points.
+size_t gbms_temp_bytes(int64_t n, int d);
+// Points -> float4 copies, cell keys and identity indices; flags non-finite input
+// (GIRA_ERR_NONFINITE_INPUT) and coordinates outside the cell range (GIRA_ERR_INVALID_ARG).
+cudaError_t launch_gbms_keys(const float* pts, int64_t n, int d, double h, float4* pts4, uint64_t* keys, int* idx,
+                             DeviceState* st, cudaStream_t s);
+// Sort (key, index) pairs by key, then the distinct keys, their run lengths and
+// starts; *ncells (device) receives the number of distinct keys.
+cudaError_t gbms_sort_cells(void* temp, size_t temp_bytes, const uint64_t* keys_in, uint64_t* keys_out,
+                            const int* idx_in, int* idx_out, int64_t n, int d, uint64_t* ukeys, int* ulen,
+                            int* ustart, int* ncells, cudaStream_t s);
+cudaError_t launch_gbms_gather(const float4* pts4, const int* idx, int64_t n, float4* spts, cudaStream_t s);
+// One warp per seed (cell): the seed's moves; modes[s] and counts[s] (0: dropped).
+cudaError_t launch_gbms_shift(const float4* spts, const uint64_t* ukeys, const int* ustart, const int* ulen,
+                              int ncells, int d, double h, int max_iter, double4* modes, int* counts,
+                              const DeviceState* st, cudaStream_t s);
+// Rank keys of the ns seeds and their sort; *nlive (device, zeroed by the caller)
+// receives the number of live modes.
+cudaError_t launch_gbms_rank(void* temp, size_t temp_bytes, const int* counts, int ns, uint64_t* rkeys,
+                             uint64_t* rkeys_sorted, int* nlive, cudaStream_t s);
+// Live modes in rank order (rmodes, rcount), their cell keys and rank indices for
+// the merge grid, and the merge state (undecided).
+cudaError_t launch_gbms_rank_modes(const uint64_t* rkeys_sorted, const int* nlive, int nmax, const double4* modes,
+                                   const int* counts, int d, double h, double4* rmodes, int* rcount, uint64_t* mkeys,
+                                   int* midx, int* state, DeviceState* st, cudaStream_t s);
+// One merge round; *undecided (zeroed by the caller) counts ranks still open.
+cudaError_t launch_gbms_merge_round(const double4* rmodes, const int* nlive, int nmax, const uint64_t* mukeys,
+                                    const int* mustart, const int* mulen, const int* mncells, const int* midx_sorted,
+                                    int d, double h, int* state, int* undecided, cudaStream_t s);
+// Kept modes in rank order -> modes_out (k x d binary64) and counts_out (nullable);
+// pos[r] is the output slot of rank r (exclusive sum of the kept flags).
+cudaError_t launch_gbms_output(void* temp, size_t temp_bytes, const int* state, const int* nlive, int nmax,
+                               const double4* rmodes, const int* rcount, int d, int* flags, int* pos,
+                               double* modes_out, int* counts_out, cudaStream_t s);
+
 // Set this thread's last-error message (msg may be nullptr to keep it) and
 // component (what gira_last_error_message / gira_last_error_component return).
 void record_error(const char* msg, int component);

@@ -64,7 +64,8 @@ def _load():
     lib.gira_gmm_loglik4.argtypes = [vp, i64, C.c_int, vp, vp, vp, dp, vp, vp]
     lib.gira_gmm_conditional4.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, vp, vp]
     lib.gira_gmm_sample.argtypes = [i64, C.c_int, C.c_int, vp, vp, vp, C.c_uint64, vp, vp, vp]
-    for f in ("gira_gmm_fit4", "gira_gmm_loglik4", "gira_gmm_conditional4", "gira_gmm_sample"):
+    lib.gira_gbms.argtypes = [vp, i64, C.c_int, C.c_double, C.c_int, ip, vp, vp, vp]
+    for f in ("gira_gmm_fit4", "gira_gmm_loglik4", "gira_gmm_conditional4", "gira_gmm_sample", "gira_gbms"):
         getattr(lib, f).restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
         getattr(lib, f).restype = C.c_int
@@ -469,3 +470,22 @@ def gira_gmm_sample(m: int, weights, means, covs, seed: int = 0, device=None, wa
     qp, kq, _ = _ptr(comp)
     _check(_lib.gira_gmm_sample(m, k, d, wp, mp, cp, seed, op, qp, s))
     return out, comp
+
+
+# ----------------------------------------------------------------------------- K from a bandwidth
+def gira_gbms(points, bandwidth: float, max_iter: int = 300):
+    """Mode seeking that sets K (Sec. V "Gaussian Blurring Mean Shift"): binned seeds
+    moved to the average of the points within ``bandwidth`` until they stop; the
+    distinct end points are the modes.  points: N x 3 or N x 4 float32.  Returns
+    (modes (K, d) float64 in rank order, counts (K,) int32) on the side of the points."""
+    if points.ndim != 2 or points.shape[1] not in (3, 4):
+        raise ValueError("points must be N x 3 or N x 4")
+    n, d = int(points.shape[0]), int(points.shape[1])
+    modes = _new(points, (n, d), np.float64)
+    counts = _new(points, (n,), np.int32)
+    pp, kp, s = _ptr(points)
+    mp, km, _ = _ptr(modes)
+    cp, kc, _ = _ptr(counts)
+    k = C.c_int(0)
+    _check(_lib.gira_gbms(pp, n, d, float(bandwidth), max_iter, C.byref(k), mp, cp, s))
+    return modes[:k.value], counts[:k.value]

@@ -146,3 +146,18 @@ def test_d4_invalid_arguments_rejected_without_gpu():
                              None) == gira.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         gira.gira_gmm_fit4(np.zeros((5, 3), np.float32), 1)
+
+
+def test_gbms_invalid_arguments_rejected_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    pts = np.zeros((10, 3), np.float32)
+    k = C.c_int(0)
+    assert L.gira_gbms(pts.ctypes.data, 10, 5, 0.1, 10, C.byref(k), None, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gbms(pts.ctypes.data, 10, 3, 0.0, 10, C.byref(k), None, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gbms(pts.ctypes.data, 10, 3, float("nan"), 10, C.byref(k), None, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gbms(pts.ctypes.data, 10, 3, 0.1, 0, C.byref(k), None, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gbms(pts.ctypes.data, 0, 3, 0.1, 10, C.byref(k), None, None, None) == gira.ERR_INVALID_ARG
+    assert L.gira_gbms(pts.ctypes.data, 10, 3, 0.1, 10, None, None, None, None) == gira.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        gira.gira_gbms(np.zeros((4, 2), np.float32), 0.1)

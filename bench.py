@@ -247,7 +247,7 @@ def bench_grad(gira, frame_pts, sms, mhz, reps=20):
     peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / GRAD_FP32_OPS
     return {"workload": f"L and all gradients: {GRAD_SCAN}-point scan, K={GRAD_K} GMM of the frame, 10 deg + 0.17 m offset",
             "unit": UNIT, "value": units / call_s, "ms_per_call": call_s * 1e3,
-            "kernel": "estep_kernel<2,8,128,2,true,true> (fused log-likelihood adjoint)",
+            "kernel": "estep_kernel<2,8,256,1,true,true> (fused log-likelihood adjoint, K=1024: 8 warps)",
             "kernel_ms": kern_s * 1e3, "kernel_units_per_s": units / kern_s if kern_s else None,
             "frac_fp32": (units / kern_s) / peak if kern_s else None,
             "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {GRAD_FP32_OPS} FP32 ops per unit"}

@@ -29,7 +29,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int Q4 = 8;
-constexpr int PPC4_MAX = 4096;                          // points staged per CTA (64 KB)
+constexpr int PPC4_MAX = 2048;                          // points staged per CTA (64 KB)
 constexpr long long MBAR_LIMIT4 = 2000000000ll;         // bound on the TMA wait: 2 s of wall time
 constexpr float LN2F4 = 0.693147180559945309f;
 constexpr double LN2_4 = 0.693147180559945309417232121458;
@@ -37,23 +37,28 @@ constexpr double LN2_4 = 0.693147180559945309417232121458;
 // lower-triangular index of (i, j), j <= i: 00,10,11,20,21,22,30,31,32,33
 __host__ __device__ constexpr int tri4(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Slot s of component b in the pair-interleaved parameter buffer.
+__host__ __device__ __forceinline__ size_t slot4(int b, int s) {
+    return (size_t)(b >> 1) * PAIR4_FLOATS + 2 * s + (b & 1);
+}
+
 template <bool STATS>
-__global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
+__global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
     extern __shared__ __align__(128) unsigned char dsm4[];
     __shared__ __align__(8) uint64_t bar_tma;
-    __shared__ float red_sum[2][32][Q4];
-    __shared__ float red_aux[2][32][Q4];
-    __shared__ float s_cmax[32], s_wsum[32];
+    __shared__ float red_sum[2][16][Q4];
+    __shared__ float red_aux[2][16][Q4];
+    __shared__ float s_cmax[16], s_wsum[16];
     __shared__ int s_skip, s_norm, s_dead;
     constexpr int LPQ = 32 / Q4;
     const int G = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = threadIdx.x;   // this lane's component
+    const int pr = threadIdx.x;   // this lane's component pair: components 2 pr, 2 pr + 1
     const int64_t begin = (int64_t)blockIdx.x * a.pts_per_cta;
     const int64_t end = min(a.n, begin + a.pts_per_cta);
     const int npts = (int)(end - begin);
     const int nb = (npts + Q4 - 1) / Q4;
-    const float4* spts = reinterpret_cast<const float4*>(dsm4);
+    const float4* spts = reinterpret_cast<const float4*>(dsm4);   // (x,x,y,y)(z,z,w,w) per point
     if (threadIdx.x == 0) {
         s_skip = (a.iter > a.st->stop_after) || (a.st->error != 0);
         s_norm = a.st->w_raw;
@@ -61,28 +66,28 @@ __global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
         if (!s_skip) {
             mbar_init(&bar_tma, 1);
             mbar_fence_init();
-            mbar_expect_tx(&bar_tma, (uint32_t)npts * 16u);
-            tma_load_1d(reinterpret_cast<void*>(dsm4), a.pts4 + begin, (uint32_t)npts * 16u, &bar_tma);
+            mbar_expect_tx(&bar_tma, (uint32_t)npts * 32u);
+            tma_load_1d(reinterpret_cast<void*>(dsm4), a.pts8 + 2 * begin, (uint32_t)npts * 32u, &bar_tma);
         }
     }
     __syncthreads();
     if (s_skip) return;
-    // ---- this lane's component -> registers (padding lanes: c = -inf, never contribute)
-    float P[10], nmu[4], c = -INFINITY, w = 0.f;
-    if (b < a.k) {
-        const float4* src = reinterpret_cast<const float4*>(a.params + (size_t)b * COMP4_FLOATS);
-        const float4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3], v4 = src[4];
-        P[0] = v0.x; P[1] = v0.y; P[2] = v0.z; P[3] = v0.w;
-        P[4] = v1.x; P[5] = v1.y; P[6] = v1.z; P[7] = v1.w;
-        P[8] = v2.x; P[9] = v2.y;
-        c = v3.z;
-        nmu[0] = v3.w; nmu[1] = v4.x; nmu[2] = v4.y; nmu[3] = v4.z;
-        w = v4.w;
-    } else {
-        for (int i = 0; i < 10; ++i) P[i] = 0.f;
-        for (int i = 0; i < 4; ++i) nmu[i] = 0.f;
+    // ---- this lane's pair -> registers (padding components: c = -inf, never contribute)
+    float2 P[10], nmu[4], c, w;
+    {
+        const float4* src = reinterpret_cast<const float4*>(a.params + (size_t)pr * PAIR4_FLOATS);
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = src[i];
+        const float2* f = reinterpret_cast<const float2*>(v);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) P[i] = f[SLOT4_P + i];
+        c = f[SLOT4_C];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nmu[i] = f[SLOT4_NMU + i];
+        w = f[SLOT4_W];
     }
-    float cm = c, ws = w;
+    float cm = fmaxf(c.x, c.y), ws = w.x + w.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         cm = fmaxf(cm, __shfl_xor_sync(FULL, cm, o));
@@ -106,39 +111,38 @@ __global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
         cmax = fmaxf(cmax, s_cmax[i]);
         wsum += s_wsum[i];
     }
-    const float cc = cmax - c;   // >= 0; +inf for padding
+    const float2 cc = f2(cmax - c.x, cmax - c.y);   // >= 0; +inf for padding
     const float ref0 = s_norm ? cmax - __log2f(wsum) : cmax;
-    float S[NSTAT4];
+    float2 S[NSTAT4];   // statistics of the lane's two components, packed
     if (STATS)
 #pragma unroll
-        for (int i = 0; i < NSTAT4; ++i) S[i] = 0.f;
+        for (int i = 0; i < NSTAT4; ++i) S[i] = f2(0.f, 0.f);
     double ll_acc = 0.0;
     const int myq = q_of_lane<Q4>(lane);
     const bool owner = (warp == 0) && ((lane & (LPQ - 1)) == 0);
 
-    // q' = |P'(x - mu)|^2 + (cmax - c): minus the base-2 logit relative to cmax
-    auto qform = [&](const float4 x, float (&d)[4]) {
-        d[0] = x.x + nmu[0];
-        d[1] = x.y + nmu[1];
-        d[2] = x.z + nmu[2];
-        d[3] = x.w + nmu[3];
-        const float y0 = P[0] * d[0];
-        const float y1 = fmaf(P[2], d[1], P[1] * d[0]);
-        const float y2 = fmaf(P[5], d[2], fmaf(P[4], d[1], P[3] * d[0]));
-        const float y3 = fmaf(P[9], d[3], fmaf(P[8], d[2], fmaf(P[7], d[1], P[6] * d[0])));
-        return fmaf(y3, y3, fmaf(y2, y2, fmaf(y1, y1, fmaf(y0, y0, cc))));
+    // q' = |P'(x - mu)|^2 + (cmax - c) for both components: minus the base-2
+    // logit relative to cmax (packed: one FFMA2 / FADD2 / FMUL2 per pair)
+    auto qform = [&](int li) {
+        const float4 xy = spts[2 * li], zw = spts[2 * li + 1];
+        const float2 d0 = add2(f2(xy.x, xy.y), nmu[0]), d1 = add2(f2(xy.z, xy.w), nmu[1]);
+        const float2 d2 = add2(f2(zw.x, zw.y), nmu[2]), d3 = add2(f2(zw.z, zw.w), nmu[3]);
+        const float2 y0 = mul2(P[0], d0);
+        const float2 y1 = fma2(P[2], d1, mul2(P[1], d0));
+        const float2 y2 = fma2(P[5], d2, fma2(P[4], d1, mul2(P[3], d0)));
+        const float2 y3 = fma2(P[9], d3, fma2(P[8], d2, fma2(P[7], d1, mul2(P[6], d0))));
+        return fma2(y3, y3, fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, cc))));
     };
-    float E[Q4];
+    float2 E[Q4];
     for (int t = 0; t < nb; ++t) {
         const int lb = t * Q4, nvalid = min(Q4, npts - lb);
-        // pass 1: e for (point, own component), per-point sums over the CTA
+        // pass 1: e for (point, own components), per-point sums over the CTA
         float part[Q4];
 #pragma unroll
         for (int q = 0; q < Q4; ++q) {
-            float d[4];
-            const float e = ex2_approx(-qform(spts[(q < nvalid) ? lb + q : lb], d));
-            E[q] = e;
-            part[q] = e;
+            const float2 nq = qform((q < nvalid) ? lb + q : lb);
+            E[q] = f2(ex2_approx(-nq.x), ex2_approx(-nq.y));
+            part[q] = E[q].x + E[q].y;
         }
         const float wt = warp_transpose_reduce<Q4>(part, lane, AddOp());
         if ((lane & (LPQ - 1)) == 0) red_sum[t & 1][warp][myq] = wt;
@@ -152,9 +156,9 @@ __global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
             float m[Q4];
 #pragma unroll
             for (int q = 0; q < Q4; ++q) {
-                float d[4];
-                E[q] = -qform(spts[(q < nvalid) ? lb + q : lb], d);
-                m[q] = E[q];
+                const float2 nq = qform((q < nvalid) ? lb + q : lb);
+                E[q] = f2(-nq.x, -nq.y);
+                m[q] = fmaxf(E[q].x, E[q].y);
             }
             float mt = warp_transpose_reduce<Q4>(m, lane, MaxOp());
             if ((lane & (LPQ - 1)) == 0) red_aux[0][warp][myq] = mt;
@@ -166,8 +170,8 @@ __global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
             for (int q = 0; q < Q4; ++q) {
                 float mq = __shfl_sync(FULL, mt, q * LPQ);
                 mq = (mq > -INFINITY) ? mq : 0.f;
-                E[q] = ex2_approx(E[q] - mq);
-                p2[q] = E[q];
+                E[q] = f2(ex2_approx(E[q].x - mq), ex2_approx(E[q].y - mq));
+                p2[q] = E[q].x + E[q].y;
             }
             const float w2 = warp_transpose_reduce<Q4>(p2, lane, AddOp());
             if ((lane & (LPQ - 1)) == 0) red_aux[1][warp][myq] = w2;
@@ -185,30 +189,39 @@ __global__ void __launch_bounds__(1024, 1) estep4_kernel(const EStep4Launch a) {
         }
         const float r = ok ? __frcp_rn(tot) : 0.f;
         if (STATS) {
-            // pass 2: S0 = sum g, S1 = sum g d, S2 = sum g d d^T about mu_b
+            // pass 2: S0 = sum g, S1 = sum g d, S2 = sum g d d^T about mu_b, both
+            // components at once (packed)
 #pragma unroll
             for (int q = 0; q < Q4; ++q) {
                 const float R = __shfl_sync(FULL, r, q * LPQ);
-                const float4 x = spts[(q < nvalid) ? lb + q : lb];
-                const float g = E[q] * R;
-                const float d[4] = {x.x + nmu[0], x.y + nmu[1], x.z + nmu[2], x.w + nmu[3]};
-                float gd[4];
+                const int li = (q < nvalid) ? lb + q : lb;
+                const float4 xy = spts[2 * li], zw = spts[2 * li + 1];
+                const float2 g = mul2(E[q], dup(R));
+                const float2 d[4] = {add2(f2(xy.x, xy.y), nmu[0]), add2(f2(xy.z, xy.w), nmu[1]),
+                                     add2(f2(zw.x, zw.y), nmu[2]), add2(f2(zw.z, zw.w), nmu[3])};
+                float2 gd[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) gd[i] = g * d[i];
-                S[0] += g;
+                for (int i = 0; i < 4; ++i) gd[i] = mul2(g, d[i]);
+                S[0] = add2(S[0], g);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) S[1 + i] += gd[i];
+                for (int i = 0; i < 4; ++i) S[1 + i] = add2(S[1 + i], gd[i]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = i; j < 4; ++j) S[5 + sym4(i, j)] = fmaf(gd[i], d[j], S[5 + sym4(i, j)]);
+                    for (int j = i; j < 4; ++j) S[5 + sym4(i, j)] = fma2(gd[i], d[j], S[5 + sym4(i, j)]);
             }
         }
     }
-    if (STATS && b < a.k) {
-        float* dst = a.partials + ((size_t)blockIdx.x * a.k + b) * NSTAT4;
+    if (STATS) {
 #pragma unroll
-        for (int i = 0; i < NSTAT4; ++i) dst[i] = S[i];
+        for (int h = 0; h < 2; ++h) {
+            const int b = 2 * pr + h;
+            if (b < a.k) {
+                float* dst = a.partials + ((size_t)blockIdx.x * a.k + b) * NSTAT4;
+#pragma unroll
+                for (int i = 0; i < NSTAT4; ++i) dst[i] = h ? S[i].y : S[i].x;
+            }
+        }
     }
     if (warp == 0) {
         double v = ll_acc;
@@ -248,14 +261,12 @@ __device__ bool build_component4(int b, double w, const double mu[4], const doub
         }
     const double alpha = 0.84932180028801904272;   // sqrt(log2(e) / 2)
     const double LOG2_2PI = 2.6514961294723187980;  // log2(2 pi)
-    float* base = params + (size_t)b * COMP4_FLOATS;
     for (int i = 0; i < 4; ++i)
-        for (int j = 0; j <= i; ++j) base[SLOT4_P + tri4(i, j)] = (float)(alpha * P[4 * i + j]);
-    for (int i = 0; i < 4; ++i) base[SLOT4_B + i] = 0.f;
+        for (int j = 0; j <= i; ++j) params[slot4(b, SLOT4_P + tri4(i, j))] = (float)(alpha * P[4 * i + j]);
     // log2 w + sum_j log2 P_jj - (4/2) log2(2 pi)
-    base[SLOT4_C] = (float)(log2(w * (P[0] * P[5] * P[10] * P[15])) - 2.0 * LOG2_2PI);
-    for (int i = 0; i < 4; ++i) base[SLOT4_NMU + i] = -(float)mu[i];
-    base[SLOT4_W] = (float)w;
+    params[slot4(b, SLOT4_C)] = (float)(log2(w * (P[0] * P[5] * P[10] * P[15])) - 2.0 * LOG2_2PI);
+    for (int i = 0; i < 4; ++i) params[slot4(b, SLOT4_NMU + i)] = -(float)mu[i];
+    params[slot4(b, SLOT4_W)] = (float)w;
     double* m = model64 + (size_t)b * MODEL4;
     m[0] = w;
     for (int i = 0; i < 4; ++i) m[1 + i] = mu[i];
@@ -302,13 +313,12 @@ __global__ void __launch_bounds__(NSTAT4 * 32) reduce_finalize4_kernel(
     }
     __syncthreads();
     if (t == 0) {
-        const float* base = params + (size_t)b * COMP4_FLOATS;
         double s[4];
         if (shift4) {
             const float4 v = shift4[b];
             s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
         } else {
-            for (int i = 0; i < 4; ++i) s[i] = -(double)base[SLOT4_NMU + i];
+            for (int i = 0; i < 4; ++i) s[i] = -(double)params[slot4(b, SLOT4_NMU + i)];
         }
         const double s0 = Sb[0];
         const double nbw = s0 + 10.0 * DBL_EPSILON;
@@ -387,20 +397,24 @@ __global__ void model_out4_kernel(const double* __restrict__ model64, int k, flo
     }
 }
 
+// Padding components b in [k, kpad): zero parameters, c = -inf.
 __global__ void fill_padding4_kernel(float* params, int k, int kpad) {
     const int b = k + blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= kpad) return;
-    float* base = params + (size_t)b * COMP4_FLOATS;
-    for (int i = 0; i < COMP4_FLOATS; ++i) base[i] = 0.f;
-    base[SLOT4_C] = -INFINITY;
+    for (int i = 0; i < PAIR4_FLOATS / 2; ++i) params[slot4(b, i)] = 0.f;
+    params[slot4(b, SLOT4_C)] = -INFINITY;
 }
 
-__global__ void pack4_kernel(const float* __restrict__ p4in, int64_t n, float4* __restrict__ p4, DeviceState* st) {
+// N x 4 -> p4 (x,y,z,I) (nullable) and p8 (x,x,y,y)(z,z,I,I); flags non-finite input.
+__global__ void pack4_kernel(const float* __restrict__ p4in, int64_t n, float4* __restrict__ p4,
+                             float4* __restrict__ p8, DeviceState* st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 v = make_float4(p4in[4 * i], p4in[4 * i + 1], p4in[4 * i + 2], p4in[4 * i + 3]);
     if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w))) set_error(st, GIRA_ERR_NONFINITE_INPUT);
-    p4[i] = v;
+    if (p4) p4[i] = v;
+    p8[2 * i] = make_float4(v.x, v.x, v.y, v.y);
+    p8[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
 }
 
 // ------------------------------------------------------------------ regression of intensity on xyz
@@ -723,14 +737,14 @@ cudaError_t launch_label_stats4(const float4* pts4, int64_t n, int k, const int3
     return cudaGetLastError();
 }
 
-int estep4_threads(int k) { return 32 * ((k + 31) / 32); }
+int estep4_threads(int k) { return 32 * ((k + 63) / 64); }
 
 // CTAs per SM of the statistics kernel for k components and ppc staged points.
 static int estep4_occupancy(int k, int64_t ppc) {
     int occ = 0;
-    const int smem = (int)(ppc * 16);
-    cudaFuncSetAttribute(estep4_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PPC4_MAX * 16);
-    cudaFuncSetAttribute(estep4_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PPC4_MAX * 16);
+    const int smem = (int)(ppc * 32);
+    cudaFuncSetAttribute(estep4_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PPC4_MAX * 32);
+    cudaFuncSetAttribute(estep4_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PPC4_MAX * 32);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep4_kernel<true>, estep4_threads(k), smem) !=
             cudaSuccess ||
         occ < 1) {
@@ -754,7 +768,7 @@ int estep4_grid(int64_t n, int k, int num_sms, int64_t* ppc) {
 }
 
 cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)a.pts_per_cta * 16;
+    const size_t smem = (size_t)a.pts_per_cta * 32;
     const void* fn = stats ? (const void*)estep4_kernel<true> : (const void*)estep4_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -784,13 +798,14 @@ cudaError_t launch_model_out4(const double* model64, int k, float* w, float* mu,
 }
 
 cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s) {
-    const int kpad = estep4_threads(k);
+    const int kpad = 2 * estep4_threads(k);
     if (kpad > k) fill_padding4_kernel<<<(kpad - k + 63) / 64, 64, 0, s>>>(params, k, kpad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, DeviceState* st, cudaStream_t s) {
-    pack4_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts4in, n, pts4, st);
+cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, float4* pts8, DeviceState* st,
+                         cudaStream_t s) {
+    pack4_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts4in, n, pts4, pts8, st);
     return cudaGetLastError();
 }
 

@@ -192,10 +192,16 @@ __global__ void gbms_keys_kernel(const float* __restrict__ pts, int64_t n, int d
     idx[i] = (int)i;
 }
 
+// Points in cell order, with their fixed-point coordinates rint(x 2^24): x 2^24
+// is exact in binary32 (|x| < 2^12), so one float -> int64 rounding gives it.
 __global__ void gbms_gather_kernel(const float4* __restrict__ pts4, const int* __restrict__ idx, int64_t n,
-                                   float4* spts) {
+                                   float4* spts, longlong2* qxy, longlong2* qzw) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) spts[i] = pts4[idx[i]];
+    if (i >= n) return;
+    const float4 x = pts4[idx[i]];
+    spts[i] = x;
+    qxy[i] = make_longlong2(__float2ll_rn(x.x * Q_SCALE_F), __float2ll_rn(x.y * Q_SCALE_F));
+    qzw[i] = make_longlong2(__float2ll_rn(x.z * Q_SCALE_F), __float2ll_rn(x.w * Q_SCALE_F));
 }
 
 // One CTA (GB_SHIFT_THREADS) per seed: the moves of the seed of cell ukeys[s]
@@ -207,64 +213,80 @@ constexpr int GB_SHIFT_THREADS = 128;
 constexpr int GB_SHIFT_WARPS = GB_SHIFT_THREADS / 32;
 
 __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
-    const float4* __restrict__ spts, const uint64_t* __restrict__ ukeys, const int* __restrict__ ustart,
-    const int* __restrict__ ulen, int ncells, int d, double h, int max_iter, double4* modes, int* counts,
-    const DeviceState* st) {
+    const float4* __restrict__ spts, const longlong2* __restrict__ qxy, const longlong2* __restrict__ qzw,
+    const uint64_t* __restrict__ ukeys, const int* __restrict__ ustart, const int* __restrict__ ulen, int ncells,
+    int d, double h, int max_iter, double4* modes, int* counts, const DeviceState* st) {
     __shared__ int s_cs[GB_MAX_CELLS];
     __shared__ int s_pre[GB_MAX_CELLS + 1];
     __shared__ int s_nf;
     __shared__ long long s_red[GB_SHIFT_WARPS][5];
     __shared__ double s_m[4];
+    __shared__ float s_mf[4];
+    __shared__ int s_lo[4], s_nr[4], s_total, s_moved_cells;
     __shared__ int s_done, s_count;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s = blockIdx.x;
     if (st->error) return;   // set before the launch: uniform
-    const uint64_t key = ukeys[s];
+    // binary64 work (the move, its stopping test, the cells around the seed) is
+    // done by thread 0 alone: GB300 runs binary64 at a small fraction of binary32
+    auto place = [&]() {   // thread 0: binary32 copy of the seed and the cells of its ball
+        double mq[4];
+        for (int i = 0; i < 4; ++i) {
+            s_mf[i] = __double2float_rn(s_m[i]);
+            mq[i] = (double)s_mf[i];
+        }
+        int lo[4], nr[4];
+        s_total = ball_cells(mq, d, h, lo, nr);
+        bool same = true;
+        for (int i = 0; i < d; ++i) {
+            same = same && lo[i] == s_lo[i] && nr[i] == s_nr[i];
+            s_lo[i] = lo[i];
+            s_nr[i] = nr[i];
+        }
+        s_moved_cells = same ? 0 : 1;
+    };
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) s_m[i] = (i < d) ? __dmul_rn((double)cell_coord(key, i), h) : 0.0;
+        const uint64_t key = ukeys[s];
+        for (int i = 0; i < 4; ++i) {
+            s_m[i] = (i < d) ? __dmul_rn((double)cell_coord(key, i), h) : 0.0;
+            s_lo[i] = INT_MIN;
+            s_nr[i] = 0;
+        }
         s_done = 0;
         s_count = 0;
+        place();
     }
     const float h2f = __double2float_rn(__dmul_rn(h, h));
     const double thr = __dmul_rn(1e-3, h), thr2 = __dmul_rn(thr, thr);
-    int lo_prev[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN}, nr_prev[4] = {0, 0, 0, 0};
     __syncthreads();
     for (int t = 1; t <= max_iter; ++t) {
-        float mf[4];
-        double mq[4];
-        for (int i = 0; i < 4; ++i) {
-            mf[i] = __double2float_rn(s_m[i]);
-            mq[i] = (double)mf[i];
-        }
-        int lo[4], nr[4];
-        const int total = ball_cells(mq, d, h, lo, nr);
-        bool same = true;
-        for (int i = 0; i < d; ++i) same = same && lo[i] == lo_prev[i] && nr[i] == nr_prev[i];
-        if (!same) {   // uniform: every thread holds the same mf
+        if (s_moved_cells) {   // uniform
             if (warp == 0) {
-                const int nf = gather_cells(ukeys, ustart, ulen, ncells, lo, nr, total, d, lane, s_cs, s_pre);
+                int lo[4], nr[4];
+                for (int i = 0; i < 4; ++i) {
+                    lo[i] = s_lo[i];
+                    nr[i] = s_nr[i];
+                }
+                const int nf = gather_cells(ukeys, ustart, ulen, ncells, lo, nr, s_total, d, lane, s_cs, s_pre);
                 if (lane == 0) s_nf = nf;
-            }
-            for (int i = 0; i < 4; ++i) {
-                lo_prev[i] = lo[i];
-                nr_prev[i] = nr[i];
             }
             __syncthreads();
         }
+        const float mf[4] = {s_mf[0], s_mf[1], s_mf[2], s_mf[3]};
         const int nf = s_nf, npts = s_pre[nf];
         long long cnt = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         int j = 0;
         for (int f = tid; f < npts; f += GB_SHIFT_THREADS) {
             while (s_pre[j + 1] <= f) ++j;   // f only grows: the cell index only moves forward
-            const float4 x = spts[s_cs[j] + (f - s_pre[j])];
+            const int pi = s_cs[j] + (f - s_pre[j]);
+            const float4 x = spts[pi];
             if (dist2_ball(x, mf, d) <= h2f) {
                 ++cnt;
-                // x * 2^24 is exact in binary32 (|x| < 2^12), so rounding it to the
-                // nearest integer gives rint(x 2^24) without binary64 arithmetic
-                s0 += __float2ll_rn(x.x * Q_SCALE_F);
-                s1 += __float2ll_rn(x.y * Q_SCALE_F);
-                s2 += __float2ll_rn(x.z * Q_SCALE_F);
-                s3 += __float2ll_rn(x.w * Q_SCALE_F);
+                const longlong2 a = qxy[pi], b = qzw[pi];
+                s0 += a.x;
+                s1 += a.y;
+                s2 += b.x;
+                s3 += b.y;
             }
         }
         cnt = warp_sum_ll(cnt);
@@ -296,7 +318,8 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
                     mv = (i == 0) ? __dmul_rn(dv, dv) : __dadd_rn(mv, __dmul_rn(dv, dv));
                     s_m[i] = v;
                 }
-                if (mv <= thr2) s_done = 1;
+                if (mv <= thr2 || t == max_iter) s_done = 1;
+                else place();
             }
         }
         __syncthreads();
@@ -436,16 +459,17 @@ cudaError_t gbms_sort_cells(void* temp, size_t temp_bytes, const uint64_t* keys_
     return cub::DeviceScan::ExclusiveSum(temp, tb, ulen, ustart, (int)n, s);
 }
 
-cudaError_t launch_gbms_gather(const float4* pts4, const int* idx, int64_t n, float4* spts, cudaStream_t s) {
-    gbms_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts4, idx, n, spts);
+cudaError_t launch_gbms_gather(const float4* pts4, const int* idx, int64_t n, float4* spts, longlong2* qxy,
+                               longlong2* qzw, cudaStream_t s) {
+    gbms_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts4, idx, n, spts, qxy, qzw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gbms_shift(const float4* spts, const uint64_t* ukeys, const int* ustart, const int* ulen,
-                              int ncells, int d, double h, int max_iter, double4* modes, int* counts,
-                              const DeviceState* st, cudaStream_t s) {
-    gbms_shift_kernel<<<ncells, GB_SHIFT_THREADS, 0, s>>>(spts, ukeys, ustart, ulen, ncells, d, h, max_iter, modes,
-                                                           counts, st);
+cudaError_t launch_gbms_shift(const float4* spts, const longlong2* qxy, const longlong2* qzw, const uint64_t* ukeys,
+                              const int* ustart, const int* ulen, int ncells, int d, double h, int max_iter,
+                              double4* modes, int* counts, const DeviceState* st, cudaStream_t s) {
+    gbms_shift_kernel<<<ncells, GB_SHIFT_THREADS, 0, s>>>(spts, qxy, qzw, ukeys, ustart, ulen, ncells, d, h, max_iter,
+                                                           modes, counts, st);
     return cudaGetLastError();
 }
 

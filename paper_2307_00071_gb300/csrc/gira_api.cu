@@ -1693,7 +1693,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
-        float4 *p4, *c4;
+        float4 *p4, *p8, *c4;
         double *model64, *stats64, *llp, *trace, *sums;
         u128 *bs, *ksums;
         int64_t* ch;
@@ -1705,7 +1705,8 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         b.st = cv.take<DeviceState>(1);
         b.pin = cv.take<float>(kp == Kind::Host ? 4 * n : 0);
         b.p4 = cv.take<float4>(n);
-        b.params = cv.take<float>((size_t)kpad * COMP4_FLOATS);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
+        b.params = cv.take<float>((size_t)kpad * PAIR4_FLOATS);
         b.model64 = cv.take<double>((size_t)k * MODEL4);
         b.stats64 = cv.take<double>((size_t)k * NSTAT4);
         b.partials = cv.take<float>((size_t)grid * k * NSTAT4);
@@ -1749,7 +1750,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         GIRA_CUDA(cudaMemcpyAsync(b.pin, points, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, c.s));
         pts = b.pin;
     }
-    COUNTED(prof, 1, launch_pack4(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_pack4(pts, n, b.p4, b.p8, b.st, c.s));
     COUNTED(prof, 1, launch_fill_padding4(b.params, k, c.s));
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
@@ -1779,7 +1780,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         COUNTED(prof, 1, launch_params_from_model4(w_d, mu_d, cov_d, k, b.model64, b.params, b.st, c.s));
     }
     prof.t_init = prof.mark();
-    EStep4Launch a{b.p4, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
+    EStep4Launch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
     for (int t = 1; t <= o.iters; ++t) {
         a.iter = t;
         cudaEvent_t e0 = prof.mark();
@@ -1832,14 +1833,14 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *mw, *mmu, *mcov, *pp;
-        float4* p4;
+        float4* p8;
         double *model64, *llp;
     } b{};
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
         b.pin = cv.take<float>(kp == Kind::Host ? 4 * n : 0);
-        b.p4 = cv.take<float4>(n);
-        b.params = cv.take<float>((size_t)kpad * COMP4_FLOATS);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
+        b.params = cv.take<float>((size_t)kpad * PAIR4_FLOATS);
         b.model64 = cv.take<double>((size_t)k * MODEL4);
         b.llp = cv.take<double>(grid);
         b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
@@ -1884,13 +1885,13 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
         GIRA_CUDA(cudaMemcpyAsync(b.mcov, covs, sizeof(float) * 16 * k, cudaMemcpyHostToDevice, c.s));
         cov_d = b.mcov;
     }
-    COUNTED(prof, 1, launch_pack4(pts, n, b.p4, b.st, c.s));
+    COUNTED(prof, 1, launch_pack4(pts, n, nullptr, b.p8, b.st, c.s));
     COUNTED(prof, 1, launch_fill_padding4(b.params, k, c.s));
     COUNTED(prof, 1, launch_params_from_model4(w_d, mu_d, cov_d, k, b.model64, b.params, b.st, c.s));
     prof.t_init = prof.mark();
     prof.t_em = prof.t_init;
     float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
-    EStep4Launch a{b.p4, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
+    EStep4Launch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
     COUNTED(prof, 1, launch_estep4(a, false, grid, c.s));
     COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
     if (per_point && kpp == Kind::Host)
@@ -2075,6 +2076,7 @@ gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, i
         int *idx, *idx2, *ulen, *ustart, *ints, *mcount, *rcount, *midx, *midx2, *mulen, *mustart, *state, *flags,
             *pos, *cout;
         double4 *modes64, *rmodes;
+        longlong2 *qxy, *qzw;
         double* mout;
         void* temp;
     } b{};
@@ -2091,6 +2093,8 @@ gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, i
         b.ints = cv.take<int>(4);   // cells, live modes, mode cells, undecided
         b.modes64 = cv.take<double4>(n);
         b.rmodes = cv.take<double4>(n);
+        b.qxy = cv.take<longlong2>(n);
+        b.qzw = cv.take<longlong2>(n);
         b.mout = cv.take<double>((modes && km == Kind::Host) ? (size_t)d * n : 0);
         b.cout = cv.take<int>((counts && kq == Kind::Host) ? n : 0);
         b.temp = cv.take<unsigned char>(tb);
@@ -2131,9 +2135,9 @@ gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, i
     TRY(device_status(h));
     const int S = hints[0];
     prof.t_init = prof.mark();
-    COUNTED(prof, 1, launch_gbms_gather(b.p4, b.idx2, n, b.spts, c.s));
-    COUNTED(prof, 1, launch_gbms_shift(b.spts, b.ukeys, b.ustart, b.ulen, S, d, bandwidth, max_iter, b.modes64,
-                                       b.mcount, b.st, c.s));
+    COUNTED(prof, 1, launch_gbms_gather(b.p4, b.idx2, n, b.spts, b.qxy, b.qzw, c.s));
+    COUNTED(prof, 1, launch_gbms_shift(b.spts, b.qxy, b.qzw, b.ukeys, b.ustart, b.ulen, S, d, bandwidth, max_iter,
+                                       b.modes64, b.mcount, b.st, c.s));
     COUNTED(prof, 2, launch_gbms_rank(b.temp, tb, b.mcount, S, b.rkeys, b.rkeys2, nlive, c.s));
     GIRA_CUDA(cudaMemcpyAsync(hints, b.ints, sizeof hints, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaStreamSynchronize(c.s));

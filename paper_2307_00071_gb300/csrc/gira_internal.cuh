@@ -484,17 +484,17 @@ cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32
 cudaError_t launch_centers_out(const float4* centers4, int k, float* centers3, cudaStream_t s);
 
 // ---------------------------------------------------------------- four dimensions (xyz + intensity)
-// E-step parameters of one component (COMP4_FLOATS floats, 16-byte aligned):
-//   0..9   P' = alpha * L^{-1}, lower triangle (00,10,11,20,21,22,30,31,32,33)
-//   10..13 unused (zero)
-//   14     c = log2 w + sum_j log2 (L^{-1})_jj - (4/2) log2(2 pi)
-//   15..18 -mu (binary32; also the shift of the M-step statistics)
-//   19     w (N_b after an M-step, or the caller's weight)
-//   20..23 unused
+// E-step parameters, pair-interleaved: components 2p, 2p+1 form pair p, which
+// owns PAIR4_FLOATS floats at params[p * PAIR4_FLOATS] as float2 slots
+// {comp 2p, comp 2p+1}:
+//   slot 0..9   P' = alpha * L^{-1}, lower triangle (00,10,11,20,21,22,30,31,32,33)
+//   slot 10     c = log2 w + sum_j log2 (L^{-1})_jj - (4/2) log2(2 pi)
+//   slot 11..14 -mu (binary32; also the shift of the M-step statistics)
+//   slot 15     w (N_b after an M-step, or the caller's weight)
 // Statistics (NSTAT4): S0, S1[4], S2[10] in the order 00,01,02,03,11,12,13,22,23,33;
 // binary64 model (MODEL4): w, mu[4], Sigma[10] in the same order.
-constexpr int COMP4_FLOATS = 24;
-constexpr int SLOT4_P = 0, SLOT4_B = 10, SLOT4_C = 14, SLOT4_NMU = 15, SLOT4_W = 19;
+constexpr int PAIR4_FLOATS = 32;
+constexpr int SLOT4_P = 0, SLOT4_C = 10, SLOT4_NMU = 11, SLOT4_W = 15;
 constexpr int NSTAT4 = 15;
 constexpr int MODEL4 = 15;
 constexpr int MAX_K4 = 1024;
@@ -502,10 +502,10 @@ constexpr int MAX_K4 = 1024;
 __host__ __device__ constexpr int sym4(int i, int j) { return i * (7 - i) / 2 + j; }
 
 struct EStep4Launch {
-    const float4* pts4;    // (x, y, z, intensity) per point
+    const float4* pts8;    // 2 float4 per point: (x,x,y,y) (z,z,I,I)
     int64_t n;
     int k;
-    const float* params;   // estep4_threads(k) * COMP4_FLOATS (padding components: c = -inf)
+    const float* params;   // estep4_threads(k) pairs * PAIR4_FLOATS (padding components: c = -inf)
     int64_t pts_per_cta;   // multiple of 8
     float* partials;       // [grid][k][NSTAT4] (stats launches)
     double* ll_partials;   // [grid]
@@ -514,12 +514,13 @@ struct EStep4Launch {
     int iter;              // 1-based EM iteration; skipped when iter > st->stop_after
 };
 
-// Components (with padding) the E-step block holds for k.
+// Threads of the E-step block for k components (one pair per lane).
 int estep4_threads(int k);
 int estep4_grid(int64_t n, int k, int num_sms, int64_t* pts_per_cta);
 cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s);
-// N x 4 -> float4; flags non-finite input.
-cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, DeviceState* st, cudaStream_t s);
+// N x 4 -> pts4 (x,y,z,I) (nullable) and pts8 (x,x,y,y)(z,z,I,I); flags non-finite input.
+cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, float4* pts8, DeviceState* st,
+                         cudaStream_t s);
 cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s);
 // M-step from the per-CTA partials (or binary64 stats64 when partials is nullptr),
 // about the shift shift4 (nullptr: the means held in params); em as in launch_reduce_finalize.
@@ -557,11 +558,13 @@ cudaError_t launch_gbms_keys(const float* pts, int64_t n, int d, double h, float
 cudaError_t gbms_sort_cells(void* temp, size_t temp_bytes, const uint64_t* keys_in, uint64_t* keys_out,
                             const int* idx_in, int* idx_out, int64_t n, int d, uint64_t* ukeys, int* ulen,
                             int* ustart, int* ncells, cudaStream_t s);
-cudaError_t launch_gbms_gather(const float4* pts4, const int* idx, int64_t n, float4* spts, cudaStream_t s);
-// One warp per seed (cell): the seed's moves; modes[s] and counts[s] (0: dropped).
-cudaError_t launch_gbms_shift(const float4* spts, const uint64_t* ukeys, const int* ustart, const int* ulen,
-                              int ncells, int d, double h, int max_iter, double4* modes, int* counts,
-                              const DeviceState* st, cudaStream_t s);
+// Points in cell order, with their fixed-point coordinates (x, y) and (z, w).
+cudaError_t launch_gbms_gather(const float4* pts4, const int* idx, int64_t n, float4* spts, longlong2* qxy,
+                               longlong2* qzw, cudaStream_t s);
+// One CTA per seed (cell): the seed's moves; modes[s] and counts[s] (0: dropped).
+cudaError_t launch_gbms_shift(const float4* spts, const longlong2* qxy, const longlong2* qzw, const uint64_t* ukeys,
+                              const int* ustart, const int* ulen, int ncells, int d, double h, int max_iter,
+                              double4* modes, int* counts, const DeviceState* st, cudaStream_t s);
 // Rank keys of the ns seeds and their sort; *nlive (device, zeroed by the caller)
 // receives the number of live modes.
 cudaError_t launch_gbms_rank(void* temp, size_t temp_bytes, const int* counts, int ns, uint64_t* rkeys,

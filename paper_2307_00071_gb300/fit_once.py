@@ -6,6 +6,8 @@
 (the benchmark's step).  ``gmm20k``: 20k points from a K=8 GMM, 20 iterations.
 ``grad1024``: L and all gradients of a 100k-point scan under a K=1024 GMM of the
 frame (``--fits`` calls).  ``chunk2048``: the chunked E-step, K=2048 on the frame.
+``frame4``: the frame with its intensity channel (N x 4), K=512, 30 iterations,
+tol 1e-4.  ``gbms``: mode seeking on the frame with intensity, bandwidth 0.05.
 Used under ncu, where a fixed, short launch sequence is wanted.
 """
 from __future__ import annotations
@@ -20,7 +22,8 @@ from . import gira, synth
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["frame", "gmm20k", "grad1024", "chunk2048"], default="frame")
+    p.add_argument("--workload", choices=["frame", "gmm20k", "grad1024", "chunk2048", "frame4", "gbms"],
+                   default="frame")
     p.add_argument("--fits", type=int, default=1)
     a = p.parse_args()
     if a.workload == "grad1024":
@@ -28,6 +31,18 @@ def main():
         return
     if a.workload == "chunk2048":
         chunk_workload(a.fits)
+        return
+    if a.workload in ("frame4", "gbms"):
+        x4 = torch.as_tensor(synth.depth_frame4(seed=1), device="cuda")
+        for _ in range(a.fits):
+            if a.workload == "frame4":
+                r = gira.gira_gmm_fit4(x4, 512, iters=30, tol=1e-4, reg_covar=1e-6, seed=0, lloyd_iters=10)
+                msg = f"iters_done={r['iters_done']} final_loglik={r['final_loglik']:.6f}"
+            else:
+                m, c = gira.gira_gbms(x4, 0.05)
+                msg = f"K={len(m)}"
+        torch.cuda.synchronize()
+        print(f"{a.workload}: N={x4.shape[0]} {msg}")
         return
     if a.workload == "frame":
         pts, k, iters, tol = synth.depth_frame(seed=1).points, 512, 30, 1e-4

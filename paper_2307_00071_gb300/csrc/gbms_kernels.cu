@@ -93,15 +93,18 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
-// The cells a ball of radius h around m can touch: per dimension [lo_i, lo_i + nr_i)
-// (the radius is inflated by 1e-6 so that rounding never hides a cell).
-__device__ __forceinline__ int ball_cells(const double* m, int d, double h, int* lo, int* nr) {
-    const double hin = h * (1.0 + 1e-6);
+// The cells a ball of radius h around m can touch: per dimension [lo_i, lo_i + nr_i).
+// Only a superset is needed (the ball test decides membership), so binary32
+// with the radius inflated by 5 % suffices: the binary32 error of m_i / h is
+// below 4e-3 cells for every |c_i| < 2^15, far inside the margin, and a point
+// in the ball lies within h (1 + 2^-23) of m in every coordinate.
+__device__ __forceinline__ int ball_cells(const float* m, int d, float h, float inv_h, int* lo, int* nr) {
+    const float hin = 1.05f * h;
     int total = 1;
     for (int i = 0; i < d; ++i) {
-        const double a = floor(__dadd_rn(__ddiv_rn(__dsub_rn(m[i], hin), h), 0.5));
-        const double b = floor(__dadd_rn(__ddiv_rn(__dadd_rn(m[i], hin), h), 0.5));
-        const int la = (int)fmax(a, -32767.0), lb = (int)fmin(b, 32767.0);
+        const float a = floorf(fmaf(m[i] - hin, inv_h, 0.5f));
+        const float b = floorf(fmaf(m[i] + hin, inv_h, 0.5f));
+        const int la = (int)fmaxf(a, -32767.f), lb = (int)fminf(b, 32767.f);
         lo[i] = la;
         nr[i] = lb >= la ? lb - la + 1 : 0;
         total *= nr[i];
@@ -210,6 +213,7 @@ __global__ void gbms_gather_kernel(const float4* __restrict__ pts4, const int* _
 // listed points (cell by cell, in flat order), the exact integer sums are
 // reduced per warp and across warps, and thread 0 takes the move.
 constexpr int GB_SHIFT_THREADS = 128;
+constexpr int GB_UNROLL = 4;
 constexpr int GB_SHIFT_WARPS = GB_SHIFT_THREADS / 32;
 
 __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
@@ -229,14 +233,11 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
     if (st->error) return;   // set before the launch: uniform
     // binary64 work (the move, its stopping test, the cells around the seed) is
     // done by thread 0 alone: GB300 runs binary64 at a small fraction of binary32
+    const float hf = (float)h, inv_hf = 1.0f / hf;
     auto place = [&]() {   // thread 0: binary32 copy of the seed and the cells of its ball
-        double mq[4];
-        for (int i = 0; i < 4; ++i) {
-            s_mf[i] = __double2float_rn(s_m[i]);
-            mq[i] = (double)s_mf[i];
-        }
+        for (int i = 0; i < 4; ++i) s_mf[i] = __double2float_rn(s_m[i]);
         int lo[4], nr[4];
-        s_total = ball_cells(mq, d, h, lo, nr);
+        s_total = ball_cells(s_mf, d, hf, inv_hf, lo, nr);
         bool same = true;
         for (int i = 0; i < d; ++i) {
             same = same && lo[i] == s_lo[i] && nr[i] == s_nr[i];
@@ -276,17 +277,37 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
         const int nf = s_nf, npts = s_pre[nf];
         long long cnt = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         int j = 0;
-        for (int f = tid; f < npts; f += GB_SHIFT_THREADS) {
-            while (s_pre[j + 1] <= f) ++j;   // f only grows: the cell index only moves forward
-            const int pi = s_cs[j] + (f - s_pre[j]);
-            const float4 x = spts[pi];
-            if (dist2_ball(x, mf, d) <= h2f) {
-                ++cnt;
-                const longlong2 a = qxy[pi], b = qzw[pi];
-                s0 += a.x;
-                s1 += a.y;
-                s2 += b.x;
-                s3 += b.y;
+        // GB_UNROLL points per thread per trip, all loads issued before any test
+        // (a seed that keeps moving runs alone on its SM: latency, not bandwidth)
+        for (int f0 = tid; f0 < npts; f0 += GB_UNROLL * GB_SHIFT_THREADS) {
+            int pi[GB_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GB_UNROLL; ++u) {
+                const int f = f0 + u * GB_SHIFT_THREADS;
+                pi[u] = -1;
+                if (f < npts) {
+                    while (s_pre[j + 1] <= f) ++j;   // f only grows: the cell index only moves forward
+                    pi[u] = s_cs[j] + (f - s_pre[j]);
+                }
+            }
+            float4 x[GB_UNROLL];
+            longlong2 qa[GB_UNROLL], qb[GB_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GB_UNROLL; ++u) {
+                const int p = pi[u] >= 0 ? pi[u] : 0;
+                x[u] = spts[p];
+                qa[u] = qxy[p];
+                qb[u] = qzw[p];
+            }
+#pragma unroll
+            for (int u = 0; u < GB_UNROLL; ++u) {
+                if (pi[u] >= 0 && dist2_ball(x[u], mf, d) <= h2f) {
+                    ++cnt;
+                    s0 += qa[u].x;
+                    s1 += qa[u].y;
+                    s2 += qb[u].x;
+                    s3 += qb[u].y;
+                }
             }
         }
         cnt = warp_sum_ll(cnt);
@@ -376,8 +397,9 @@ __global__ void __launch_bounds__(GB_WARPS * 32) gbms_merge_round_kernel(
     const double4 mr = rmodes[r];
     const double a[4] = {mr.x, mr.y, mr.z, mr.w};
     const double h2 = __dmul_rn(h, h);
+    const float af[4] = {(float)mr.x, (float)mr.y, (float)mr.z, (float)mr.w};
     int lo[4], nr[4];
-    const int total = ball_cells(a, d, h, lo, nr);
+    const int total = ball_cells(af, d, (float)h, 1.0f / (float)h, lo, nr);
     const int nf = gather_cells(mukeys, mustart, mulen, *mncells, lo, nr, total, d, lane, s_cs[warp], s_pre[warp]);
     const int nmodes = s_pre[warp][nf];
     bool kept_near = false, pending = false;

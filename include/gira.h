@@ -1,6 +1,8 @@
 /*
- * gira.h -- C ABI of libgira: EM fitting of full-covariance 3D Gaussian mixture
- * models to point clouds on one NVIDIA GB300 (sm_103a).
+ * gira.h -- C ABI of libgira: EM fitting of full-covariance Gaussian mixture
+ * models to point clouds (xyz, or xyz + intensity) on one NVIDIA GB300 (sm_103a),
+ * with the log-likelihood, its gradient, intensity regression, sampling and the
+ * mode seeking that sets the number of components.
  *
  * The operations follow GIRA (Goel & Tabib, arXiv 2307.00071), Sec. V
  * "Implementation Details": KInit (Fig. "information flow": a k-means
@@ -8,11 +10,11 @@
  * (Eq. estep, computed in the log form of Eq. logestep with the Cholesky
  * log-density of Eq. simplifiedGaussian) and the M-step.  The model layout is
  * the paper's (Sec. V: weights (1,K,1), means (1,K,D), covariances (1,K,D,D))
- * with D = 3.
+ * with D = 3 (the calls without a suffix) or D = 4 (the calls ending in 4).
  *
  * Conventions shared by every call
  * --------------------------------
- *  - Points are N x 3 binary32, row-major (x0,y0,z0,x1,...), N >= 1.
+ *  - Points are N x D binary32, row-major (x0,y0,z0,x1,... for D = 3), N >= 1.
  *  - Pointer arguments marked [host|device] may point to host memory or to
  *    device memory of the current CUDA device; the library detects which
  *    (cudaPointerGetAttributes).  Host buffers are staged through

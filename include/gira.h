@@ -376,6 +376,23 @@ gira_status gira_gmm_loglik_noalloc(const float *points, int64_t n, int k, const
                                     const float *means, const float *covs, double *mean_loglik,
                                     float *per_point, void *stream);
 
+/*
+ * Test hooks: failures made on purpose without faulting the GPU.
+ *
+ * gira_test_fail_next_allocations -- the next `count` workspace allocations
+ * (made when a call needs more device workspace than is cached) fail with
+ * GIRA_ERR_OOM before cudaMalloc is called; 0 clears.  Process-wide.
+ *
+ * gira_test_bounded_wait -- launches one wait that nothing will end and returns
+ * the status the kernel recorded: mode 0 waits on an mbarrier phase that never
+ * completes (the wait the E-step kernels use for their TMA copies) for `limit`
+ * nanoseconds of wall time; mode 1 polls a global counter that nobody
+ * increments (the wait of the persistent seeding kernel) `limit` times.  Both
+ * return GIRA_ERR_TIMEOUT, and the context stays usable.  limit in [1, 2e9].
+ */
+void gira_test_fail_next_allocations(int count);
+gira_status gira_test_bounded_wait(int mode, long long limit, void *stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *gira_last_error_message(void);
 

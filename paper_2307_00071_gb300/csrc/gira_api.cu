@@ -89,8 +89,12 @@ struct Carver {
     }
 };
 
+std::atomic<int> g_fail_allocs{0};   // test hook: workspace allocations still to fail
+
 gira_status ensure(DeviceWs* ws, size_t need, cudaStream_t s) {
     if (ws->bytes >= need) return GIRA_OK;
+    if (g_fail_allocs.load() > 0 && g_fail_allocs.fetch_sub(1) > 0)
+        return fail(GIRA_ERR_OOM, "workspace allocation of %zu bytes failed (injected by the test hook)", need);
     GIRA_CUDA(cudaStreamSynchronize(s));
     drop_graph(ws);
     if (ws->ptr) GIRA_CUDA(cudaFree(ws->ptr));
@@ -2183,6 +2187,42 @@ gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, i
     TRY(device_status(h));
     *k_out = K;
     return GIRA_OK;
+}
+
+
+// ================================================================ test hooks
+void gira_test_fail_next_allocations(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
+gira_status gira_test_bounded_wait(int mode, long long limit, void* stream) {
+    reset_error();
+    if (mode != 0 && mode != 1) return fail(GIRA_ERR_INVALID_ARG, "mode = %d is neither 0 nor 1", mode);
+    if (limit < 1 || limit > 2000000000ll) return fail(GIRA_ERR_INVALID_ARG, "limit outside [1, 2e9]");
+    Ctx c;
+    TRY(begin(c, stream));
+    struct Bufs {
+        DeviceState* st;
+        int* ints;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.ints = cv.take<int>(2);
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemsetAsync(b.ints, 0, sizeof(int) * 2, c.s));
+    GIRA_CUDA(launch_wait_probe(mode, limit, b.ints, b.ints + 1, b.st, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    return device_status(h);
 }
 
 }  // extern "C"

@@ -164,6 +164,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// ---------------------------------------------------------------- bounded waits on global memory
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Wait until *counter >= target.  false when *abort is raised by another waiter,
+// or after `limit` polls (each followed by a short sleep): then this waiter
+// records GIRA_ERR_TIMEOUT and raises *abort so that the others leave too.
+__device__ __forceinline__ bool wait_counter_bounded(const int* counter, int target, int* abort, long long limit,
+                                                     DeviceState* st) {
+    long long spins = 0;
+    while (ld_acquire(counter) < target) {
+        if (ld_acquire(abort)) return false;
+        if (++spins > limit) {
+            set_error(st, GIRA_ERR_TIMEOUT);
+            st_release(abort, 1);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
 // binary32 squared distance in the fixed order d_i = x_i - c_i; (d0^2 + d1^2) + d2^2,
 // every operation rounded separately (no contraction): k-means decisions are taken
 // in exactly this arithmetic.
@@ -583,6 +610,11 @@ cudaError_t launch_gbms_merge_round(const double4* rmodes, const int* nlive, int
 cudaError_t launch_gbms_output(void* temp, size_t temp_bytes, const int* state, const int* nlive, int nmax,
                                const double4* rmodes, const int* rcount, int d, int* flags, int* pos,
                                double* modes_out, int* counts_out, cudaStream_t s);
+
+// Test hook: one wait that nothing ends (mode 0: mbarrier, limit in ns; mode 1:
+// global counter, limit in polls); counter and abort_flag: zeroed device ints.
+cudaError_t launch_wait_probe(int mode, long long limit, int* counter, int* abort_flag, DeviceState* st,
+                              cudaStream_t s);
 
 // Set this thread's last-error message (msg may be nullptr to keep it) and
 // component (what gira_last_error_message / gira_last_error_component return).

@@ -166,14 +166,7 @@ constexpr int KPPP_THREADS = 512;
 constexpr int KPPP_WARPS = KPPP_THREADS / 32;
 constexpr long long SPIN_LIMIT = 1ll << 22;   // polls of >= 100 ns: ~0.4 s or more
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+
 // Range of lane `lane` of warp `warp` of CTA `c` (contiguous sub-ranges, so the
 // running sum in point order is: CTA prefix, warp prefix, lane prefix, then the
 // lane's points in order).
@@ -261,17 +254,7 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
             if (lane == 0) {
                 sums[(size_t)j * G + c] = csum_me;
                 red_release_add(&arrive[j], 1);
-                long long spins = 0;
-                while (ld_acquire(&arrive[j]) < G) {
-                    if (ld_acquire(abort_flag)) { ok = false; break; }
-                    if (++spins > SPIN_LIMIT) {
-                        set_error(st, GIRA_ERR_TIMEOUT);
-                        st_release(abort_flag, 1);
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
+                ok = wait_counter_bounded(&arrive[j], G, abort_flag, SPIN_LIMIT, st);
             }
             ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
             __syncwarp();
@@ -1028,6 +1011,30 @@ cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32
     const int64_t want = (n + 255) / 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
     label_stats_kernel<<<grid, 256, 0, s>>>(pts4, n, k, labels, shift4, stats64, st);
+    return cudaGetLastError();
+}
+
+namespace {
+// Test hook: waits that nothing will end, to exercise the bounded-wait exits.
+// mode 0: an mbarrier phase that never completes (limit: wall time in ns);
+// mode 1: a global counter that nobody increments (limit: polls), the wait of
+// the persistent seeding kernel.
+__global__ void wait_probe_kernel(int mode, long long limit, int* counter, int* abort_flag, DeviceState* st) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    if (mode == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        if (!mbar_wait_bounded(&bar, 0u, limit)) set_error(st, GIRA_ERR_TIMEOUT);
+    } else {
+        wait_counter_bounded(counter, 1, abort_flag, limit, st);
+    }
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(int mode, long long limit, int* counter, int* abort_flag, DeviceState* st,
+                              cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(mode, limit, counter, abort_flag, st);
     return cudaGetLastError();
 }
 

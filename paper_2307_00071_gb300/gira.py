@@ -65,6 +65,10 @@ def _load():
     lib.gira_gmm_conditional4.argtypes = [vp, i64, C.c_int, vp, vp, vp, vp, vp, vp]
     lib.gira_gmm_sample.argtypes = [i64, C.c_int, C.c_int, vp, vp, vp, C.c_uint64, vp, vp, vp]
     lib.gira_gbms.argtypes = [vp, i64, C.c_int, C.c_double, C.c_int, ip, vp, vp, vp]
+    lib.gira_test_fail_next_allocations.argtypes = [C.c_int]
+    lib.gira_test_fail_next_allocations.restype = None
+    lib.gira_test_bounded_wait.argtypes = [C.c_int, C.c_longlong, vp]
+    lib.gira_test_bounded_wait.restype = C.c_int
     for f in ("gira_gmm_fit4", "gira_gmm_loglik4", "gira_gmm_conditional4", "gira_gmm_sample", "gira_gbms"):
         getattr(lib, f).restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
@@ -489,3 +493,17 @@ def gira_gbms(points, bandwidth: float, max_iter: int = 300):
     k = C.c_int(0)
     _check(_lib.gira_gbms(pp, n, d, float(bandwidth), max_iter, C.byref(k), mp, cp, s))
     return modes[:k.value], counts[:k.value]
+
+
+# ----------------------------------------------------------------------------- test hooks
+def gira_test_fail_next_allocations(count: int):
+    """The next ``count`` workspace allocations fail with ERR_OOM (0 clears)."""
+    _lib.gira_test_fail_next_allocations(count)
+
+
+def gira_test_bounded_wait(mode: int, limit: int) -> int:
+    """Run one device wait that nothing ends (0: mbarrier, limit in ns; 1: global counter,
+    limit in polls) and return the status it recorded (ERR_TIMEOUT when the bound fired)."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    return _lib.gira_test_bounded_wait(mode, limit, s)

@@ -161,3 +161,11 @@ def test_gbms_invalid_arguments_rejected_without_gpu():
     assert L.gira_gbms(pts.ctypes.data, 10, 3, 0.1, 10, None, None, None, None) == gira.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         gira.gira_gbms(np.zeros((4, 2), np.float32), 0.1)
+
+
+def test_test_hooks_check_arguments_without_gpu():
+    from paper_2307_00071_gb300 import gira
+    L = gira._lib
+    assert L.gira_test_bounded_wait(2, 10, None) == gira.ERR_INVALID_ARG
+    assert L.gira_test_bounded_wait(0, 0, None) == gira.ERR_INVALID_ARG
+    gira.gira_test_fail_next_allocations(0)   # clearing is a no-op without a GPU

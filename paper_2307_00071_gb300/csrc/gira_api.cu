@@ -22,11 +22,19 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gira_internal.cuh"
 
 using namespace gira;
 
 namespace {
+
+// One NVTX range per library call (visible in Nsight Systems; no cost without a tool attached).
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+};
 
 thread_local std::string t_msg;
 thread_local int t_bad = -1;
@@ -487,6 +495,7 @@ gira_status gira_release_workspace(void) {
 // ================================================================ kmeans_init
 gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t seed, int lloyd_iters, float* centers,
                              int32_t* labels, int* iters_done, void* stream) {
+    CallRange nvtx_range("gira_kmeans_init");
     reset_error();
     TRY(check_nk(n, k));
     if (lloyd_iters < 0) return fail(GIRA_ERR_INVALID_ARG, "lloyd_iters < 0");
@@ -583,6 +592,7 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
 gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_opts* opts, float* weights,
                          float* means, float* covs, double* loglik_trace, int* iters_done, double* final_loglik,
                          void* stream) {
+    CallRange nvtx_range("gira_gmm_fit");
     reset_error();
     if (!opts) return fail(GIRA_ERR_INVALID_ARG, "opts is NULL");
     TRY(check_nk(n, k));
@@ -769,6 +779,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
 // ================================================================ gmm_loglik
 gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* weights, const float* means,
                             const float* covs, double* mean_loglik, float* per_point, void* stream) {
+    CallRange nvtx_range("gira_gmm_loglik");
     reset_error();
     TRY(check_nk(n, k));
     if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -879,6 +890,7 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
                                  const float* means, const float* chol, double* loglik, float* grad_points,
                                  double* grad_pose, double* grad_twist, float* grad_logits, float* grad_means,
                                  float* grad_chol, void* stream) {
+    CallRange nvtx_range("gira_gmm_loglik_grad");
     reset_error();
     TRY(check_nk(n, k));
     if (k > GIRA_MAX_K_BATCHED) return fail(GIRA_ERR_INVALID_ARG, "k = %d > %d for the gradient", k, GIRA_MAX_K_BATCHED);
@@ -1014,6 +1026,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                                  const gira_fit_opts* opts, float* weights, float* means, float* covs,
                                  double* loglik_traces, int* iters_done, double* final_loglik, int* statuses,
                                  void* stream) {
+    CallRange nvtx_range("gira_gmm_fit_batched");
     reset_error();
     if (!opts || !offsets || !ks) return fail(GIRA_ERR_INVALID_ARG, "opts, offsets and ks must not be NULL");
     if (batch < 1) return fail(GIRA_ERR_INVALID_ARG, "batch = %d < 1", batch);
@@ -1420,6 +1433,7 @@ gira_status gira_gmm_loglik_grad_batched(const float* points, const int64_t* off
                                          const float* chol, double* logliks, float* grad_points, double* grad_pose,
                                          double* grad_twist, float* grad_logits, float* grad_means,
                                          float* grad_chol, int* statuses, void* stream) {
+    CallRange nvtx_range("gira_gmm_loglik_grad_batched");
     reset_error();
     if (!offsets || !ks) return fail(GIRA_ERR_INVALID_ARG, "offsets and ks must not be NULL");
     if (batch < 1) return fail(GIRA_ERR_INVALID_ARG, "batch = %d < 1", batch);
@@ -1674,6 +1688,7 @@ gira_status check_nk4(int64_t n, int k) {
 gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_opts* opts, float* weights,
                           float* means, float* covs, double* loglik_trace, int* iters_done, double* final_loglik,
                           void* stream) {
+    CallRange nvtx_range("gira_gmm_fit4");
     reset_error();
     if (!opts) return fail(GIRA_ERR_INVALID_ARG, "opts is NULL");
     TRY(check_nk4(n, k));
@@ -1820,6 +1835,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
 
 gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float* weights, const float* means,
                              const float* covs, double* mean_loglik, float* per_point, void* stream) {
+    CallRange nvtx_range("gira_gmm_loglik4");
     reset_error();
     TRY(check_nk4(n, k));
     if (!points || !weights || !means || !covs) return fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -1911,6 +1927,7 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
 
 gira_status gira_gmm_conditional4(const float* locs, int64_t m, int k, const float* weights, const float* means,
                                   const float* covs, float* cond_mean, float* cond_var, void* stream) {
+    CallRange nvtx_range("gira_gmm_conditional4");
     reset_error();
     if (m < 1) return fail(GIRA_ERR_INVALID_ARG, "m = %lld < 1", (long long)m);
     if (k < 1 || k > GIRA_MAX_K4) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K4);
@@ -1981,6 +1998,7 @@ gira_status gira_gmm_conditional4(const float* locs, int64_t m, int k, const flo
 
 gira_status gira_gmm_sample(int64_t m, int k, int d, const float* weights, const float* means, const float* covs,
                             uint64_t seed, float* out, int32_t* components, void* stream) {
+    CallRange nvtx_range("gira_gmm_sample");
     reset_error();
     if (m < 1) return fail(GIRA_ERR_INVALID_ARG, "m = %lld < 1", (long long)m);
     if (d != 3 && d != 4) return fail(GIRA_ERR_INVALID_ARG, "d = %d is neither 3 nor 4", d);
@@ -2059,6 +2077,7 @@ gira_status gira_gmm_sample(int64_t m, int k, int d, const float* weights, const
 // ================================================================ gbms (K from a bandwidth)
 gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, int max_iter, int* k_out,
                       double* modes, int32_t* counts, void* stream) {
+    CallRange nvtx_range("gira_gbms");
     reset_error();
     if (n < 1 || n > (int64_t)INT_MAX / 2) return fail(GIRA_ERR_INVALID_ARG, "n = %lld outside [1, 2^30]", (long long)n);
     if (d != 3 && d != 4) return fail(GIRA_ERR_INVALID_ARG, "d = %d is neither 3 nor 4", d);

@@ -281,3 +281,17 @@ def test_frame_fit_is_valid_and_monotone(gira, frame):
     assert abs(w.sum() - 1) < 1e-5 and np.all(w > 0)
     c = to_np(r["covs"]).astype(np.float64)
     assert np.all(np.linalg.eigvalsh(0.5 * (c + c.transpose(0, 2, 1))) > 0)
+
+
+def test_resume_from_saved_parameters(gira):
+    """Checkpoint / resume: a fit continued from the parameters it returned (the
+    caller's saved binary32 model) follows the uninterrupted fit."""
+    cl = synth.gmm_cloud(20_000, 8, seed=12)
+    full = gira.gira_gmm_fit(dev(cl.points), 8, iters=16, tol=0.0, seed=3)
+    first = gira.gira_gmm_fit(dev(cl.points), 8, iters=8, tol=0.0, seed=3)
+    saved = tuple(to_np(first[a]).copy() for a in ("weights", "means", "covs"))
+    rest = gira.gira_gmm_fit(dev(cl.points), 8, iters=8, tol=0.0, init=saved)
+    np.testing.assert_allclose(first["trace"], full["trace"][:8], atol=1e-12)
+    assert np.max(np.abs(rest["trace"] - full["trace"][8:])) <= LL_ABS
+    assert_model_close((rest["weights"], rest["means"], rest["covs"]),
+                       tuple(to_np(full[a]).astype(np.float64) for a in ("weights", "means", "covs")))

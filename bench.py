@@ -502,6 +502,31 @@ def bench_gbms(gira, frame_pts, reps=5):
             "largest_mode_count": int(c[0])}
 
 
+def bench_size_sweep(gira, frame, reps=5):
+    """The paper's smaller image sizes: the frame's pixels at strides 2, 3, 4 (320x240,
+    213x160, 160x120), each fitted like the main step (K=512, up to 30 iterations, tol 1e-4)."""
+    import torch
+    from paper_2307_00071_gb300 import synth
+    out = {}
+    for step, name in ((2, "320x240"), (3, "213x160"), (4, "160x120")):
+        pts = synth.frame_subsampled(frame, step)
+        x = torch.as_tensor(pts, device="cuda")
+        fit = lambda: gira.gira_gmm_fit(x, K, iters=ITERS, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD)
+        fit()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        iters = 0
+        for _ in range(reps):
+            iters += fit()["iters_done"]
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        out[name] = {"N": len(pts), "ms_per_frame": ms, "iters": iters / reps,
+                     "units_per_s": len(pts) * K * iters / reps / (ms / 1e3)}
+    return out
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -617,7 +642,8 @@ def run_gira(args):
                               "large_map": bench_large_map(gira),
                               "batched_registrations": bench_batched_registrations(gira, frame.points),
                               "xyz_intensity": bench_d4(gira, frame.points, sms, mhz),
-                              "gbms": bench_gbms(gira, frame.points)}
+                              "gbms": bench_gbms(gira, frame.points),
+                              "size_sweep": bench_size_sweep(gira, frame)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

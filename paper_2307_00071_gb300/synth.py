@@ -200,6 +200,19 @@ def gmm_cloud4(n: int = 20_000, k: int = 8, seed: int = 0, lam_lo: float = 1e-4,
     return GMMCloud(pts[perm].astype(np.float32), weights, means, covs, labels[perm])
 
 
+def frame_subsampled(frame: DepthFrame, step: int) -> np.ndarray:
+    """The frame's points on every ``step``-th pixel row and column: the smaller image
+    sizes the paper times (320x240 at step 2, 213x160 at step 3, 160x120 at step 4),
+    back-projected with the full-size intrinsics (the same 3D points as those pixels)."""
+    depth = frame.depth.astype(np.float64)
+    v, u = np.meshgrid(np.arange(0, HEIGHT, step, dtype=np.float64), np.arange(0, WIDTH, step, dtype=np.float64),
+                       indexing="ij")
+    zz = depth[::step, ::step]
+    m = zz > 0
+    pts = np.stack([(u[m] - CX) * zz[m] / FX, (v[m] - CY) * zz[m] / FY, zz[m]], axis=1)
+    return pts.astype(np.float32)
+
+
 def frame_intensity(pts: np.ndarray, seed: int = 1, noise_sigma: float = 0.01) -> np.ndarray:
     """An intensity channel for a depth frame (the paper fits xyz + intensity): a smooth
     procedural texture of the 3D position plus N(0, noise_sigma), in [0, 1]."""

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include <cooperative_groups.h>
 
@@ -863,7 +864,8 @@ cudaError_t launch_kpp_persistent(const float4* pts4, int64_t n, int k, uint64_t
 // Cluster size for the one-cluster seeding of n points, or 0 when it does not
 // apply (too many points, or no cluster of that size fits on this GPU).
 int kpp_cluster_size(int64_t n) {
-    static int cached = -1;   // largest usable cluster size on the current device
+    static std::atomic<int> cached_size{-1};   // largest usable cluster size (one GPU model per process)
+    int cached = cached_size.load();
     if (cached < 0) {
         cached = 0;
         const size_t smem = kc_smem_bytes();
@@ -892,6 +894,7 @@ int kpp_cluster_size(int64_t n) {
             }
         }
         cudaGetLastError();
+        cached_size.store(cached);   // racing first calls compute the same value
     }
     if (cached == 0 || n > (int64_t)cached * KC_THREADS * KC_LMAX) return 0;
     return cached;

@@ -120,9 +120,13 @@ def test_loglik4_per_point_matches_oracle(gira, frame4, k):
         assert abs(mean - ll_ref) <= LL_ABS
 
 
-def test_conditional4_matches_oracle(gira):
+@pytest.mark.parametrize("k", [12, 300])   # 300: two shared-memory tiles of components
+def test_conditional4_matches_oracle(gira, k):
     cl = synth.gmm_cloud4(20_000, 12, seed=11)
-    r = oracle.gmm_fit(cl.points, 12, iters=10, tol=0.0, reg=1e-6, seed=1, lloyd_iters=5)
+    if k == 12:
+        r = oracle.gmm_fit(cl.points, 12, iters=10, tol=0.0, reg=1e-6, seed=1, lloyd_iters=5)
+    else:
+        r = oracle.kinit(cl.points, k, seed=1, lloyd_iters=3, reg=1e-6)
     w, m, c = (r[a].astype(np.float32) for a in ("weights", "means", "covs"))
     rng = np.random.default_rng(0)
     locs = np.concatenate([cl.points[rng.choice(len(cl.points), 3000, replace=False), :3],

@@ -527,6 +527,38 @@ def bench_size_sweep(gira, frame, reps=5):
     return out
 
 
+PIPE_H = (0.08, 0.1, 0.15)
+
+
+def bench_pipeline(gira, frame_pts, reps=3):
+    """The paper's timed pipeline on the frame with intensity (N x 4): mode seeking
+    gives K for a bandwidth, then KInit and EM fit K components (tol 1e-4, up to
+    30 iterations), one call after the other, timed together."""
+    import torch
+    from paper_2307_00071_gb300 import synth
+    pts4 = np.concatenate([frame_pts, synth.frame_intensity(frame_pts, 1)[:, None]], axis=1)
+    x = torch.as_tensor(pts4, device="cuda")
+    out = {}
+    for h in PIPE_H:
+        def run():
+            m, _ = gira.gira_gbms(x, h)
+            k = min(len(m), gira.MAX_K4)
+            r = gira.gira_gmm_fit4(x, k, iters=ITERS, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD)
+            return len(m), k, r
+        run()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            nm, k, r = run()
+        ev1.record()
+        torch.cuda.synchronize()
+        out[f"h={h}"] = {"modes": nm, "K": k, "iters_done": r["iters_done"],
+                         "final_loglik": r["final_loglik"], "ms_total": ev0.elapsed_time(ev1) / reps}
+    return {"workload": f"frame with intensity (N={len(pts4)} x 4): mode seeking at bandwidth h, then KInit + EM "
+                        f"with K = the number of modes (tol {TOL}, up to {ITERS} iterations)", "runs": out}
+
+
 # --------------------------------------------------------------------------- gira arm
 def cpu_baseline(frame_pts, init):
     import oracle
@@ -643,7 +675,8 @@ def run_gira(args):
                               "batched_registrations": bench_batched_registrations(gira, frame.points),
                               "xyz_intensity": bench_d4(gira, frame.points, sms, mhz),
                               "gbms": bench_gbms(gira, frame.points),
-                              "size_sweep": bench_size_sweep(gira, frame)}
+                              "size_sweep": bench_size_sweep(gira, frame),
+                              "sogmm_pipeline": bench_pipeline(gira, frame.points)}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

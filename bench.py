@@ -527,7 +527,7 @@ def bench_size_sweep(gira, frame, reps=5):
     return out
 
 
-PIPE_H = (0.08, 0.1, 0.15)
+PIPE_H = (0.05, 0.08, 0.1, 0.15)
 
 
 def bench_pipeline(gira, frame_pts, reps=3):

@@ -242,11 +242,13 @@ gira_status gira_gmm_loglik_grad_batched(const float *points, const int64_t *off
  * over all four coordinates, binary32 in the order ((d0^2 + d1^2) + d2^2) + d3^2),
  * the same E-step (Eq. estep / logestep with the log-density of
  * Eq. simplifiedGaussian for D = 4) and M-step, the same opts and stopping rule.
- * k <= GIRA_MAX_K4.
+ * k <= GIRA_MAX_K4 (above 1024 the log-sum-exp runs in two levels, over chunks
+ * of 512 components, with the exact per-point maximum for points whose total
+ * underflows, as gira_gmm_fit does).
  *   weights [host|device] K binary32, means K x 4, covs K x 4 x 4 (row-major;
  *   the lower triangle is read when GIRA_INIT_PARAMS), written on return.
  */
-#define GIRA_MAX_K4 1024
+#define GIRA_MAX_K4 8192   /* above 1024: the E-step runs over chunks of 512 components */
 gira_status gira_gmm_fit4(const float *points, int64_t n, int k, const gira_fit_opts *opts, float *weights,
                           float *means, float *covs, double *loglik_trace, int *iters_done, double *final_loglik,
                           void *stream);

@@ -42,7 +42,9 @@ __host__ __device__ __forceinline__ size_t slot4(int b, int s) {
     return (size_t)(b >> 1) * PAIR4_FLOATS + 2 * s + (b & 1);
 }
 
-template <bool STATS>
+// CH = 0: the whole E-step of one CTA (every component); CH = 1: pass A of a
+// chunk (per-point sums only); CH = 2: pass B of a chunk (statistics from pref).
+template <bool STATS, int CH = 0>
 __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
     extern __shared__ __align__(128) unsigned char dsm4[];
     __shared__ __align__(8) uint64_t bar_tma;
@@ -53,7 +55,10 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
     constexpr int LPQ = 32 / Q4;
     const int G = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pr = threadIdx.x;   // this lane's component pair: components 2 pr, 2 pr + 1
+    const int chunk = (CH != 0) ? (int)blockIdx.y : 0;
+    const int pr = threadIdx.x;   // this lane's component pair: components 2 pr, 2 pr + 1 of the chunk
+    const int k_here = (CH != 0) ? min(CHUNK4, a.k - chunk * CHUNK4) : a.k;
+    const float* params = a.params + (size_t)chunk * (CHUNK4 / 2) * PAIR4_FLOATS;
     const int64_t begin = (int64_t)blockIdx.x * a.pts_per_cta;
     const int64_t end = min(a.n, begin + a.pts_per_cta);
     const int npts = (int)(end - begin);
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
     // ---- this lane's pair -> registers (padding components: c = -inf, never contribute)
     float2 P[10], nmu[4], c, w;
     {
-        const float4* src = reinterpret_cast<const float4*>(a.params + (size_t)pr * PAIR4_FLOATS);
+        const float4* src = reinterpret_cast<const float4*>(params + (size_t)pr * PAIR4_FLOATS);
         float4 v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = src[i];
@@ -111,6 +116,7 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
         cmax = fmaxf(cmax, s_cmax[i]);
         wsum += s_wsum[i];
     }
+    if (CH != 0) cmax = a.gref[0];   // chunks: one reference for all K components
     const float2 cc = f2(cmax - c.x, cmax - c.y);   // >= 0; +inf for padding
     const float ref0 = s_norm ? cmax - __log2f(wsum) : cmax;
     float2 S[NSTAT4];   // statistics of the lane's two components, packed
@@ -133,9 +139,43 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
         const float2 y3 = fma2(P[9], d3, fma2(P[8], d2, fma2(P[7], d1, mul2(P[6], d0))));
         return fma2(y3, y3, fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, cc))));
     };
+    // pass 2: S0 = sum g, S1 = sum g d, S2 = sum g d d^T about mu_b for both
+    // components at once (packed); g = e * R with R the owner lane's 1 / total
+    // (r != nullptr) or already folded into e (pass B)
+    auto accumulate = [&](int lb, int nvalid, const float2 (&Eq)[Q4], const float* r) {
+#pragma unroll
+        for (int q = 0; q < Q4; ++q) {
+            const int li = (q < nvalid) ? lb + q : lb;
+            const float4 xy = spts[2 * li], zw = spts[2 * li + 1];
+            const float2 g = r ? mul2(Eq[q], dup(__shfl_sync(FULL, *r, q * LPQ))) : Eq[q];
+            const float2 d[4] = {add2(f2(xy.x, xy.y), nmu[0]), add2(f2(xy.z, xy.w), nmu[1]),
+                                 add2(f2(zw.x, zw.y), nmu[2]), add2(f2(zw.z, zw.w), nmu[3])};
+            float2 gd[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) gd[i] = mul2(g, d[i]);
+            S[0] = add2(S[0], g);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S[1 + i] = add2(S[1 + i], gd[i]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = i; j < 4; ++j) S[5 + sym4(i, j)] = fma2(gd[i], d[j], S[5 + sym4(i, j)]);
+        }
+    };
     float2 E[Q4];
     for (int t = 0; t < nb; ++t) {
         const int lb = t * Q4, nvalid = min(Q4, npts - lb);
+        if (CH == 2) {
+            // pass B: e relative to the point's reference, times 1 / total, into the statistics
+#pragma unroll
+            for (int q = 0; q < Q4; ++q) {
+                const float2 prq = (q < nvalid) ? a.pref[begin + lb + q] : f2(0.f, 0.f);
+                const float2 nq = qform((q < nvalid) ? lb + q : lb);
+                E[q] = f2(ex2_approx(prq.x - nq.x) * prq.y, ex2_approx(prq.x - nq.y) * prq.y);
+            }
+            if (STATS) accumulate(lb, nvalid, E, nullptr);
+            continue;
+        }
         // pass 1: e for (point, own components), per-point sums over the CTA
         float part[Q4];
 #pragma unroll
@@ -150,6 +190,10 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
         float tot = red_sum[t & 1][0][myq];
         for (int i = 1; i < G; ++i) tot += red_sum[t & 1][i][myq];
         const bool myvalid = myq < nvalid;
+        if (CH == 1) {   // pass A: the chunk's sum for each point
+            if (owner && myvalid) a.psum[(size_t)chunk * a.n + begin + lb + myq] = tot;
+            continue;
+        }
         float ref = ref0;
         if (__any_sync(FULL, myvalid && !(tot >= 0x1p-100f))) {
             // rare: a point > 100 binades below cmax everywhere; exact per-point maximum
@@ -188,41 +232,21 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
             if (!STATS && a.per_point) a.per_point[begin + lb + myq] = lse2 * LN2F4;
         }
         const float r = ok ? __frcp_rn(tot) : 0.f;
-        if (STATS) {
-            // pass 2: S0 = sum g, S1 = sum g d, S2 = sum g d d^T about mu_b, both
-            // components at once (packed)
-#pragma unroll
-            for (int q = 0; q < Q4; ++q) {
-                const float R = __shfl_sync(FULL, r, q * LPQ);
-                const int li = (q < nvalid) ? lb + q : lb;
-                const float4 xy = spts[2 * li], zw = spts[2 * li + 1];
-                const float2 g = mul2(E[q], dup(R));
-                const float2 d[4] = {add2(f2(xy.x, xy.y), nmu[0]), add2(f2(xy.z, xy.w), nmu[1]),
-                                     add2(f2(zw.x, zw.y), nmu[2]), add2(f2(zw.z, zw.w), nmu[3])};
-                float2 gd[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) gd[i] = mul2(g, d[i]);
-                S[0] = add2(S[0], g);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) S[1 + i] = add2(S[1 + i], gd[i]);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = i; j < 4; ++j) S[5 + sym4(i, j)] = fma2(gd[i], d[j], S[5 + sym4(i, j)]);
-            }
-        }
+        if (STATS) accumulate(lb, nvalid, E, &r);
     }
     if (STATS) {
+        const int kc = (CH != 0) ? CHUNK4 : a.k;   // components per partial block
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int b = 2 * pr + h;
-            if (b < a.k) {
-                float* dst = a.partials + ((size_t)blockIdx.x * a.k + b) * NSTAT4;
+            if (b < k_here) {
+                float* dst = a.partials + (((size_t)chunk * gridDim.x + blockIdx.x) * kc + b) * NSTAT4;
 #pragma unroll
                 for (int i = 0; i < NSTAT4; ++i) dst[i] = h ? S[i].y : S[i].x;
             }
         }
     }
+    if (CH != 0) return;
     if (warp == 0) {
         double v = ll_acc;
 #pragma unroll
@@ -280,9 +304,9 @@ __device__ bool build_component4(int b, double w, const double mu[4], const doub
 // The E-step kept mu_b (as binary32) as the shift, so the statistics are about
 // the previous mean, and the update un-shifts them exactly in binary64.
 __global__ void __launch_bounds__(NSTAT4 * 32) reduce_finalize4_kernel(
-    const float* __restrict__ partials, int grid, const double* __restrict__ llp, const double* __restrict__ stats64,
-    const float4* __restrict__ shift4, int k, int64_t n, double reg, double tol, double* model64, float* params,
-    double* trace, DeviceState* st, int iter, int em) {
+    const float* __restrict__ partials, int grid, int kc, const double* __restrict__ llp, int ll_count,
+    const double* __restrict__ stats64, const float4* __restrict__ shift4, int k, int64_t n, double reg, double tol,
+    double* model64, float* params, double* trace, DeviceState* st, int iter, int em) {
     __shared__ double part[32][NSTAT4];
     __shared__ double Sb[NSTAT4];
     __shared__ int s_skip;
@@ -293,12 +317,12 @@ __global__ void __launch_bounds__(NSTAT4 * 32) reduce_finalize4_kernel(
     if (partials) {
         const int o = t % NSTAT4, q = t / NSTAT4;
         const int c0 = q * grid / 32, c1 = (q + 1) * grid / 32;
+        const float* src = partials + ((size_t)(b / kc) * grid * kc + b % kc) * NSTAT4 + o;
         double acc = 0.0;
         for (int cta = c0; cta < c1; cta += 8) {
             float f = 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                f += (cta + u < c1) ? __ldcg(partials + ((size_t)(cta + u) * k + b) * NSTAT4 + o) : 0.f;
+            for (int u = 0; u < 8; ++u) f += (cta + u < c1) ? __ldcg(src + (size_t)(cta + u) * kc * NSTAT4) : 0.f;
             acc += (double)f;
         }
         part[q][o] = acc;
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(NSTAT4 * 32) reduce_finalize4_kernel(
     if (em && b == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
         const int lane = t - 32;
         double v = 0.0;
-        for (int cta = lane; cta < grid; cta += 32) v += llp[cta];
+        for (int cta = lane; cta < ll_count; cta += 32) v += llp[cta];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
         if (lane == 0) {
@@ -631,6 +655,86 @@ __global__ void sample_kernel(int64_t m, int k, int d, const float* __restrict__
     if (comp) comp[i] = b;
 }
 
+// ------------------------------------------------------------------ chunks (K above MAX_K4_DIRECT)
+// gref[0] = max_b c_b over all k components; gref[1] = the log-likelihood
+// reference (gref[0] - log2 sum_a w_a once the weights are raw N_b).
+__global__ void chunk_ref4_kernel(const float* __restrict__ params, int k, const DeviceState* st, float* gref) {
+    __shared__ float s_m[8];
+    __shared__ double s_w[8];
+    float m = -INFINITY;
+    double w = 0.0;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+        m = fmaxf(m, params[slot4(b, SLOT4_C)]);
+        w += (double)params[slot4(b, SLOT4_W)];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+        w += __shfl_xor_sync(FULL, w, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_m[threadIdx.x >> 5] = m;
+        s_w[threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = s_m[0];
+        double ww = s_w[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mm = fmaxf(mm, s_m[i]);
+            ww += s_w[i];
+        }
+        gref[0] = mm;
+        gref[1] = st->w_raw ? (float)((double)mm - log2(ww)) : mm;
+    }
+}
+
+// One warp per listed point (total over the chunks below 2^-100): the exact
+// maximum of the logits over all k components, then (shift, 1 / sum) relative
+// to it, with the E-step's arithmetic.
+__global__ void chunk_exact4_kernel(const float4* __restrict__ pts8, const float* __restrict__ params, int k,
+                                    const float* __restrict__ gref, const int* __restrict__ flags,
+                                    const int* __restrict__ flag_count, float2* pref, double* llpt, DeviceState* st) {
+    const int count = *flag_count;
+    const float cmax = gref[0], ref0 = gref[1];
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int f = wg; f < count; f += nw) {
+        const int64_t i = flags[f];
+        const float4 xy = pts8[2 * i], zw = pts8[2 * i + 1];
+        const float x[4] = {xy.x, xy.z, zw.x, zw.z};
+        auto nlog = [&](int b) {   // q' = |P'(x - mu)|^2 + (cmax - c_b)
+            float P[10], d[4];
+            for (int j = 0; j < 10; ++j) P[j] = params[slot4(b, SLOT4_P + j)];
+            for (int j = 0; j < 4; ++j) d[j] = x[j] + params[slot4(b, SLOT4_NMU + j)];
+            const float y0 = P[0] * d[0];
+            const float y1 = fmaf(P[2], d[1], P[1] * d[0]);
+            const float y2 = fmaf(P[5], d[2], fmaf(P[4], d[1], P[3] * d[0]));
+            const float y3 = fmaf(P[9], d[3], fmaf(P[8], d[2], fmaf(P[7], d[1], P[6] * d[0])));
+            const float cc = cmax - params[slot4(b, SLOT4_C)];
+            return fmaf(y3, y3, fmaf(y2, y2, fmaf(y1, y1, fmaf(y0, y0, cc))));
+        };
+        float mx = -INFINITY;
+        for (int b = lane; b < k; b += 32) mx = fmaxf(mx, -nlog(b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+        float sum = 0.f;
+        if (mx > -INFINITY)
+            for (int b = lane; b < k; b += 32) sum += ex2_approx(-nlog(b) - mx);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+        if (lane == 0) {
+            if (!(mx > -INFINITY) || !(sum > 0.f)) {
+                set_error(st, GIRA_ERR_NUMERIC);
+                pref[i] = make_float2(0.f, 0.f);
+            } else {
+                pref[i] = make_float2(-mx, __frcp_rn(sum));
+                llpt[i] = (double)(lg2_approx(sum) + mx + ref0) * LN2_4;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ k-means in four dimensions
 // labels = argmin_b ||x - c_b||^2 (binary32 in the order of dist2_f32_4, ties to
 // the lowest b); binary64 sums of the coordinates and counts per label;
@@ -720,6 +824,11 @@ cudaError_t launch_lloyd4(const float4* pts4, int64_t n, int k, int lloyd_iters,
     const size_t smem = sizeof(float4) * (size_t)k;
     const int64_t want = (n + LL4_THREADS - 1) / LL4_THREADS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms_now() * 8));
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(lloyd4_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     lloyd4_assign_kernel<<<grid, LL4_THREADS, smem, s>>>(pts4, n, k, centers, labels, sums, changed, 0, st);
     for (int it = 1; it <= lloyd_iters; ++it) {
         lloyd4_update_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, sums, centers, changed, it, st);
@@ -776,12 +885,33 @@ cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStrea
     return cudaLaunchKernel(fn, dim3(grid), dim3(estep4_threads(a.k)), args, smem, s);
 }
 
-cudaError_t launch_reduce_finalize4(const float* partials, int grid, const double* ll_partials,
-                                    const double* stats64, const float4* shift4, int k, int64_t n, double reg,
-                                    double tol, double* model64, float* params, double* trace, DeviceState* st,
-                                    int iter, bool em, cudaStream_t s) {
-    reduce_finalize4_kernel<<<k, NSTAT4 * 32, 0, s>>>(partials, grid, ll_partials, stats64, shift4, k, n, reg, tol,
-                                                      model64, params, trace, st, iter, em ? 1 : 0);
+cudaError_t launch_reduce_finalize4(const float* partials, int grid, int kc, const double* ll_partials,
+                                    int ll_count, const double* stats64, const float4* shift4, int k, int64_t n,
+                                    double reg, double tol, double* model64, float* params, double* trace,
+                                    DeviceState* st, int iter, bool em, cudaStream_t s) {
+    reduce_finalize4_kernel<<<k, NSTAT4 * 32, 0, s>>>(partials, grid, kc, ll_partials, ll_count, stats64, shift4, k,
+                                                      n, reg, tol, model64, params, trace, st, iter, em ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_ref4(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s) {
+    chunk_ref4_kernel<<<1, 256, 0, s>>>(params, k, st, gref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estep4_chunks(const EStep4Launch& a, int pass, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)a.pts_per_cta * 32;
+    const void* fn = (pass == 1) ? (const void*)estep4_kernel<false, 1> : (const void*)estep4_kernel<true, 2>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int chunks = (a.k + CHUNK4 - 1) / CHUNK4;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid, chunks), dim3(CHUNK4 / 2), args, smem, s);
+}
+
+cudaError_t launch_chunk_exact4(const float4* pts8, const float* params, int k, const float* gref, const int* flags,
+                                const int* flag_count, float2* pref, double* llpt, DeviceState* st, cudaStream_t s) {
+    chunk_exact4_kernel<<<152, 256, 0, s>>>(pts8, params, k, gref, flags, flag_count, pref, llpt, st);
     return cudaGetLastError();
 }
 
@@ -797,8 +927,12 @@ cudaError_t launch_model_out4(const double* model64, int k, float* w, float* mu,
     return cudaGetLastError();
 }
 
+int params4_pairs(int k) {
+    return k > MAX_K4_DIRECT ? ((k + CHUNK4 - 1) / CHUNK4) * (CHUNK4 / 2) : estep4_threads(k);
+}
+
 cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s) {
-    const int kpad = 2 * estep4_threads(k);
+    const int kpad = 2 * params4_pairs(k);
     if (kpad > k) fill_padding4_kernel<<<(kpad - k + 63) / 64, 64, 0, s>>>(params, k, kpad);
     return cudaGetLastError();
 }

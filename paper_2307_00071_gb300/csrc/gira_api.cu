@@ -1683,6 +1683,45 @@ gira_status check_nk4(int64_t n, int k) {
     if (k > n) return fail(GIRA_ERR_INVALID_ARG, "k = %d > n = %lld", k, (long long)n);
     return GIRA_OK;
 }
+
+// K above MAX_K4_DIRECT: per-point state of the two-level log-sum-exp.
+struct Chunk4Bufs {
+    float* gref = nullptr;     // [2]: max_b c_b, log-likelihood reference
+    float* psum = nullptr;     // [chunks][n]
+    float2* pref = nullptr;    // [n] (shift, 1 / total)
+    double* llpt = nullptr;    // [n] natural-log per-point log-likelihood
+    int* flags = nullptr;      // [n] points for the exact step
+    int* flag_count = nullptr;
+};
+
+void carve_chunk4(Carver& cv, int64_t n, int chunks, Chunk4Bufs* b) {
+    b->gref = cv.take<float>(2);
+    b->psum = cv.take<float>((size_t)chunks * n);
+    b->pref = cv.take<float2>(n);
+    b->llpt = cv.take<double>(n);
+    b->flags = cv.take<int>(n);
+    b->flag_count = cv.take<int>(1);
+}
+
+// Reference, pass A, per-point totals, exact step for underflowing points, and
+// the fixed-order log-likelihood partials (into st->ll_sum when ll_to_state).
+cudaError_t chunk4_lse(const Chunk4Bufs& b, EStep4Launch a, int grid, double* llp, bool ll_to_state,
+                       long long* launches, cudaStream_t s) {
+    const int chunks = (a.k + CHUNK4 - 1) / CHUNK4;
+    a.partials = nullptr;
+    a.gref = b.gref;
+    a.psum = b.psum;
+    cudaError_t e = launch_chunk_ref4(a.params, a.k, a.st, b.gref, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.flag_count, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_estep4_chunks(a, 1, grid, s);
+    if (e == cudaSuccess)
+        e = launch_chunk_combine(b.psum, chunks, a.n, b.gref, b.pref, b.llpt, b.flag_count, b.flags, a.st, s);
+    if (e == cudaSuccess)
+        e = launch_chunk_exact4(a.pts8, a.params, a.k, b.gref, b.flags, b.flag_count, b.pref, b.llpt, a.st, s);
+    if (e == cudaSuccess) e = launch_points_ll_reduce(b.llpt, a.n, llp, ll_to_state ? a.st : nullptr, s);
+    *launches += 5 + (ll_to_state ? 1 : 0);
+    return e;
+}
 }  // namespace
 
 gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_opts* opts, float* weights,
@@ -1703,12 +1742,16 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
     TRY(check_ptr(means, "means", c.dev, &km));
     TRY(check_ptr(covs, "covs", c.dev, &kc));
     const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
-    const int kpad = estep4_threads(k);
+    const bool chunked = k > MAX_K4_DIRECT;   // two-level log-sum-exp over chunks of CHUNK4 components
+    const int chunks = chunked ? (k + CHUNK4 - 1) / CHUNK4 : 1;
+    const int kpad = params4_pairs(k);
     int64_t ppc = 0;
-    const int grid = estep4_grid(n, k, c.sms, &ppc);
+    const int grid = estep4_grid(n, chunked ? CHUNK4 : k, c.sms, &ppc);   // CTAs per chunk when chunked
+    const int kblk = chunked ? CHUNK4 : k;                                 // components per partial block
     const int nblk = kpp_num_blocks(n);
     int kgrid = kinit ? kpp_persistent_grid() : 0;
     if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
+    Chunk4Bufs cb;
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *partials, *d2, *mw, *mmu, *mcov;
@@ -1728,8 +1771,9 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         b.params = cv.take<float>((size_t)kpad * PAIR4_FLOATS);
         b.model64 = cv.take<double>((size_t)k * MODEL4);
         b.stats64 = cv.take<double>((size_t)k * NSTAT4);
-        b.partials = cv.take<float>((size_t)grid * k * NSTAT4);
-        b.llp = cv.take<double>(grid);
+        b.partials = cv.take<float>((size_t)chunks * grid * kblk * NSTAT4);
+        b.llp = cv.take<double>(std::max(grid, chunk_combine_grid()));
+        if (chunked) carve_chunk4(cv, n, chunks, &cb);
         b.trace = cv.take<double>(std::max(o.iters, 1));
         b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
         b.mmu = cv.take<float>(km == Kind::Host ? 4 * (size_t)k : 0);
@@ -1788,8 +1832,8 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
                                                           b.st, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT4 * k, c.s));
         COUNTED(prof, 1, launch_label_stats4(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
-        COUNTED(prof, 1, launch_reduce_finalize4(nullptr, 0, nullptr, b.stats64, b.c4, k, n, o.reg_covar, o.tol,
-                                                 b.model64, b.params, b.trace, b.st, 0, false, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize4(nullptr, 0, k, nullptr, 0, b.stats64, b.c4, k, n, o.reg_covar,
+                                                 o.tol, b.model64, b.params, b.trace, b.st, 0, false, c.s));
     } else {
         if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(b.mw, weights, sizeof(float) * k, cudaMemcpyHostToDevice, c.s));
         if (km == Kind::Host)
@@ -1802,20 +1846,36 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
     EStep4Launch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
     for (int t = 1; t <= o.iters; ++t) {
         a.iter = t;
+        if (chunked) {
+            GIRA_CUDA(chunk4_lse(cb, a, grid, b.llp, false, &prof.launches, c.s));
+            EStep4Launch pb = a;
+            pb.gref = cb.gref;
+            pb.pref = cb.pref;
+            COUNTED(prof, 1, launch_estep4_chunks(pb, 2, grid, c.s));
+            COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, kblk, b.llp, chunk_combine_grid(), nullptr,
+                                                     nullptr, k, n, o.reg_covar, o.tol, b.model64, b.params, b.trace,
+                                                     b.st, t, true, c.s));
+            continue;
+        }
         cudaEvent_t e0 = prof.mark();
         COUNTED(prof, 1, launch_estep4(a, true, grid, c.s));
         cudaEvent_t e1 = prof.mark();
         if (prof.on) prof.estep.emplace_back(e0, e1);
-        COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, b.llp, nullptr, nullptr, k, n, o.reg_covar, o.tol,
-                                                 b.model64, b.params, b.trace, b.st, t, true, c.s));
+        COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, kblk, b.llp, grid, nullptr, nullptr, k, n,
+                                                 o.reg_covar, o.tol, b.model64, b.params, b.trace, b.st, t, true,
+                                                 c.s));
     }
     prof.t_em = prof.mark();
     if (final_loglik) {
         EStep4Launch f = a;
         f.iter = 0;
         f.partials = nullptr;
-        COUNTED(prof, 1, launch_estep4(f, false, grid, c.s));
-        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+        if (chunked) {
+            GIRA_CUDA(chunk4_lse(cb, f, grid, b.llp, true, &prof.launches, c.s));
+        } else {
+            COUNTED(prof, 1, launch_estep4(f, false, grid, c.s));
+            COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+        }
     }
     COUNTED(prof, 1, launch_model_out4(b.model64, k, w_d, mu_d, cov_d, b.st, c.s));
     if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
@@ -1847,9 +1907,12 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
     TRY(check_ptr(means, "means", c.dev, &km));
     TRY(check_ptr(covs, "covs", c.dev, &kc));
     if (per_point) TRY(check_ptr(per_point, "per_point", c.dev, &kpp));
-    const int kpad = estep4_threads(k);
+    const bool chunked = k > MAX_K4_DIRECT;
+    const int chunks = chunked ? (k + CHUNK4 - 1) / CHUNK4 : 1;
+    const int kpad = params4_pairs(k);
     int64_t ppc = 0;
-    const int grid = estep4_grid(n, k, c.sms, &ppc);
+    const int grid = estep4_grid(n, chunked ? CHUNK4 : k, c.sms, &ppc);
+    Chunk4Bufs cb;
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *mw, *mmu, *mcov, *pp;
@@ -1862,7 +1925,8 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
         b.p8 = cv.take<float4>(2 * (size_t)n);
         b.params = cv.take<float>((size_t)kpad * PAIR4_FLOATS);
         b.model64 = cv.take<double>((size_t)k * MODEL4);
-        b.llp = cv.take<double>(grid);
+        b.llp = cv.take<double>(std::max(grid, chunk_combine_grid()));
+        if (chunked) carve_chunk4(cv, n, chunks, &cb);
         b.mw = cv.take<float>(kw == Kind::Host ? k : 0);
         b.mmu = cv.take<float>(km == Kind::Host ? 4 * (size_t)k : 0);
         b.mcov = cv.take<float>(kc == Kind::Host ? 16 * (size_t)k : 0);
@@ -1912,8 +1976,13 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
     prof.t_em = prof.t_init;
     float* ppd = per_point ? ((kpp == Kind::Device) ? per_point : b.pp) : nullptr;
     EStep4Launch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
-    COUNTED(prof, 1, launch_estep4(a, false, grid, c.s));
-    COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    if (chunked) {
+        GIRA_CUDA(chunk4_lse(cb, a, grid, b.llp, true, &prof.launches, c.s));
+        if (ppd) COUNTED(prof, 1, launch_double_to_float(cb.llpt, n, ppd, c.s));
+    } else {
+        COUNTED(prof, 1, launch_estep4(a, false, grid, c.s));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
+    }
     if (per_point && kpp == Kind::Host)
         GIRA_CUDA(cudaMemcpyAsync(per_point, b.pp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));

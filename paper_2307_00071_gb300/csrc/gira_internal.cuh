@@ -539,10 +539,23 @@ struct EStep4Launch {
     float* per_point;      // [n] natural-log lse, or nullptr
     DeviceState* st;
     int iter;              // 1-based EM iteration; skipped when iter > st->stop_after
+    // K above MAX_K4_DIRECT: chunks of CHUNK4 components (blockIdx.y = chunk, all over
+    // the same points, logits relative to gref[0] = max_b c_b).  Pass A writes
+    // psum[chunk][n] = sum over the chunk of 2^(l - cmax); pass B takes
+    // pref[n] = (shift, 1 / total) and writes the statistics, partials laid out
+    // [chunk][grid][CHUNK4][NSTAT4].
+    const float* gref = nullptr;
+    float* psum = nullptr;
+    const float2* pref = nullptr;
 };
+
+constexpr int MAX_K4_DIRECT = 1024;   // one CTA holds every component up to here
+constexpr int CHUNK4 = 512;           // components per chunk above it
 
 // Threads of the E-step block for k components (one pair per lane).
 int estep4_threads(int k);
+// Component pairs the parameter buffer holds for k (chunks padded to CHUNK4).
+int params4_pairs(int k);
 int estep4_grid(int64_t n, int k, int num_sms, int64_t* pts_per_cta);
 cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s);
 // N x 4 -> pts4 (x,y,z,I) (nullable) and pts8 (x,x,y,y)(z,z,I,I); flags non-finite input.
@@ -551,10 +564,19 @@ cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, float4* p
 cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s);
 // M-step from the per-CTA partials (or binary64 stats64 when partials is nullptr),
 // about the shift shift4 (nullptr: the means held in params); em as in launch_reduce_finalize.
-cudaError_t launch_reduce_finalize4(const float* partials, int grid, const double* ll_partials,
-                                    const double* stats64, const float4* shift4, int k, int64_t n, double reg,
-                                    double tol, double* model64, float* params, double* trace, DeviceState* st,
-                                    int iter, bool em, cudaStream_t s);
+// kc: components per partial block (k for the direct E-step, CHUNK4 for chunks:
+// component b's partials at ((b / kc) * grid + cta) * kc + b % kc); the
+// log-likelihood is the sum of ll_partials[0 .. ll_count).
+cudaError_t launch_reduce_finalize4(const float* partials, int grid, int kc, const double* ll_partials,
+                                    int ll_count, const double* stats64, const float4* shift4, int k, int64_t n,
+                                    double reg, double tol, double* model64, float* params, double* trace,
+                                    DeviceState* st, int iter, bool em, cudaStream_t s);
+// Chunked E-step (K > MAX_K4_DIRECT): gref from all k components; pass A / B over
+// chunks x grid CTAs (pass 1 or 2); exact maximum for the points combine listed.
+cudaError_t launch_chunk_ref4(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s);
+cudaError_t launch_estep4_chunks(const EStep4Launch& a, int pass, int grid, cudaStream_t s);
+cudaError_t launch_chunk_exact4(const float4* pts8, const float* params, int k, const float* gref, const int* flags,
+                                const int* flag_count, float2* pref, double* llpt, DeviceState* st, cudaStream_t s);
 cudaError_t launch_params_from_model4(const float* w, const float* mu, const float* cov, int k, double* model64,
                                       float* params, DeviceState* st, cudaStream_t s);
 cudaError_t launch_model_out4(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,

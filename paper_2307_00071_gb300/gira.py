@@ -19,7 +19,7 @@ from . import build_lib
 OK = 0
 ERR_INVALID_ARG, ERR_NONFINITE_INPUT, ERR_NOT_PD, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC = 1, 2, 3, 4, 5, 6, 7
 INIT_KMEANS, INIT_PARAMS = 0, 1
-MAX_K, MAX_K_BATCHED, MAX_K4 = 8192, 1024, 1024
+MAX_K, MAX_K_BATCHED, MAX_K4 = 8192, 1024, 8192
 
 
 class GiraError(RuntimeError):

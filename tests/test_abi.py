@@ -130,7 +130,7 @@ def test_d4_invalid_arguments_rejected_without_gpu():
                                        c.ctypes.data, None, None, None, None)
     assert fit(0, 1) == gira.ERR_INVALID_ARG
     assert fit(10, 11) == gira.ERR_INVALID_ARG
-    assert fit(5000, 1025) == gira.ERR_INVALID_ARG                     # above GIRA_MAX_K4
+    assert fit(9000, 8193) == gira.ERR_INVALID_ARG                     # above GIRA_MAX_K4
     assert L.gira_gmm_loglik4(pts.ctypes.data, 10, 0, w.ctypes.data, m.ctypes.data, c.ctypes.data, None, None,
                               None) == gira.ERR_INVALID_ARG
     loc = np.zeros((3, 3), np.float32)

@@ -176,3 +176,53 @@ def test_d4_errors(gira):
     with pytest.raises(gira.GiraError) as e:
         gira.gira_gmm_sample(10, w, m, c2, seed=0)
     assert e.value.status == gira.ERR_NOT_PD
+
+
+# ----------------------------------------------------------------------------- K above 1024 (chunks of 512)
+def test_fit4_chunked_from_given_init_matches_oracle(gira, frame4):
+    pts = subset(frame4, 30_000, 5)
+    K = 1100   # chunks of 512, 512, 76
+    ki = oracle.kinit(pts, K, seed=0, lloyd_iters=4, reg=1e-6)
+    w0, m0, c0 = (ki[a].astype(np.float32) for a in ("weights", "means", "covs"))
+    r = gira.gira_gmm_fit4(pts, K, iters=3, tol=0.0, init=(w0, m0, c0))
+    ref = oracle.em(pts, w0, m0, c0, iters=3, tol=0.0, reg=1e-6)
+    assert r["iters_done"] == 3
+    assert np.max(np.abs(r["trace"] - ref["trace"])) <= LL_ABS
+    assert abs(r["final_loglik"] - ref["final_ll"]) <= LL_ABS
+    assert_model_close((r["weights"], r["means"], r["covs"]), (ref["weights"], ref["means"], ref["covs"]))
+
+
+def test_fit4_chunked_kmeans_init_matches_oracle_fit(gira, frame4):
+    pts = subset(frame4, 20_000, 6)
+    K = 1030
+    r = gira.gira_gmm_fit4(pts, K, iters=2, tol=0.0, seed=7, lloyd_iters=3)
+    ref = oracle.gmm_fit(pts, K, iters=2, tol=0.0, reg=1e-6, seed=7, lloyd_iters=3)
+    assert np.max(np.abs(r["trace"] - ref["trace"])) <= LL_ABS
+    assert_model_close((r["weights"], r["means"], r["covs"]), (ref["weights"], ref["means"], ref["covs"]))
+
+
+def test_loglik4_chunked_k2048_with_outliers(gira, frame4):
+    rng = np.random.default_rng(8)
+    pts = subset(frame4, 25_000, 8)
+    K = 2048
+    idx = rng.choice(len(pts), K, replace=False)
+    means = pts[idx].astype(np.float64) + rng.normal(scale=0.01, size=(K, 4))
+    covs = []
+    for _ in range(K):
+        Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+        lam = np.array([rng.uniform(0.02, 0.1), rng.uniform(0.02, 0.1), 0.01, 0.03]) ** 2
+        covs.append(Q @ np.diag(lam) @ Q.T)
+    w = rng.dirichlet(np.ones(K)).astype(np.float32)
+    m, c = means.astype(np.float32), np.stack(covs).astype(np.float32)
+    # far points: every component's term underflows the common reference -> exact step
+    far = np.concatenate([rng.normal(size=(15, 3)) * 5.0 + np.array([0.0, 0.0, 300.0]), rng.uniform(size=(15, 1))],
+                         axis=1).astype(np.float32)
+    allp = np.concatenate([pts, far])
+    mean, pp = gira.gira_gmm_loglik4(allp, w, m, c, per_point=True)
+    pp = to_np(pp).astype(np.float64)
+    assert np.all(np.isfinite(pp))
+    assert mean == pytest.approx(pp.mean(), rel=1e-6)
+    sample = np.concatenate([rng.choice(len(pts), 300, replace=False), np.arange(len(pts), len(allp))])
+    _, _, lse = oracle.estep(allp[sample], w, m, c, want_resp=False, want_lse=True)
+    err = np.abs(pp[sample] - lse)
+    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))

@@ -234,8 +234,7 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
     // binary64 work (the move, its stopping test, the cells around the seed) is
     // done by thread 0 alone: GB300 runs binary64 at a small fraction of binary32
     const float hf = (float)h, inv_hf = 1.0f / hf;
-    auto place = [&]() {   // thread 0: binary32 copy of the seed and the cells of its ball
-        for (int i = 0; i < 4; ++i) s_mf[i] = __double2float_rn(s_m[i]);
+    auto place_cells = [&]() {   // thread 0: the cells of the ball around the binary32 seed s_mf
         int lo[4], nr[4];
         s_total = ball_cells(s_mf, d, hf, inv_hf, lo, nr);
         bool same = true;
@@ -253,9 +252,10 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
             s_lo[i] = INT_MIN;
             s_nr[i] = 0;
         }
+        for (int i = 0; i < 4; ++i) s_mf[i] = __double2float_rn(s_m[i]);
         s_done = 0;
         s_count = 0;
-        place();
+        place_cells();
     }
     const float h2f = __double2float_rn(__dmul_rn(h, h));
     const double thr = __dmul_rn(1e-3, h), thr2 = __dmul_rn(thr, thr);
@@ -323,24 +323,41 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
             s_red[warp][4] = s3;
         }
         __syncthreads();
-        if (tid == 0) {
-            long long tot[5] = {0, 0, 0, 0, 0};
-            for (int w = 0; w < GB_SHIFT_WARPS; ++w)
-                for (int q = 0; q < 5; ++q) tot[q] += s_red[w][q];
-            const int count = (int)tot[0];
-            s_count = count;
+        if (warp == 0) {
+            // the move: lane i < d takes coordinate i (one binary64 instruction serves
+            // every coordinate), lane 0 sums the squared steps in coordinate order
+            long long tot = 0;
+            if (lane < 5)
+                for (int w = 0; w < GB_SHIFT_WARPS; ++w) tot += s_red[w][lane];
+            const long long count = __shfl_sync(FULL, tot, 0);
+            const long long si = __shfl_down_sync(FULL, tot, 1);   // lane i: sum of coordinate i
             if (count == 0) {
-                s_done = 1;
-            } else {
-                double mv = 0.0;
-                for (int i = 0; i < d; ++i) {
-                    const double v = __dmul_rn(__ddiv_rn(__ll2double_rn(tot[1 + i]), (double)count), 1.0 / Q_SCALE);
-                    const double dv = __dsub_rn(v, s_m[i]);
-                    mv = (i == 0) ? __dmul_rn(dv, dv) : __dadd_rn(mv, __dmul_rn(dv, dv));
-                    s_m[i] = v;
+                if (lane == 0) {
+                    s_count = 0;
+                    s_done = 1;
                 }
-                if (mv <= thr2 || t == max_iter) s_done = 1;
-                else place();
+            } else {
+                double sq = 0.0, v = 0.0;
+                if (lane < d) {
+                    v = __dmul_rn(__ddiv_rn(__ll2double_rn(si), (double)count), 1.0 / Q_SCALE);
+                    const double dv = __dsub_rn(v, s_m[lane]);
+                    sq = __dmul_rn(dv, dv);
+                }
+                const double sq1 = __shfl_sync(FULL, sq, 1), sq2 = __shfl_sync(FULL, sq, 2),
+                             sq3 = __shfl_sync(FULL, sq, 3);
+                __syncwarp();
+                if (lane < d) {
+                    s_m[lane] = v;
+                    s_mf[lane] = __double2float_rn(v);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    double mv = __dadd_rn(__dadd_rn(sq, sq1), sq2);
+                    if (d == 4) mv = __dadd_rn(mv, sq3);
+                    s_count = (int)count;
+                    if (mv <= thr2 || t == max_iter) s_done = 1;
+                    else place_cells();
+                }
             }
         }
         __syncthreads();

@@ -470,7 +470,7 @@ def bench_d4(gira, frame_pts, sms, mhz, reps=5):
             "unit": UNIT, "value": float(n) * D4_K * iters / reps / (ms / 1e3), "ms_per_frame": ms,
             "em_ms_per_frame": prof["em_ms"] / reps, "init_ms_per_frame": prof["init_ms"] / reps,
             "iters_done": r["iters_done"], "final_loglik": r["final_loglik"],
-            "kernel": "estep4_kernel<true> (4D fused E-step + statistics)", "kernel_ms": kern_s * 1e3,
+            "kernel": "estep4_kernel<true, 0> (4D fused E-step + statistics)", "kernel_ms": kern_s * 1e3,
             "kernel_units_per_s": n * D4_K / kern_s if kern_s else None,
             "frac_fp32": (n * D4_K / kern_s) / peak if kern_s else None,
             "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {D4_FP32_OPS} FP32 ops per unit",

@@ -714,14 +714,21 @@ def run_gira(args):
             "clocks": clk,
         }
         if not args.no_extras:
-            line["extras"] = {"grad": bench_grad(gira, frame.points, sms, mhz), "batched": bench_batched(gira),
-                              "large_map": bench_large_map(gira),
-                              "batched_registrations": bench_batched_registrations(gira, frame.points),
-                              "xyz_intensity": bench_d4(gira, frame.points, sms, mhz),
-                              "gbms": bench_gbms(gira, frame.points),
-                              "size_sweep": bench_size_sweep(gira, frame),
-                              "sogmm_pipeline": bench_pipeline(gira, frame.points),
-                              "frames_batched": bench_frames_batched(gira)}
+            extras = (("grad", lambda: bench_grad(gira, frame.points, sms, mhz)),
+                      ("batched", lambda: bench_batched(gira)),
+                      ("large_map", lambda: bench_large_map(gira)),
+                      ("batched_registrations", lambda: bench_batched_registrations(gira, frame.points)),
+                      ("xyz_intensity", lambda: bench_d4(gira, frame.points, sms, mhz)),
+                      ("gbms", lambda: bench_gbms(gira, frame.points)),
+                      ("size_sweep", lambda: bench_size_sweep(gira, frame)),
+                      ("sogmm_pipeline", lambda: bench_pipeline(gira, frame.points)),
+                      ("frames_batched", lambda: bench_frames_batched(gira)))
+            line["extras"] = {}
+            for name, fn in extras:   # a failing extra is reported, the headline line still prints
+                try:
+                    line["extras"][name] = fn()
+                except Exception as e:  # noqa: BLE001
+                    line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.no_cpu_baseline:
             init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
                                      final_loglik=False)

@@ -730,9 +730,12 @@ def run_gira(args):
                 except Exception as e:  # noqa: BLE001
                     line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.no_cpu_baseline:
-            init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED, lloyd_iters=LLOYD,
-                                     final_loglik=False)
-            line["cpu_baseline"] = cpu_baseline(frame.points, (init["weights"], init["means"], init["covs"]))
+            try:
+                init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED,
+                                         lloyd_iters=LLOYD, final_loglik=False)
+                line["cpu_baseline"] = cpu_baseline(frame.points, (init["weights"], init["means"], init["covs"]))
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -295,3 +295,20 @@ def test_resume_from_saved_parameters(gira):
     assert np.max(np.abs(rest["trace"] - full["trace"][8:])) <= LL_ABS
     assert_model_close((rest["weights"], rest["means"], rest["covs"]),
                        tuple(to_np(full[a]).astype(np.float64) for a in ("weights", "means", "covs")))
+
+
+def test_calls_on_a_side_stream_match_the_default_stream(gira):
+    """Every call runs on torch's current stream: on a side stream, with device inputs
+    written on that stream, the results equal those on the default stream."""
+    cl = synth.gmm_cloud(10_000, 6, seed=21)
+    ref = gira.gira_gmm_fit(dev(cl.points), 6, iters=6, tol=0.0, seed=2)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        x = torch.as_tensor(cl.points, device="cuda")   # written on the side stream
+        r = gira.gira_gmm_fit(x, 6, iters=6, tol=0.0, seed=2)
+        ll = gira.gira_gmm_loglik(x, r["weights"], r["means"], r["covs"])
+    side.synchronize()
+    for key in ("weights", "means", "covs"):
+        assert torch.equal(r[key], ref[key])
+    np.testing.assert_array_equal(r["trace"], ref["trace"])
+    assert abs(ll - r["final_loglik"]) < 1e-9

@@ -524,7 +524,6 @@ constexpr int PAIR4_FLOATS = 32;
 constexpr int SLOT4_P = 0, SLOT4_C = 10, SLOT4_NMU = 11, SLOT4_W = 15;
 constexpr int NSTAT4 = 15;
 constexpr int MODEL4 = 15;
-constexpr int MAX_K4 = 1024;
 // index of (i, j), i <= j, in the upper-triangle order 00,01,02,03,11,12,13,22,23,33
 __host__ __device__ constexpr int sym4(int i, int j) { return i * (7 - i) / 2 + j; }
 

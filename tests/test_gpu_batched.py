@@ -118,3 +118,23 @@ def test_batched_single_instance_large_k(gira):
     ref = oracle.gmm_fit(cl.points, 600, iters=3, tol=0.0, reg=1e-6, seed=4, lloyd_iters=2)
     assert np.max(np.abs(r["trace"][0] - ref["trace"])) <= LL_ABS
     assert_model_close((r["weights"], r["means"], r["covs"]), (ref["weights"], ref["means"], ref["covs"]))
+
+
+def test_full_size_batch_sampled_instances_match_oracle(gira):
+    """The benchmark's batch at full size (256 clouds, N log-uniform in [2k, 200k],
+    about 11 M points, K in {16 ... 512}) in one call; the six instances with the
+    smallest N x K are checked against the oracle's own fit of each."""
+    rng = np.random.default_rng(7)
+    sizes = np.exp(rng.uniform(np.log(2_000), np.log(200_000), size=256)).astype(np.int64)
+    kk = rng.choice((16, 32, 64, 128, 256, 512), size=256).astype(np.int32)
+    clouds = [synth.gmm_cloud(int(n), 8, seed=1000 + i).points for i, n in enumerate(sizes)]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    import torch
+    r = gira.gira_gmm_fit_batched(torch.as_tensor(np.concatenate(clouds), device="cuda"), offs, kk, iters=3, tol=0.0,
+                                  seed=0, lloyd_iters=5)
+    assert np.all(r["status"] == 0)
+    ws, ms, cs = split(r["weights"], kk), split(r["means"], kk), split(r["covs"], kk)
+    for i in np.argsort(sizes * kk)[:6]:
+        ref = oracle.gmm_fit(clouds[i], int(kk[i]), iters=3, tol=0.0, reg=1e-6, seed=0, lloyd_iters=5)
+        assert np.max(np.abs(r["trace"][i] - ref["trace"])) <= LL_ABS, i
+        assert_model_close((ws[i], ms[i], cs[i]), (ref["weights"], ref["means"], ref["covs"]))

@@ -96,3 +96,35 @@ def test_chunked_loglik_equals_direct_where_both_apply(gira, frame):
     c2 = np.concatenate([c, [np.eye(3, dtype=np.float32) * 1e-4]])
     chunked = gira.gira_gmm_loglik(pts, w2, m2, c2)
     assert abs(chunked - direct) <= LL_ABS
+
+
+def test_full_size_map_sampled_points_match_oracle(gira):
+    """The large-map size: 16 depth frames under random poses, the first 4M points,
+    K = 8192 from means at random points.  Per-point log-likelihoods are checked on
+    sampled points against the oracle; one EM iteration keeps every property that
+    holds at any size (weights summing to 1, finite PD covariances, trace finite)."""
+    import torch
+    rng = np.random.default_rng(11)
+    parts = []
+    for i in range(16):
+        f = synth.depth_frame(seed=100 + i).points.astype(np.float64)
+        th = rng.uniform(0, 2 * np.pi)
+        R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+        parts.append(f @ R.T + np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), 0.0]))
+    pts = np.concatenate(parts)[:4_000_000].astype(np.float32)
+    K = 8192
+    w, m, c = large_model(pts, K, rng)
+    x = torch.as_tensor(pts, device="cuda")
+    mean, pp = gira.gira_gmm_loglik(x, torch.as_tensor(w, device="cuda"), torch.as_tensor(m, device="cuda"),
+                                    torch.as_tensor(c, device="cuda"), per_point=True)
+    pp = pp.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(pp)) and mean == pytest.approx(pp.mean(), rel=1e-6)
+    sample = rng.choice(len(pts), 400, replace=False)
+    _, _, lse = oracle.estep(pts[sample], w, m, c, want_resp=False, want_lse=True)
+    err = np.abs(pp[sample] - lse)
+    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))
+    r = gira.gira_gmm_fit(x, K, iters=1, tol=0.0, init=(w, m, c), final_loglik=False)
+    wr, cr = r["weights"].cpu().numpy().astype(np.float64), r["covs"].cpu().numpy().astype(np.float64)
+    assert abs(wr.sum() - 1.0) < 1e-4 and np.all(np.isfinite(r["trace"]))
+    live = wr > 1e-6
+    assert np.all(np.linalg.eigvalsh(0.5 * (cr[live] + np.transpose(cr[live], (0, 2, 1)))) > 0)

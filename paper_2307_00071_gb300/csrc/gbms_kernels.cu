@@ -112,38 +112,46 @@ __device__ __forceinline__ int ball_cells(const float* m, int d, float h, float 
     return total;
 }
 
-// Lanes enumerate the candidate cells, look each up in the sorted cell keys and
-// list the occupied ones (start, length) in the warp's shared arrays; returns
-// the number listed and fills pre[] with the exclusive prefix of the lengths
-// (pre[count] = total points).
+// Lanes list the occupied cells of the candidate box (start, length) in the
+// warp's shared arrays and fill pre[] with the exclusive prefix of the lengths
+// (pre[count] = total points); returns the count.  The box is walked in rows
+// along the first coordinate: the cells of a row have consecutive keys (the
+// first coordinate is the key's lowest field), so one binary search per row
+// finds the row's first occupied cell and the rest follow in order.
 __device__ int gather_cells(const uint64_t* ukeys, const int* ustart, const int* ulen, int ncells, const int* lo,
                             const int* nr, int total, int d, int lane, int* cs, int* pre) {
+    const int nrows = (nr[0] > 0) ? total / nr[0] : 0;
     int nfound = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int cid = base + lane;
-        int st = 0, ln = 0;
-        bool found = false;
-        if (cid < total) {
-            int c[4], r = cid;
-            for (int i = 0; i < d; ++i) {
+    for (int base = 0; base < nrows; base += 32) {
+        const int row = base + lane;
+        int st[4], ln[4], cnt = 0;
+        if (row < nrows) {
+            int c[4] = {lo[0], 0, 0, 0}, r = row;
+            for (int i = 1; i < d; ++i) {
                 c[i] = lo[i] + r % nr[i];
                 r /= nr[i];
             }
-            const uint64_t key = key_of(c, d);
-            const int pos = lower_bound_u64(ukeys, ncells, key);
-            if (pos < ncells && ukeys[pos] == key) {
-                found = true;
-                st = ustart[pos];
-                ln = ulen[pos];
+            const uint64_t k0 = key_of(c, d);             // (lo_0, c_1, ...)
+            const uint64_t k1 = k0 + (uint64_t)nr[0];      // one past the row's last candidate
+            for (int pos = lower_bound_u64(ukeys, ncells, k0); pos < ncells && ukeys[pos] < k1 && cnt < 4; ++pos) {
+                st[cnt] = ustart[pos];
+                ln[cnt] = ulen[pos];
+                ++cnt;
             }
         }
-        const unsigned bal = __ballot_sync(FULL, found);
-        const int at = nfound + __popc(bal & ((1u << lane) - 1u));
-        if (found) {
-            cs[at] = st;
-            pre[at] = ln;   // lengths for now
+        // this lane's cells go after those of the lower lanes
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += u;
         }
-        nfound += __popc(bal);
+        const int at = nfound + inc - cnt;
+        for (int q = 0; q < cnt; ++q) {
+            cs[at + q] = st[q];
+            pre[at + q] = ln[q];   // lengths for now
+        }
+        nfound += __shfl_sync(FULL, inc, 31);
     }
     __syncwarp();
     // exclusive prefix of the lengths, 32 at a time

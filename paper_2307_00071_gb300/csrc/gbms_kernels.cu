@@ -299,23 +299,26 @@ __global__ void __launch_bounds__(GB_SHIFT_THREADS) gbms_shift_kernel(
                 }
             }
             float4 x[GB_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GB_UNROLL; ++u) x[u] = spts[pi[u] >= 0 ? pi[u] : 0];
+            bool in[GB_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GB_UNROLL; ++u) in[u] = pi[u] >= 0 && dist2_ball(x[u], mf, d) <= h2f;
+            // the fixed-point coordinates only for points in the ball (a few per cent
+            // of the candidates), all loads issued before any use
             longlong2 qa[GB_UNROLL], qb[GB_UNROLL];
 #pragma unroll
             for (int u = 0; u < GB_UNROLL; ++u) {
-                const int p = pi[u] >= 0 ? pi[u] : 0;
-                x[u] = spts[p];
-                qa[u] = qxy[p];
-                qb[u] = qzw[p];
+                qa[u] = in[u] ? qxy[pi[u]] : make_longlong2(0, 0);
+                qb[u] = in[u] ? qzw[pi[u]] : make_longlong2(0, 0);
             }
 #pragma unroll
             for (int u = 0; u < GB_UNROLL; ++u) {
-                if (pi[u] >= 0 && dist2_ball(x[u], mf, d) <= h2f) {
-                    ++cnt;
-                    s0 += qa[u].x;
-                    s1 += qa[u].y;
-                    s2 += qb[u].x;
-                    s3 += qb[u].y;
-                }
+                cnt += in[u] ? 1 : 0;
+                s0 += qa[u].x;
+                s1 += qa[u].y;
+                s2 += qb[u].x;
+                s3 += qb[u].y;
             }
         }
         cnt = warp_sum_ll(cnt);

@@ -380,11 +380,20 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
 // exact fixed-point sum of its own D^2, recomputed only when a new centre
 // lowers one of them.  Per centre j:
 //  1. update D^2 and the lane sums; warp / CTA prefixes of the lane sums; each
-//     CTA writes its total into every CTA's shared memory (DSMEM);
-//  2. cluster barrier; every CTA evaluates the same prefix over the cs totals
-//     and finds the CTA holding the threshold;
+//     CTA stores its total into every CTA's shared memory (st.async, DSMEM),
+//     completing bytes on the receiver's mbarrier;
+//  2. once its mbarrier has all cs totals, every CTA evaluates the same prefix
+//     over them and finds the CTA holding the threshold;
 //  3. that CTA locates the point (warp, lane, then the lane's points in order)
-//     and writes it into every CTA's shared memory; cluster barrier.
+//     and stores it into every CTA's shared memory the same way; every CTA
+//     waits for it on a second mbarrier.
+// No cluster barrier per centre: each CTA waits only for the bytes it reads.
+// Buffers and mbarriers alternate by the parity of j: a CTA can send centre
+// j + 1's total while a slower peer still has centre j's in flight, but not
+// centre j + 2's (that needs centre j + 1's point, which needs every total of
+// j + 1, which each CTA sends only after reading centre j's).  Every wait is
+// bounded (GIRA_ERR_TIMEOUT); a thread that timed out stops waiting and the
+// loop runs to its end, so no CTA leaves while a peer may still store to it.
 // The arithmetic is the exact fixed point of the other seeding kernels, so the
 // chosen indices are identical.
 constexpr int KC_THREADS = 512;
@@ -393,14 +402,62 @@ constexpr int KC_PMAX = 18;               // point pairs per lane
 constexpr int KC_LMAX = 2 * KC_PMAX;      // points per lane
 constexpr int KC_MAX_CS = 16;
 
+constexpr long long KC_WAIT_NS = 2000000000ll;   // bound on any wait: 2 s of wall time
+
 struct KcShared {
     u128 wtot[KC_WARPS], wincl[KC_WARPS];
-    u128 csum[KC_MAX_CS];   // written by every CTA of the cluster (DSMEM)
+    u128 csum[2][KC_MAX_CS];   // by parity of j: stored by every CTA of the cluster
+    float4 cen[2];             // by parity of j: stored by the CTA holding the chosen point
+    long long idx[2];
+    uint64_t bar_sum[2], bar_cen[2];
     u128 rel;
-    float4 cen;             // written by the CTA holding the chosen point (DSMEM)
-    long long idx;
     int win, mode;
 };
+
+// st.async: a store into a peer CTA's shared memory that completes its byte
+// count on the peer's mbarrier (release at cluster scope); addresses in the
+// shared::cluster window (mapa).
+__device__ __forceinline__ uint32_t kc_peer(const void* local, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void kc_send_u128(uint32_t dst, u128 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(dst),
+                 "l"(v.lo), "l"(v.hi), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void kc_send_f4(uint32_t dst, float4 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     dst),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void kc_send_s64(uint32_t dst, long long v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(dst), "l"(v),
+                 "r"(bar)
+                 : "memory");
+}
+// The phase with the given parity has completed; acquire at cluster scope (the
+// bytes were stored by peers).  False after KC_WAIT_NS of wall time.
+__device__ __forceinline__ bool kc_wait(uint64_t* bar, uint32_t parity) {
+    auto try_wait = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (try_wait()) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (try_wait()) return true;
+        if (globaltimer_ns() - t0 > (uint64_t)KC_WAIT_NS) return false;
+    }
+}
 
 size_t kc_smem_bytes() { return (size_t)3 * KC_PMAX * KC_THREADS * sizeof(float2) + sizeof(KcShared) + 16; }
 
@@ -471,8 +528,18 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         centers[0] = cen;
         chosen[0] = idx;
     }
-    cluster.sync();   // every CTA of the cluster has started before any DSMEM access
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh.bar_sum[b], 1);
+            mbar_init(&sh.bar_cen[b], 1);
+        }
+        mbar_fence_init();
+    }
+    cluster.sync();   // every CTA has started and initialised its mbarriers before any DSMEM access
+    unsigned ph_sum = 0u, ph_cen = 0u;   // per parity b: the parity of the phase to wait for next
+    bool dead = false;                    // this thread gave up a wait: stop waiting, run to the end
     for (int j = 1; j < k; ++j) {
+        const int b = j & 1;
         // ---- 1. D^2 (packed: each lane of FADD2/FMUL2 rounds like dist2_f32) and,
         //         where any D^2 dropped, the lane's exact sum from scratch (raster-
         //         order lanes see their points' D^2 drop together, so one pass over
@@ -512,6 +579,9 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 }
             }
         }
+        // this phase of bar_sum[b] expects the cs totals (the previous phase of it
+        // completed before this CTA read centre j - 2's totals)
+        if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)cs * (uint32_t)sizeof(u128));
         const u128 linc = u128_warp_incl_scan(ls, lane);
         if (lane == 31) sh.wtot[warp] = linc;
         __syncthreads();
@@ -520,11 +590,13 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
             const u128 wi = u128_warp_incl_scan(wv, lane);
             if (lane < KC_WARPS) sh.wincl[lane] = wi;
             const u128 total = u128_shfl(wi, KC_WARPS - 1);
-            if (lane < cs) cluster.map_shared_rank(&sh, lane)->csum[me] = total;
-        }
-        cluster.sync();   // ---- 2. every CTA total is in every CTA's csum
-        if (warp == 0) {
-            const u128 v = (lane < cs) ? sh.csum[lane] : u128{0ull, 0ull};
+            if (lane < cs) kc_send_u128(kc_peer(&sh.csum[b][me], lane), total, kc_peer(&sh.bar_sum[b], lane));
+            // ---- 2. every CTA's total has arrived
+            if (!dead && !kc_wait(&sh.bar_sum[b], (ph_sum >> b) & 1u)) {
+                dead = true;
+                set_error(st, GIRA_ERR_TIMEOUT);
+            }
+            const u128 v = (lane < cs) ? sh.csum[b][lane] : u128{0ull, 0ull};
             const u128 inc = u128_warp_incl_scan(v, lane);
             const u128 T = u128_shfl(inc, 31);
             if (!u128_zero(T)) {
@@ -536,20 +608,24 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                     sh.rel = u128_sub(t, u128_sub(inc, v));
                     sh.mode = 0;
                 }
-            } else if (lane == 0) {   // every weight is zero: uniform index
+                // this phase of bar_cen[b] expects the chosen point and its index
+                if (lane == 0 && !dead) mbar_expect_tx(&sh.bar_cen[b], (uint32_t)(sizeof(float4) + sizeof(long long)));
+            } else if (lane == 0) {   // every weight is zero: uniform index, the same in every CTA
                 long long id2 = (long long)floor(uniform53(seed, (uint64_t)j) * (double)n);
                 if (id2 > n - 1) id2 = n - 1;
-                sh.idx = id2;
-                sh.cen = __ldg(pts + id2);
+                sh.idx[b] = id2;
+                sh.cen[b] = __ldg(pts + id2);
                 sh.mode = 2;
                 if (me == 0) {
-                    centers[j] = sh.cen;
+                    centers[j] = sh.cen[b];
                     chosen[j] = id2;
                 }
             }
         }
+        ph_sum ^= 1u << b;
         __syncthreads();
-        if (sh.mode == 0 && sh.win == me) {
+        const int mode = sh.mode;
+        if (mode == 0 && sh.win == me) {
             // ---- 3. this CTA holds the point: warp, lane, then the lane's points
             const u128 rel = sh.rel;
             const u128 wi = (lane < KC_WARPS) ? sh.wincl[lane] : u128{0ull, 0ull};
@@ -588,9 +664,9 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 const long long lo_src = __shfl_sync(FULL, (long long)llo, src);
                 const long long found = min((long long)n - 1, lo_src + qf);   // clamp never taken
                 if (lane < cs) {
-                    KcShared* dst = cluster.map_shared_rank(&sh, lane);
-                    dst->cen = pf;
-                    dst->idx = found;
+                    const uint32_t bar = kc_peer(&sh.bar_cen[b], lane);
+                    kc_send_f4(kc_peer(&sh.cen[b], lane), pf, bar);
+                    kc_send_s64(kc_peer(&sh.idx[b], lane), found, bar);
                 }
                 if (lane == 0) {
                     centers[j] = pf;
@@ -598,10 +674,17 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 }
             }
         }
-        cluster.sync();   // the chosen centre is in every CTA's shared memory
-        cen = sh.cen;
-        idx = sh.idx;
+        if (mode == 0) {   // uniform over the cluster: the same totals give the same mode
+            if (!dead && !kc_wait(&sh.bar_cen[b], (ph_cen >> b) & 1u)) {
+                dead = true;
+                set_error(st, GIRA_ERR_TIMEOUT);
+            }
+            ph_cen ^= 1u << b;
+        }
+        cen = sh.cen[b];
+        idx = sh.idx[b];
     }
+    cluster.sync();   // no CTA leaves while a peer may still address its shared memory
 }
 
 // ---------------------------------------------------------------- Lloyd

@@ -338,7 +338,13 @@ typedef struct {
     double total_ms;            /* whole calls, first upload to last download */
 } gira_profile;
 
-/* Turn profiling on (on != 0) or off. */
+/*
+ * Profiling: on = 0 off; on = 2 CUDA events at the phase boundaries of each call
+ * (init_ms, em_ms, total_ms); any other nonzero value also brackets every
+ * E-step launch with an event pair (estep_launches, estep_ms), for which the EM
+ * loop launches its kernels plainly instead of as programmatic dependents of
+ * one another (the results are the same).
+ */
 void gira_profile_enable(int on);
 
 /* Copy the accumulated profile to *out (may be NULL); reset it when reset != 0. */

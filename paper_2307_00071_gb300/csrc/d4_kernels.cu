@@ -65,18 +65,25 @@ __global__ void __launch_bounds__(512, 1) estep4_kernel(const EStep4Launch a) {
     const int nb = (npts + Q4 - 1) / Q4;
     const float4* spts = reinterpret_cast<const float4*>(dsm4);   // (x,x,y,y)(z,z,w,w) per point
     if (threadIdx.x == 0) {
+        // the points are never written by the kernel this one may overlap
+        // (dependent launch), so their copy starts before the wait below
+        mbar_init(&bar_tma, 1);
+        mbar_fence_init();
+        mbar_expect_tx(&bar_tma, (uint32_t)npts * 32u);
+        tma_load_1d(reinterpret_cast<void*>(dsm4), a.pts8 + 2 * begin, (uint32_t)npts * 32u, &bar_tma);
+    }
+    pdl_wait();   // the parameters and the state written by the previous kernel
+    if (threadIdx.x == 0) {
         s_skip = (a.iter > a.st->stop_after) || (a.st->error != 0);
         s_norm = a.st->w_raw;
         s_dead = 0;
-        if (!s_skip) {
-            mbar_init(&bar_tma, 1);
-            mbar_fence_init();
-            mbar_expect_tx(&bar_tma, (uint32_t)npts * 32u);
-            tma_load_1d(reinterpret_cast<void*>(dsm4), a.pts8 + 2 * begin, (uint32_t)npts * 32u, &bar_tma);
-        }
     }
     __syncthreads();
-    if (s_skip) return;
+    if (s_skip) {   // let the copy land before leaving
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar_tma, 0u, MBAR_LIMIT4);
+        return;
+    }
+    pdl_allow_next();
     // ---- this lane's pair -> registers (padding components: c = -inf, never contribute)
     float2 P[10], nmu[4], c, w;
     {
@@ -310,6 +317,8 @@ __global__ void __launch_bounds__(NSTAT4 * 32) reduce_finalize4_kernel(
     __shared__ double part[32][NSTAT4];
     __shared__ double Sb[NSTAT4];
     __shared__ int s_skip;
+    pdl_wait();         // the E-step's partials (dependent launch)
+    pdl_allow_next();   // the next E-step may stage its points meanwhile
     if (threadIdx.x == 0) s_skip = (em && iter > st->stop_after) || st->error != 0;
     __syncthreads();
     if (s_skip) return;
@@ -876,22 +885,23 @@ int estep4_grid(int64_t n, int k, int num_sms, int64_t* ppc) {
     return (int)((n + p - 1) / p);
 }
 
-cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s) {
+cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s, bool pdl) {
     const size_t smem = (size_t)a.pts_per_cta * 32;
     const void* fn = stats ? (const void*)estep4_kernel<true> : (const void*)estep4_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(estep4_threads(a.k)), args, smem, s);
+    PdlConfig c(dim3(grid), dim3(estep4_threads(a.k)), smem, s, pdl);
+    return cudaLaunchKernelExC(&c.cfg, fn, args);
 }
 
 cudaError_t launch_reduce_finalize4(const float* partials, int grid, int kc, const double* ll_partials,
                                     int ll_count, const double* stats64, const float4* shift4, int k, int64_t n,
                                     double reg, double tol, double* model64, float* params, double* trace,
-                                    DeviceState* st, int iter, bool em, cudaStream_t s) {
-    reduce_finalize4_kernel<<<k, NSTAT4 * 32, 0, s>>>(partials, grid, kc, ll_partials, ll_count, stats64, shift4, k,
-                                                      n, reg, tol, model64, params, trace, st, iter, em ? 1 : 0);
-    return cudaGetLastError();
+                                    DeviceState* st, int iter, bool em, cudaStream_t s, bool pdl) {
+    PdlConfig c(dim3(k), dim3(NSTAT4 * 32), 0, s, pdl);
+    return cudaLaunchKernelEx(&c.cfg, reduce_finalize4_kernel, partials, grid, kc, ll_partials, ll_count, stats64,
+                              shift4, k, n, reg, tol, model64, params, trace, st, iter, em ? 1 : 0);
 }
 
 cudaError_t launch_chunk_ref4(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s) {

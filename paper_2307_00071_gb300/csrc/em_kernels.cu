@@ -124,18 +124,25 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
     const int nb = (npts + Q - 1) / Q;
     const float4* spts = reinterpret_cast<const float4*>(dsm);
     if (threadIdx.x == 0) {
+        // the points are never written by the kernel this one may overlap
+        // (dependent launch), so their copy starts before the wait below
+        mbar_init(&bar_tma, 1);
+        mbar_fence_init();
+        mbar_expect_tx(&bar_tma, (uint32_t)npts * 32u);
+        tma_load_1d(reinterpret_cast<void*>(dsm), a.pts8 + 2 * begin, (uint32_t)npts * 32u, &bar_tma);
+    }
+    pdl_wait();   // the parameters and the state written by the previous kernel
+    if (threadIdx.x == 0) {
         s_skip = (a.iter > a.st->stop_after) || (a.st->error != 0);
         s_norm = a.st->w_raw;
         s_dead = 0;
-        if (!s_skip) {
-            mbar_init(&bar_tma, 1);
-            mbar_fence_init();
-            mbar_expect_tx(&bar_tma, (uint32_t)npts * 32u);
-            tma_load_1d(reinterpret_cast<void*>(dsm), a.pts8 + 2 * begin, (uint32_t)npts * 32u, &bar_tma);
-        }
     }
     __syncthreads();
-    if (s_skip) return;
+    if (s_skip) {   // let the copy land before leaving
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar_tma, 0u, MBAR_POLL_LIMIT);
+        return;
+    }
+    pdl_allow_next();
 
     // ---- this lane's component pairs -> registers (overlaps the TMA)
     PairParams prm[NP];
@@ -586,14 +593,15 @@ cudaError_t launch_estep_chunks(const EStepLaunch& a, int pass, int nunits, int6
     return cudaLaunchKernel(fn, dim3(nunits), dim3(128), args, smem, s);
 }
 
-cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad) {
+cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad, bool pdl) {
     const Shape sh = shape_for(a.k);
     void* args[] = {(void*)&a};
     const void* fn = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
     const size_t smem = estep_smem(a.pts_per_cta);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernel(fn, dim3(grid), dim3(sh.threads), args, smem, s);
+    PdlConfig c(dim3(grid), dim3(sh.threads), smem, s, pdl);
+    return cudaLaunchKernelExC(&c.cfg, fn, args);
 }
 
 // ------------------------------------------------------------------ pack + padding
@@ -999,6 +1007,8 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
 }
 
 __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(const FinArgs f) {
+    pdl_wait();         // the E-step's partials (dependent launch)
+    pdl_allow_next();   // the next E-step may stage its points meanwhile
     reduce_finalize_body(f, blockIdx.x);
 }
 
@@ -1397,11 +1407,11 @@ __device__ void grad_finalize_body(const GradFinArgs& f, int blk) {
 cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool pdl) {
     const FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
                     em ? 1 : 0, 0, 1};
-    reduce_finalize_kernel<<<(k + FIN_CPB - 1) / FIN_CPB, FIN_THREADS, 0, s>>>(f);
-    return cudaGetLastError();
+    PdlConfig c(dim3((k + FIN_CPB - 1) / FIN_CPB), dim3(FIN_THREADS), 0, s, pdl);
+    return cudaLaunchKernelEx(&c.cfg, reduce_finalize_kernel, f);
 }
 
 int fin_components_per_block() { return FIN_CPB; }

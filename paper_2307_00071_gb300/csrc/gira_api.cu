@@ -218,6 +218,7 @@ gira_profile g_prof{};
 // Events of one call: phase marks plus a pair per E-step launch.
 struct CallProfile {
     bool on = false;
+    bool per_launch = false;   // an event pair around every E-step launch (plain launches)
     cudaStream_t s = nullptr;
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
@@ -225,6 +226,7 @@ struct CallProfile {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> estep;
     long long launches = 0;
 
+    cudaEvent_t mark_launch() { return per_launch ? mark() : nullptr; }
     cudaEvent_t mark() {
         if (!on) return nullptr;
         if (used == pool.size()) {
@@ -455,7 +457,7 @@ void gira_fit_opts_default(gira_fit_opts* o) {
     o->init_mode = GIRA_INIT_KMEANS;
 }
 
-void gira_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+void gira_profile_enable(int on) { g_prof_on.store(on == 2 ? 2 : on ? 1 : 0); }
 
 gira_status gira_profile_read(gira_profile* out, int reset) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -548,6 +550,7 @@ gira_status gira_kmeans_init(const float* points, int64_t n, int k, uint64_t see
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -669,6 +672,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -744,12 +748,16 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     EStepLaunch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
     for (int t = 1; t <= o.iters && !chunked; ++t) {
         a.iter = t;
-        cudaEvent_t e0 = prof.mark();
-        COUNTED(prof, 1, launch_estep(a, true, grid, c.s));
-        cudaEvent_t e1 = prof.mark();
-        if (prof.on) prof.estep.emplace_back(e0, e1);
+        // dependent launches unless an event pair brackets each E-step: each
+        // kernel is resident before the previous one ends and waits on the
+        // device for its results
+        const bool pdl = !prof.per_launch;
+        cudaEvent_t e0 = prof.mark_launch();
+        COUNTED(prof, 1, launch_estep(a, true, grid, c.s, false, pdl));
+        cudaEvent_t e1 = prof.mark_launch();
+        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
         COUNTED(prof, 1, launch_reduce_finalize(b.partials, grid, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
-                                                o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s));
+                                                o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s, pdl));
     }
     if (!chunked) prof.t_em = prof.mark();
     if (final_loglik && !chunked) {
@@ -828,6 +836,7 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -953,6 +962,7 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -992,10 +1002,10 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
         a.grad_pts = gp_d;
         a.rot = pose_d;
         a.pose_partials = b.ppart;
-        cudaEvent_t e0 = prof.mark();
+        cudaEvent_t e0 = prof.mark_launch();
         COUNTED(prof, 1, launch_estep(a, true, grid, c.s, true));
-        cudaEvent_t e1 = prof.mark();
-        if (prof.on) prof.estep.emplace_back(e0, e1);
+        cudaEvent_t e1 = prof.mark_launch();
+        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
         COUNTED(prof, 1, launch_grad_finalize(b.partials, grid, b.llp, b.ppart, pose_d, ch_d, b.model64, k, n, gl_d,
                                               gm_d, gc_d, po_d, tw_d, b.st, c.s));
     } else {
@@ -1207,6 +1217,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     std::vector<DeviceState> hs(batch);
@@ -1558,6 +1569,7 @@ gira_status gira_gmm_loglik_grad_batched(const float* points, const int64_t* off
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     std::vector<DeviceState> hs(batch);
@@ -1801,6 +1813,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -1857,13 +1870,14 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
                                                      b.st, t, true, c.s));
             continue;
         }
-        cudaEvent_t e0 = prof.mark();
-        COUNTED(prof, 1, launch_estep4(a, true, grid, c.s));
-        cudaEvent_t e1 = prof.mark();
-        if (prof.on) prof.estep.emplace_back(e0, e1);
+        const bool pdl = !prof.per_launch;   // dependent launches, as in the 3-D loop
+        cudaEvent_t e0 = prof.mark_launch();
+        COUNTED(prof, 1, launch_estep4(a, true, grid, c.s, pdl));
+        cudaEvent_t e1 = prof.mark_launch();
+        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
         COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, kblk, b.llp, grid, nullptr, nullptr, k, n,
                                                  o.reg_covar, o.tol, b.model64, b.params, b.trace, b.st, t, true,
-                                                 c.s));
+                                                 c.s, pdl));
     }
     prof.t_em = prof.mark();
     if (final_loglik) {
@@ -1943,6 +1957,7 @@ gira_status gira_gmm_loglik4(const float* points, int64_t n, int k, const float*
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -2035,6 +2050,7 @@ gira_status gira_gmm_conditional4(const float* locs, int64_t m, int k, const flo
     layout(cv);
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -2107,6 +2123,7 @@ gira_status gira_gmm_sample(int64_t m, int k, int d, const float* weights, const
     layout(cv);
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};
@@ -2206,6 +2223,7 @@ gira_status gira_gbms(const float* points, int64_t n, int d, double bandwidth, i
 
     CallProfile prof;
     prof.on = g_prof_on.load() != 0;
+    prof.per_launch = g_prof_on.load() == 1;
     prof.s = c.s;
     prof.t0 = prof.mark();
     DeviceState h{};

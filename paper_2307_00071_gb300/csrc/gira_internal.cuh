@@ -145,6 +145,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Programmatic dependent launch (PTX griddepcontrol).  In a kernel launched with
+// programmatic stream serialisation, pdl_wait() returns once the previous kernel
+// of the stream has completed and its writes are visible, and pdl_allow_next()
+// lets the next such kernel be scheduled before this one ends.  In a plain
+// launch both have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -343,7 +350,27 @@ struct EStepLaunch {
 // Chooses the template instance and block shape for K; returns the CTA count
 // actually used in *grid_out (needed for the partials buffer size).
 // grad: the differentiable path's kernels (d-form logits; with stats, the adjoint).
-cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad = false);
+// A launch configuration, with programmatic stream serialisation when pdl (the
+// kernel may start before the previous kernel in the stream has finished, and
+// waits for it with pdl_wait()).
+struct PdlConfig {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    PdlConfig(dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl) {
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = pdl ? 1 : 0;
+    }
+};
+// pdl: launch as a programmatic dependent of the previous kernel in s (that kernel
+// must not write the points).
+cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad = false,
+                         bool pdl = false);
 // Occupancy-derived grid size for (k, stats) with n points.
 int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta, bool grad = false);
 // Pairs (padded) the parameter buffer must hold for k components.
@@ -360,7 +387,7 @@ cudaError_t launch_ll_reduce(const double* ll_partials, int grid, DeviceState* s
 cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool pdl = false);
 cudaError_t launch_params_from_model(const float* w, const float* mu, const float* cov, int k, double* model64,
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
 cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
@@ -556,7 +583,8 @@ int estep4_threads(int k);
 // Component pairs the parameter buffer holds for k (chunks padded to CHUNK4).
 int params4_pairs(int k);
 int estep4_grid(int64_t n, int k, int num_sms, int64_t* pts_per_cta);
-cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s);
+// pdl: as for launch_estep.
+cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s, bool pdl = false);
 // N x 4 -> pts4 (x,y,z,I) (nullable) and pts8 (x,x,y,y)(z,z,I,I); flags non-finite input.
 cudaError_t launch_pack4(const float* pts4in, int64_t n, float4* pts4, float4* pts8, DeviceState* st,
                          cudaStream_t s);
@@ -569,7 +597,7 @@ cudaError_t launch_fill_padding4(float* params, int k, cudaStream_t s);
 cudaError_t launch_reduce_finalize4(const float* partials, int grid, int kc, const double* ll_partials,
                                     int ll_count, const double* stats64, const float4* shift4, int k, int64_t n,
                                     double reg, double tol, double* model64, float* params, double* trace,
-                                    DeviceState* st, int iter, bool em, cudaStream_t s);
+                                    DeviceState* st, int iter, bool em, cudaStream_t s, bool pdl = false);
 // Chunked E-step (K > MAX_K4_DIRECT): gref from all k components; pass A / B over
 // chunks x grid CTAs (pass 1 or 2); exact maximum for the points combine listed.
 cudaError_t launch_chunk_ref4(const float* params, int k, const DeviceState* st, float* gref, cudaStream_t s);

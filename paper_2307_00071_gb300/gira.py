@@ -142,9 +142,11 @@ def version() -> str:
     return _lib.gira_version().decode()
 
 
-def gira_profile_enable(on: bool = True):
-    """Record CUDA events around each call's phases and E-step launches (process-wide)."""
-    _lib.gira_profile_enable(1 if on else 0)
+def gira_profile_enable(on: bool = True, launches: bool = True):
+    """Record CUDA events around each call's phases, and with ``launches`` around
+    every E-step launch too (process-wide).  Without ``launches`` the EM loop keeps
+    its dependent launches (the E-step and the finalize overlap at their edges)."""
+    _lib.gira_profile_enable(0 if not on else 1 if launches else 2)
 
 
 def gira_profile_read(reset: bool = False) -> dict:

@@ -226,3 +226,20 @@ def test_loglik4_chunked_k2048_with_outliers(gira, frame4):
     _, _, lse = oracle.estep(allp[sample], w, m, c, want_resp=False, want_lse=True)
     err = np.abs(pp[sample] - lse)
     assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))
+
+
+def test_fit4_dependent_launches_give_the_same_fit(gira):
+    """As in 3D: the 4D EM loop's dependent launches and plain launches (per-launch
+    profiling) give the same bits."""
+    cl = synth.gmm_cloud4(30_000, 10, seed=32)
+    runs = []
+    for launches in (False, True):
+        gira.gira_profile_enable(True, launches=launches)
+        try:
+            runs.append(gira.gira_gmm_fit4(cl.points, 40, iters=12, tol=0.0, seed=6, lloyd_iters=4))
+        finally:
+            gira.gira_profile_enable(False)
+    gira.gira_profile_read(reset=True)
+    for key in ("weights", "means", "covs"):
+        np.testing.assert_array_equal(to_np(runs[0][key]), to_np(runs[1][key]))
+    assert runs[0]["final_loglik"] == runs[1]["final_loglik"]

@@ -312,3 +312,26 @@ def test_calls_on_a_side_stream_match_the_default_stream(gira):
         assert torch.equal(r[key], ref[key])
     np.testing.assert_array_equal(r["trace"], ref["trace"])
     assert abs(ll - r["final_loglik"]) < 1e-5
+
+
+def test_dependent_launches_give_the_same_fit(gira):
+    """The EM loop launches the E-step and the binary64 finalize as programmatic
+    dependents of one another, except when per-launch profiling brackets every
+    E-step with an event pair (plain launches): both orders of execution give
+    the same bits, including a run that stops early on its tolerance."""
+    cl = synth.gmm_cloud(30_000, 10, seed=31)
+    x = dev(cl.points)
+    for tol in (0.0, 1e-3):
+        runs = []
+        for launches in (False, True):
+            gira.gira_profile_enable(True, launches=launches)
+            try:
+                runs.append(gira.gira_gmm_fit(x, 48, iters=14, tol=tol, seed=5, lloyd_iters=4))
+            finally:
+                gira.gira_profile_enable(False)
+        prof = gira.gira_profile_read(reset=True)
+        assert prof["estep_launches"] > 0   # the second run was timed launch by launch
+        for key in ("weights", "means", "covs"):
+            assert torch.equal(runs[0][key], runs[1][key])
+        np.testing.assert_array_equal(runs[0]["trace"], runs[1]["trace"])
+        assert runs[0]["iters_done"] == runs[1]["iters_done"]

@@ -253,6 +253,26 @@ def frame_init(frame):
     return oracle.kinit(frame.points, 512, seed=0, lloyd_iters=10, reg=1e-6)
 
 
+def test_kmeanspp_cluster_exchange_is_stable_over_many_draws(gira, frame):
+    """The cluster seeding kernel exchanges each centre's totals and chosen point
+    as point-to-point messages on mbarriers that alternate by the parity of the
+    centre: 48 seeds on the frame (K = 512, 511 exchanges each), each run twice,
+    give the same centres run to run, and two of them equal the oracle's draws."""
+    x = dev(frame.points)
+    first = {}
+    for rep in range(2):
+        for seed in range(100, 148):
+            c, _, _ = gira.gira_kmeans_init(x, 512, seed=seed, lloyd_iters=0, want_labels=False)
+            c = to_np(c).copy()
+            if rep == 0:
+                first[seed] = c
+            else:
+                assert np.array_equal(c, first[seed]), seed
+    for seed in (100, 129):
+        ref_c, _ = oracle.kmeanspp(frame.points, 512, seed)
+        assert np.array_equal(first[seed], ref_c), seed
+
+
 def test_frame_kmeans_init_bit_exact(gira, frame, frame_init):
     c, lab, done = gira.gira_kmeans_init(dev(frame.points), 512, seed=0, lloyd_iters=10)
     assert done == frame_init["lloyd_done"]

@@ -392,8 +392,9 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
 // j + 1's total while a slower peer still has centre j's in flight, but not
 // centre j + 2's (that needs centre j + 1's point, which needs every total of
 // j + 1, which each CTA sends only after reading centre j's).  Every wait is
-// bounded (GIRA_ERR_TIMEOUT); a thread that timed out stops waiting and the
-// loop runs to its end, so no CTA leaves while a peer may still store to it.
+// bounded (GIRA_ERR_TIMEOUT); a thread that timed out stops waiting and sending
+// and the loop runs to its end, so every CTA reaches the final cluster barrier
+// and none leaves while a live peer may still store to it.
 // The arithmetic is the exact fixed point of the other seeding kernels, so the
 // chosen indices are identical.
 constexpr int KC_THREADS = 512;
@@ -590,7 +591,8 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
             const u128 wi = u128_warp_incl_scan(wv, lane);
             if (lane < KC_WARPS) sh.wincl[lane] = wi;
             const u128 total = u128_shfl(wi, KC_WARPS - 1);
-            if (lane < cs) kc_send_u128(kc_peer(&sh.csum[b][me], lane), total, kc_peer(&sh.bar_sum[b], lane));
+            if (lane < cs && !dead)
+                kc_send_u128(kc_peer(&sh.csum[b][me], lane), total, kc_peer(&sh.bar_sum[b], lane));
             // ---- 2. every CTA's total has arrived
             if (!dead && !kc_wait(&sh.bar_sum[b], (ph_sum >> b) & 1u)) {
                 dead = true;
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 const float4 pf = (qf & 1) ? make_float4(px.y, py.y, pz.y, 0.f) : make_float4(px.x, py.x, pz.x, 0.f);
                 const long long lo_src = __shfl_sync(FULL, (long long)llo, src);
                 const long long found = min((long long)n - 1, lo_src + qf);   // clamp never taken
-                if (lane < cs) {
+                if (lane < cs && !dead) {
                     const uint32_t bar = kc_peer(&sh.bar_cen[b], lane);
                     kc_send_f4(kc_peer(&sh.cen[b], lane), pf, bar);
                     kc_send_s64(kc_peer(&sh.idx[b], lane), found, bar);

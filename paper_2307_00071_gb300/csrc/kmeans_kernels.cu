@@ -856,23 +856,56 @@ __global__ void lloyd_update_batched_kernel(int total_k, const int* __restrict__
 }
 
 // One-hot statistics about the shift s_b (the final centre): S0 = count,
-// S1 = sum (x - s), S2 = sum (x - s)(x - s)^T, binary64.
+// S1 = sum (x - s), S2 = sum (x - s)(x - s)^T, binary64.  Each thread takes
+// LS_PPT consecutive points and sums each run of equal labels in registers
+// before its atomics (raster-order neighbours share labels, so most threads
+// flush once).
+constexpr int LS_PPT = 8;
+
+__device__ __forceinline__ void label_stats_flush(double* stats64, int b, const double* a) {
+    double* S = stats64 + (size_t)b * NSTAT;
+#pragma unroll
+    for (int t = 0; t < NSTAT; ++t) atomicAdd(&S[t], a[t]);
+}
+
 __global__ void label_stats_kernel(const float4* __restrict__ pts, int64_t n, int k, const int32_t* __restrict__ labels,
                                    const float4* __restrict__ shift4, double* stats64, DeviceState* st) {
     if (st->error) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = labels[i];
-        const float4 x = pts[i], s = shift4[b];
-        const double d[3] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z};
-        double* S = stats64 + (size_t)b * NSTAT;
-        atomicAdd(&S[0], 1.0);
-        for (int t = 0; t < 3; ++t) atomicAdd(&S[1 + t], d[t]);
-        atomicAdd(&S[4], d[0] * d[0]);
-        atomicAdd(&S[5], d[0] * d[1]);
-        atomicAdd(&S[6], d[0] * d[2]);
-        atomicAdd(&S[7], d[1] * d[1]);
-        atomicAdd(&S[8], d[1] * d[2]);
-        atomicAdd(&S[9], d[2] * d[2]);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * LS_PPT;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * LS_PPT; i0 < n; i0 += step) {
+        int key = -1;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        double a[NSTAT];
+#pragma unroll
+        for (int t = 0; t < NSTAT; ++t) a[t] = 0.0;
+#pragma unroll
+        for (int r = 0; r < LS_PPT; ++r) {
+            const int64_t i = i0 + r;
+            if (i < n) {
+                const int b = labels[i];
+                if (b != key) {
+                    if (key >= 0) label_stats_flush(stats64, key, a);
+#pragma unroll
+                    for (int t = 0; t < NSTAT; ++t) a[t] = 0.0;
+                    key = b;
+                    s = shift4[b];
+                }
+                const float4 x = pts[i];
+                const double d0 = (double)x.x - (double)s.x, d1 = (double)x.y - (double)s.y,
+                             d2 = (double)x.z - (double)s.z;
+                a[0] += 1.0;
+                a[1] += d0;
+                a[2] += d1;
+                a[3] += d2;
+                a[4] += d0 * d0;
+                a[5] += d0 * d1;
+                a[6] += d0 * d2;
+                a[7] += d1 * d1;
+                a[8] += d1 * d2;
+                a[9] += d2 * d2;
+            }
+        }
+        if (key >= 0) label_stats_flush(stats64, key, a);
     }
 }
 
@@ -1096,7 +1129,7 @@ cudaError_t launch_label_stats(const float4* pts4, int64_t n, int k, const int32
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (n + 255) / 256;
+    const int64_t want = (n + 256 * LS_PPT - 1) / (256 * LS_PPT);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
     label_stats_kernel<<<grid, 256, 0, s>>>(pts4, n, k, labels, shift4, stats64, st);
     return cudaGetLastError();

@@ -802,19 +802,51 @@ __global__ void lloyd4_update_kernel(int k, double* sums, float4* centers, const
 
 // One-hot statistics about the final centres: S0 = count, S1 = sum (x - s),
 // S2 = sum (x - s)(x - s)^T, binary64.
+// Each thread takes LS4_PPT consecutive points and sums each run of equal labels
+// in registers (binary64) before its atomics, as in 3D.
+constexpr int LS4_PPT = 8;
+
 __global__ void label_stats4_kernel(const float4* __restrict__ pts, int64_t n, const int32_t* __restrict__ labels,
                                     const float4* __restrict__ shift4, double* stats64, DeviceState* st) {
     if (st->error) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = labels[i];
-        const float4 x = pts[i], s = shift4[b];
-        const double d[4] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z,
-                             (double)x.w - (double)s.w};
-        double* S = stats64 + (size_t)b * NSTAT4;
-        atomicAdd(&S[0], 1.0);
-        for (int t = 0; t < 4; ++t) atomicAdd(&S[1 + t], d[t]);
-        for (int i2 = 0; i2 < 4; ++i2)
-            for (int j = i2; j < 4; ++j) atomicAdd(&S[5 + sym4(i2, j)], d[i2] * d[j]);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * LS4_PPT;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * LS4_PPT; i0 < n; i0 += step) {
+        int key = -1;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        double a[NSTAT4];
+#pragma unroll
+        for (int t = 0; t < NSTAT4; ++t) a[t] = 0.0;
+        for (int r = 0; r < LS4_PPT; ++r) {
+            const int64_t i = i0 + r;
+            if (i >= n) break;
+            const int b = labels[i];
+            if (b != key) {
+                if (key >= 0) {
+                    double* S = stats64 + (size_t)key * NSTAT4;
+#pragma unroll
+                    for (int t = 0; t < NSTAT4; ++t) atomicAdd(&S[t], a[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < NSTAT4; ++t) a[t] = 0.0;
+                key = b;
+                s = shift4[b];
+            }
+            const float4 x = pts[i];
+            const double d[4] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z,
+                                 (double)x.w - (double)s.w};
+            a[0] += 1.0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) a[1 + t] += d[t];
+#pragma unroll
+            for (int i2 = 0; i2 < 4; ++i2)
+#pragma unroll
+                for (int j = i2; j < 4; ++j) a[5 + sym4(i2, j)] += d[i2] * d[j];
+        }
+        if (key >= 0) {
+            double* S = stats64 + (size_t)key * NSTAT4;
+#pragma unroll
+            for (int t = 0; t < NSTAT4; ++t) atomicAdd(&S[t], a[t]);
+        }
     }
 }
 
@@ -849,7 +881,7 @@ cudaError_t launch_lloyd4(const float4* pts4, int64_t n, int k, int lloyd_iters,
 cudaError_t launch_label_stats4(const float4* pts4, int64_t n, int k, const int32_t* labels, const float4* shift4,
                                 double* stats64, DeviceState* st, cudaStream_t s) {
     (void)k;
-    const int64_t want = (n + 255) / 256;
+    const int64_t want = (n + 256 * LS4_PPT - 1) / (256 * LS4_PPT);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms_now() * 8));
     label_stats4_kernel<<<grid, 256, 0, s>>>(pts4, n, labels, shift4, stats64, st);
     return cudaGetLastError();

@@ -169,3 +169,16 @@ def test_test_hooks_check_arguments_without_gpu():
     assert L.gira_test_bounded_wait(2, 10, None) == gira.ERR_INVALID_ARG
     assert L.gira_test_bounded_wait(0, 0, None) == gira.ERR_INVALID_ARG
     gira.gira_test_fail_next_allocations(0)   # clearing is a no-op without a GPU
+
+
+def test_profile_levels_without_gpu():
+    """Profiling is host state: off, phase events only (the EM loop keeps its
+    dependent launches), or phase events plus an event pair per E-step launch;
+    reading and resetting the accumulated profile needs no GPU."""
+    from paper_2307_00071_gb300 import gira
+    gira.gira_profile_read(reset=True)   # whatever earlier calls in this process left
+    for on, launches in ((True, False), (True, True), (False, True)):
+        gira.gira_profile_enable(on, launches=launches)
+        p = gira.gira_profile_read(reset=True)
+        assert p["calls"] == 0 and p["estep_launches"] == 0 and p["estep_ms"] == 0.0
+    gira.gira_profile_enable(False)

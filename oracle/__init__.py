@@ -76,6 +76,10 @@ def lib():
         L.oracle_conditional4.argtypes = [fp, C.c_int64, ci, dp, dp, dp, dp, dp]
         L.oracle_sample_d.argtypes = [C.c_int64, ci, ci, dp, dp, dp, C.c_uint64, fp, i32p]
         L.oracle_gbms_d.argtypes = [fp, C.c_int64, ci, C.c_double, ci, C.POINTER(ci), dp, i32p]
+        L.oracle_max_threads.restype = ci
+        L.oracle_estep_par_d.argtypes = [fp, C.c_int64, ci, ci, dp, dp, dp, dp, dp, ci]
+        L.oracle_em_par_d.argtypes = [fp, C.c_int64, ci, ci, ci, C.c_double, C.c_double, dp, dp, dp, dp,
+                                      C.POINTER(ci), dp, ci]
         _lib = L
     return _lib
 
@@ -241,6 +245,43 @@ def em(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-
                            _p(c, C.c_double), _p(trace, C.c_double), C.byref(done), C.byref(fll))
     _check(st, "em")
     return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
+
+
+def max_threads() -> int:
+    """Threads the parallel oracle uses by default (OpenMP: OMP_NUM_THREADS, else every core)."""
+    return int(lib().oracle_max_threads())
+
+
+def em_par(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-6, threads: int = 0):
+    """``em`` over all host cores (``gira_oracle_par.c``): the same iteration, point
+    arithmetic and stopping rule; sums over fixed chunks of points added in chunk
+    order, so the result does not depend on ``threads`` (0 = every core)."""
+    pts = _f32(pts)
+    d = _dim(pts)
+    N = pts.shape[0]
+    w, m, c = _f64(weights).copy(), _f64(means).copy(), _f64(covs).copy()
+    K = w.shape[0]
+    trace = np.full(max(iters, 1), np.nan)
+    done, fll = C.c_int(), C.c_double()
+    st = lib().oracle_em_par_d(_p(pts, C.c_float), N, K, d, iters, tol, reg, _p(w, C.c_double),
+                               _p(m, C.c_double), _p(c, C.c_double), _p(trace, C.c_double), C.byref(done),
+                               C.byref(fll), int(threads))
+    _check(st, "em_par")
+    return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
+
+
+def loglik_par(pts, weights, means, covs, per_point: bool = False, threads: int = 0):
+    """Mean per-point log-likelihood (and the per-point values) over all host cores."""
+    pts = _f32(pts)
+    d = _dim(pts)
+    N, K = pts.shape[0], len(weights)
+    w, m, c = _f64(weights), _f64(means), _f64(covs)
+    lse = np.empty(N) if per_point else None
+    ll = C.c_double()
+    st = lib().oracle_estep_par_d(_p(pts, C.c_float), N, K, d, _p(w, C.c_double), _p(m, C.c_double),
+                                  _p(c, C.c_double), _p(lse, C.c_double), C.byref(ll), int(threads))
+    _check(st, "estep_par")
+    return (ll.value, lse) if per_point else ll.value
 
 
 def gmm_fit(pts, K: int, iters: int, tol: float = 0.0, reg: float = 1e-6, seed: int = 0, lloyd_iters: int = 10):

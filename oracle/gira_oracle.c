@@ -69,6 +69,7 @@ enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_NONFINITE = 2, OR_ERR_NOT_PD = 
 
 static int g_last_bad_component = -1;
 int oracle_last_bad_component(void) { return g_last_bad_component; }
+void oracle_note_bad_component(int b) { g_last_bad_component = b; }
 
 /* ---------------------------------------------------------------- RNG -- */
 uint64_t oracle_splitmix64(uint64_t seed, uint64_t j) {

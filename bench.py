@@ -13,9 +13,10 @@ roofline    the fused E-step/statistics kernel against the FP32-pipe roofline
             (23 FP32-pipe operations per point-component-iteration)
 e2e         the same metric through the C ABI with host buffers (pinned points in,
             model and log-likelihood trace out, copies inside the timed region)
-cpu_baseline  the FP64 oracle on the host cores, one EM iteration of the frame
+cpu_baseline  the FP64 oracle on the host: EM iterations of the frame over every
+            core (OpenMP), and the single-threaded oracle on one core
 
-``--impl reference`` times the oracle alone (rank 0; the baseline arm).
+``--impl reference`` times the all-core oracle alone (rank 0; the baseline arm).
 Multi-GPU (torchrun): every rank fits its own frame (weak scaling, no collective
 on the data path; barriers only bracket the timed region).
 """
@@ -173,35 +174,72 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- reference arm
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count(), model or "unknown"
+
+
+def oracle_start_model(frame_pts, seed=123):
+    """A K-component start for the oracle's timing runs: thin discs (20 cm x 10 cm x 1 cm)
+    centred on random frame points, Dirichlet weights.  The oracle's cost does not depend
+    on the parameters (it evaluates every point-component pair)."""
+    rng = np.random.default_rng(seed)
+    m = frame_pts[rng.choice(len(frame_pts), K, replace=False)].astype(np.float64)
+    c = np.empty((K, 3, 3))
+    for b in range(K):
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        c[b] = q @ np.diag([0.2 ** 2, 0.1 ** 2, 0.01 ** 2]) @ q.T
+    return rng.dirichlet(np.ones(K)), m, c
+
+
 def run_reference(args):
+    """The baseline arm: the FP64 oracle over every host core (OpenMP), one EM
+    iteration (E-step + M-step) of the full frame per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     from paper_2307_00071_gb300 import synth
     frame = synth.depth_frame(seed=1)
-    rng = np.random.default_rng(123)
-    m = 32_768
-    sample = frame.points[np.sort(rng.choice(len(frame.points), m, replace=False))]
-    ki = oracle.kinit(sample, K, seed=SEED, lloyd_iters=LLOYD, reg=REG)
-    w, mu, cov = ki["weights"], ki["means"], ki["covs"]
+    n = len(frame.points)
+    w, mu, cov = oracle_start_model(frame.points)
     times = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        _, resp, _ = oracle.estep(sample, w, mu, cov)
-        w, mu, cov = oracle.mstep(sample, resp, REG)
+        r = oracle.em_par(frame.points, w, mu, cov, iters=1, tol=0.0, reg=REG, final=False)
         dt = time.perf_counter() - t0
+        w, mu, cov = r["weights"], r["means"], r["covs"]
         if step >= args.warmup:
             times.append(dt)
     tot = sum(times)
-    value = m * K * len(times) / tot
+    value = n * K * len(times) / tot
+    cores, model = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(len(frame.points)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one EM iteration (E-step + M-step) per step on a {m}-point random subset "
-                                       f"of the frame, K={K}, from the oracle's own k-means init"},
+            "config": workload_config(n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "nproc": cores,
+                             "cpu_model": model, "kind": "oracle",
+                             "sample": f"one EM iteration (E-step + M-step, binary64, OpenMP over "
+                                       f"{oracle.max_threads()} threads) of the full {n}-point frame per step, "
+                                       f"K={K}, from a seeded start model"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -247,7 +285,7 @@ def bench_grad(gira, frame_pts, sms, mhz, reps=20):
     peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / GRAD_FP32_OPS
     return {"workload": f"L and all gradients: {GRAD_SCAN}-point scan, K={GRAD_K} GMM of the frame, 10 deg + 0.17 m offset",
             "unit": UNIT, "value": units / call_s, "ms_per_call": call_s * 1e3,
-            "kernel": "estep_kernel<2,8,256,1,true,true> (fused log-likelihood adjoint, K=1024: 8 warps)",
+            "kernel": prof["estep_kernel"],
             "kernel_ms": kern_s * 1e3, "kernel_units_per_s": units / kern_s if kern_s else None,
             "frac_fp32": (units / kern_s) / peak if kern_s else None,
             "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {GRAD_FP32_OPS} FP32 ops per unit"}
@@ -318,6 +356,44 @@ def bench_batched(gira):
             "speedup_vs_loop": out["loop"] / out["batched"],
             "with_kinit": {"ms_batched": out["batched_full"], "ms_per_instance_loop": out["loop_full"],
                            "speedup_vs_loop": out["loop_full"] / out["batched_full"]}}
+
+
+REG_STEPS, REG_SEEDS = 100, (3, 4, 5)
+
+
+def bench_registration(gira, frame_pts):
+    """The differentiable-registration configuration end to end: a K=1024 GMM fitted to
+    the frame; a second scan of the same scene (own 5 mm sensor noise and dropout), 100k
+    points under a random rigid offset (<= 15 deg, <= 0.5 m); 100 Adam steps on the twist,
+    each one call of the fused log-likelihood / adjoint kernel.  Timed per registration."""
+    import torch
+    from paper_2307_00071_gb300 import autograd as ag, synth
+    x = torch.as_tensor(frame_pts, device="cuda")
+    fit = gira.gira_gmm_fit(x, GRAD_K, iters=ITERS, tol=TOL, seed=0, lloyd_iters=LLOYD)
+    logits = torch.log(fit["weights"])
+    chol = torch.linalg.cholesky(fit["covs"].double()).float()
+    runs = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for seed in REG_SEEDS:
+        scan, R_off, t_off = synth.registration_scan(seed=1, offset_seed=seed)
+        s = torch.as_tensor(scan, device="cuda")
+        ag.register_scan(s, logits, fit["means"], chol, steps=3)   # warm
+        torch.cuda.synchronize()
+        ev0.record()
+        R, t, ll = ag.register_scan(s, logits, fit["means"], chol, steps=REG_STEPS)
+        ev1.record()
+        torch.cuda.synchronize()
+        R, t = R.cpu().numpy(), t.cpu().numpy()
+        dR = R @ R_off
+        ang = float(np.degrees(np.arccos(np.clip((np.trace(dR) - 1) / 2, -1, 1))))
+        off = float(np.degrees(np.arccos(np.clip((np.trace(R_off) - 1) / 2, -1, 1))))
+        runs.append({"offset_deg": off, "offset_m": float(np.linalg.norm(t_off)), "ms": ev0.elapsed_time(ev1),
+                     "rot_err_deg": ang, "trans_err_m": float(np.linalg.norm(t + R_off.T @ t_off)),
+                     "mean_loglik": ll})
+    ms = float(np.mean([r["ms"] for r in runs]))
+    return {"workload": f"K={GRAD_K} GMM of the frame; second scan of the scene, {GRAD_SCAN} points, random rigid "
+                        f"offset <= 15 deg / 0.5 m; {REG_STEPS} Adam steps on the twist (L and its gradient per step)",
+            "ms_per_registration": ms, "ms_per_step": ms / REG_STEPS, "runs": runs}
 
 
 REG_B, REG_N, REG_K = 64, 100_000, 1024
@@ -474,7 +550,7 @@ def bench_d4(gira, frame_pts, sms, mhz, reps=5):
             "unit": UNIT, "value": float(n) * D4_K * iters / reps / (ms / 1e3), "ms_per_frame": ms,
             "em_ms_per_frame": prof["em_ms"] / reps, "init_ms_per_frame": prof["init_ms"] / reps,
             "iters_done": r["iters_done"], "final_loglik": r["final_loglik"],
-            "kernel": "estep4_kernel<true, 0> (4D fused E-step + statistics)", "kernel_ms": kern_s * 1e3,
+            "kernel": prof["estep_kernel"], "kernel_ms": kern_s * 1e3,
             "kernel_units_per_s": n * D4_K / kern_s if kern_s else None,
             "frac_fp32": (n * D4_K / kern_s) / peak if kern_s else None,
             "peak_basis": f"{FP32_LANES_PER_SM} lanes x {sms} SMs x {mhz:.0f} MHz / {D4_FP32_OPS} FP32 ops per unit",
@@ -634,21 +710,35 @@ def bench_small_config(gira, reps=20):
 
 
 # --------------------------------------------------------------------------- gira arm
-CPU_ITERS = 2   # about 13 s of single-core work on the GPU machine's host
+CPU_ALL_S = 10.0   # whole EM iterations over every host core until this much time has passed
+CPU_ONE_ITERS = 1  # single-threaded oracle: one EM iteration of the frame (several seconds)
 
 
-def cpu_baseline(frame_pts, init):
+def cpu_baseline(frame_pts):
+    """The FP64 oracle on this host: EM iterations of the full frame over every core
+    (OpenMP, deterministic chunked sums), and one iteration on a single core."""
     import oracle
-    w, mu, cov = init
-    t0 = time.perf_counter()
-    for _ in range(CPU_ITERS):
-        _, resp, _ = oracle.estep(frame_pts, w, mu, cov)
-        w, mu, cov = oracle.mstep(frame_pts, resp, REG)
-    dt = time.perf_counter() - t0
     n = len(frame_pts)
-    return {"value": n * K * CPU_ITERS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_ITERS} EM iterations (E-step + M-step, binary64, single thread) on the full {n}-point "
-                      f"frame, K={K}, from the library's KInit parameters; {dt:.1f} s"}
+    w, mu, cov = oracle_start_model(frame_pts)
+    t0 = time.perf_counter()
+    it = 0
+    while True:
+        r = oracle.em_par(frame_pts, w, mu, cov, iters=1, tol=0.0, reg=REG, final=False)
+        w, mu, cov = r["weights"], r["means"], r["covs"]
+        it += 1
+        dt = time.perf_counter() - t0
+        if dt >= CPU_ALL_S or it >= 30:
+            break
+    t1 = time.perf_counter()
+    oracle.em(frame_pts, w, mu, cov, iters=CPU_ONE_ITERS, tol=0.0, reg=REG)
+    dt1 = time.perf_counter() - t1
+    cores, model = host_cpu()
+    threads = oracle.max_threads()
+    return {"value": n * K * it / dt, "unit": UNIT, "cores": threads, "nproc": cores, "cpu_model": model,
+            "kind": "oracle", "single_core_value": n * K * CPU_ONE_ITERS / dt1,
+            "sample": f"{it} EM iterations (E-step + M-step, binary64) of the full {n}-point frame, K={K}, over "
+                      f"{threads} OpenMP threads ({dt:.1f} s), from a seeded start model; single core: "
+                      f"{CPU_ONE_ITERS} iteration of the single-threaded oracle ({dt1:.1f} s)"}
 
 
 def run_gira(args):
@@ -743,7 +833,7 @@ def run_gira(args):
             "iters_done": iters_seen,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_units, "unit": UNIT,
                          "frac": achieved / peak_units, "traffic": tr,
-                         "kernel": "estep_kernel<2,8,128,3,true> (fused E-step + M-step statistics)",
+                         "kernel": prof["estep_kernel"],
                          "launch_ms": avg_estep_s * 1e3, "launches_timed": prof["estep_launches"],
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {mhz:.0f} MHz ({mhz_src}) / "
                                        f"{FP32_OPS_PER_UNIT} FP32 ops per unit"},
@@ -754,6 +844,7 @@ def run_gira(args):
         }
         if not args.no_extras:
             extras = (("grad", lambda: bench_grad(gira, frame.points, sms, mhz)),
+                      ("registration", lambda: bench_registration(gira, frame.points)),
                       ("batched", lambda: bench_batched(gira)),
                       ("large_map", lambda: bench_large_map(gira)),
                       ("batched_registrations", lambda: bench_batched_registrations(gira, frame.points)),
@@ -771,9 +862,7 @@ def run_gira(args):
                     line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.no_cpu_baseline:
             try:
-                init = gira.gira_gmm_fit(frame.points, K, iters=0, tol=TOL, reg_covar=REG, seed=SEED,
-                                         lloyd_iters=LLOYD, final_loglik=False)
-                line["cpu_baseline"] = cpu_baseline(frame.points, (init["weights"], init["means"], init["covs"]))
+                line["cpu_baseline"] = cpu_baseline(frame.points)
             except Exception as e:  # noqa: BLE001
                 line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)

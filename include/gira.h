@@ -81,10 +81,15 @@ void gira_fit_opts_default(gira_fit_opts *opts);
  * gira_kmeans_init -- KInit seeding (Sec. V, Fig. "information flow").
  *
  * k-means++ (Arthur & Vassilvitskii 2007, one candidate per step): centre 0
- * is point floor(u_0 N); centre j is the first point n whose running sum of
- * D^2 (binary64 over binary32 squared distances to the nearest centre chosen
- * so far) exceeds u_j * sum D^2, where u_j is draw j of the SplitMix64
- * counter stream of `seed` (top 53 bits / 2^53).  Then Lloyd iterations:
+ * is point floor(u_0 N); for centre j every point's weight is its binary32
+ * squared distance D^2 to the nearest centre chosen so far (fixed order
+ * (d0^2 + d1^2) + d2^2, no fused multiply-add), taken in exact fixed point as
+ * the integer floor(D^2 2^48) (saturating at 2^95 - 1); with T the exact
+ * integer total and k_j the top 53 bits of draw j of the SplitMix64 counter
+ * stream of `seed` (u_j = k_j / 2^53), centre j is the first point n whose
+ * exact running sum exceeds floor(k_j T / 2^53) (if T = 0: point
+ * floor(u_j N)).  No rounding enters the choice, so the centres do not depend
+ * on the order in which the GPU sums.  Then Lloyd iterations:
  * labels = argmin_b ||x - c_b||^2 (binary32, ties to the lowest b), centres
  * = binary64 mean of their points rounded to binary32 (empty clusters keep
  * their centre), until no label changes or `lloyd_iters` updates were made.
@@ -336,6 +341,7 @@ typedef struct {
     double init_ms;             /* pack + KInit (k-means++, Lloyd, one-hot M-step) or parameter upload */
     double em_ms;               /* the EM loop: E-step, reduction and FP64 finalize of every iteration */
     double total_ms;            /* whole calls, first upload to last download */
+    char estep_kernel[128];     /* name of the last E-step kernel timed launch by launch ("" if none) */
 } gira_profile;
 
 /*
@@ -354,10 +360,11 @@ gira_status gira_profile_read(gira_profile *out, int reset);
  * gira_gmm_loglik_noalloc -- gira_gmm_loglik for callers that cannot allocate
  * device memory.  (An engineering addition: the paper has no counterpart.)
  *
- * Who needs it: code that runs while a CUDA graph is being captured (where
- * cudaMalloc is not allowed), real-time control loops that forbid allocation
- * after start-up, and hosts whose device memory is owned by a pool they do not
- * control.  It computes the same mean and per-point log-likelihoods as
+ * Who needs it: real-time control loops that forbid allocation after start-up
+ * (cudaMalloc can block for an unbounded time, and can fail in the middle of a
+ * run), and hosts whose device memory is owned by a pool they do not control
+ * (memory the library took would be missing from the pool's budget).  It
+ * computes the same mean and per-point log-likelihoods as
  * gira_gmm_loglik, with the same kernels, but never calls cudaMalloc,
  * cudaFree or any allocating routine: its scratch (packed points, component
  * parameters, per-CTA partial sums, status word) is one static device array of

@@ -252,10 +252,12 @@ def max_threads() -> int:
     return int(lib().oracle_max_threads())
 
 
-def em_par(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-6, threads: int = 0):
+def em_par(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float = 1e-6, threads: int = 0,
+           final: bool = True):
     """``em`` over all host cores (``gira_oracle_par.c``): the same iteration, point
     arithmetic and stopping rule; sums over fixed chunks of points added in chunk
-    order, so the result does not depend on ``threads`` (0 = every core)."""
+    order, so the result does not depend on ``threads`` (0 = every core).
+    ``final=False`` skips the log-likelihood of the returned model (final_ll = nan)."""
     pts = _f32(pts)
     d = _dim(pts)
     N = pts.shape[0]
@@ -265,9 +267,10 @@ def em_par(pts, weights, means, covs, iters: int, tol: float = 0.0, reg: float =
     done, fll = C.c_int(), C.c_double()
     st = lib().oracle_em_par_d(_p(pts, C.c_float), N, K, d, iters, tol, reg, _p(w, C.c_double),
                                _p(m, C.c_double), _p(c, C.c_double), _p(trace, C.c_double), C.byref(done),
-                               C.byref(fll), int(threads))
+                               C.byref(fll) if final else None, int(threads))
     _check(st, "em_par")
-    return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value, final_ll=fll.value)
+    return dict(weights=w, means=m, covs=c, trace=trace[:done.value], iters_done=done.value,
+                final_ll=fll.value if final else float("nan"))
 
 
 def loglik_par(pts, weights, means, covs, per_point: bool = False, threads: int = 0):

@@ -21,8 +21,11 @@
  *     with the same expressions, which gives the same values bit for bit.
  *     This is what lets it run at N = 4M, K = 8192.
  *
- * Per point it calls the single-threaded oracle's own log-density
- * (oracle_log_gaussian_d) and the same log-sum-exp expressions.
+ * Per point it evaluates Eq. (simplifiedGaussian) with the expressions of the
+ * single-threaded oracle_log_gaussian_d, in the same order, except that the
+ * log-determinant sum_i ln P_ii (the same sum, in the same order) is taken once
+ * per component instead of once per point; the values are the same bit for bit
+ * (pinned against the single-threaded E-step).
  */
 #include <float.h>
 #include <math.h>
@@ -40,7 +43,6 @@ enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_NONFINITE = 2, OR_ERR_NOT_PD = 
 /* from gira_oracle.c */
 int oracle_cholesky_d(const double *S, double *L, int d);
 void oracle_tri_inverse_d(const double *L, double *P, int d);
-double oracle_log_gaussian_d(const double *x, const double *mu, const double *P, int d);
 void oracle_note_bad_component(int b);
 
 /* OpenMP's default team size (OMP_NUM_THREADS, else every core); never changed here */
@@ -49,8 +51,20 @@ static int team(int threads) { return threads > 0 ? threads : omp_get_max_thread
 
 typedef struct {
     int K, d;
-    const double *logw, *means, *P;
+    const double *logw, *logdet, *means, *P;
 } Model;
+
+/* Eq. (simplifiedGaussian): ln N(x | mu, Sigma) with P = L^{-1} and
+ * logdet = sum_i ln P_ii; the expressions of oracle_log_gaussian_d. */
+static double log_gaussian(const double *x, const double *mu, const double *P, double logdet, int d) {
+    double q = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double y = 0.0;
+        for (int j = 0; j <= i; ++j) y += P[i * d + j] * (x[j] - mu[j]);
+        q += y * y;
+    }
+    return -0.5 * (d * log(2.0 * M_PI) + q) + logdet;
+}
 
 /* One point: a[b] <- r_nb (responsibilities); returns lse_n = ln sum_b pi_b N(x_n|b).
  * The same expressions, in the same order, as oracle_estep_d. */
@@ -60,7 +74,7 @@ static double point_resp(const Model *M, const float *xp, double *a) {
     for (int i = 0; i < d; ++i) x[i] = xp[i];
     double m = -INFINITY;
     for (int b = 0; b < K; ++b) {
-        a[b] = M->logw[b] + oracle_log_gaussian_d(x, M->means + (size_t)d * b, M->P + (size_t)dd * b, d);
+        a[b] = M->logw[b] + log_gaussian(x, M->means + (size_t)d * b, M->P + (size_t)dd * b, M->logdet[b], d);
         if (a[b] > m) m = a[b];
     }
     double s = 0.0;
@@ -83,21 +97,28 @@ static int finite_inputs(const float *pts, int64_t N, int K, int d, const double
     return 1;
 }
 
+/* logw and logdet: 2K doubles */
 static int model_setup(int K, int d, const double *weights, const double *means, const double *covs, double *logw,
                        double *P, Model *M) {
     const int dd = d * d;
+    double *logdet = logw + K;
     for (int b = 0; b < K; ++b) {
         double L[DMAX * DMAX];
         if (oracle_cholesky_d(covs + (size_t)dd * b, L, d) != 0) {
             oracle_note_bad_component(b);
             return OR_ERR_NOT_PD;
         }
-        oracle_tri_inverse_d(L, P + (size_t)dd * b, d);
+        double *Pb = P + (size_t)dd * b;
+        oracle_tri_inverse_d(L, Pb, d);
         logw[b] = log(weights[b]);
+        double ld = 0.0;
+        for (int i = 0; i < d; ++i) ld += log(Pb[i * d + i]);
+        logdet[b] = ld;
     }
     M->K = K;
     M->d = d;
     M->logw = logw;
+    M->logdet = logdet;
     M->means = means;
     M->P = P;
     return OR_OK;
@@ -110,7 +131,7 @@ int oracle_estep_par_d(const float *pts, int64_t N, int K, int d, const double *
         return OR_ERR_INVALID_ARG;
     if (!finite_inputs(pts, N, K, d, weights, means, covs)) return OR_ERR_NONFINITE;
     const int nt = team(threads);
-    double *logw = malloc(sizeof(double) * K), *P = malloc(sizeof(double) * d * d * K);
+    double *logw = malloc(sizeof(double) * 2 * K), *P = malloc(sizeof(double) * d * d * K);
     const int64_t nch = (N + PAR_CHUNK - 1) / PAR_CHUNK;
     double *part = malloc(sizeof(double) * nch);
     if (!logw || !P || !part) { free(logw); free(P); free(part); return OR_ERR_OOM; }
@@ -158,7 +179,7 @@ static int em_iteration(const float *pts, int64_t N, int K, int d, double reg, d
     const int64_t nch = (N + PAR_CHUNK - 1) / PAR_CHUNK;
     const size_t w1 = 1 + (size_t)K * (1 + d); /* pass 1 partial: ll, N_b, sum r x */
     const size_t w2 = (size_t)K * dd;          /* pass 2 partial: sum r (x-mu)(x-mu)^T */
-    double *logw = malloc(sizeof(double) * K), *P = malloc(sizeof(double) * dd * K);
+    double *logw = malloc(sizeof(double) * 2 * K), *P = malloc(sizeof(double) * dd * K);
     double *tot1 = calloc(w1, sizeof(double)), *tot2 = calloc(w2, sizeof(double));
     double *grp = malloc(sizeof(double) * PAR_GROUP * (w1 > w2 ? w1 : w2));
     double *mu = malloc(sizeof(double) * d * K), *nb = malloc(sizeof(double) * K);

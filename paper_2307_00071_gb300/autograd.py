@@ -88,3 +88,41 @@ def se3_exp(xi):
     R = eye + A * W + B * W2
     V = eye + B * W + C * W2
     return R, V @ v
+
+
+def register_scan(scan, logits, means, chol, steps=100, lr=0.02, decay=0.96, t0=None):
+    """Likelihood-based rigid registration as a gradient solve: the pose (R, t)
+    that maximises the mean log-likelihood of ``R scan + t`` under the mixture
+    (logits, means, Cholesky factors), by ``steps`` Adam steps on the twist of a
+    left perturbation.  The scan is rotated about its own centroid and the
+    translation starts at ``t0`` (default: the mixture's weighted mean of the
+    means), which keeps rotation and translation well scaled.  Every likelihood
+    and gradient comes from the library's fused kernel; the optimiser updates six
+    numbers.  Returns (R (3, 3), t (3,)) in binary64 such that R scan + t lies on
+    the mixture, and the final mean log-likelihood."""
+    dev = scan.device
+    c = scan.double().mean(0)
+    s = (scan.double() - c).float().contiguous()
+    R0 = torch.eye(3, dtype=torch.float64, device=dev)
+    if t0 is None:
+        w = torch.softmax(logits.double(), 0)
+        t0 = (w[:, None] * means.double()).sum(0)
+    t_base = torch.as_tensor(t0, dtype=torch.float64, device=dev)
+    xi = torch.zeros(6, dtype=torch.float64, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([xi], lr=lr)
+    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=decay)
+    n = len(scan)
+    for _ in range(steps):
+        opt.zero_grad()
+        Rd, td = se3_exp(xi)
+        L = gmm_loglik(s, logits, means, chol, Rd @ R0, Rd @ t_base + td)
+        (-L / n).backward()
+        opt.step()
+        sched.step()
+    with torch.no_grad():
+        Rd, td = se3_exp(xi)
+        R = Rd @ R0
+        t = Rd @ t_base + td
+        L = gmm_loglik(s, logits, means, chol, R, t)
+    # R (scan - c) + t = R scan + (t - R c)
+    return R, t - R @ c, float(L) / n

@@ -920,6 +920,7 @@ int estep4_grid(int64_t n, int k, int num_sms, int64_t* ppc) {
 cudaError_t launch_estep4(const EStep4Launch& a, bool stats, int grid, cudaStream_t s, bool pdl) {
     const size_t smem = (size_t)a.pts_per_cta * 32;
     const void* fn = stats ? (const void*)estep4_kernel<true> : (const void*)estep4_kernel<false>;
+    note_estep_kernel(fn);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};

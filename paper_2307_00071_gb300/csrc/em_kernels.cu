@@ -6,19 +6,30 @@
 // written in the paper) is fed by per-component sufficient statistics.
 //
 // Mapping (component-stationary): one CTA holds ALL K components, spread over
-// its G warps; lane (warp w, lane l) owns NP component pairs in registers.  All
-// lanes walk the CTA's contiguous range of points together, Q_BATCH points at a
-// time.  Pass 1 computes e_nb = 2^(l_nb - cmax) for the lane's components
-// (kept in registers), the per-point sums are combined across lanes (shuffle
+// its G warps; lane (warp w, lane l) owns NP component pairs in registers, and
+// warp w the contiguous block of pairs [w NP 32, (w + 1) NP 32).  All lanes walk
+// the CTA's contiguous range of points together, Q_BATCH points at a time.
+// Pass 1 computes e_nb = 2^(l_nb - cmax) for the lane's components (kept in
+// registers), the per-point sums are combined across lanes (shuffle
 // transpose-reduce) and warps (shared memory), and pass 2 accumulates the
 // per-component statistics S0 = sum r, S1 = sum r d, S2 = sum r d d^T with
 // d = x - mu_old (binary32, per-CTA partials).  Pass 1 processes component
 // pairs with packed FP32 (FFMA2/FADD2); pass 2 uses scalar FP32.  The
 // responsibility matrix is never stored.
+//
+// Pass 2 skips a (point, pair of lanes' components) wherever e is exactly 0
+// for every lane of the warp (ex2.approx.ftz returns +0 below 2^-126, and a
+// zero responsibility adds exactly nothing to any accumulator, so the skip
+// changes no bit).  The fit orders the components along a space-filling curve
+// of their means (order_components_kernel), so a warp's 128 components are
+// close together and most of them are out of reach of any given point.
+#include <cxxabi.h>
 #include <float.h>
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 
 #include "gira_internal.cuh"
 
@@ -32,27 +43,34 @@ constexpr double LN2 = 0.693147180559945309417232121458;
 
 // Log-density in base 2 for a component pair and one point (pairs packed).
 struct PairParams {
-    float2 p[6], b[3], c, nmu[3], w;
+    float2 p[6], c, nmu[3], w;
 };
 
-// P.c holds (cmax - c) >= 0: q' = |y|^2 + (cmax - c) and the logit relative to
-// cmax is -q' (three FFMA2 for the quadratic form, no negated operands).
+// P.c holds (cmax - c) >= 0: q' = |y|^2 + (cmax - c), y = P'(x - mu), and the
+// logit relative to cmax is -q'.  The difference x - mu is taken first: it is
+// exact or nearly so for the points a component reaches, so y carries only a
+// few roundings relative to itself.  (The expanded form P'x + b' with
+// b' = -P'mu would cancel two numbers of size |P'||x| -- a point metres from
+// the origin against a millimetre-thin component: ~10^3 -- and carry the
+// binary32 rounding of b' into every y; measured on the frame, one EM
+// iteration in that form moves weights and covariances 10-20 times further from
+// the binary64 result than this one.)
 __device__ __forceinline__ float2 neg_logit2(const PairParams& P, float2 X0, float2 X1, float2 X2) {
-    const float2 y0 = fma2(P.p[0], X0, P.b[0]);
-    const float2 y1 = fma2(P.p[1], X0, fma2(P.p[2], X1, P.b[1]));
-    const float2 y2 = fma2(P.p[3], X0, fma2(P.p[4], X1, fma2(P.p[5], X2, P.b[2])));
-    return fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, P.c)));
-}
-// The same from d = x - mu (three more operations): P'x + b' cancels two
-// numbers of size |P'| |x| (a point metres from the origin against a
-// centimetre factor) and carries the binary32 rounding of b' as a fixed offset
-// of every y of the component; P'd does not.  Used where the log-likelihood
-// itself is the product (the differentiable path).
-__device__ __forceinline__ float2 neg_logit2_d(const PairParams& P, float2 X0, float2 X1, float2 X2) {
     const float2 d0 = add2(X0, P.nmu[0]), d1 = add2(X1, P.nmu[1]), d2 = add2(X2, P.nmu[2]);
     const float2 y0 = mul2(P.p[0], d0);
     const float2 y1 = fma2(P.p[2], d1, mul2(P.p[1], d0));
     const float2 y2 = fma2(P.p[5], d2, fma2(P.p[4], d1, mul2(P.p[3], d0)));
+    return fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, P.c)));
+}
+
+// The same, also returning the whitened coordinates y = P'(x - mu) it formed
+// (the same operations, so the same bits).
+__device__ __forceinline__ float2 neg_logit2_y(const PairParams& P, float2 X0, float2 X1, float2 X2, float2& y0,
+                                               float2& y1, float2& y2) {
+    const float2 d0 = add2(X0, P.nmu[0]), d1 = add2(X1, P.nmu[1]), d2 = add2(X2, P.nmu[2]);
+    y0 = mul2(P.p[0], d0);
+    y1 = fma2(P.p[2], d1, mul2(P.p[1], d0));
+    y2 = fma2(P.p[5], d2, fma2(P.p[4], d1, mul2(P.p[3], d0)));
     return fma2(y2, y2, fma2(y1, y1, fma2(y0, y0, P.c)));
 }
 
@@ -79,7 +97,7 @@ constexpr int PPC_MAX = 2048;                         // points staged per CTA (
 // CH = 1 (pass A): pass 1 and the per-point sums of the chunk into psum, no
 // log-sum-exp; CH = 2 (pass B): e = 2^(shift_n - q') with (shift_n, 1 / total_n)
 // from pref, pass 2 only -- no cross-lane reduction and no barrier per batch.
-template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, bool DFORM = GRAD, int CH = 0>
+template <int NP, int Q, int MAXT, int MINB, bool STATS, bool GRAD = false, int CH = 0>
 __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_in) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar_tma;
@@ -106,9 +124,9 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         a.ll_partials = a_in.ll_partials + I.ll_off;
         a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
         a.st = a_in.states + u.inst;
-        if (CH != 0) {   // chunks share the points and the state
+        if (CH != 0) {   // chunks share the points and the state; pass A's sums of this chunk
             a.st = a_in.states;
-            if (CH == 1) a.psum = a_in.psum + (size_t)u.inst * I.n;
+            if (a_in.psum) a.psum = a_in.psum + (size_t)u.inst * I.n;
         }
         if (GRAD) {   // per-instance scan gradient rows, pose and pose sums
             a.grad_pts = a_in.grad_pts ? a_in.grad_pts + 3 * I.pt_off : nullptr;
@@ -149,14 +167,13 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
     float cm = -INFINITY, ws = 0.f;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        const int pp = (j * G + warp) * 32 + lane;
+        const int pp = (warp * NP + j) * 32 + lane;
         const float4* src = reinterpret_cast<const float4*>(a.params + (size_t)pp * PAIR_FLOATS);
-        const float4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3], v4 = src[4], v5 = src[5], v6 = src[6];
+        const float4 v0 = src[0], v1 = src[1], v2 = src[2], v4 = src[4], v5 = src[5], v6 = src[6];
         prm[j].p[0] = f2(v0.x, v0.y); prm[j].p[1] = f2(v0.z, v0.w);
         prm[j].p[2] = f2(v1.x, v1.y); prm[j].p[3] = f2(v1.z, v1.w);
         prm[j].p[4] = f2(v2.x, v2.y); prm[j].p[5] = f2(v2.z, v2.w);
-        prm[j].b[0] = f2(v3.x, v3.y); prm[j].b[1] = f2(v3.z, v3.w);
-        prm[j].b[2] = f2(v4.x, v4.y); prm[j].c = f2(v4.z, v4.w);
+        prm[j].c = f2(v4.z, v4.w);
         prm[j].nmu[0] = f2(v5.x, v5.y); prm[j].nmu[1] = f2(v5.z, v5.w);
         prm[j].nmu[2] = f2(v6.x, v6.y);
         cm = fmaxf(cm, fmaxf(prm[j].c.x, prm[j].c.y));
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
             float2 acc = f2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const float2 nq = DFORM ? neg_logit2_d(prm[j], X0, X1, X2) : neg_logit2(prm[j], X0, X1, X2);
+                const float2 nq = neg_logit2(prm[j], X0, X1, X2);
                 const float sh = (CH == 2) ? pr[q].x : 0.f;
                 const float2 e = f2(ex2_approx(sh - nq.x), ex2_approx(sh - nq.y));
                 E[j][q] = e;
@@ -248,15 +265,31 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         float gq[Q][3];   // GRAD: this lane's share of sum_b gamma P'^T P' d, per point
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+            if (GRAD) gq[q][0] = gq[q][1] = gq[q][2] = 0.f;
+            // pairs with a nonzero e for this point on some lane of the warp (warp-uniform)
+            bool live[NP], any = false;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                live[j] = __any_sync(FULL, (E[j][q].x != 0.f) || (E[j][q].y != 0.f));
+                any = any || live[j];
+            }
+            if (!any) continue;
             float2 X0, X1, X2;
             load_pt((q < nvalid) ? lb + q : lb, X0, X1, X2);
             const float R = (CH == 2) ? pr[q].y : __shfl_sync(FULL, r, q * LPQ);
-            if (GRAD) gq[q][0] = gq[q][1] = gq[q][2] = 0.f;
             // scalar FP32: measured faster than the packed form for this
             // accumulate-heavy pattern
             auto acc1 = [&](float e, float m0, float m1, float m2, float (&T)[NSTAT], const float2 (&pp)[6], int h) {
                 const float g = e * R;
-                const float d0 = X0.x + m0, d1 = X1.x + m1, d2 = X2.x + m2;
+                float d0 = X0.x + m0, d1 = X1.x + m1, d2 = X2.x + m2;
+                if (!GRAD) {   // the fit's statistics: whitened coordinates y = P'd, as the tile kernel
+                    const float p0 = h ? pp[0].y : pp[0].x, p1 = h ? pp[1].y : pp[1].x, p2 = h ? pp[2].y : pp[2].x;
+                    const float p3 = h ? pp[3].y : pp[3].x, p4 = h ? pp[4].y : pp[4].x, p5 = h ? pp[5].y : pp[5].x;
+                    const float y0 = p0 * d0, y1 = fmaf(p2, d1, p1 * d0), y2 = fmaf(p5, d2, fmaf(p4, d1, p3 * d0));
+                    d0 = y0;
+                    d1 = y1;
+                    d2 = y2;
+                }
                 if (GRAD) {
                     const float p0 = h ? pp[0].y : pp[0].x, p1 = h ? pp[1].y : pp[1].x, p2 = h ? pp[2].y : pp[2].x;
                     const float p3 = h ? pp[3].y : pp[3].x, p4 = h ? pp[4].y : pp[4].x, p5 = h ? pp[5].y : pp[5].x;
@@ -280,6 +313,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
             };
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
+                if (!live[j]) continue;
                 acc1(E[j][q].x, prm[j].nmu[0].x, prm[j].nmu[1].x, prm[j].nmu[2].x, Sx[j], prm[j].p, 0);
                 acc1(E[j][q].y, prm[j].nmu[0].y, prm[j].nmu[1].y, prm[j].nmu[2].y, Sy[j], prm[j].p, 1);
             }
@@ -314,7 +348,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
                 float mm = -INFINITY;
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    const float2 nq = DFORM ? neg_logit2_d(prm[j], X0, X1, X2) : neg_logit2(prm[j], X0, X1, X2);
+                    const float2 nq = neg_logit2(prm[j], X0, X1, X2);
                     const float2 l = f2(-nq.x, -nq.y);
                     E[j][q] = l;
                     mm = fmaxf(mm, fmaxf(l.x, l.y));
@@ -359,6 +393,18 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
     float2 E[NP][Q];
     float tw[12] = {};   // GRAD owner lanes: sum g x'^T (row-major), sum g
     for (int t = 0; t < nb; ++t) {
+        if (CH == 2 && a.psum) {
+            // pass B: a batch whose every point had an exactly zero sum over this
+            // chunk in pass A (and takes the common reference, shift 0) has
+            // e = 0 for every component of the chunk: nothing to accumulate
+            const int lb = t * Q;
+            bool live = false;
+            if (lane < Q && lane < npts - lb) {
+                const int64_t i = begin + lb + lane;
+                live = (a.psum[i] != 0.f) || (a.pref[i].x != 0.f);
+            }
+            if (!__any_sync(FULL, live)) continue;
+        }
         pass1(t, E);
         if (CH == 2) {
             pass2(t, E, 0.f);
@@ -417,7 +463,7 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
         float* dst = a.partials + (size_t)cta * a.k * NSTAT;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const int b0 = 2 * ((j * G + warp) * 32 + lane);
+            const int b0 = 2 * ((warp * NP + j) * 32 + lane);
             if (b0 < a.k)
 #pragma unroll
                 for (int s = 0; s < NSTAT; ++s) dst[(size_t)b0 * NSTAT + s] = Sx[j][s];
@@ -440,6 +486,294 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
                 if (lane == 0) a.pose_partials[(size_t)cta * 12 + i] = u;
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------ point-stationary E-step
+// The E-step with the roles of the operands the other way round: each lane owns
+// PT_P points in registers (a warp: 32 PT_P consecutive points), and every pair
+// of components is read from shared memory as a broadcast (the CTA's copy of
+// the parameters, staged once by one TMA bulk copy).  Per-point sums stay in
+// their lane: no cross-lane or cross-warp reduction, no barrier.
+//  phase 1  for every pair: both logits at the lane's points, e = 2^-q', the
+//           per-point totals; one warp vote records whether the pair reaches any
+//           point of the warp (some e nonzero: ex2.approx.ftz gives exact zeros);
+//  totals   1 / total per point and the log-likelihood; a point whose total
+//           falls below 2^-100 takes the exact per-point maximum (Eq. logestep's
+//           max-subtraction) and makes every pair live for its warp;
+//  phase 2  for the live pairs only: e again (the same instructions, so the same
+//           bits), the statistics of both components over the warp's points in
+//           whitened coordinates y = P'(x - mu_old) -- S0 = sum r, S1 = sum r y,
+//           S2 = sum r y y^T -- reduced over the warp's lanes and written to the
+//           warp's partials; the warp's live mask tells the finalize which ones.
+// With the components in space-filling-curve order a warp's 128 neighbouring
+// points reach about a sixth of the pairs (the depth frame at K = 512), and the
+// other pairs cost only phase 1.  The statistics are sums of the same terms as
+// the other kernels' in another order.
+constexpr int PT_P = 4;           // points per lane
+constexpr int PT_W = 4;           // warps per CTA
+constexpr int PT_PTS = 32 * PT_P * PT_W;   // points per CTA
+
+// Pairs the kernel reads for k components: ceil(k / 2) rounded up to a multiple
+// of 32 (never beyond the padded parameter block, whose extra slots are padding
+// components with c = -inf).
+__host__ __device__ constexpr int pt_pairs(int k) { return (((k + 1) / 2) + 31) & ~31; }
+__host__ __device__ constexpr size_t pt_smem_bytes(int k) {
+    return (size_t)pt_pairs(k) * PAIR_FLOATS * 4 + (size_t)PT_W * (pt_pairs(k) / 32) * 4;
+}
+
+// Sum of 20 values (10 float2: component 2p in .x, 2p+1 in .y) over the warp's
+// lanes.  On return lane l with (l & 7) < 5 holds value 10 (l >> 4) + 5 ((l >> 3) & 1) + (l & 7):
+// halving exchanges for the first two levels, butterflies for the last three.
+__device__ __forceinline__ float pt_warp_reduce20(const float2 (&S)[NSTAT], int lane, int* vidx) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float w[NSTAT];
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) {
+        const float keep = b4 ? S[i].y : S[i].x, send = b4 ? S[i].x : S[i].y;
+        w[i] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+    float z[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float keep = b3 ? w[5 + i] : w[i], send = b3 ? w[i] : w[5 + i];
+        z[i] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) z[i] += __shfl_xor_sync(FULL, z[i], o);
+    const int i = lane & 7;
+    *vidx = 10 * (b4 ? 1 : 0) + 5 * (b3 ? 1 : 0) + i;
+    return i == 0 ? z[0] : i == 1 ? z[1] : i == 2 ? z[2] : i == 3 ? z[3] : z[4];
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunch a_in) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar_tma;
+    __shared__ int s_skip, s_norm, s_dead;
+    __shared__ double s_ll[PT_W];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int cta = blockIdx.x;
+    EStepLaunch a = a_in;
+    if (a_in.units) {
+        const BatchUnit u = a_in.units[blockIdx.x];
+        const BatchInst I = a_in.insts[u.inst];
+        cta = u.cta;
+        a.pts8 = a_in.pts8 + 2 * I.pt_off;
+        a.n = I.n;
+        a.k = I.k;
+        a.params = a_in.params + I.par_off;
+        a.partials = a_in.partials ? a_in.partials + I.part_off : nullptr;
+        a.masks = a_in.masks ? a_in.masks + I.mask_off : nullptr;
+        a.pt_rows = (int64_t)I.ctas * PT_W;
+        a.ll_partials = a_in.ll_partials ? a_in.ll_partials + I.ll_off : nullptr;
+        a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
+        a.st = a_in.states + u.inst;
+    }
+    // pairs evaluated: ceil(k / 2) rounded up to even (within the padded block, whose
+    // extra slots are padding components with c = -inf); mask words for pt_pairs(k)
+    const int npairs = ((((a.k + 1) >> 1) + 1) & ~1);
+    const int nwords = pt_pairs(a.k) / 32;
+    const float4* spar = reinterpret_cast<const float4*>(dsm);   // [npairs][8]
+    uint32_t* smask = reinterpret_cast<uint32_t*>(dsm + (size_t)pt_pairs(a.k) * PAIR_FLOATS * 4) + warp * nwords;
+    // the lane's points (never written inside a fit: loaded before the wait); a slot
+    // beyond n holds a point 1e18 m away, where every q' is +inf and e exactly 0
+    const int64_t base = (int64_t)cta * PT_PTS + (int64_t)warp * 32 * PT_P + lane;
+    float2 X[PT_P][3];
+    bool valid[PT_P];
+#pragma unroll
+    for (int p = 0; p < PT_P; ++p) {
+        const int64_t i = base + 32 * p;
+        valid[p] = i < a.n;
+        if (valid[p]) {
+            const float4 xy = a.pts8[2 * i], zz = a.pts8[2 * i + 1];
+            X[p][0] = f2(xy.x, xy.y);
+            X[p][1] = f2(xy.z, xy.w);
+            X[p][2] = f2(zz.x, zz.y);
+        } else {
+            X[p][0] = X[p][1] = X[p][2] = dup(1e18f);
+        }
+    }
+    pdl_wait();   // the parameters and the state written by the previous kernel
+    if (threadIdx.x == 0) {
+        s_skip = (a.iter > a.st->stop_after) || (a.st->error != 0);
+        s_norm = a.st->w_raw;
+        s_dead = 0;
+        if (!s_skip) {
+            mbar_init(&bar_tma, 1);
+            mbar_fence_init();
+            const uint32_t bytes = (uint32_t)npairs * PAIR_FLOATS * 4u;
+            mbar_expect_tx(&bar_tma, bytes);
+            tma_load_1d(reinterpret_cast<void*>(dsm), a.params, bytes, &bar_tma);
+            if (!mbar_wait_bounded(&bar_tma, 0u, MBAR_POLL_LIMIT)) {
+                s_dead = 1;
+                set_error(a.st, GIRA_ERR_TIMEOUT);
+                mbar_wait_bounded(&bar_tma, 0u, MBAR_POLL_LIMIT);   // let the copy land
+            }
+        }
+    }
+    __syncthreads();
+    if (s_skip || s_dead) return;
+    pdl_allow_next();
+
+    // reference cmax = max_b c_b and the weight normaliser (every warp, same order)
+    float cm = -INFINITY, wsv = 0.f;
+    for (int pp = lane; pp < npairs; pp += 32) {
+        const float4 v4 = spar[pp * 8 + 4], v6 = spar[pp * 8 + 6];
+        cm = fmaxf(cm, fmaxf(v4.z, v4.w));
+        wsv += v6.z + v6.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cm = fmaxf(cm, __shfl_xor_sync(FULL, cm, o));
+        wsv += __shfl_xor_sync(FULL, wsv, o);
+    }
+    const float cmax = cm;
+    const float ref0 = s_norm ? cmax - __log2f(wsv) : cmax;
+
+    auto load_pair = [&](int pp, PairParams& P) {
+        const float4* q = spar + (size_t)pp * 8;
+        const float4 v0 = q[0], v1 = q[1], v2 = q[2], v4 = q[4], v5 = q[5], v6 = q[6];
+        P.p[0] = f2(v0.x, v0.y); P.p[1] = f2(v0.z, v0.w);
+        P.p[2] = f2(v1.x, v1.y); P.p[3] = f2(v1.z, v1.w);
+        P.p[4] = f2(v2.x, v2.y); P.p[5] = f2(v2.z, v2.w);
+        P.c = f2(cmax - v4.z, cmax - v4.w);
+        P.nmu[0] = f2(v5.x, v5.y); P.nmu[1] = f2(v5.z, v5.w);
+        P.nmu[2] = f2(v6.x, v6.y);
+    };
+
+    // ---- phase 1: every pair, the lane's points (two pairs per step)
+    if (STATS && lane < nwords) smask[lane] = 0u;
+    __syncwarp();
+    float2 tot[PT_P];
+#pragma unroll
+    for (int p = 0; p < PT_P; ++p) tot[p] = f2(0.f, 0.f);
+    uint32_t word = 0u;
+    for (int pp = 0; pp < npairs; pp += 2) {
+        PairParams P0, P1;
+        load_pair(pp, P0);
+        load_pair(pp + 1, P1);
+        uint32_t nz0 = 0u, nz1 = 0u;   // OR of the bits of e: nonzero iff some e is
+#pragma unroll
+        for (int p = 0; p < PT_P; ++p) {
+            const float2 nq0 = neg_logit2(P0, X[p][0], X[p][1], X[p][2]);
+            const float2 nq1 = neg_logit2(P1, X[p][0], X[p][1], X[p][2]);
+            const float2 e0 = f2(ex2_approx(-nq0.x), ex2_approx(-nq0.y));
+            const float2 e1 = f2(ex2_approx(-nq1.x), ex2_approx(-nq1.y));
+            tot[p] = add2(tot[p], add2(e0, e1));
+            if (STATS) {
+                nz0 |= __float_as_uint(e0.x) | __float_as_uint(e0.y);
+                nz1 |= __float_as_uint(e1.x) | __float_as_uint(e1.y);
+            }
+        }
+        if (STATS) {
+            const uint32_t v0 = __ballot_sync(FULL, nz0 != 0u) ? 1u : 0u;
+            const uint32_t v1 = __ballot_sync(FULL, nz1 != 0u) ? 2u : 0u;
+            word |= (v0 | v1) << (pp & 31);
+            if ((pp & 31) == 30 || pp + 2 >= npairs) {
+                if (lane == 0) smask[pp >> 5] = word;
+                word = 0u;
+            }
+        }
+    }
+
+    // ---- totals, log-likelihood, rare points
+    float2 pr[PT_P];   // (shift, 1 / total) per point
+    double ll = 0.0;
+    bool rare_any = false;
+#pragma unroll
+    for (int p = 0; p < PT_P; ++p) {
+        pr[p] = f2(0.f, 0.f);
+        if (!valid[p]) continue;
+        float t = tot[p].x + tot[p].y;
+        float sh = 0.f;
+        if (!(t >= 0x1p-100f)) {
+            // every component is > 100 binades below cmax at this point: the exact maximum
+            rare_any = true;
+            float mx = -INFINITY;
+            for (int pp = 0; pp < npairs; ++pp) {
+                PairParams P;
+                load_pair(pp, P);
+                const float2 nq = neg_logit2(P, X[p][0], X[p][1], X[p][2]);
+                mx = fmaxf(mx, fmaxf(-nq.x, -nq.y));
+            }
+            if (!(mx > -INFINITY)) {
+                set_error(a.st, GIRA_ERR_NUMERIC);
+                continue;
+            }
+            float sm = 0.f;
+            for (int pp = 0; pp < npairs; ++pp) {
+                PairParams P;
+                load_pair(pp, P);
+                const float2 nq = neg_logit2(P, X[p][0], X[p][1], X[p][2]);
+                sm += ex2_approx(-nq.x - mx) + ex2_approx(-nq.y - mx);
+            }
+            t = sm;
+            sh = -mx;
+        }
+        pr[p] = f2(sh, __frcp_rn(t));
+        const float lse2 = lg2_approx(t) + ref0 - sh;   // log2 sum_b pi_b N(x|b)
+        ll += (double)lse2;
+        if (!STATS && a.per_point) a.per_point[base + 32 * p] = lse2 * LN2F;
+    }
+
+    if (STATS) {
+        __syncwarp();
+        if (__any_sync(FULL, rare_any) && lane < nwords) {   // every evaluated pair, this warp
+            const int lo = lane * 32;
+            smask[lane] = (lo + 32 <= npairs) ? 0xffffffffu : (lo < npairs) ? ((1u << (npairs - lo)) - 1u) : 0u;
+        }
+        __syncwarp();
+        // ---- phase 2: the live pairs; partials [k * NSTAT][rows], masks [nwords][rows]
+        const int64_t gw = (int64_t)cta * PT_W + warp;
+        const int64_t rows = a.pt_rows;
+        for (int wd = 0; wd < nwords; ++wd) {
+            uint32_t m = smask[wd];
+            if (lane == 0) a.masks[wd * rows + gw] = m;
+            while (m) {
+                const int pp = wd * 32 + __ffs(m) - 1;
+                m &= m - 1u;
+                PairParams P;
+                load_pair(pp, P);
+                float2 S[NSTAT];
+#pragma unroll
+                for (int s2 = 0; s2 < NSTAT; ++s2) S[s2] = f2(0.f, 0.f);
+#pragma unroll
+                for (int p = 0; p < PT_P; ++p) {
+                    float2 y0, y1, y2;
+                    const float2 nq = neg_logit2_y(P, X[p][0], X[p][1], X[p][2], y0, y1, y2);
+                    const float2 e = f2(ex2_approx(pr[p].x - nq.x), ex2_approx(pr[p].x - nq.y));
+                    const float2 g = mul2(e, dup(pr[p].y));   // pr = 0 for invalid points: g = 0
+                    const float2 g0 = mul2(g, y0), g1 = mul2(g, y1), g2 = mul2(g, y2);
+                    S[0] = add2(S[0], g);
+                    S[1] = add2(S[1], g0);
+                    S[2] = add2(S[2], g1);
+                    S[3] = add2(S[3], g2);
+                    S[4] = fma2(g0, y0, S[4]);
+                    S[5] = fma2(g0, y1, S[5]);
+                    S[6] = fma2(g0, y2, S[6]);
+                    S[7] = fma2(g1, y1, S[7]);
+                    S[8] = fma2(g1, y2, S[8]);
+                    S[9] = fma2(g2, y2, S[9]);
+                }
+                int v;
+                const float r = pt_warp_reduce20(S, lane, &v);
+                const int b = 2 * pp + (v >= NSTAT ? 1 : 0);
+                if ((lane & 7) < 5 && b < a.k) a.partials[((size_t)b * NSTAT + (v % NSTAT)) * rows + gw] = r;
+            }
+        }
+    }
+    // the CTA's log-likelihood: lanes, then warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(FULL, ll, o);
+    if (lane == 0) s_ll[warp] = ll;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = s_ll[0];
+        for (int w = 1; w < PT_W; ++w) v += s_ll[w];
+        a.ll_partials[cta] = v * LN2;
     }
 }
 
@@ -469,26 +803,27 @@ Shape shape_for(int k) {
     return {2, g, 32 * g};
 }
 
+// A kernel of the launch policy (the batch-synchronous estep_kernel).
+struct KSel {
+    const void* fn;
+};
+
 template <bool STATS>
-const void* kernel_for(const Shape& sh) {
-    if (sh.np == 1) return (const void*)estep_kernel<1, QB, 32, 16, STATS>;
-    if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 3, STATS>;
-    return (const void*)estep_kernel<2, QB, 256, 1, STATS>;
+KSel kernel_for(const Shape& sh) {
+    if (sh.np == 1) return {(const void*)estep_kernel<1, QB, 32, 16, STATS>};
+    if (sh.g <= 4) return {(const void*)estep_kernel<2, QB, 128, 3, STATS>};
+    return {(const void*)estep_kernel<2, QB, 256, 1, STATS>};
 }
-// Differentiable path: the adjoint kernel, or (forward only) the log-likelihood
-// with the same d-form logits.
-const void* grad_kernel_for(const Shape& sh, bool stats) {
-    if (!stats) {
-        if (sh.np == 1) return (const void*)estep_kernel<1, QB, 32, 16, false, false, true>;
-        if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 3, false, false, true>;
-        return (const void*)estep_kernel<2, QB, 256, 1, false, false, true>;
-    }
-    if (sh.np == 1) return (const void*)estep_kernel<1, QB, 32, 16, true, true>;
-    if (sh.g <= 4) return (const void*)estep_kernel<2, QB, 128, 2, true, true>;
-    return (const void*)estep_kernel<2, QB, 256, 1, true, true>;
+// Differentiable path: the adjoint kernel, or (forward only) the log-likelihood.
+KSel grad_kernel_for(const Shape& sh, bool stats) {
+    if (!stats) return kernel_for<false>(sh);
+    if (sh.np == 1) return {(const void*)estep_kernel<1, QB, 32, 16, true, true>};
+    if (sh.g <= 4) return {(const void*)estep_kernel<2, QB, 128, 2, true, true>};
+    return {(const void*)estep_kernel<2, QB, 256, 1, true, true>};
 }
 
 size_t estep_smem(int64_t ppc) { return (size_t)ppc * 32; }
+size_t smem_of(const KSel&, const Shape&, int64_t ppc) { return estep_smem(ppc); }
 
 }  // namespace
 
@@ -501,12 +836,14 @@ int params_pairs_padded(int k) {
 // staged in shared memory, at most PPC_MAX per CTA).
 int estep_grid(int64_t n, int k, bool stats, int num_sms, int64_t* pts_per_cta, bool grad) {
     const Shape sh = shape_for(k);
-    const void* fn = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const KSel ks = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = ks.fn;
     int occ = 1;
     // occupancy with the largest staging buffer the launch could use
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estep_smem(PPC_MAX));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, estep_smem(PPC_MAX / 4)) != cudaSuccess ||
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(ks, sh, PPC_MAX));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, smem_of(ks, sh, PPC_MAX / 4)) !=
+            cudaSuccess ||
         occ < 1) {
         cudaGetLastError();
         occ = 1;
@@ -532,11 +869,13 @@ int estep_ppc_max() { return PPC_MAX; }
 
 int estep_occupancy(int k, bool stats, int64_t ppc) {
     const Shape sh = shape_for(k);
-    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const KSel ks = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = ks.fn;
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estep_smem(PPC_MAX));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(ks, sh, PPC_MAX));
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, estep_smem(ppc)) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, smem_of(ks, sh, ppc)) != cudaSuccess ||
+        occ < 1) {
         cudaGetLastError();
         occ = 1;
     }
@@ -547,8 +886,9 @@ cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int
                                cudaStream_t s) {
     const Shape sh = shape_for(k_class);
     void* args[] = {(void*)&a};
-    const void* fn = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
-    const size_t smem = estep_smem(ppc_class);
+    const KSel ks = stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = ks.fn;
+    const size_t smem = smem_of(ks, sh, ppc_class);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
@@ -557,8 +897,9 @@ cudaError_t launch_estep_units(const EStepLaunch& a, bool stats, int nunits, int
 cudaError_t launch_estep_grad_units(const EStepLaunch& a, int nunits, int k_class, int64_t ppc_class, cudaStream_t s) {
     const Shape sh = shape_for(k_class);
     void* args[] = {(void*)&a};
-    const void* fn = grad_kernel_for(sh, true);
-    const size_t smem = estep_smem(ppc_class);
+    const KSel ks = grad_kernel_for(sh, true);
+    const void* fn = ks.fn;
+    const size_t smem = smem_of(ks, sh, ppc_class);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(fn, dim3(nunits), dim3(sh.threads), args, smem, s);
@@ -566,11 +907,13 @@ cudaError_t launch_estep_grad_units(const EStepLaunch& a, int nunits, int k_clas
 
 int estep_grad_occupancy(int k, int64_t ppc) {
     const Shape sh = shape_for(k);
-    const void* fn = grad_kernel_for(sh, true);
+    const KSel ks = grad_kernel_for(sh, true);
+    const void* fn = ks.fn;
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)estep_smem(PPC_MAX));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(ks, sh, PPC_MAX));
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, estep_smem(ppc)) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.threads, smem_of(ks, sh, ppc)) != cudaSuccess ||
+        occ < 1) {
         cudaGetLastError();
         occ = 1;
     }
@@ -585,19 +928,80 @@ int64_t chunk_param_floats() { return (int64_t)params_pairs_padded(KCHUNK) * PAI
 
 cudaError_t launch_estep_chunks(const EStepLaunch& a, int pass, int nunits, int64_t ppc, cudaStream_t s) {
     void* args[] = {(void*)&a};
-    const void* fn = (pass == 1) ? (const void*)estep_kernel<2, QB, 128, 3, false, false, false, 1>
-                                 : (const void*)estep_kernel<2, QB, 128, 3, true, false, false, 2>;
+    const void* fn = (pass == 1) ? (const void*)estep_kernel<2, QB, 128, 3, false, false, 1>
+                                 : (const void*)estep_kernel<2, QB, 128, 3, true, false, 2>;
     const size_t smem = estep_smem(ppc);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(fn, dim3(nunits), dim3(128), args, smem, s);
 }
 
+namespace {
+thread_local std::string t_estep_name;
+thread_local const void* t_estep_fn = nullptr;
+}  // namespace
+
+// The launched function's name as the runtime reports it, demangled, without
+// its namespaces and parameter list.
+void note_estep_kernel(const void* fn) {
+    if (fn == t_estep_fn) return;
+    t_estep_fn = fn;
+    const char* raw = nullptr;
+    if (cudaFuncGetName(&raw, fn) != cudaSuccess || !raw) {
+        cudaGetLastError();
+        t_estep_name = "estep_kernel";
+        return;
+    }
+    int ok = -1;
+    char* dem = abi::__cxa_demangle(raw, nullptr, nullptr, &ok);
+    std::string name = (ok == 0 && dem) ? dem : raw;
+    std::free(dem);
+    size_t at = name.find("estep_kernel<");
+    if (at == std::string::npos) at = name.find("estep_pt_kernel<");
+    if (at == std::string::npos) at = name.find("estep4_kernel<");
+    if (at != std::string::npos) name = name.substr(at);
+    const size_t par = name.rfind(">(");
+    if (par != std::string::npos) name = name.substr(0, par + 1);
+    t_estep_name = name;
+}
+
+const char* last_estep_kernel() { return t_estep_name.c_str(); }
+
+int estep_pt_grid(int64_t n) { return (int)std::max<int64_t>(1, (n + PT_PTS - 1) / PT_PTS); }
+int estep_pt_rows(int grid) { return grid * PT_W; }
+int estep_pt_mask_words(int k) { return pt_pairs(k) / 32; }
+
+cudaError_t launch_estep_pt(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool pdl) {
+    void* args[] = {(void*)&a};
+    const void* fn = stats ? (const void*)estep_pt_kernel<true> : (const void*)estep_pt_kernel<false>;
+    note_estep_kernel(fn);
+    const size_t smem = pt_smem_bytes(a.k);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    PdlConfig c(dim3(grid), dim3(32 * PT_W), smem, s, pdl);
+    return cudaLaunchKernelExC(&c.cfg, fn, args);
+}
+
+cudaError_t launch_estep_pt_units(const EStepLaunch& a, bool stats, int nunits, int kmax, cudaStream_t s) {
+    void* args[] = {(void*)&a};
+    const void* fn = stats ? (const void*)estep_pt_kernel<true> : (const void*)estep_pt_kernel<false>;
+    note_estep_kernel(fn);
+    const size_t smem = pt_smem_bytes(kmax);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(nunits), dim3(32 * PT_W), args, smem, s);
+}
+
+int estep_pt_points() { return PT_PTS; }
+int estep_pt_warps() { return PT_W; }
+
 cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad, bool pdl) {
     const Shape sh = shape_for(a.k);
     void* args[] = {(void*)&a};
-    const void* fn = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
-    const size_t smem = estep_smem(a.pts_per_cta);
+    const KSel ks = grad ? grad_kernel_for(sh, stats) : stats ? kernel_for<true>(sh) : kernel_for<false>(sh);
+    const void* fn = ks.fn;
+    note_estep_kernel(fn);
+    const size_t smem = smem_of(ks, sh, a.pts_per_cta);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     PdlConfig c(dim3(grid), dim3(sh.threads), smem, s, pdl);
@@ -761,12 +1165,12 @@ __global__ void chunk_exact_kernel(const float4* __restrict__ pts8, const float*
         const int64_t i = flags[f];
         const float4 xy = pts8[2 * i], zz = pts8[2 * i + 1];
         const float x0 = xy.x, x1 = xy.z, x2 = zz.x;
-        auto nlog = [&](int b) {   // q' = |P'x + b'|^2 + (cmax - c_b), as the E-step forms it
+        auto nlog = [&](int b) {   // q' = |P'(x - mu)|^2 + (cmax - c_b), as the E-step forms it
             const float* p = chunk_slot(params, b);
-            const float y0 = fmaf(p[2 * (SLOT_P + 0)], x0, p[2 * (SLOT_B + 0)]);
-            const float y1 = fmaf(p[2 * (SLOT_P + 1)], x0, fmaf(p[2 * (SLOT_P + 2)], x1, p[2 * (SLOT_B + 1)]));
-            const float y2 = fmaf(p[2 * (SLOT_P + 3)], x0,
-                                  fmaf(p[2 * (SLOT_P + 4)], x1, fmaf(p[2 * (SLOT_P + 5)], x2, p[2 * (SLOT_B + 2)])));
+            const float d0 = x0 + p[2 * (SLOT_NMU + 0)], d1 = x1 + p[2 * (SLOT_NMU + 1)], d2 = x2 + p[2 * (SLOT_NMU + 2)];
+            const float y0 = p[2 * (SLOT_P + 0)] * d0;
+            const float y1 = fmaf(p[2 * (SLOT_P + 2)], d1, p[2 * (SLOT_P + 1)] * d0);
+            const float y2 = fmaf(p[2 * (SLOT_P + 5)], d2, fmaf(p[2 * (SLOT_P + 4)], d1, p[2 * (SLOT_P + 3)] * d0));
             return fmaf(y2, y2, fmaf(y1, y1, fmaf(y0, y0, cmax - p[2 * SLOT_C])));
         };
         float mx = -INFINITY;
@@ -839,12 +1243,16 @@ namespace {
 constexpr int FIN_CPB = 2;          // components per block: spreads the binary64 work over SMs
 constexpr int FIN_SPLIT = 16;       // the CTA partials of one output are summed in 16 fixed slices
 constexpr int FIN_THREADS = FIN_CPB * NSTAT * FIN_SPLIT;   // 320
+constexpr int ORDER_THREADS = 1024;   // order_components_kernel: one block
+constexpr int ORDER_MAX_K = 8192;     // keys in dynamic shared memory (64 KB)
 
 // From (w, mu, Sigma) in binary64 to the E-step parameters of component b:
 // Cholesky Sigma = L L^T (closed form 3x3), P = L^{-1}, scaled to base 2.
 // Returns false (and flags GIRA_ERR_NOT_PD) if a pivot is not positive.
+// report: the caller's index of the component (differs from b when the fit
+// holds its components in another order).
 __device__ bool build_component(int b, double w, const double mu[3], const double c[6], float* params,
-                                float4* shift4, double* model64, DeviceState* st) {
+                                float4* shift4, double* model64, DeviceState* st, int report) {
     // c = (00, 01, 02, 11, 12, 22)
     const double a00 = c[0];
     bool pd = a00 > 0.0;
@@ -860,7 +1268,7 @@ __device__ bool build_component(int b, double w, const double mu[3], const doubl
     pd = pd && a22 > 0.0;
     const double L22 = pd ? sqrt(a22) : 1.0;
     if (!pd) {
-        atomicMin(&st->bad_component, b);
+        atomicMin(&st->bad_component, report);
         set_error(st, GIRA_ERR_NOT_PD);
         return false;
     }
@@ -921,11 +1329,49 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
     }
 }
 
-// M-step from the shifted statistics (d = x - s_b):
-//   N_b = S0 + 10 eps, mu = (S0 s + S1) / N_b, delta = mu - s,
-//   sum r (x-mu)(x-mu)^T = S2 - delta S1^T - S1 delta^T + S0 delta delta^T,
-//   Sigma = that / N_b + reg I.  The weight N_b is normalised by sum_a N_a
-//   where it is used (E-step reference, model output).
+// The same for per-warp partials of the point-stationary E-step ([k * NSTAT][rows],
+// live masks [nwords][rows]): only the rows whose warp's mask has the pair's bit
+// are read (the others were not written); fixed slices of warps, eight loads in
+// flight per thread, binary64 in warp order, slices summed in order.
+__device__ void reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
+                                       int b0, int nout, double (*part)[FIN_CPB * NSTAT], double* S) {
+    const int t = threadIdx.x;
+    const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
+    if (o < nout) {
+        const int b = b0 + o / NSTAT;
+        const uint32_t* mrow = masks + (size_t)((b >> 1) >> 5) * rows;
+        const uint32_t bit = 1u << ((b >> 1) & 31);
+        const float* src = partials + ((size_t)b0 * NSTAT + o) * rows;
+        const int w0 = q * rows / FIN_SPLIT, w1 = (q + 1) * rows / FIN_SPLIT;
+        double acc = 0.0;
+        for (int w = w0; w < w1; w += 8) {
+            uint32_t mk[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mk[u] = (w + u < w1) ? __ldg(mrow + w + u) : 0u;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (mk[u] & bit) ? __ldcg(src + w + u) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += (double)v[u];
+        }
+        part[q][o] = acc;
+    }
+    __syncthreads();
+    if (t < nout) {
+        double v = 0.0;
+        for (int q2 = 0; q2 < FIN_SPLIT; ++q2) v += part[q2][t];
+        S[t] = v;
+    }
+}
+
+// M-step (the standard full-covariance update) from shifted statistics:
+//   N_b = S0 + 10 eps; with v = y = P'(x - s_b) (E-step partials, whitened) or
+//   v = d = x - s_b (one-hot KInit statistics), vbar = S1 / N_b and
+//   sum r (v - vbar)(v - vbar)^T = S2 - vbar S1^T - S1 vbar^T + S0 vbar vbar^T;
+//   mu = s + vbar (d) or s + P'^-1 vbar (y), and Sigma the centred sum / N_b,
+//   mapped back by P'^-1 (.) P'^-T in the whitened case, plus reg I.  The
+//   weight N_b is normalised by sum_a N_a where it is used (E-step reference,
+//   model output).
 struct FinArgs {
     const float* partials;     // [grid][k][NSTAT], or nullptr (then stats64)
     int grid;
@@ -942,6 +1388,11 @@ struct FinArgs {
     int iter, em;
     int ll_count;   // log-likelihood partials to sum (grid when 0)
     int do_ll;      // this launch's block 0 does the log-likelihood / convergence step
+    const int* perm;   // slot b holds the caller's component perm[b] (nullptr: b)
+    // point-stationary E-step: partials per warp ([grid warps][k][NSTAT]), a row
+    // valid only where the warp's live mask ([grid][nwords]) has the pair's bit
+    const uint32_t* masks;
+    int nwords;
 };
 
 // Components blk * FIN_CPB .. of one fit; block index blk == 0 also does the
@@ -957,7 +1408,9 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
     const int b0 = blk * FIN_CPB;
     const int nb = min(FIN_CPB, f.k - b0);
     const int nout = nb * NSTAT;
-    if (f.partials) {
+    if (f.partials && f.masks) {
+        reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, part, S);
+    } else if (f.partials) {
         reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
     } else if (t < nout) {
         S[t] = f.stats64[(size_t)b0 * NSTAT + t];
@@ -971,20 +1424,56 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
         const double s0 = Sb[0];
         const double nbw = s0 + 10.0 * DBL_EPSILON;
         const double inv = 1.0 / nbw;
-        double mu[3], dl[3];
-        for (int i = 0; i < 3; ++i) {
-            mu[i] = (s0 * s[i] + Sb[1 + i]) * inv;
-            dl[i] = mu[i] - s[i];
-        }
         // S2 index: 00->4, 01->5, 02->6, 11->7, 12->8, 22->9
         const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-        double c[6];
-        for (int u = 0; u < 6; ++u) {
-            const int i = ij[u][0], j = ij[u][1];
-            const double v = Sb[4 + u] - dl[i] * Sb[1 + j] - Sb[1 + i] * dl[j] + s0 * dl[i] * dl[j];
-            c[u] = v * inv + ((i == j) ? f.reg : 0.0);
+        double mu[3], c[6];
+        if (f.partials) {
+            // E-step statistics: S1 = sum r y, S2 = sum r y y^T in the whitened
+            // coordinates y = P'(x - s) of the parameters the E-step used (P' the
+            // binary32 lower triangle alpha L^-1 in params, s = shift4).  With
+            // ybar = S1 / N_b and C = sum r (y - ybar)(y - ybar)^T / N_b:
+            // mu = s + P'^-1 ybar, Sigma = P'^-1 C P'^-T + reg I.  Every direction
+            // of a thin component keeps binary32 relative precision in y.
+            const float* pp = f.params + (size_t)(b >> 1) * PAIR_FLOATS + (b & 1);
+            const double q00 = pp[2 * (SLOT_P + 0)], q10 = pp[2 * (SLOT_P + 1)], q11 = pp[2 * (SLOT_P + 2)];
+            const double q20 = pp[2 * (SLOT_P + 3)], q21 = pp[2 * (SLOT_P + 4)], q22 = pp[2 * (SLOT_P + 5)];
+            // M = P'^-1 (lower triangular, forward substitution)
+            const double m00 = 1.0 / q00, m11 = 1.0 / q11, m22 = 1.0 / q22;
+            const double m10 = -q10 * m00 * m11;
+            const double m21 = -q21 * m11 * m22;
+            const double m20 = -(q20 * m00 + q21 * m10) * m22;
+            const double M[3][3] = {{m00, 0.0, 0.0}, {m10, m11, 0.0}, {m20, m21, m22}};
+            double yb[3];
+            for (int i = 0; i < 3; ++i) yb[i] = Sb[1 + i] * inv;
+            double Cy[3][3];
+            for (int u = 0; u < 6; ++u) {
+                const int i = ij[u][0], j = ij[u][1];
+                const double v = (Sb[4 + u] - yb[i] * Sb[1 + j] - Sb[1 + i] * yb[j] + s0 * yb[i] * yb[j]) * inv;
+                Cy[i][j] = Cy[j][i] = v;
+            }
+            for (int i = 0; i < 3; ++i) mu[i] = s[i] + M[i][0] * yb[0] + M[i][1] * yb[1] + M[i][2] * yb[2];
+            double MC[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) MC[i][j] = M[i][0] * Cy[0][j] + M[i][1] * Cy[1][j] + M[i][2] * Cy[2][j];
+            for (int u = 0; u < 6; ++u) {
+                const int i = ij[u][0], j = ij[u][1];
+                const double v = MC[i][0] * M[j][0] + MC[i][1] * M[j][1] + MC[i][2] * M[j][2];
+                c[u] = v + ((i == j) ? f.reg : 0.0);
+            }
+        } else {
+            // one-hot statistics about the centres (KInit): S1, S2 of d = x - s
+            double dl[3];
+            for (int i = 0; i < 3; ++i) {
+                mu[i] = (s0 * s[i] + Sb[1 + i]) * inv;
+                dl[i] = mu[i] - s[i];
+            }
+            for (int u = 0; u < 6; ++u) {
+                const int i = ij[u][0], j = ij[u][1];
+                const double v = Sb[4 + u] - dl[i] * Sb[1 + j] - Sb[1 + i] * dl[j] + s0 * dl[i] * dl[j];
+                c[u] = v * inv + ((i == j) ? f.reg : 0.0);
+            }
         }
-        build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st);
+        build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st, f.perm ? f.perm[b] : b);
         if (b == 0) f.st->w_raw = 1;
     }
     if (f.em && f.do_ll && blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
@@ -1033,12 +1522,19 @@ __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_batched_kernel(co
         f.n = I.n;
         f.model64 = base.model64 + (size_t)I.comp_off * MODEL;
         f.params = base.params + I.par_off;
+        f.perm = base.perm ? base.perm + I.comp_off : nullptr;
         f.st = states;
         f.do_ll = (bi.x == 0);
         reduce_finalize_body(f, bi.y);
         return;
     }
     f.llp = base.llp ? base.llp + I.ll_off : nullptr;
+    f.perm = base.perm ? base.perm + I.comp_off : nullptr;
+    if (base.masks) {   // point-stationary E-step: per-warp rows, live masks, one ll slot per CTA
+        f.masks = base.masks + I.mask_off;
+        f.grid = I.ctas * PT_W;
+        f.ll_count = I.ctas;
+    }
     f.stats64 = base.stats64 ? base.stats64 + (size_t)I.comp_off * NSTAT : nullptr;
     f.shift4 = base.shift4 + I.comp_off;
     f.k = I.k;
@@ -1063,7 +1559,7 @@ __global__ void params_from_model_kernel(const float* __restrict__ w, const floa
     for (int i = 0; i < 9; ++i) fin = fin && isfinite(S[i]);
     if (!fin) { set_error(st, GIRA_ERR_NONFINITE_INPUT); return; }
     if (!(pi > 0.0)) { set_error(st, GIRA_ERR_INVALID_ARG); return; }
-    build_component(b, pi, m, c, params, shift4, model64, st);
+    build_component(b, pi, m, c, params, shift4, model64, st, b);
 }
 
 // ------------------------------------------------------------------ batched helpers
@@ -1086,11 +1582,13 @@ __global__ void params_from_model_batched_kernel(const float* __restrict__ w, co
     for (int q = 0; q < 9; ++q) fin = fin && isfinite(S[q]);
     if (!fin) { set_error(st, GIRA_ERR_NONFINITE_INPUT); return; }
     if (!(pi > 0.0)) { set_error(st, GIRA_ERR_INVALID_ARG); return; }
-    build_component(b, pi, m, c, params + I.par_off, shift4 + I.comp_off, model64 + (size_t)I.comp_off * MODEL, st);
+    build_component(b, pi, m, c, params + I.par_off, shift4 + I.comp_off, model64 + (size_t)I.comp_off * MODEL, st,
+                    b);
 }
 
 __global__ void model_out_batched_kernel(const double* __restrict__ model64, const BatchInst* __restrict__ insts,
-                                         float* w, float* mu, float* cov, const DeviceState* states) {
+                                         float* w, float* mu, float* cov, const DeviceState* states,
+                                         const int* __restrict__ perm) {
     __shared__ double s_part[2];
     const BatchInst I = insts[blockIdx.x];
     const DeviceState* st = states + blockIdx.x;
@@ -1103,9 +1601,9 @@ __global__ void model_out_batched_kernel(const double* __restrict__ model64, con
     __syncthreads();
     const double nsum = s_part[0] + s_part[1];
     if (st->error) return;
-    for (int b = threadIdx.x; b < I.k; b += blockDim.x) {
-        const double* m = M + (size_t)b * MODEL;
-        const size_t g = (size_t)I.comp_off + b;
+    for (int sl = threadIdx.x; sl < I.k; sl += blockDim.x) {   // slot; the caller's index is perm[slot]
+        const double* m = M + (size_t)sl * MODEL;
+        const size_t g = (size_t)I.comp_off + (perm ? perm[I.comp_off + sl] : sl);
         w[g] = (float)(st->w_raw ? m[0] / nsum : m[0]);
         for (int q = 0; q < 3; ++q) mu[3 * g + q] = (float)m[1 + q];
         const int idx[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
@@ -1114,7 +1612,7 @@ __global__ void model_out_batched_kernel(const double* __restrict__ model64, con
 }
 
 __global__ void model_out_kernel(const double* __restrict__ model64, int k, float* w, float* mu, float* cov,
-                                 const DeviceState* st) {
+                                 const DeviceState* st, const int* __restrict__ perm) {
     __shared__ double s_part[2];
     // after an M-step the stored weights are N_b: pi_b = N_b / sum_a N_a (fixed order)
     double part = 0.0;
@@ -1124,13 +1622,117 @@ __global__ void model_out_kernel(const double* __restrict__ model64, int k, floa
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
     __syncthreads();
     const double nsum = s_part[0] + s_part[1];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= k) return;
-    const double* m = model64 + (size_t)b * MODEL;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;   // slot; the caller's index is perm[s]
+    if (s >= k) return;
+    const int b = perm ? perm[s] : s;
+    const double* m = model64 + (size_t)s * MODEL;
     w[b] = (float)(st->w_raw ? m[0] / nsum : m[0]);
-    for (int i = 0; i < 3; ++i) mu[3 * b + i] = (float)m[1 + i];
+    for (int i = 0; i < 3; ++i) mu[3 * (size_t)b + i] = (float)m[1 + i];
     const int idx[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
     for (int i = 0; i < 9; ++i) cov[9 * (size_t)b + i] = (float)m[4 + idx[i]];
+}
+
+// Components in the order of a space-filling curve of their means: the Morton
+// code (10 bits per axis over the means' bounding box, binary64) with the index
+// as the low bits, sorted by one block (bitonic network in shared memory).
+// Slot s then takes the component perm[s]: its row of `old` (a copy of model64)
+// is rebuilt into slot s of model64, params and shift4.  Only the order of the
+// components in the fit changes: the E-step's per-point sums see them in
+// another order, and nothing else.
+__device__ __forceinline__ unsigned spread10(unsigned v) {   // bit i -> bit 3 i
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// insts (batched fits): block i orders instance i (its own k, offsets and state).
+__global__ void __launch_bounds__(ORDER_THREADS) order_components_kernel(const double* __restrict__ old, int k,
+                                                                        int kp2, int* perm, double* model64,
+                                                                        float* params, float4* shift4,
+                                                                        DeviceState* st,
+                                                                        const BatchInst* __restrict__ insts) {
+    extern __shared__ unsigned long long keys[];   // kp2 = power of two >= k
+    __shared__ double s_lo[3][32], s_hi[3][32];
+    if (insts) {
+        const BatchInst I = insts[blockIdx.x];
+        k = I.k;
+        old += (size_t)I.comp_off * MODEL;
+        model64 += (size_t)I.comp_off * MODEL;
+        perm += I.comp_off;
+        params += I.par_off;
+        shift4 += I.comp_off;
+        st += blockIdx.x;
+        kp2 = 1;
+        while (kp2 < k) kp2 <<= 1;
+    }
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = t; b < k; b += blockDim.x)
+        for (int i = 0; i < 3; ++i) {
+            const double v = old[(size_t)b * MODEL + 1 + i];
+            lo[i] = fmin(lo[i], v);
+            hi[i] = fmax(hi[i], v);
+        }
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[i] = fmin(lo[i], __shfl_xor_sync(FULL, lo[i], o));
+            hi[i] = fmax(hi[i], __shfl_xor_sync(FULL, hi[i], o));
+        }
+        if (lane == 0) {
+            s_lo[i][warp] = lo[i];
+            s_hi[i][warp] = hi[i];
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = s_lo[i][0];
+        hi[i] = s_hi[i][0];
+        for (int w = 1; w < nw; ++w) {
+            lo[i] = fmin(lo[i], s_lo[i][w]);
+            hi[i] = fmax(hi[i], s_hi[i][w]);
+        }
+    }
+    for (int b = t; b < kp2; b += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (b < k) {
+            unsigned code = 0;
+            for (int i = 0; i < 3; ++i) {
+                const double span = hi[i] - lo[i];
+                const double u = span > 0.0 ? (old[(size_t)b * MODEL + 1 + i] - lo[i]) / span : 0.0;
+                const unsigned q = (unsigned)fmin(1023.0, fmax(0.0, floor(u * 1024.0)));
+                code |= spread10(q) << i;
+            }
+            key = ((unsigned long long)code << 32) | (unsigned)b;
+        }
+        keys[b] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= kp2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = t; i < kp2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const unsigned long long a = keys[i], c = keys[j];
+                    const bool up = (i & size) == 0;
+                    if ((a > c) == up) {
+                        keys[i] = c;
+                        keys[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int slot = t; slot < k; slot += blockDim.x) {
+        const int b = (int)(keys[slot] & 0xffffffffu);
+        perm[slot] = b;
+        const double* r = old + (size_t)b * MODEL;
+        build_component(slot, r[0], r + 1, r + 4, params, shift4, model64, st, b);
+    }
 }
 
 // ------------------------------------------------------------------ differentiable log-likelihood
@@ -1252,7 +1854,7 @@ __device__ void params_from_chol_body(const float* __restrict__ logits, const fl
         }
         const double c[6] = {L00 * L00, L00 * L10, L00 * L20, L10 * L10 + L11 * L11, L10 * L20 + L11 * L21,
                              L20 * L20 + L21 * L21 + L22 * L22};
-        build_component(b, exp((double)logits[b] - lz), m3, c, params, shift4, model64, st);
+        build_component(b, exp((double)logits[b] - lz), m3, c, params, shift4, model64, st, b);
     }
 }
 
@@ -1407,9 +2009,10 @@ __device__ void grad_finalize_body(const GradFinArgs& f, int blk) {
 cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
-                                   cudaStream_t s, bool pdl) {
+                                   cudaStream_t s, bool pdl, const int* perm, const uint32_t* masks, int nwords,
+                                   int ll_count) {
     const FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
-                    em ? 1 : 0, 0, 1};
+                    em ? 1 : 0, ll_count, 1, perm, masks, nwords};
     PdlConfig c(dim3((k + FIN_CPB - 1) / FIN_CPB), dim3(FIN_THREADS), 0, s, pdl);
     return cudaLaunchKernelEx(&c.cfg, reduce_finalize_kernel, f);
 }
@@ -1419,9 +2022,10 @@ int fin_components_per_block() { return FIN_CPB; }
 cudaError_t launch_reduce_finalize_batched(const float* partials, const double* ll_partials, const double* stats64,
                                            float4* shift4, const BatchInst* insts, const int2* blocks, int nblocks,
                                            double reg, double tol, int iters, double* model64, float* params,
-                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s) {
+                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s,
+                                           const int* perm, const uint32_t* masks) {
     const FinArgs f{partials, 0, ll_partials, stats64, shift4, 0, 0, reg, tol, model64, params, trace, nullptr,
-                    iter, em ? 1 : 0, 0, 1};
+                    iter, em ? 1 : 0, 0, 1, perm, masks, 0};
     reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, states, std::max(iters, 1), 0);
     return cudaGetLastError();
 }
@@ -1430,9 +2034,9 @@ cudaError_t launch_reduce_finalize_chunks(const float* partials, const double* l
                                           const double* stats64, float4* shift4, const BatchInst* insts,
                                           const int2* blocks, int nblocks, int64_t n, double reg, double tol,
                                           double* model64, float* params, double* trace, DeviceState* st, int iter,
-                                          bool em, cudaStream_t s) {
+                                          bool em, cudaStream_t s, const int* perm) {
     const FinArgs f{partials, 0, ll_partials, stats64, shift4, 0, n, reg, tol, model64, params, trace, nullptr,
-                    iter, em ? 1 : 0, ll_count, 1};
+                    iter, em ? 1 : 0, ll_count, 1, perm};
     reduce_finalize_batched_kernel<<<nblocks, FIN_THREADS, 0, s>>>(f, insts, blocks, st, 1, 1);
     return cudaGetLastError();
 }
@@ -1452,8 +2056,8 @@ cudaError_t launch_params_from_model_batched(const float* w, const float* mu, co
 }
 
 cudaError_t launch_model_out_batched(const double* model64, const BatchInst* insts, int batch, float* w, float* mu,
-                                     float* cov, const DeviceState* states, cudaStream_t s) {
-    model_out_batched_kernel<<<batch, 64, 0, s>>>(model64, insts, w, mu, cov, states);
+                                     float* cov, const DeviceState* states, cudaStream_t s, const int* perm) {
+    model_out_batched_kernel<<<batch, 64, 0, s>>>(model64, insts, w, mu, cov, states, perm);
     return cudaGetLastError();
 }
 
@@ -1470,8 +2074,40 @@ cudaError_t launch_params_from_model(const float* w, const float* mu, const floa
 }
 
 cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
-                             cudaStream_t s) {
-    model_out_kernel<<<(k + 63) / 64, 64, 0, s>>>(model64, k, w, mu, cov, st);
+                             cudaStream_t s, const int* perm) {
+    model_out_kernel<<<(k + 63) / 64, 64, 0, s>>>(model64, k, w, mu, cov, st, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_components(double* model64, double* scratch, int k, int* perm, float* params,
+                                    float4* shift4, DeviceState* st, cudaStream_t s) {
+    if (k > ORDER_MAX_K) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(scratch, model64, sizeof(double) * (size_t)k * MODEL, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    int kp2 = 1;
+    while (kp2 < k) kp2 <<= 1;
+    const size_t smem = sizeof(unsigned long long) * (size_t)kp2;
+    e = cudaFuncSetAttribute(order_components_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    order_components_kernel<<<1, ORDER_THREADS, smem, s>>>(scratch, k, kp2, perm, model64, params, shift4, st,
+                                                           nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_components_batched(double* model64, double* scratch, int total_k, int kmax,
+                                            const BatchInst* insts, int batch, int* perm, float* params,
+                                            float4* shift4, DeviceState* states, cudaStream_t s) {
+    if (kmax > ORDER_MAX_K) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaMemcpyAsync(scratch, model64, sizeof(double) * (size_t)total_k * MODEL, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    int kp2 = 1;
+    while (kp2 < kmax) kp2 <<= 1;
+    const size_t smem = sizeof(unsigned long long) * (size_t)kp2;
+    e = cudaFuncSetAttribute(order_components_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    order_components_kernel<<<batch, ORDER_THREADS, smem, s>>>(scratch, 0, 0, perm, model64, params, shift4, states,
+                                                               insts);
     return cudaGetLastError();
 }
 

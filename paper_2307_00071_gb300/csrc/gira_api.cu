@@ -164,21 +164,6 @@ gira_status check_ptr(const void* p, const char* name, int dev, Kind* k) {
     return GIRA_OK;
 }
 
-gira_status device_status(const DeviceState& h) {
-    switch (h.error) {
-        case 0: return GIRA_OK;
-        case GIRA_ERR_NONFINITE_INPUT: return fail(GIRA_ERR_NONFINITE_INPUT, "NaN or Inf in the points or parameters");
-        case GIRA_ERR_NOT_PD:
-            t_bad = h.bad_component;
-            return fail(GIRA_ERR_NOT_PD, "covariance of component %d is not positive definite", h.bad_component);
-        case GIRA_ERR_INVALID_ARG: return fail(GIRA_ERR_INVALID_ARG, "a mixture weight is not positive");
-        case GIRA_ERR_NUMERIC:
-            return fail(GIRA_ERR_NUMERIC, "a point's likelihood underflows binary32 under every component");
-        case GIRA_ERR_TIMEOUT: return fail(GIRA_ERR_TIMEOUT, "a bounded device-side wait ran out (k-means++ seeding)");
-        default: return fail((gira_status)h.error, "device error %d", h.error);
-    }
-}
-
 gira_status check_nk(int64_t n, int k) {
     if (n < 1) return fail(GIRA_ERR_INVALID_ARG, "n = %lld < 1", (long long)n);
     if (k < 1 || k > GIRA_MAX_K) return fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, GIRA_MAX_K);
@@ -224,7 +209,13 @@ struct CallProfile {
     size_t used = 0;
     cudaEvent_t t0 = nullptr, t_init = nullptr, t_em = nullptr, t_end = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> estep;
+    std::string estep_name;   // the kernel those event pairs bracket
     long long launches = 0;
+
+    void timed(cudaEvent_t e0, cudaEvent_t e1) {
+        estep.emplace_back(e0, e1);
+        estep_name = last_estep_kernel();
+    }
 
     cudaEvent_t mark_launch() { return per_launch ? mark() : nullptr; }
     cudaEvent_t mark() {
@@ -254,6 +245,10 @@ struct CallProfile {
         if (!on) return;
         for (int i = 0; i < (int)estep.size() && i < estep_done; ++i) g_prof.estep_ms += ms(estep[i].first, estep[i].second);
         g_prof.estep_launches += std::min<long long>((long long)estep.size(), estep_done);
+        if (!estep_name.empty()) {
+            std::strncpy(g_prof.estep_kernel, estep_name.c_str(), sizeof g_prof.estep_kernel - 1);
+            g_prof.estep_kernel[sizeof g_prof.estep_kernel - 1] = 0;
+        }
         g_prof.em_iters += em_iters;
         g_prof.init_ms += ms(t0, t_init);
         g_prof.em_ms += ms(t_init, t_em);
@@ -266,6 +261,21 @@ struct CallProfile {
 void gira::record_error(const char* msg, int component) {
     if (msg) t_msg = msg;
     t_bad = component;
+}
+
+gira_status gira::device_status(const DeviceState& h) {
+    switch (h.error) {
+        case 0: return GIRA_OK;
+        case GIRA_ERR_NONFINITE_INPUT: return fail(GIRA_ERR_NONFINITE_INPUT, "NaN or Inf in the points or parameters");
+        case GIRA_ERR_NOT_PD:
+            t_bad = h.bad_component;
+            return fail(GIRA_ERR_NOT_PD, "covariance of component %d is not positive definite", h.bad_component);
+        case GIRA_ERR_INVALID_ARG: return fail(GIRA_ERR_INVALID_ARG, "a mixture weight is not positive");
+        case GIRA_ERR_NUMERIC:
+            return fail(GIRA_ERR_NUMERIC, "a point's likelihood underflows binary32 under every component");
+        case GIRA_ERR_TIMEOUT: return fail(GIRA_ERR_TIMEOUT, "a bounded device-side wait ran out (k-means++ seeding)");
+        default: return fail((gira_status)h.error, "device error %d", h.error);
+    }
 }
 
 
@@ -426,7 +436,7 @@ cudaError_t chunk_lse(const ChunkPlan& P, const ChunkBufs& b, const float4* p8, 
 
 cudaError_t chunk_em_iteration(const ChunkPlan& P, const ChunkBufs& b, const float4* p8, int64_t n, int k,
                                float4* shift4, double* model64, double* trace, const gira_fit_opts& o,
-                               DeviceState* st, int iter, long long* launches, cudaStream_t s) {
+                               DeviceState* st, int iter, long long* launches, cudaStream_t s, const int* perm) {
     cudaError_t e = chunk_lse(P, b, p8, n, k, st, iter, false, launches, s);
     EStepLaunch a{p8, n, k, b.params, P.ppc, b.partials, nullptr, nullptr, nullptr, iter};
     a.insts = b.insts;
@@ -434,11 +444,12 @@ cudaError_t chunk_em_iteration(const ChunkPlan& P, const ChunkBufs& b, const flo
     a.states = st;
     a.gref = b.gref;
     a.pref = b.pref;
+    a.psum = b.psum;   // pass B skips the batches pass A found out of this chunk's reach
     if (e == cudaSuccess) e = launch_estep_chunks(a, 2, (int)P.units.size(), P.ppc, s);
     if (e == cudaSuccess)
         e = launch_reduce_finalize_chunks(b.partials, b.llp, chunk_combine_grid(), nullptr, shift4, b.insts,
                                           b.blocks, (int)P.blocks.size(), n, o.reg_covar, o.tol, model64, b.params,
-                                          trace, st, iter, true, s);
+                                          trace, st, iter, true, s, perm);
     *launches += 2;
     return e;
 }
@@ -615,9 +626,11 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     const ChunkPlan P = chunked ? plan_chunks(n, k, c.sms) : ChunkPlan{};
     ChunkBufs cb;
     const int npairs = chunked ? 0 : params_pairs_padded(k);
-    int64_t ppc = 0, ppc_ll = 0;
-    const int grid = chunked ? 0 : estep_grid(n, k, true, c.sms, &ppc);
-    const int grid_ll = chunked ? 0 : estep_grid(n, k, false, c.sms, &ppc_ll);
+    // point-stationary E-step: one grid for the EM loop and the final log-likelihood;
+    // per-warp partial rows and live masks
+    const int grid = chunked ? 0 : estep_pt_grid(n);
+    const int rows = chunked ? 0 : estep_pt_rows(grid);
+    const int nwords = chunked ? 0 : estep_pt_mask_words(k);
     const int nblk = kpp_num_blocks(n);
     int kgrid = kinit ? kpp_persistent_grid() : 0;
     if (kgrid > 0 && n > kpp_persistent_max_n(kgrid)) kgrid = 0;
@@ -630,11 +643,13 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         u128 *bs, *ksums;
         int64_t* ch;
         int32_t* lab;
-        int* ksync;
+        int *ksync, *perm;
+        uint32_t* masks;
         unsigned long long* chg;
     } b{};
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
+        b.perm = cv.take<int>(k);
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
         b.p4 = cv.take<float4>(kinit ? n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)n);
@@ -642,8 +657,9 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.shift4 = cv.take<float4>(k);
         b.model64 = cv.take<double>((size_t)k * MODEL);
         b.stats64 = cv.take<double>((size_t)k * NSTAT);
-        b.partials = cv.take<float>((size_t)grid * k * NSTAT);
-        b.llp = cv.take<double>(std::max(grid, grid_ll));
+        b.partials = cv.take<float>((size_t)rows * k * NSTAT);
+        b.masks = cv.take<uint32_t>((size_t)rows * nwords);
+        b.llp = cv.take<double>(grid);
         b.trace = cv.take<double>(std::max(o.iters, 1));
         if (chunked) carve_chunks(cv, P, n, true, &cb);
         b.mw = cv.take<float>(model_host ? k : 0);
@@ -736,16 +752,23 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
             COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
         }
     }
+    // the EM runs with the components along a space-filling curve of their means
+    // (the E-step then skips the many point-component pairs out of reach);
+    // model_out puts them back in the caller's order
+    const int* perm = b.perm;
+    COUNTED(prof, 1, launch_order_components(b.model64, b.stats64, k, b.perm, b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
 
     if (chunked) {
         for (int t = 1; t <= o.iters; ++t)
             GIRA_CUDA(chunk_em_iteration(P, cb, b.p8, n, k, b.shift4, b.model64, b.trace, o, b.st, t, &prof.launches,
-                                         c.s));
+                                         c.s, perm));
         prof.t_em = prof.mark();
         if (final_loglik) GIRA_CUDA(chunk_lse(P, cb, b.p8, n, k, b.st, 0, true, &prof.launches, c.s));
     }
-    EStepLaunch a{b.p8, n, k, b.params, ppc, b.partials, b.llp, nullptr, b.st, 0};
+    EStepLaunch a{b.p8, n, k, b.params, 0, b.partials, b.llp, nullptr, b.st, 0};
+    a.masks = b.masks;
+    a.pt_rows = rows;
     for (int t = 1; t <= o.iters && !chunked; ++t) {
         a.iter = t;
         // dependent launches unless an event pair brackets each E-step: each
@@ -753,22 +776,23 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         // device for its results
         const bool pdl = !prof.per_launch;
         cudaEvent_t e0 = prof.mark_launch();
-        COUNTED(prof, 1, launch_estep(a, true, grid, c.s, false, pdl));
+        COUNTED(prof, 1, launch_estep_pt(a, true, grid, c.s, pdl));
         cudaEvent_t e1 = prof.mark_launch();
-        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
-        COUNTED(prof, 1, launch_reduce_finalize(b.partials, grid, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
-                                                o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s, pdl));
+        if (prof.per_launch) prof.timed(e0, e1);
+        COUNTED(prof, 1, launch_reduce_finalize(b.partials, rows, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
+                                                o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s, pdl, perm,
+                                                b.masks, nwords, grid));
     }
     if (!chunked) prof.t_em = prof.mark();
     if (final_loglik && !chunked) {
         EStepLaunch f = a;
         f.iter = 0;
-        f.pts_per_cta = ppc_ll;
         f.partials = nullptr;
-        COUNTED(prof, 1, launch_estep(f, false, grid_ll, c.s));
-        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid_ll, b.st, c.s));
+        f.masks = nullptr;
+        COUNTED(prof, 1, launch_estep_pt(f, false, grid, c.s));
+        COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
     }
-    COUNTED(prof, 1, launch_model_out(b.model64, k, w_d, mu_d, cov_d, b.st, c.s));
+    COUNTED(prof, 1, launch_model_out(b.model64, k, w_d, mu_d, cov_d, b.st, c.s, perm));
     if (kw == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
     if (km == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(means, b.mmu, sizeof(float) * 3 * k, cudaMemcpyDeviceToHost, c.s));
     if (kc == Kind::Host) GIRA_CUDA(cudaMemcpyAsync(covs, b.mcov, sizeof(float) * 9 * k, cudaMemcpyDeviceToHost, c.s));
@@ -803,8 +827,7 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
     const ChunkPlan P = chunked ? plan_chunks(n, k, c.sms) : ChunkPlan{};
     ChunkBufs cb;
     const int npairs = chunked ? 0 : params_pairs_padded(k);
-    int64_t ppc = 0;
-    const int grid = chunked ? 0 : estep_grid(n, k, false, c.sms, &ppc);
+    const int grid = chunked ? 0 : estep_pt_grid(n);
     struct Bufs {
         DeviceState* st;
         float *pin, *params, *mw, *mmu, *mcov, *pp;
@@ -879,8 +902,8 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
         COUNTED(prof, 1, launch_params_from_model(w_d, mu_d, cov_d, k, b.model64, b.params, b.shift4, b.st, c.s));
         prof.t_init = prof.mark();
         prof.t_em = prof.t_init;
-        EStepLaunch a{b.p8, n, k, b.params, ppc, nullptr, b.llp, ppd, b.st, 0};
-        COUNTED(prof, 1, launch_estep(a, false, grid, c.s));
+        EStepLaunch a{b.p8, n, k, b.params, 0, nullptr, b.llp, ppd, b.st, 0};
+        COUNTED(prof, 1, launch_estep_pt(a, false, grid, c.s));
         COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
     }
     if (per_point && kpp == Kind::Host)
@@ -1005,7 +1028,7 @@ gira_status gira_gmm_loglik_grad(const float* points, int64_t n, int k, const fl
         cudaEvent_t e0 = prof.mark_launch();
         COUNTED(prof, 1, launch_estep(a, true, grid, c.s, true));
         cudaEvent_t e1 = prof.mark_launch();
-        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
+        if (prof.per_launch) prof.timed(e0, e1);
         COUNTED(prof, 1, launch_grad_finalize(b.partials, grid, b.llp, b.ppart, pose_d, ch_d, b.model64, k, n, gl_d,
                                               gm_d, gc_d, po_d, tw_d, b.st, c.s));
     } else {
@@ -1060,16 +1083,13 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     TRY(check_ptr(covs, "covs", c.dev, &kc));
     const bool model_host = kw == Kind::Host || km == Kind::Host || kc == Kind::Host;
     const bool kinit = o.init_mode == GIRA_INIT_KMEANS;
-    const int Q = estep_batch_q();
     const int iters = std::max(o.iters, 1);
 
-    // ---- host tables: instances, shape classes, finalize blocks
+    // ---- host tables: instances, finalize blocks
     std::vector<BatchInst> hi(batch);
     std::vector<int> npairs_of(batch);
     int total_k = 0;
     int64_t par_floats = 0;
-    std::map<std::pair<int, int>, int> class_of_shape;
-    std::vector<BatchClass> cls;
     for (int i = 0; i < batch; ++i) {
         BatchInst& I = hi[i];
         I.pt_off = offsets[i];
@@ -1080,21 +1100,6 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         npairs_of[i] = params_pairs_padded(ks[i]);
         I.par_off = par_floats;
         par_floats += (int64_t)npairs_of[i] * PAIR_FLOATS;
-        int np, g, th;
-        estep_shape(ks[i], &np, &g, &th);
-        auto key = std::make_pair(np, g);
-        auto it = class_of_shape.find(key);
-        if (it == class_of_shape.end()) {
-            it = class_of_shape.emplace(key, (int)cls.size()).first;
-            cls.emplace_back();
-            cls.back().np = np;
-            cls.back().g = g;
-            cls.back().threads = th;
-        }
-        BatchClass& C = cls[it->second];
-        C.insts.push_back(i);
-        C.points += I.n;
-        C.kmax = std::max(C.kmax, ks[i]);
     }
     std::vector<int> comp_inst(total_k);
     std::vector<int2> fin_blocks;
@@ -1103,27 +1108,27 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         for (int b = 0; b < ks[i]; ++b) comp_inst[hi[i].comp_off + b] = i;
         for (int j = 0; j * cpb < ks[i]; ++j) fin_blocks.push_back(make_int2(i, j));
     }
-    // points per CTA: measured per shape and size (first call), else at least two waves of CTAs
-    const int64_t cand[4] = {256, 512, 1024, 2048};
-    std::vector<bool> tune(cls.size(), false);
-    for (size_t ci = 0; ci < cls.size(); ++ci) {
-        BatchClass& C = cls[ci];
-        const int occ = estep_occupancy(C.kmax, true, 1024);
-        int64_t ppc = (C.points + 2LL * c.sms * occ - 1) / (2LL * c.sms * occ);
-        ppc = std::min<int64_t>(estep_ppc_max(), std::max<int64_t>(cand[0], (ppc + Q - 1) / Q * Q));
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(std::make_tuple(c.dev, C.np, C.g, ilog2(C.points)));
-        if (it != g_tuned.end()) {
-            ppc = it->second;
-        } else if (o.iters > 0) {   // (without iterations the E-step launches would exit at once)
-            tune[ci] = true;
-            ppc = cand[0];   // size the buffers for the smallest candidate
-        }
-        C.ppc = ppc;
-    }
+    // the point-stationary E-step: every instance in one launch, a fixed number of
+    // points per CTA; per-warp partial rows and live masks per instance
     std::vector<BatchUnit> units;
-    int64_t part_floats = 0, ll_slots = 0;
-    build_tables(hi, cls, units, &part_floats, &ll_slots);   // the largest sizes any candidate needs
+    int64_t part_floats = 0, mask_words = 0, ll_slots = 0;
+    int kmax_all = 0;
+    {
+        const int PTS = estep_pt_points(), W = estep_pt_warps();
+        for (int i = 0; i < batch; ++i) {
+            BatchInst& I = hi[i];
+            I.ppc = PTS;
+            I.ctas = (int)((I.n + PTS - 1) / PTS);
+            I.part_off = part_floats;
+            I.mask_off = mask_words;
+            I.ll_off = ll_slots;
+            part_floats += (int64_t)I.ctas * W * I.k * NSTAT;
+            mask_words += (int64_t)I.ctas * W * estep_pt_mask_words(I.k);
+            ll_slots += I.ctas;
+            kmax_all = std::max(kmax_all, I.k);
+            for (int t = 0; t < I.ctas; ++t) units.push_back(BatchUnit{i, t});
+        }
+    }
     const size_t max_units = units.size();
 
     // per-instance KInit scratch
@@ -1138,7 +1143,8 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         BatchInst* insts;
         BatchUnit* units;
         int2* blocks;
-        int *comp_inst, *npairs;
+        int *comp_inst, *npairs, *perm;
+        uint32_t* masks;
         int64_t *offs, *ch;
         int32_t* lab;
         u128* bs;
@@ -1182,6 +1188,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         b.model64 = cv.take<double>((size_t)total_k * MODEL);
         b.stats64 = cv.take<double>((size_t)total_k * NSTAT);
         b.partials = cv.take<float>((size_t)part_floats);
+        b.masks = cv.take<uint32_t>((size_t)mask_words);
         b.llp = cv.take<double>((size_t)ll_slots);
         b.trace = cv.take<double>((size_t)batch * iters);
         b.mw = cv.take<float>(model_host ? total_k : 0);
@@ -1191,6 +1198,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         b.units = cv.take<BatchUnit>(max_units);
         b.blocks = cv.take<int2>(fin_blocks.size());
         b.comp_inst = cv.take<int>(total_k);
+        b.perm = cv.take<int>(total_k);
         b.npairs = cv.take<int>(batch);
         b.offs = cv.take<int64_t>(batch + 1);
         if (kinit) {
@@ -1287,66 +1295,25 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         COUNTED(prof, 1, launch_params_from_model_batched(w_d, mu_d, cov_d, total_k, b.comp_inst, b.insts, b.model64,
                                                           b.params, b.shift4, b.st, c.s));
     }
+    // every instance's components along a space-filling curve of their means (as in the single fit)
+    COUNTED(prof, 1, launch_order_components_batched(b.model64, b.stats64, total_k, kmax_all, b.insts, batch, b.perm,
+                                                     b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
 
     EStepLaunch base{b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
     base.insts = b.insts;
     base.units = b.units;
     base.states = b.st;
+    base.masks = b.masks;
     auto estep_all = [&](bool stats, int iter, cudaStream_t s) -> cudaError_t {
         EStepLaunch a = base;
         a.iter = iter;
-        if (!stats) a.partials = nullptr;
-        for (const BatchClass& C : cls) {
-            if (!C.nunits) continue;
-            a.units = b.units + C.unit_begin;
-            cudaError_t e = launch_estep_units(a, stats, C.nunits, C.kmax, C.ppc, s);
-            if (e != cudaSuccess) return e;
+        if (!stats) {
+            a.partials = nullptr;
+            a.masks = nullptr;
         }
-        return cudaSuccess;
+        return launch_estep_pt_units(a, stats, (int)units.size(), kmax_all, s);
     };
-
-    // ---- autotune: time one E-step of each untuned class for every candidate
-    bool any_tune = false;
-    for (bool t : tune) any_tune = any_tune || t;
-    if (any_tune) {
-        cudaEvent_t e0, e1;
-        GIRA_CUDA(cudaEventCreate(&e0));
-        GIRA_CUDA(cudaEventCreate(&e1));
-        for (size_t ci = 0; ci < cls.size(); ++ci) {
-            if (!tune[ci]) continue;
-            double best = 1e30;
-            int64_t best_ppc = cand[0];
-            for (int64_t pc : cand) {
-                if (pc > estep_ppc_max()) continue;
-                cls[ci].ppc = pc;
-                build_tables(hi, cls, units, &part_floats, &ll_slots);
-                GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
-                GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(BatchUnit) * units.size(),
-                                          cudaMemcpyHostToDevice, c.s));
-                EStepLaunch a = base;
-                a.iter = 1;
-                a.units = b.units + cls[ci].unit_begin;
-                GIRA_CUDA(launch_estep_units(a, true, cls[ci].nunits, cls[ci].kmax, pc, c.s));   // warm
-                GIRA_CUDA(cudaEventRecord(e0, c.s));
-                for (int r = 0; r < 2; ++r) GIRA_CUDA(launch_estep_units(a, true, cls[ci].nunits, cls[ci].kmax, pc, c.s));
-                GIRA_CUDA(cudaEventRecord(e1, c.s));
-                GIRA_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                GIRA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    best_ppc = pc;
-                }
-            }
-            cls[ci].ppc = best_ppc;
-            std::lock_guard<std::mutex> lk2(g_tune_mu);
-            g_tuned[std::make_tuple(c.dev, cls[ci].np, cls[ci].g, ilog2(cls[ci].points))] = best_ppc;
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
-    build_tables(hi, cls, units, &part_floats, &ll_slots);
     GIRA_CUDA(cudaMemcpyAsync(b.insts, hi.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, c.s));
     GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, c.s));
 
@@ -1357,7 +1324,6 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                       std::to_string((int)kinit) + std::to_string((int)(kp == Kind::Host)) +
                       std::to_string((int)model_host);
     for (int i = 0; i < batch; ++i) key += "|" + std::to_string(hi[i].n) + ":" + std::to_string(hi[i].k);
-    for (const auto& C : cls) key += "|p" + std::to_string(C.ppc);
     if (o.iters > 0) {
         if (ws->graph_key != key || !ws->graph_exec) {
             drop_graph(ws);
@@ -1370,7 +1336,8 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                 if (e == cudaSuccess)
                     e = launch_reduce_finalize_batched(b.partials, b.llp, nullptr, b.shift4, b.insts, b.blocks,
                                                        (int)fin_blocks.size(), o.reg_covar, o.tol, o.iters,
-                                                       b.model64, b.params, b.trace, b.st, t, true, cs);
+                                                       b.model64, b.params, b.trace, b.st, t, true, cs, b.perm,
+                                                       b.masks);
             }
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1390,16 +1357,16 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
             ws->graph_exec = exec;
             ws->graph_key = key;
         }
-        prof.launches += (long long)o.iters * ((long long)cls.size() + 1);
+        prof.launches += (long long)o.iters * 2;
         GIRA_CUDA(cudaGraphLaunch(ws->graph_exec, c.s));
     }
     prof.t_em = prof.mark();
     if (final_loglik) {
         GIRA_CUDA(estep_all(false, 0, c.s));
-        prof.launches += (long long)cls.size();
+        prof.launches += 1;
         COUNTED(prof, 1, launch_ll_reduce_batched(b.llp, b.insts, batch, b.st, c.s));
     }
-    COUNTED(prof, 1, launch_model_out_batched(b.model64, b.insts, batch, w_d, mu_d, cov_d, b.st, c.s));
+    COUNTED(prof, 1, launch_model_out_batched(b.model64, b.insts, batch, w_d, mu_d, cov_d, b.st, c.s, b.perm));
     if (kw == Kind::Host)
         GIRA_CUDA(cudaMemcpyAsync(weights, b.mw, sizeof(float) * total_k, cudaMemcpyDeviceToHost, c.s));
     if (km == Kind::Host)
@@ -1772,11 +1739,12 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         u128 *bs, *ksums;
         int64_t* ch;
         int32_t* lab;
-        int* ksync;
+        int *ksync, *perm;
         unsigned long long* chg;
     } b{};
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
+        b.perm = cv.take<int>(k);
         b.pin = cv.take<float>(kp == Kind::Host ? 4 * n : 0);
         b.p4 = cv.take<float4>(n);
         b.p8 = cv.take<float4>(2 * (size_t)n);
@@ -1874,7 +1842,7 @@ gira_status gira_gmm_fit4(const float* points, int64_t n, int k, const gira_fit_
         cudaEvent_t e0 = prof.mark_launch();
         COUNTED(prof, 1, launch_estep4(a, true, grid, c.s, pdl));
         cudaEvent_t e1 = prof.mark_launch();
-        if (prof.per_launch) prof.estep.emplace_back(e0, e1);
+        if (prof.per_launch) prof.timed(e0, e1);
         COUNTED(prof, 1, launch_reduce_finalize4(b.partials, grid, kblk, b.llp, grid, nullptr, nullptr, k, n,
                                                  o.reg_covar, o.tol, b.model64, b.params, b.trace, b.st, t, true,
                                                  c.s, pdl));

@@ -313,6 +313,7 @@ struct BatchInst {
     int comp_off;       // first component in the per-component arrays
     int ctas;           // E-step CTAs of the instance
     int pad_;
+    int64_t mask_off;   // word offset of its per-warp live masks (point-stationary E-step)
 };
 // One E-step CTA of a batched launch: instance and CTA index within it.
 struct BatchUnit {
@@ -345,6 +346,12 @@ struct EStepLaunch {
     const float* gref = nullptr;   // [0] cmax over all K, [1] log-likelihood reference (base 2)
     float* psum = nullptr;
     const float2* pref = nullptr;
+    // point-stationary E-step (estep_pt_kernel): per-warp partials [k * NSTAT][rows],
+    // row cta * W + warp written only where the warp's live mask has the pair's
+    // bit, and the live masks [npairs / 32][rows] (bit p: pair p reaches some point
+    // of the warp)
+    uint32_t* masks = nullptr;
+    int64_t pt_rows = 0;   // warps of the launch (the row count of partials and masks)
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count
@@ -387,11 +394,31 @@ cudaError_t launch_ll_reduce(const double* ll_partials, int grid, DeviceState* s
 cudaError_t launch_reduce_finalize(const float* partials, int grid, const double* ll_partials,
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
-                                   cudaStream_t s, bool pdl = false);
+                                   cudaStream_t s, bool pdl = false, const int* perm = nullptr,
+                                   const uint32_t* masks = nullptr, int nwords = 0, int ll_count = 0);
+// Point-stationary E-step (3-D fits and log-likelihood, k <= 1024): CTAs for n
+// points; partial rows (warps) of a grid; live-mask words per warp for k.
+int estep_pt_grid(int64_t n);
+int estep_pt_rows(int grid);
+int estep_pt_mask_words(int k);
+// a.partials: [k * NSTAT][rows] (stats), a.masks: [mask words][rows], a.pt_rows = rows,
+// a.ll_partials: [grid]
+cudaError_t launch_estep_pt(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool pdl = false);
+// The same over a unit table (batched fits; a.insts / a.units / a.states; every
+// instance's part_off, mask_off, ll_off and ctas for PT points per CTA).
+cudaError_t launch_estep_pt_units(const EStepLaunch& a, bool stats, int nunits, int kmax, cudaStream_t s);
+int estep_pt_points();   // points per CTA
+int estep_pt_warps();    // warps per CTA (partial rows per CTA)
 cudaError_t launch_params_from_model(const float* w, const float* mu, const float* cov, int k, double* model64,
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
+// perm (nullable): slot s of model64 is the caller's component perm[s].
 cudaError_t launch_model_out(const double* model64, int k, float* w, float* mu, float* cov, const DeviceState* st,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* perm = nullptr);
+// Reorder the k <= 8192 components of model64 along a space-filling curve of
+// their means (Morton order) and rebuild params / shift4 / model64 in that order:
+// slot s holds the caller's component perm[s].  scratch: k * MODEL doubles.
+cudaError_t launch_order_components(double* model64, double* scratch, int k, int* perm, float* params,
+                                    float4* shift4, DeviceState* st, cudaStream_t s);
 
 // Batched EM (per-instance tables on the device).
 // E-step block shape for k components (pairs per lane, warps, threads); the
@@ -411,7 +438,8 @@ int fin_components_per_block();
 cudaError_t launch_reduce_finalize_batched(const float* partials, const double* ll_partials, const double* stats64,
                                            float4* shift4, const BatchInst* insts, const int2* blocks, int nblocks,
                                            double reg, double tol, int iters, double* model64, float* params,
-                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s);
+                                           double* trace, DeviceState* states, int iter, bool em, cudaStream_t s,
+                                           const int* perm = nullptr, const uint32_t* masks = nullptr);
 // Padding slots of every instance's parameter block (one block per instance).
 cudaError_t launch_fill_padding_batched(float* params, const BatchInst* insts, int batch, int npairs_max,
                                         const int* npairs_of, cudaStream_t s);
@@ -421,7 +449,12 @@ cudaError_t launch_params_from_model_batched(const float* w, const float* mu, co
                                              float* params, float4* shift4, DeviceState* states, cudaStream_t s);
 // Normalised model of every instance (one block per instance).
 cudaError_t launch_model_out_batched(const double* model64, const BatchInst* insts, int batch, float* w, float* mu,
-                                     float* cov, const DeviceState* states, cudaStream_t s);
+                                     float* cov, const DeviceState* states, cudaStream_t s,
+                                     const int* perm = nullptr);
+// launch_order_components for every instance of a batch (one block each, k <= 8192).
+cudaError_t launch_order_components_batched(double* model64, double* scratch, int total_k, int kmax,
+                                            const BatchInst* insts, int batch, int* perm, float* params,
+                                            float4* shift4, DeviceState* states, cudaStream_t s);
 // Per-instance sums of the log-likelihood partials into states[i].ll_sum.
 cudaError_t launch_ll_reduce_batched(const double* ll_partials, const BatchInst* insts, int batch,
                                      DeviceState* states, cudaStream_t s);
@@ -454,7 +487,7 @@ cudaError_t launch_reduce_finalize_chunks(const float* partials, const double* l
                                           const double* stats64, float4* shift4, const BatchInst* insts,
                                           const int2* blocks, int nblocks, int64_t n, double reg, double tol,
                                           double* model64, float* params, double* trace, DeviceState* st, int iter,
-                                          bool em, cudaStream_t s);
+                                          bool em, cudaStream_t s, const int* perm = nullptr);
 
 // Batched differentiable log-likelihood (a batch table of scans, each with its
 // own model and pose; poses: batch x 12, or nullptr for identities).
@@ -668,5 +701,16 @@ cudaError_t launch_wait_probe(int mode, long long limit, int* counter, int* abor
 // Set this thread's last-error message (msg may be nullptr to keep it) and
 // component (what gira_last_error_message / gira_last_error_component return).
 void record_error(const char* msg, int component);
+
+// The status a call returns for the device status word it read back (GIRA_OK
+// when no kernel recorded an error), with this thread's last-error message and,
+// for GIRA_ERR_NOT_PD, the component.
+gira_status device_status(const DeviceState& h);
+
+// Name of the E-step kernel this host thread launched last (the runtime's name
+// of the function, demangled; "" before the first launch).
+const char* last_estep_kernel();
+// Record fn (an E-step kernel about to be launched) as the last one.
+void note_estep_kernel(const void* fn);
 
 }  // namespace gira

@@ -1,14 +1,16 @@
 // gira_noalloc.cu -- gira_gmm_loglik_noalloc: the log-likelihood entry point for
 // callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured, real-time loops on a robot that forbid allocation after start-up,
-// and hosts whose device memory is handed out by a pool they do not control.
-// This entry point computes exactly what gira_gmm_loglik computes, with the
-// same kernels, but its scratch memory (packed points, component parameters,
-// per-CTA partial sums, the device status word) lives in one file-scope
-// __device__ array of NOALLOC_SCRATCH_BYTES.  Every GPU that loads the library
-// holds that array until the process exits.
+// Some callers cannot call cudaMalloc: real-time loops on a robot that forbid
+// allocation after start-up (an allocation can block for an unbounded time and
+// can fail in the middle of a mission), and hosts whose device memory is
+// handed out by a pool they do not control (memory the library took would be
+// missing from the pool's budget).  This entry point computes exactly what
+// gira_gmm_loglik computes, with the same kernels, but its scratch memory
+// (packed points, component parameters, per-CTA partial sums, the device
+// status word) lives in one file-scope __device__ array of
+// NOALLOC_SCRATCH_BYTES.  Every GPU that loads the library holds that array
+// until the process exits.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -106,8 +108,7 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
     if (st0 != GIRA_OK) return st0;
 
     const int npairs = params_pairs_padded(k);
-    int64_t ppc = 0;
-    const int grid = estep_grid(n, k, false, sms, &ppc);
+    const int grid = estep_pt_grid(n);
     if (grid > NOALLOC_MAX_CTAS) return na_fail(GIRA_ERR_INVALID_ARG, "launch needs %d CTAs > %d", grid, NOALLOC_MAX_CTAS);
     // carve the scratch
     size_t off = 0;
@@ -135,22 +136,13 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
     NA_CUDA(launch_pack(points, n, nullptr, p8, st, s));
     NA_CUDA(launch_fill_padding(params, k, npairs, s));
     NA_CUDA(launch_params_from_model(weights, means, covs, k, model64, params, shift4, st, s));
-    EStepLaunch a{p8, n, k, params, ppc, nullptr, llp, per_point, st, 0};
-    NA_CUDA(launch_estep(a, false, grid, s));
+    EStepLaunch a{p8, n, k, params, 0, nullptr, llp, per_point, st, 0};
+    NA_CUDA(launch_estep_pt(a, false, grid, s));
     NA_CUDA(launch_ll_reduce(llp, grid, st, s));
     NA_CUDA(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
-    switch (h.error) {
-        case 0: break;
-        case GIRA_ERR_NOT_PD: {
-            gira_status r = na_fail(GIRA_ERR_NOT_PD, "covariance of component %d is not positive definite", h.bad_component);
-            record_error(nullptr, h.bad_component);
-            return r;
-        }
-        case GIRA_ERR_NONFINITE_INPUT: return na_fail(GIRA_ERR_NONFINITE_INPUT, "NaN or Inf in the points or parameters");
-        case GIRA_ERR_INVALID_ARG: return na_fail(GIRA_ERR_INVALID_ARG, "a mixture weight is not positive");
-        default: return na_fail((gira_status)h.error, "device error %d", h.error);
-    }
+    const gira_status dst = device_status(h);   // the allocating entry points' mapping and messages
+    if (dst != GIRA_OK) return dst;
     if (mean_loglik) *mean_loglik = h.ll_sum / (double)n;
     return GIRA_OK;
 }

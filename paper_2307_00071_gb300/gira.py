@@ -37,7 +37,7 @@ class FitOpts(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("calls", C.c_longlong), ("kernel_launches", C.c_longlong), ("estep_launches", C.c_longlong),
                 ("estep_ms", C.c_double), ("em_iters", C.c_longlong), ("init_ms", C.c_double), ("em_ms", C.c_double),
-                ("total_ms", C.c_double)]
+                ("total_ms", C.c_double), ("estep_kernel", C.c_char * 128)]
 
 
 def _load():
@@ -152,7 +152,9 @@ def gira_profile_enable(on: bool = True, launches: bool = True):
 def gira_profile_read(reset: bool = False) -> dict:
     p = Profile()
     _check(_lib.gira_profile_read(C.byref(p), 1 if reset else 0))
-    return {name: getattr(p, name) for name, _ in Profile._fields_}
+    out = {name: getattr(p, name) for name, _ in Profile._fields_}
+    out["estep_kernel"] = out["estep_kernel"].decode()
+    return out
 
 
 def gira_release_workspace():

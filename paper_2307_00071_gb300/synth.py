@@ -105,8 +105,12 @@ def _rays_world(pitch: float):
 
 
 def depth_frame(seed: int = 1, n_objects: int = 20, noise_sigma: float = 0.005, dropout: float = 0.1,
-                wall_dist: float = 8.0, cam_height: float = 1.5) -> DepthFrame:
-    """Ray-cast a procedural scene into a 640x480 depth image and back-project it."""
+                wall_dist: float = 8.0, cam_height: float = 1.5, scan_seed: int | None = None) -> DepthFrame:
+    """Ray-cast a procedural scene into a 640x480 depth image and back-project it.
+
+    ``seed`` fixes the scene (camera pitch, objects) and, by default, the sensor
+    noise and dropout; ``scan_seed`` draws the noise and dropout from a stream of
+    their own instead, which gives another scan of the same scene."""
     rng = np.random.default_rng(seed)
     pitch = np.deg2rad(rng.uniform(20.0, 30.0))
     dw, dc, rot = _rays_world(pitch)
@@ -155,10 +159,11 @@ def depth_frame(seed: int = 1, n_objects: int = 20, noise_sigma: float = 0.005, 
             tmax = np.nanmin(np.maximum(t1, t2), axis=1)
             take(np.where((tmax >= tmin) & (tmax > 0), tmin, np.inf))
     hit = np.isfinite(t_best)
+    sensor = rng if scan_seed is None else np.random.default_rng(scan_seed)
     # depth along the optical axis: dirs_cam has z == 1, so z_cam == t
     z = np.where(hit, t_best, 0.0)
-    z = z + rng.normal(0.0, noise_sigma, size=n_rays) * hit
-    keep = hit & (rng.uniform(size=n_rays) >= dropout) & (z > 0)
+    z = z + sensor.normal(0.0, noise_sigma, size=n_rays) * hit
+    keep = hit & (sensor.uniform(size=n_rays) >= dropout) & (z > 0)
     depth = np.where(keep, z, 0.0).reshape(HEIGHT, WIDTH).astype(np.float32)
     u, v = np.meshgrid(np.arange(WIDTH, dtype=np.float64), np.arange(HEIGHT, dtype=np.float64))
     zz = depth.astype(np.float64)
@@ -198,6 +203,31 @@ def gmm_cloud4(n: int = 20_000, k: int = 8, seed: int = 0, lam_lo: float = 1e-4,
         at += c
     perm = rng.permutation(n)
     return GMMCloud(pts[perm].astype(np.float32), weights, means, covs, labels[perm])
+
+
+def rigid_offset(rng: np.random.Generator, max_deg: float = 15.0, max_t: float = 0.5):
+    """A random rigid motion: rotation about a uniformly random axis by an angle
+    uniform in [0, max_deg] degrees, translation uniform in [-max_t, max_t]^3 m.
+    Returns (R (3, 3), t (3,)) in binary64."""
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    ang = np.deg2rad(rng.uniform(0.0, max_deg))
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    R = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * (K @ K)
+    return R, rng.uniform(-max_t, max_t, size=3)
+
+
+def registration_scan(seed: int = 1, scan_seed: int = 1001, n: int = 100_000, offset_seed: int = 3,
+                      max_deg: float = 15.0, max_t: float = 0.5):
+    """A second scan of the scene of ``depth_frame(seed)``: the same scene with its
+    own sensor noise (5 mm) and dropout, ``n`` of its points at random, moved by a
+    random rigid offset (``rigid_offset``).  Returns (scan (n, 3) float32, R, t):
+    scan = R x + t for points x of the scene in the first scan's frame."""
+    second = depth_frame(seed=seed, scan_seed=scan_seed).points.astype(np.float64)
+    rng = np.random.default_rng(offset_seed)
+    R, t = rigid_offset(rng, max_deg, max_t)
+    sub = second[rng.choice(len(second), n, replace=False)]
+    return (sub @ R.T + t).astype(np.float32), R, t
 
 
 def frame_subsampled(frame: DepthFrame, step: int) -> np.ndarray:

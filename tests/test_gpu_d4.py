@@ -8,11 +8,10 @@ import pytest
 
 import oracle
 from paper_2307_00071_gb300 import synth
-from tests._parity import LL_ABS, assert_model_close, to_np
+from tests._parity import LL_ABS, assert_model_close, per_point_bound, to_np
 
 pytestmark = pytest.mark.gpu
 
-PP_ABS, PP_REL = 2e-3, 1e-5   # per-point log-likelihood (binary32 logits), as in 3D
 
 
 @pytest.fixture(scope="module")
@@ -113,7 +112,8 @@ def test_loglik4_per_point_matches_oracle(gira, frame4, k):
     sample = rng.choice(len(pts), 400, replace=False)
     _, _, lse = oracle.estep(pts[sample], w, m, c, want_resp=False, want_lse=True)
     err = np.abs(pp[sample] - lse)
-    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err)
+    bound = per_point_bound(pts[sample], w, m, c, form="d")   # the 4-D E-step's d form
+    assert np.all(err <= bound), np.max(err / bound)
     assert mean == pytest.approx(pp.mean(), rel=1e-6)
     if k <= 33:
         ll_ref, _, _ = oracle.estep(pts, w, m, c, want_resp=False)
@@ -225,7 +225,8 @@ def test_loglik4_chunked_k2048_with_outliers(gira, frame4):
     sample = np.concatenate([rng.choice(len(pts), 300, replace=False), np.arange(len(pts), len(allp))])
     _, _, lse = oracle.estep(allp[sample], w, m, c, want_resp=False, want_lse=True)
     err = np.abs(pp[sample] - lse)
-    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))
+    bound = per_point_bound(allp[sample], w, m, c, form="d")
+    assert np.all(err <= bound), np.max(err / bound)
 
 
 def test_fit4_dependent_launches_give_the_same_fit(gira):

@@ -312,3 +312,25 @@ def test_batched_grad_matches_oracle_per_instance(gira):
         ref = ref_grads(scans[i], *models[i], R, t)
         assert abs(r2["loglik"][i] - ref["loglik"]) <= ll_tol(ref["loglik"], sizes[i])
         assert_group(to_np(r2["grad_twist"])[i], ref["grad_twist"], "twist")
+
+
+@pytest.mark.parametrize("offset_seed", [3, 4])
+def test_registration_k1024_second_scan_of_the_scene(gira, offset_seed):
+    """The differentiable-registration configuration: a K = 1024 GMM fitted to the
+    depth frame; a second scan of the same scene (its own 5 mm sensor noise and
+    dropout), 100k of its points under a random rigid offset (<= 15 deg, <= 0.5 m);
+    100 Adam steps on the twist recover the offset."""
+    import torch
+    from paper_2307_00071_gb300 import autograd as ag
+    frame = synth.depth_frame(seed=1).points
+    fit = gira.gira_gmm_fit(torch.as_tensor(frame, device="cuda"), 1024, iters=30, tol=1e-4, seed=0, lloyd_iters=10)
+    logits = torch.log(fit["weights"])
+    chol = torch.linalg.cholesky(fit["covs"].double()).float()
+    scan, R_off, t_off = synth.registration_scan(seed=1, offset_seed=offset_seed)
+    R, t, ll = ag.register_scan(torch.as_tensor(scan, device="cuda"), logits, fit["means"], chol, steps=100)
+    R, t = R.cpu().numpy(), t.cpu().numpy()
+    # truth: x = R_off^T (scan - t_off)
+    dR = R @ R_off
+    ang = math.degrees(math.acos(np.clip((np.trace(dR) - 1) / 2, -1, 1)))
+    dt = np.linalg.norm(t + R_off.T @ t_off)
+    assert ang < 0.5 and dt < 0.02, (ang, dt, ll)

@@ -5,11 +5,10 @@ import pytest
 
 import oracle
 from paper_2307_00071_gb300 import synth
-from tests._parity import LL_ABS, assert_model_close, to_np
+from tests._parity import LL_ABS, assert_model_close, per_point_bound, to_np
 
 pytestmark = pytest.mark.gpu
 
-PP_ABS, PP_REL = 2e-3, 1e-5   # per-point log-likelihood (binary32 logits), as for the direct path
 
 
 @pytest.fixture(scope="module")
@@ -81,7 +80,8 @@ def test_chunked_loglik_k8192_with_outliers(gira, frame):
     sample = np.concatenate([rng.choice(len(pts), 300, replace=False), np.arange(len(pts), len(allp))])
     _, _, lse = oracle.estep(allp[sample], w, m, c, want_resp=False, want_lse=True)
     err = np.abs(pp[sample] - lse)
-    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))
+    bound = per_point_bound(allp[sample], w, m, c)
+    assert np.all(err <= bound), np.max(err / bound)
 
 
 def test_chunked_loglik_equals_direct_where_both_apply(gira, frame):
@@ -122,7 +122,8 @@ def test_full_size_map_sampled_points_match_oracle(gira):
     sample = rng.choice(len(pts), 400, replace=False)
     _, _, lse = oracle.estep(pts[sample], w, m, c, want_resp=False, want_lse=True)
     err = np.abs(pp[sample] - lse)
-    assert np.all(err <= PP_ABS + PP_REL * np.abs(lse)), np.max(err / (PP_ABS + PP_REL * np.abs(lse)))
+    bound = per_point_bound(pts[sample], w, m, c)
+    assert np.all(err <= bound), np.max(err / bound)
     r = gira.gira_gmm_fit(x, K, iters=1, tol=0.0, init=(w, m, c), final_loglik=False)
     wr, cr = r["weights"].cpu().numpy().astype(np.float64), r["covs"].cpu().numpy().astype(np.float64)
     assert abs(wr.sum() - 1.0) < 1e-4 and np.all(np.isfinite(r["trace"]))

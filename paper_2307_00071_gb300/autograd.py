@@ -11,6 +11,7 @@ module marshals tensors.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import gira
@@ -90,39 +91,58 @@ def se3_exp(xi):
     return R, V @ v
 
 
+def _exp_se3_np(xi):
+    """(R, t) = exp(xi^) for xi = (omega, v), binary64 numpy (Rodrigues, series near 0)."""
+    w, v = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    th2 = float(w @ w)
+    th = np.sqrt(th2)
+    W = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if th2 < 1e-8:
+        A, B, Cc = 1 - th2 / 6, 0.5 - th2 / 24, 1.0 / 6 - th2 / 120
+    else:
+        A, B, Cc = np.sin(th) / th, (1 - np.cos(th)) / th2, (th - np.sin(th)) / (th2 * th)
+    R = np.eye(3) + A * W + B * (W @ W)
+    V = np.eye(3) + B * W + Cc * (W @ W)
+    return R, V @ v
+
+
 def register_scan(scan, logits, means, chol, steps=100, lr=0.02, decay=0.96, t0=None):
     """Likelihood-based rigid registration as a gradient solve: the pose (R, t)
     that maximises the mean log-likelihood of ``R scan + t`` under the mixture
-    (logits, means, Cholesky factors), by ``steps`` Adam steps on the twist of a
-    left perturbation.  The scan is rotated about its own centroid and the
-    translation starts at ``t0`` (default: the mixture's weighted mean of the
-    means), which keeps rotation and translation well scaled.  Every likelihood
-    and gradient comes from the library's fused kernel; the optimiser updates six
-    numbers.  Returns (R (3, 3), t (3,)) in binary64 such that R scan + t lies on
-    the mixture, and the final mean log-likelihood."""
+    (logits, means, Cholesky factors).  Each of ``steps`` Adam steps takes one
+    library call for L and its gradient with respect to a left perturbation
+    (twist) of the current pose, and moves the pose by the exponential of the
+    step: the optimiser itself is six numbers on the host.  The scan is rotated
+    about its own centroid and the translation starts at ``t0`` (default: the
+    mixture's weighted mean of the means), which keeps rotation and translation
+    well scaled.  Returns (R (3, 3), t (3,)) in binary64 such that R scan + t lies
+    on the mixture, and the final mean log-likelihood."""
     dev = scan.device
     c = scan.double().mean(0)
     s = (scan.double() - c).float().contiguous()
-    R0 = torch.eye(3, dtype=torch.float64, device=dev)
     if t0 is None:
         w = torch.softmax(logits.double(), 0)
         t0 = (w[:, None] * means.double()).sum(0)
-    t_base = torch.as_tensor(t0, dtype=torch.float64, device=dev)
-    xi = torch.zeros(6, dtype=torch.float64, device=dev, requires_grad=True)
-    opt = torch.optim.Adam([xi], lr=lr)
-    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=decay)
+    R = np.eye(3)
+    t = np.asarray(torch.as_tensor(t0, dtype=torch.float64).cpu().numpy(), np.float64).copy()
+    lg, mu, ch = logits.detach().contiguous(), means.detach().contiguous(), chol.detach().contiguous()
     n = len(scan)
-    for _ in range(steps):
-        opt.zero_grad()
-        Rd, td = se3_exp(xi)
-        L = gmm_loglik(s, logits, means, chol, Rd @ R0, Rd @ t_base + td)
-        (-L / n).backward()
-        opt.step()
-        sched.step()
-    with torch.no_grad():
-        Rd, td = se3_exp(xi)
-        R = Rd @ R0
-        t = Rd @ t_base + td
-        L = gmm_loglik(s, logits, means, chol, R, t)
-    # R (scan - c) + t = R scan + (t - R c)
-    return R, t - R @ c, float(L) / n
+    m1, m2 = np.zeros(6), np.zeros(6)
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    step = lr
+    for it in range(1, steps + 1):
+        pose = torch.as_tensor(np.concatenate([R.reshape(9), t]).astype(np.float32), device=dev)
+        r = gira.gira_gmm_loglik_grad(s, lg, mu, ch, pose, want=("twist",))
+        g = -np.asarray(r["grad_twist"].cpu().numpy() if hasattr(r["grad_twist"], "cpu") else r["grad_twist"],
+                        np.float64) / n
+        m1 = b1 * m1 + (1 - b1) * g
+        m2 = b2 * m2 + (1 - b2) * g * g
+        d = -step * (m1 / (1 - b1 ** it)) / (np.sqrt(m2 / (1 - b2 ** it)) + eps)
+        Rd, td = _exp_se3_np(d)
+        R, t = Rd @ R, Rd @ t + td
+        step *= decay
+    pose = torch.as_tensor(np.concatenate([R.reshape(9), t]).astype(np.float32), device=dev)
+    ll = gira.gira_gmm_loglik_grad(s, lg, mu, ch, pose, want=())["loglik"]
+    cn = c.cpu().numpy()
+    R_t, t_t = torch.as_tensor(R, device=dev), torch.as_tensor(t - R @ cn, device=dev)
+    return R_t, t_t, float(ll) / n

@@ -556,12 +556,16 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     __shared__ double s_ll[PT_W];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int cta = blockIdx.x;
+    // the instance's first point (batched launches); the loads below index the
+    // launch's own pointer by it (loads through the pointer advanced in the local
+    // copy of the launch struct read the unadvanced one under nvcc 13.0 for sm_103a)
+    int64_t pt0 = 0;
     EStepLaunch a = a_in;
     if (a_in.units) {
         const BatchUnit u = a_in.units[blockIdx.x];
         const BatchInst I = a_in.insts[u.inst];
         cta = u.cta;
-        a.pts8 = a_in.pts8 + 2 * I.pt_off;
+        pt0 = I.pt_off;
         a.n = I.n;
         a.k = I.k;
         a.params = a_in.params + I.par_off;
@@ -588,7 +592,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         const int64_t i = base + 32 * p;
         valid[p] = i < a.n;
         if (valid[p]) {
-            const float4 xy = a.pts8[2 * i], zz = a.pts8[2 * i + 1];
+            const float4 xy = a_in.pts8[2 * (pt0 + i)], zz = a_in.pts8[2 * (pt0 + i) + 1];
             X[p][0] = f2(xy.x, xy.y);
             X[p][1] = f2(xy.z, xy.w);
             X[p][2] = f2(zz.x, zz.y);
@@ -1351,8 +1355,10 @@ __device__ void reduce_partials_masked(const float* __restrict__ partials, int r
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = (mk[u] & bit) ? __ldcg(src + w + u) : 0.f;
+            float f = 0.f;   // binary32 groups of 8 (GB300 runs binary64 at 1/64 of the binary32 rate)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += (double)v[u];
+            for (int u = 0; u < 8; ++u) f += v[u];
+            acc += (double)f;
         }
         part[q][o] = acc;
     }

@@ -518,8 +518,11 @@ constexpr int PT_PTS = 32 * PT_P * PT_W;   // points per CTA
 // of 32 (never beyond the padded parameter block, whose extra slots are padding
 // components with c = -inf).
 __host__ __device__ constexpr int pt_pairs(int k) { return (((k + 1) / 2) + 31) & ~31; }
+constexpr float PT_REACH = 128.f;  // q' above which a component is out of reach (e = 0 from q' > 126)
+// parameters, then per warp the live-mask words and the list of reachable pairs
 __host__ __device__ constexpr size_t pt_smem_bytes(int k) {
-    return (size_t)pt_pairs(k) * PAIR_FLOATS * 4 + (size_t)PT_W * (pt_pairs(k) / 32) * 4;
+    return (size_t)pt_pairs(k) * PAIR_FLOATS * 4 + (size_t)PT_W * (pt_pairs(k) / 32) * 4 +
+           (size_t)PT_W * pt_pairs(k) * 2;
 }
 
 // Sum of 20 values (10 float2: component 2p in .x, 2p+1 in .y) over the warp's
@@ -581,7 +584,9 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     const int npairs = ((((a.k + 1) >> 1) + 1) & ~1);
     const int nwords = pt_pairs(a.k) / 32;
     const float4* spar = reinterpret_cast<const float4*>(dsm);   // [npairs][8]
-    uint32_t* smask = reinterpret_cast<uint32_t*>(dsm + (size_t)pt_pairs(a.k) * PAIR_FLOATS * 4) + warp * nwords;
+    uint32_t* smask_all = reinterpret_cast<uint32_t*>(dsm + (size_t)pt_pairs(a.k) * PAIR_FLOATS * 4);
+    uint32_t* smask = smask_all + warp * nwords;   // [nwords] live bits of the warp's pairs
+    uint16_t* slist = reinterpret_cast<uint16_t*>(smask_all + PT_W * nwords) + warp * pt_pairs(a.k);
     // the lane's points (never written inside a fit: loaded before the wait); a slot
     // beyond n holds a point 1e18 m away, where every q' is +inf and e exactly 0
     const int64_t base = (int64_t)cta * PT_PTS + (int64_t)warp * 32 * PT_P + lane;
@@ -648,17 +653,88 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         P.nmu[2] = f2(v6.x, v6.y);
     };
 
-    // ---- phase 1: every pair, the lane's points (two pairs per step)
+    // ---- phase 0: the pairs that can reach a point of the warp.  Over the box of
+    // the warp's points, two lower bounds of q' = |P'(x - mu)|^2 + (cmax - c):
+    //   |P'(x - mu)| >= |P'(ctr - mu)| - sum_j h_j |column j of P'|  (h: half-extents)
+    //   |P'(x - mu)|^2 >= sigma_min(P')^2 dist(mu, box)^2
+    // A component whose bound exceeds PT_REACH (with relative slack for the binary32
+    // rounding of the bound and of q' itself) has q' > 126 at every point of the warp,
+    // where ex2.approx.ftz gives exact zeros: skipping it leaves every sum unchanged.
+    int nlive = 0;
+    {
+        float lo[3], hi[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = INFINITY;
+            hi[j] = -INFINITY;
+        }
+#pragma unroll
+        for (int p = 0; p < PT_P; ++p)
+            if (valid[p])
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    lo[j] = fminf(lo[j], X[p][j].x);
+                    hi[j] = fmaxf(hi[j], X[p][j].x);
+                }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                lo[j] = fminf(lo[j], __shfl_xor_sync(FULL, lo[j], o));
+                hi[j] = fmaxf(hi[j], __shfl_xor_sync(FULL, hi[j], o));
+            }
+        const bool any_point = lo[0] <= hi[0];
+        float ctr[3], h[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            ctr[j] = 0.5f * (lo[j] + hi[j]);
+            h[j] = fmaxf(hi[j] - ctr[j], ctr[j] - lo[j]);
+        }
+        for (int j0 = 0; j0 < npairs; j0 += 32) {
+            const int pp = j0 + lane;
+            bool live = false;
+            if (any_point && pp < npairs) {
+                const float4* q = spar + (size_t)pp * 8;
+                const float4 v0 = q[0], v1 = q[1], v2 = q[2], v4 = q[4], v5 = q[5], v6 = q[6], v7 = q[7];
+                const float pc[2][6] = {{v0.x, v0.z, v1.x, v1.z, v2.x, v2.z}, {v0.y, v0.w, v1.y, v1.w, v2.y, v2.w}};
+                const float nm[2][3] = {{v5.x, v5.z, v6.x}, {v5.y, v5.w, v6.y}};
+                const float cc[2] = {v4.z, v4.w}, s2[2] = {v7.x, v7.y};
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const float room = PT_REACH - (cmax - cc[m]);   // q' budget left for |y|^2
+                    const float* P = pc[m];
+                    const float d0 = ctr[0] + nm[m][0], d1 = ctr[1] + nm[m][1], d2 = ctr[2] + nm[m][2];
+                    const float y0 = P[0] * d0, y1 = fmaf(P[2], d1, P[1] * d0);
+                    const float y2 = fmaf(P[5], d2, fmaf(P[4], d1, P[3] * d0));
+                    const float yy = fmaf(y2, y2, fmaf(y1, y1, y0 * y0));
+                    const float r = fmaf(h[0], sqrtf(fmaf(P[0], P[0], fmaf(P[1], P[1], P[3] * P[3]))),
+                                         fmaf(h[1], sqrtf(fmaf(P[2], P[2], P[4] * P[4])), h[2] * fabsf(P[5])));
+                    const float reach = (r + sqrtf(fmaxf(room, 0.f))) * (1.f + 1.f / 256.f);
+                    const float e0 = fmaxf(fabsf(d0) - h[0], 0.f), e1 = fmaxf(fabsf(d1) - h[1], 0.f),
+                                e2 = fmaxf(fabsf(d2) - h[2], 0.f);
+                    const float iso = s2[m] * fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) * (1.f - 1.f / 128.f);
+                    live = live || (room > 0.f && yy <= reach * reach && iso <= room);
+                }
+            }
+            const uint32_t m = __ballot_sync(FULL, live);
+            if (live) slist[nlive + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pp;
+            nlive += __popc(m);
+        }
+    }
+    __syncwarp();
+
+    // ---- phase 1: the reachable pairs, the lane's points (two pairs per step)
     if (STATS && lane < nwords) smask[lane] = 0u;
     __syncwarp();
     float2 tot[PT_P];
 #pragma unroll
     for (int p = 0; p < PT_P; ++p) tot[p] = f2(0.f, 0.f);
-    uint32_t word = 0u;
-    for (int pp = 0; pp < npairs; pp += 2) {
+    for (int i = 0; i < nlive; i += 2) {
+        const int pa = slist[i], pb = (i + 1 < nlive) ? (int)slist[i + 1] : -1;
         PairParams P0, P1;
-        load_pair(pp, P0);
-        load_pair(pp + 1, P1);
+        load_pair(pa, P0);
+        load_pair(pb < 0 ? pa : pb, P1);
+        if (pb < 0) P1.c = dup(INFINITY);   // no second pair: q' = inf, e = 0
         uint32_t nz0 = 0u, nz1 = 0u;   // OR of the bits of e: nonzero iff some e is
 #pragma unroll
         for (int p = 0; p < PT_P; ++p) {
@@ -673,15 +749,14 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             }
         }
         if (STATS) {
-            const uint32_t v0 = __ballot_sync(FULL, nz0 != 0u) ? 1u : 0u;
-            const uint32_t v1 = __ballot_sync(FULL, nz1 != 0u) ? 2u : 0u;
-            word |= (v0 | v1) << (pp & 31);
-            if ((pp & 31) == 30 || pp + 2 >= npairs) {
-                if (lane == 0) smask[pp >> 5] = word;
-                word = 0u;
+            const bool v0 = __ballot_sync(FULL, nz0 != 0u) != 0u, v1 = __ballot_sync(FULL, nz1 != 0u) != 0u;
+            if (lane == 0) {
+                if (v0) smask[pa >> 5] |= 1u << (pa & 31);
+                if (v1) smask[pb >> 5] |= 1u << (pb & 31);   // v1 implies pb >= 0
             }
         }
     }
+    __syncwarp();
 
     // ---- totals, log-likelihood, rare points
     float2 pr[PT_P];   // (shift, 1 / total) per point
@@ -1293,6 +1368,28 @@ __device__ bool build_component(int b, double w, const double mu[3], const doubl
     float m32[3] = {(float)mu[0], (float)mu[1], (float)mu[2]};
     for (int i = 0; i < 3; ++i) base[2 * (SLOT_NMU + i)] = -m32[i];
     base[2 * SLOT_W] = (float)w;
+    // lambda_max(Sigma) by the trigonometric solution of the characteristic cubic of a
+    // symmetric 3x3 matrix, raised by 1e-9 relative (an upper bound); its reciprocal
+    // times alpha^2, lowered by 1e-6 relative, bounds sigma_min(P')^2 from below
+    {
+        const double tr3 = (c[0] + c[3] + c[5]) / 3.0;
+        const double off = c[1] * c[1] + c[2] * c[2] + c[4] * c[4];
+        const double e0 = c[0] - tr3, e1 = c[3] - tr3, e2 = c[5] - tr3;
+        const double p2 = e0 * e0 + e1 * e1 + e2 * e2 + 2.0 * off;
+        double lmax = tr3;
+        if (p2 > 0.0) {
+            const double pp = sqrt(p2 / 6.0), ip = 1.0 / pp;
+            // det((Sigma - tr3 I) / pp) / 2
+            const double b00 = e0 * ip, b11 = e1 * ip, b22 = e2 * ip, b01 = c[1] * ip, b02 = c[2] * ip,
+                         b12 = c[4] * ip;
+            const double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                               b02 * (b01 * b12 - b11 * b02);
+            const double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+            lmax = tr3 + 2.0 * pp * cos(acos(r) / 3.0);
+        }
+        lmax = fmax(lmax, fmax(c[0], fmax(c[3], c[5]))) * (1.0 + 1e-9);
+        base[2 * SLOT_S] = (float)(alpha * alpha / lmax * (1.0 - 1e-6));
+    }
     shift4[b] = make_float4(m32[0], m32[1], m32[2], 0.f);
     double* m = model64 + (size_t)b * MODEL;
     m[0] = w;

@@ -408,6 +408,18 @@ gira_status gira_gmm_loglik_noalloc(const float *points, int64_t n, int k, const
 void gira_test_fail_next_allocations(int count);
 gira_status gira_test_bounded_wait(int mode, long long limit, void *stream);
 
+/*
+ * gira_test_point_order -- the spatial order the fits' E-steps visit points in:
+ * order[j] = the index of the j-th point after a stable sort of each instance
+ * (points[offsets[i] .. offsets[i+1]), or all n points when batch = 1 and
+ * offsets = NULL) by the Morton code of the point in the instance's bounding
+ * cube (6 bits per axis, cells of the largest extent / 64, clamped to [0, 63];
+ * code bit 3 b + a = bit b of the cell index on axis a).  points: device,
+ * n x 3 binary32; order: device, n ints; offsets: host, batch + 1 entries.
+ */
+gira_status gira_test_point_order(const float *points, int64_t n, int batch, const int64_t *offsets, int *order,
+                                  void *stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *gira_last_error_message(void);
 

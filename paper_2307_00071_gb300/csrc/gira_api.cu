@@ -646,13 +646,20 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         int *ksync, *perm;
         uint32_t* masks;
         unsigned long long* chg;
+        float4* p8s;
+        void* osc;
     } b{};
+    // the E-steps run on the points in a spatial order (a warp's points then reach
+    // fewer components); k-means++ and Lloyd on the caller's order
+    const bool sorted = !chunked;
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
         b.perm = cv.take<int>(k);
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * n : 0);
         b.p4 = cv.take<float4>(kinit ? n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)n);
+        b.p8s = cv.take<float4>(sorted ? 2 * (size_t)n : 0);
+        b.osc = cv.take<char>(sorted ? point_order_scratch_bytes(n, 1) : 0);
         b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
         b.shift4 = cv.take<float4>(k);
         b.model64 = cv.take<double>((size_t)k * MODEL);
@@ -702,6 +709,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         pts = b.pin;
     }
     COUNTED(prof, 1, launch_pack(pts, n, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
+    if (sorted) COUNTED(prof, 13, launch_point_order(b.p8, n, nullptr, nullptr, 0, 1, b.osc, b.p8s, nullptr, c.s));
     if (chunked) {
         GIRA_CUDA(upload_chunks(P, cb, c.s));
         b.params = cb.params;
@@ -766,7 +774,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         prof.t_em = prof.mark();
         if (final_loglik) GIRA_CUDA(chunk_lse(P, cb, b.p8, n, k, b.st, 0, true, &prof.launches, c.s));
     }
-    EStepLaunch a{b.p8, n, k, b.params, 0, b.partials, b.llp, nullptr, b.st, 0};
+    EStepLaunch a{sorted ? b.p8s : b.p8, n, k, b.params, 0, b.partials, b.llp, nullptr, b.st, 0};
     a.masks = b.masks;
     a.pt_rows = rows;
     for (int t = 1; t <= o.iters && !chunked; ++t) {
@@ -2294,6 +2302,60 @@ gira_status gira_test_bounded_wait(int mode, long long limit, void* stream) {
     GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
     GIRA_CUDA(cudaMemsetAsync(b.ints, 0, sizeof(int) * 2, c.s));
     GIRA_CUDA(launch_wait_probe(mode, limit, b.ints, b.ints + 1, b.st, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
+    GIRA_CUDA(cudaStreamSynchronize(c.s));
+    return device_status(h);
+}
+
+gira_status gira_test_point_order(const float* points, int64_t n, int batch, const int64_t* offsets, int* order,
+                                  void* stream) {
+    reset_error();
+    if (n < 1 || batch < 1 || !points || !order) return fail(GIRA_ERR_INVALID_ARG, "n, batch, points or order");
+    if (batch > 1 && !offsets) return fail(GIRA_ERR_INVALID_ARG, "offsets is NULL with batch > 1");
+    std::vector<int64_t> offs(batch + 1);
+    if (offsets) offs.assign(offsets, offsets + batch + 1);
+    else offs = {0, n};
+    if (offs[0] != 0 || offs[batch] != n) return fail(GIRA_ERR_INVALID_ARG, "offsets must run from 0 to n");
+    for (int i = 0; i < batch; ++i)
+        if (offs[i + 1] <= offs[i]) return fail(GIRA_ERR_INVALID_ARG, "instance %d is empty", i);
+    Ctx c;
+    TRY(begin(c, stream));
+    Kind kp, ko;
+    TRY(check_ptr(points, "points", c.dev, &kp));
+    TRY(check_ptr(order, "order", c.dev, &ko));
+    if (kp != Kind::Device || ko != Kind::Device) return fail(GIRA_ERR_INVALID_ARG, "points and order: device");
+    const int64_t nunits = point_order_box_units(offs.data(), batch);
+    std::vector<int2> units((size_t)nunits);
+    point_order_fill_units(offs.data(), batch, units.data());
+    struct Bufs {
+        DeviceState* st;
+        float4* p8;
+        int64_t* offs;
+        int2* units;
+        void* osc;
+    } b{};
+    auto layout = [&](Carver& cv) {
+        b.st = cv.take<DeviceState>(1);
+        b.p8 = cv.take<float4>(2 * (size_t)n);
+        b.offs = cv.take<int64_t>(batch + 1);
+        b.units = cv.take<int2>((size_t)nunits);
+        b.osc = cv.take<char>(point_order_scratch_bytes(n, batch));
+    };
+    Carver sizer;
+    layout(sizer);
+    DeviceWs* ws = ws_for(c.dev);
+    std::lock_guard<std::mutex> lk(ws->mu);
+    TRY(ensure(ws, sizer.off, c.s));
+    Carver cv;
+    cv.base = static_cast<char*>(ws->ptr);
+    layout(cv);
+    DeviceState h{};
+    h.bad_component = INT_MAX;
+    GIRA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.offs, offs.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, c.s));
+    GIRA_CUDA(launch_pack(points, n, nullptr, b.p8, b.st, c.s));
+    GIRA_CUDA(launch_point_order(b.p8, n, b.offs, b.units, (int)nunits, batch, b.osc, nullptr, order, c.s));
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaStreamSynchronize(c.s));
     return device_status(h);

@@ -388,6 +388,18 @@ int params_pairs_padded(int k);
 
 // N x 3 -> pts4 (x,y,z,0) (nullable) and pts8 (x,x,y,y)(z,z,0,0); flags non-finite input.
 cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, float4* pts8, DeviceState* st, cudaStream_t s);
+// Spatial order of packed points (order_kernels.cu): a stable radix sort by
+// (instance, 18-bit Morton code in the instance's bounding cube).  offsets_d /
+// units_d: the batch's point offsets and its (instance, chunk) bounding-box
+// blocks (point_order_fill_units), or nullptr for one instance of n points.
+// Writes the sorted points to p8_out and, if order_out, the source index of
+// every sorted point.  scratch: point_order_scratch_bytes(n, batch) bytes.
+int64_t point_order_box_units(const int64_t* offsets, int batch);
+void point_order_fill_units(const int64_t* offsets, int batch, int2* units);
+size_t point_order_scratch_bytes(int64_t n, int batch);
+cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offsets_d, const int2* units_d,
+                               int nunits, int batch, void* scratch, float4* p8_out, int* order_out,
+                               cudaStream_t s);
 cudaError_t launch_fill_padding(float* params, int k, int npairs_pad, cudaStream_t s);
 // Sum of the per-CTA log-likelihoods into st->ll_sum (fixed order).
 cudaError_t launch_ll_reduce(const double* ll_partials, int grid, DeviceState* st, cudaStream_t s);

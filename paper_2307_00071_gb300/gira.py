@@ -69,6 +69,8 @@ def _load():
     lib.gira_test_fail_next_allocations.restype = None
     lib.gira_test_bounded_wait.argtypes = [C.c_int, C.c_longlong, vp]
     lib.gira_test_bounded_wait.restype = C.c_int
+    lib.gira_test_point_order.argtypes = [vp, i64, C.c_int, vp, vp, vp]
+    lib.gira_test_point_order.restype = C.c_int
     for f in ("gira_gmm_fit4", "gira_gmm_loglik4", "gira_gmm_conditional4", "gira_gmm_sample", "gira_gbms"):
         getattr(lib, f).restype = C.c_int
     for f in ("gira_kmeans_init", "gira_gmm_fit", "gira_gmm_loglik", "gira_release_workspace"):
@@ -503,6 +505,19 @@ def gira_gbms(points, bandwidth: float, max_iter: int = 300):
 def gira_test_fail_next_allocations(count: int):
     """The next ``count`` workspace allocations fail with ERR_OOM (0 clears)."""
     _lib.gira_test_fail_next_allocations(count)
+
+
+def gira_test_point_order(points, offsets=None):
+    """The order the fits' E-steps visit the points in (torch int32 on the points' device)."""
+    import torch
+    n = int(points.shape[0])
+    offs = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
+    batch = 1 if offs is None else len(offs) - 1
+    order = torch.empty(n, dtype=torch.int32, device=points.device)
+    s = torch.cuda.current_stream(points.device).cuda_stream
+    _check(_lib.gira_test_point_order(points.data_ptr(), n, batch, None if offs is None else offs.ctypes.data,
+                                      order.data_ptr(), s))
+    return order
 
 
 def gira_test_bounded_wait(mode: int, limit: int) -> int:

@@ -42,6 +42,10 @@ METRIC = "EM point-component-iters/sec and ms per 300k-pt K=512 frame; % FP32/SF
 UNIT = "point-component-iters/s"
 K, ITERS, TOL, REG, SEED, LLOYD = 512, 30, 1e-4, 1e-6, 0, 10
 FP32_OPS_PER_UNIT = 23          # algorithmic FP32-pipe operations per (point, component, iteration)
+# the point-stationary E-step's FP32-pipe lane operations per (component pair, point) it evaluates:
+# reach-listed pairs (q' of both components, exp2 argument, running total) and live pairs
+# (q' again, responsibilities, 10 statistics of both components)
+PT_OPS_NEAR, PT_OPS_LIVE, PT_WARP_POINTS = 26, 54, 128
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "estep_frame276k_k512.traffic.json")
@@ -820,7 +824,15 @@ def run_gira(args):
         peak_units = FP32_LANES_PER_SM * sms * mhz * 1e6 / FP32_OPS_PER_UNIT
         est_launches = max(prof["estep_launches"], 1)
         avg_estep_s = prof["estep_ms"] / est_launches / 1e3
-        achieved = n * K / avg_estep_s if avg_estep_s > 0 else 0.0
+        dense = n * K / avg_estep_s if avg_estep_s > 0 else 0.0
+        # FP32 lane operations the E-step issued per launch: the pairs within reach of a
+        # warp's points and the live pairs, counted by the kernel, times their op counts
+        near = prof["estep_pairs_near"] / est_launches
+        live = prof["estep_pairs_live"] / est_launches
+        slots = max(prof["estep_pair_slots"] / est_launches, 1.0)
+        ops = PT_WARP_POINTS * (PT_OPS_NEAR * near + PT_OPS_LIVE * live)
+        achieved = ops / avg_estep_s if avg_estep_s > 0 else 0.0
+        peak_ops = FP32_LANES_PER_SM * sms * mhz * 1e6
         tr = traffic_per_launch()
         line = {
             "metric": METRIC, "value": units_all / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -831,12 +843,19 @@ def run_gira(args):
                              "em_only": prof["em_ms"] / args.steps, "init": prof["init_ms"] / args.steps},
             "em_only_units_per_s": n * K * prof["em_iters"] / (prof["em_ms"] / 1e3) if prof["em_ms"] else None,
             "iters_done": iters_seen,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_units, "unit": UNIT,
-                         "frac": achieved / peak_units, "traffic": tr,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "FP32 lane-op/s",
+                         "frac": achieved / peak_ops, "traffic": tr,
                          "kernel": prof["estep_kernel"],
                          "launch_ms": avg_estep_s * 1e3, "launches_timed": prof["estep_launches"],
-                         "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {mhz:.0f} MHz ({mhz_src}) / "
-                                       f"{FP32_OPS_PER_UNIT} FP32 ops per unit"},
+                         "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {mhz:.0f} MHz ({mhz_src})",
+                         "achieved_basis": f"per launch {near:.0f} warp-pairs evaluated x {PT_WARP_POINTS} points x "
+                                           f"{PT_OPS_NEAR} ops + {live:.0f} live warp-pairs x {PT_WARP_POINTS} "
+                                           f"x {PT_OPS_LIVE} ops (counted by the kernel)",
+                         "pairs_evaluated_frac": near / slots, "pairs_live_frac": live / slots,
+                         "dense_equivalent": {"units_per_s": dense, "peak_units_per_s": peak_units,
+                                              "frac": dense / peak_units,
+                                              "basis": f"N x K per launch against {FP32_OPS_PER_UNIT} FP32 ops "
+                                                       f"per unit at the dense rate"}},
             "e2e": {"value": e2e_units_all / e2e_tmax, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernel_launches"],

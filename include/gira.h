@@ -342,6 +342,12 @@ typedef struct {
     double em_ms;               /* the EM loop: E-step, reduction and FP64 finalize of every iteration */
     double total_ms;            /* whole calls, first upload to last download */
     char estep_kernel[128];     /* name of the last E-step kernel timed launch by launch ("" if none) */
+    /* gira_gmm_fit's point-stationary E-step, over the launches timed launch by launch
+       (warps x component pairs): the pairs a dense E-step would evaluate, those within
+       reach of the warp's points (evaluated), and those with statistics */
+    long long estep_pair_slots;
+    long long estep_pairs_near;
+    long long estep_pairs_live;
 } gira_profile;
 
 /*

@@ -557,6 +557,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     __shared__ __align__(8) uint64_t bar_tma;
     __shared__ int s_skip, s_norm, s_dead;
     __shared__ double s_ll[PT_W];
+    __shared__ unsigned s_pairs[PT_W][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int cta = blockIdx.x;
     // the instance's first point (batched launches); the loads below index the
@@ -805,6 +806,12 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             smask[lane] = (lo + 32 <= npairs) ? 0xffffffffu : (lo < npairs) ? ((1u << (npairs - lo)) - 1u) : 0u;
         }
         __syncwarp();
+        if (lane == 0) {
+            unsigned live = 0;
+            for (int wd = 0; wd < nwords; ++wd) live += __popc(smask[wd]);
+            s_pairs[warp][0] = (unsigned)nlive;
+            s_pairs[warp][1] = live;
+        }
         // ---- phase 2: the live pairs; partials [k * NSTAT][rows], masks [nwords][rows]
         const int64_t gw = (int64_t)cta * PT_W + warp;
         const int64_t rows = a.pt_rows;
@@ -853,6 +860,15 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         double v = s_ll[0];
         for (int w = 1; w < PT_W; ++w) v += s_ll[w];
         a.ll_partials[cta] = v * LN2;
+        if (STATS) {
+            unsigned long long near = 0, live = 0;
+            for (int w = 0; w < PT_W; ++w) {
+                near += s_pairs[w][0];
+                live += s_pairs[w][1];
+            }
+            atomicAdd(&a.st->pairs_near, near);
+            atomicAdd(&a.st->pairs_live, live);
+        }
     }
 }
 

@@ -211,6 +211,7 @@ struct CallProfile {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> estep;
     std::string estep_name;   // the kernel those event pairs bracket
     long long launches = 0;
+    long long pair_slots = 0, pairs_near = 0, pairs_live = 0;   // point-stationary E-step pair counts
 
     void timed(cudaEvent_t e0, cudaEvent_t e1) {
         estep.emplace_back(e0, e1);
@@ -245,6 +246,11 @@ struct CallProfile {
         if (!on) return;
         for (int i = 0; i < (int)estep.size() && i < estep_done; ++i) g_prof.estep_ms += ms(estep[i].first, estep[i].second);
         g_prof.estep_launches += std::min<long long>((long long)estep.size(), estep_done);
+        if (per_launch) {
+            g_prof.estep_pair_slots += pair_slots;
+            g_prof.estep_pairs_near += pairs_near;
+            g_prof.estep_pairs_live += pairs_live;
+        }
         if (!estep_name.empty()) {
             std::strncpy(g_prof.estep_kernel, estep_name.c_str(), sizeof g_prof.estep_kernel - 1);
             g_prof.estep_kernel[sizeof g_prof.estep_kernel - 1] = 0;
@@ -709,7 +715,9 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         pts = b.pin;
     }
     COUNTED(prof, 1, launch_pack(pts, n, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
-    if (sorted) COUNTED(prof, 13, launch_point_order(b.p8, n, nullptr, nullptr, 0, 1, b.osc, b.p8s, nullptr, c.s));
+    if (sorted)
+        COUNTED(prof, point_order_launches(1),
+                launch_point_order(b.p8, n, nullptr, nullptr, 0, 1, b.osc, b.p8s, nullptr, c.s));
     if (chunked) {
         GIRA_CUDA(upload_chunks(P, cb, c.s));
         b.params = cb.params;
@@ -809,6 +817,11 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
     prof.t_end = prof.mark();
     GIRA_CUDA(cudaStreamSynchronize(c.s));
+    if (!chunked) {
+        prof.pair_slots = (long long)h.iters_done * rows * ((((k + 1) >> 1) + 1) & ~1);
+        prof.pairs_near = (long long)h.pairs_near;
+        prof.pairs_live = (long long)h.pairs_live;
+    }
     prof.commit(h.iters_done, h.iters_done);
     TRY(device_status(h));
     if (iters_done) *iters_done = h.iters_done;
@@ -1159,7 +1172,14 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         unsigned long long* chg;
         KppInst *ktab, *kseed;
         BatchUnit* lunits;
+        float4* p8s;
+        int2* ounits;
+        void* osc;
     } b{};
+    // the E-steps run on every instance's points in a spatial order
+    const int64_t nounits = point_order_box_units(offsets, batch);
+    std::vector<int2> ounits((size_t)nounits);
+    point_order_fill_units(offsets, batch, ounits.data());
     // KInit tables: every instance; the seeding clusters grouped by cluster size
     // (instances beyond one 16-CTA cluster are seeded alone); Lloyd tiles
     std::vector<KppInst> ktab(batch);
@@ -1191,6 +1211,9 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * (size_t)total_n : 0);
         b.p4 = cv.take<float4>(kinit ? (size_t)total_n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)total_n);
+        b.p8s = cv.take<float4>(2 * (size_t)total_n);
+        b.ounits = cv.take<int2>((size_t)nounits);
+        b.osc = cv.take<char>(point_order_scratch_bytes(total_n, batch));
         b.params = cv.take<float>((size_t)par_floats);
         b.shift4 = cv.take<float4>(total_k);
         b.model64 = cv.take<double>((size_t)total_k * MODEL);
@@ -1255,6 +1278,9 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         pts = b.pin;
     }
     COUNTED(prof, 1, launch_pack_batched(pts, total_n, b.offs, batch, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
+    GIRA_CUDA(cudaMemcpyAsync(b.ounits, ounits.data(), sizeof(int2) * ounits.size(), cudaMemcpyHostToDevice, c.s));
+    COUNTED(prof, point_order_launches(batch),
+            launch_point_order(b.p8, total_n, b.offs, b.ounits, (int)nounits, batch, b.osc, b.p8s, nullptr, c.s));
     COUNTED(prof, 1, launch_fill_padding_batched(b.params, b.insts, batch, 0, b.npairs, c.s));
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
@@ -1308,7 +1334,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                                                      b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
 
-    EStepLaunch base{b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
+    EStepLaunch base{b.p8s, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
     base.insts = b.insts;
     base.units = b.units;
     base.states = b.st;

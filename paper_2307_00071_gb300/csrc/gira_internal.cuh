@@ -42,6 +42,9 @@ struct DeviceState {
     double prev_ll;        // l_{t-1}
     double ll_sum;         // sum_n lse_n of the last E-step (natural log)
     int64_t chosen_last;   // k-means++: index chosen by the last select step
+    // point-stationary E-step with statistics, summed over its launches: warp x pair
+    // evaluations made (pairs within reach of the warp's box) and with statistics
+    unsigned long long pairs_near, pairs_live;
 };
 
 __device__ __forceinline__ void set_error(DeviceState* st, int code) { atomicCAS(&st->error, 0, code); }
@@ -397,6 +400,7 @@ cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, float4* pts8
 int64_t point_order_box_units(const int64_t* offsets, int batch);
 void point_order_fill_units(const int64_t* offsets, int batch, int2* units);
 size_t point_order_scratch_bytes(int64_t n, int batch);
+int point_order_launches(int batch);   // kernels one launch_point_order makes
 cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offsets_d, const int2* units_d,
                                int nunits, int batch, void* scratch, float4* p8_out, int* order_out,
                                cudaStream_t s);

@@ -300,6 +300,8 @@ void point_order_fill_units(const int64_t* offsets, int batch, int2* units) {
         for (int64_t c = 0; c * BOX_CHUNK < offsets[i + 1] - offsets[i]; ++c) units[u++] = make_int2(i, (int)c);
 }
 
+int point_order_launches(int batch) { return 3 + 5 * radix_passes(batch); }
+
 size_t point_order_scratch_bytes(int64_t n, int batch) {
     const int64_t ntiles = ceil_div(n, TILE);
     const int64_t m = ntiles * RADIX;

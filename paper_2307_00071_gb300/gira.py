@@ -37,7 +37,8 @@ class FitOpts(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("calls", C.c_longlong), ("kernel_launches", C.c_longlong), ("estep_launches", C.c_longlong),
                 ("estep_ms", C.c_double), ("em_iters", C.c_longlong), ("init_ms", C.c_double), ("em_ms", C.c_double),
-                ("total_ms", C.c_double), ("estep_kernel", C.c_char * 128)]
+                ("total_ms", C.c_double), ("estep_kernel", C.c_char * 128), ("estep_pair_slots", C.c_longlong),
+                ("estep_pairs_near", C.c_longlong), ("estep_pairs_live", C.c_longlong)]
 
 
 def _load():

@@ -462,15 +462,28 @@ __device__ __forceinline__ bool kc_wait(uint64_t* bar, uint32_t parity) {
 
 size_t kc_smem_bytes() { return (size_t)3 * KC_PMAX * KC_THREADS * sizeof(float2) + sizeof(KcShared) + 16; }
 
-// fx48(d) for 0 <= d < 2^10 as a 64-bit integer (36 of them sum below 2^64);
-// raises `big` for larger d, whose callers take the 128-bit fx48.
-__device__ __forceinline__ unsigned long long fx48_small(float d, bool& big) {
-    const unsigned bits = __float_as_uint(d);
-    const int ex = (int)(bits >> 23);
-    big |= ex >= 137;
-    const unsigned long long mant = (bits & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
-    const int sh = (ex ? ex : 1) - 102;   // d * 2^48 = mant * 2^sh
-    return sh >= 0 ? mant << min(sh, 63) : mant >> min(-sh, 63);
+// fx48(d) = floor(d 2^48) for 0 <= d < 2^10, on the FMA pipe: d 2^48 = h 2^35 +
+// m 2^12 + l with integers h, m < 2^23 and l < 2^12.  Each piece is taken exactly
+// by a round-toward-zero fused multiply-add onto 2^23 (binary32's integer grid on
+// [2^23, 2^24)), whose bit pattern is then 0x4B000000 + the piece; the remainders
+// d - h 2^-13 and r1 - m 2^-36 are exact (they keep low bits of d's significand).
+// The three bit patterns are summed in 32-bit integers (fx48_join removes the
+// biases; 36 pieces stay below 2^32).
+__device__ __forceinline__ void fx48_parts(float d, unsigned& ah, unsigned& am, unsigned& al) {
+    const float y1 = __fmaf_rz(d, 0x1p13f, 0x1p23f);
+    const float r1 = fmaf(-(y1 - 0x1p23f), 0x1p-13f, d);
+    const float y2 = __fmaf_rz(r1, 0x1p36f, 0x1p23f);
+    const float r2 = fmaf(-(y2 - 0x1p23f), 0x1p-36f, r1);
+    const float y3 = __fmaf_rz(r2, 0x1p48f, 0x1p23f);
+    ah += __float_as_uint(y1);
+    am += __float_as_uint(y2);
+    al += __float_as_uint(y3);
+}
+// the sum of `count` fx48_parts terms (below 2^64 for count <= 36)
+__device__ __forceinline__ unsigned long long fx48_join(unsigned ah, unsigned am, unsigned al, unsigned count) {
+    const unsigned bias = count * 0x4B000000u;
+    return ((unsigned long long)(ah - bias) << 35) + ((unsigned long long)(am - bias) << 12) +
+           (unsigned long long)(al - bias);
 }
 
 // table (batched seeding): cluster c of the launch seeds instance table[c]; the
@@ -564,13 +577,15 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         }
         if (changed) {
             bool big = false;   // a weight >= 2^10: sum in 128 bits
-            unsigned long long s64 = 0ull;
+            unsigned ah = 0u, am = 0u, al = 0u;
 #pragma unroll
-            for (int p = 0; p < KC_PMAX; ++p) {
-                if (2 * p < mcnt) s64 += fx48_small(D[p].x, big);
-                if (2 * p + 1 < mcnt) s64 += fx48_small(D[p].y, big);
+            for (int p = 0; p < KC_PMAX; ++p) {   // padding points add fx48(0) = 0
+                const float dx = (2 * p < mcnt) ? D[p].x : 0.f, dy = (2 * p + 1 < mcnt) ? D[p].y : 0.f;
+                big |= !(dx < 1024.f) || !(dy < 1024.f);
+                fx48_parts(dx, ah, am, al);
+                fx48_parts(dy, ah, am, al);
             }
-            ls = u128{s64, 0ull};
+            ls = u128{fx48_join(ah, am, al, 2 * KC_PMAX), 0ull};
             if (big) {
                 ls = u128{0ull, 0ull};
 #pragma unroll

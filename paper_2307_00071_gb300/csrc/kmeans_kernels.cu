@@ -413,7 +413,18 @@ struct KcShared {
     uint64_t bar_sum[2], bar_cen[2];
     u128 rel;
     int win, mode;
+    float2 dsrc[KC_PMAX];      // the D^2 of the lane holding the chosen point
 };
+
+// Inclusive warp scan of 64-bit integers (exact).
+__device__ __forceinline__ unsigned long long u64_warp_incl_scan(unsigned long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
 
 // st.async: a store into a peer CTA's shared memory that completes its byte
 // count on the peer's mbarrier (release at cluster scope); addresses in the
@@ -656,24 +667,35 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 const u128 base = u128_sub(u128_shfl(linc, src), u128_shfl(ls, src));
                 const u128 rel2 = u128_sub(wrel, base);
                 const int cnt = __shfl_sync(FULL, mcnt, src);
-                float a0 = 0.f, a1 = 0.f;
+                // the src lane's weights through shared memory: lane l takes points 2l, 2l + 1;
+                // the hit is the first point whose running sum from the lane's start exceeds rel2
+                if (lane == src) {
 #pragma unroll
-                for (int p = 0; p < KC_PMAX; ++p) {
-                    const float vx = __shfl_sync(FULL, D[p].x, src), vy = __shfl_sync(FULL, D[p].y, src);
-                    if (lane == ((2 * p) & 31)) {
-                        if (2 * p < 32) a0 = vx; else a1 = vx;
-                    }
-                    if (lane == ((2 * p + 1) & 31)) {
-                        if (2 * p + 1 < 32) a0 = vy; else a1 = vy;
-                    }
+                    for (int p = 0; p < KC_PMAX; ++p) sh.dsrc[p] = D[p];
                 }
-                const u128 u0 = (lane < cnt) ? fx48(a0) : u128{0ull, 0ull};
-                const u128 u1 = (32 + lane < cnt) ? fx48(a1) : u128{0ull, 0ull};
-                const u128 p0 = u128_warp_incl_scan(u0, lane);
-                const u128 p1 = u128_add(u128_warp_incl_scan(u1, lane), u128_shfl(p0, 31));
-                const unsigned h0 = __ballot_sync(FULL, lane < cnt && u128_gt(p0, rel2));
-                const unsigned h1 = __ballot_sync(FULL, 32 + lane < cnt && u128_gt(p1, rel2));
-                const int qf = h0 ? __ffs(h0) - 1 : (h1 ? 32 + __ffs(h1) - 1 : 0);   // some hit: exact search
+                __syncwarp();
+                const float2 dl = (lane < KC_PMAX) ? sh.dsrc[lane] : f2(0.f, 0.f);
+                const float a0 = (2 * lane < cnt) ? dl.x : 0.f, a1 = (2 * lane + 1 < cnt) ? dl.y : 0.f;
+                int qf;
+                if (__all_sync(FULL, a0 < 1024.f && a1 < 1024.f)) {   // the lane's sum is below 2^64
+                    unsigned h0 = 0u, m0 = 0u, l0 = 0u, h1 = 0u, m1 = 0u, l1 = 0u;
+                    fx48_parts(a0, h0, m0, l0);
+                    fx48_parts(a1, h1, m1, l1);
+                    const unsigned long long f0 = fx48_join(h0, m0, l0, 1), f1 = fx48_join(h1, m1, l1, 1);
+                    const unsigned long long inc2 = u64_warp_incl_scan(f0 + f1, lane);
+                    const unsigned long long r = rel2.lo;   // rel2 < the lane's sum < 2^64
+                    const unsigned hh = __ballot_sync(FULL, inc2 > r);   // rel2 < the sum: not empty
+                    const int hl = hh ? __ffs(hh) - 1 : 0;
+                    const bool second = inc2 - f1 <= r;   // point 2l reaches no further than rel2
+                    qf = 2 * hl + (__shfl_sync(FULL, second ? 1 : 0, hl));
+                } else {
+                    const u128 u0 = fx48(a0), u1 = fx48(a1);
+                    const u128 inc2 = u128_warp_incl_scan(u128_add(u0, u1), lane);
+                    const unsigned hh = __ballot_sync(FULL, u128_gt(inc2, rel2));
+                    const int hl = hh ? __ffs(hh) - 1 : 0;
+                    const bool second = !u128_gt(u128_sub(inc2, u1), rel2);
+                    qf = 2 * hl + (__shfl_sync(FULL, second ? 1 : 0, hl));
+                }
                 const int ft = warp * 32 + src;   // the src lane's column in xs / ys / zs
                 const float2 px = xs[(qf >> 1) * KC_THREADS + ft], py = ys[(qf >> 1) * KC_THREADS + ft],
                              pz = zs[(qf >> 1) * KC_THREADS + ft];

@@ -1385,26 +1385,27 @@ __device__ bool build_component(int b, double w, const double mu[3], const doubl
     for (int i = 0; i < 3; ++i) base[2 * (SLOT_NMU + i)] = -m32[i];
     base[2 * SLOT_W] = (float)w;
     // lambda_max(Sigma) by the trigonometric solution of the characteristic cubic of a
-    // symmetric 3x3 matrix, raised by 1e-9 relative (an upper bound); its reciprocal
-    // times alpha^2, lowered by 1e-6 relative, bounds sigma_min(P')^2 from below
+    // symmetric 3x3 matrix, in binary32 (its error is a few ulps of lambda_max), raised
+    // by 1e-4 relative to an upper bound; trace(Sigma) where the cubic is degenerate.
+    // alpha^2 over it, lowered by 1e-4 relative, bounds sigma_min(P')^2 from below.
     {
-        const double tr3 = (c[0] + c[3] + c[5]) / 3.0;
-        const double off = c[1] * c[1] + c[2] * c[2] + c[4] * c[4];
-        const double e0 = c[0] - tr3, e1 = c[3] - tr3, e2 = c[5] - tr3;
-        const double p2 = e0 * e0 + e1 * e1 + e2 * e2 + 2.0 * off;
-        double lmax = tr3;
-        if (p2 > 0.0) {
-            const double pp = sqrt(p2 / 6.0), ip = 1.0 / pp;
-            // det((Sigma - tr3 I) / pp) / 2
-            const double b00 = e0 * ip, b11 = e1 * ip, b22 = e2 * ip, b01 = c[1] * ip, b02 = c[2] * ip,
-                         b12 = c[4] * ip;
-            const double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                               b02 * (b01 * b12 - b11 * b02);
-            const double r = fmin(1.0, fmax(-1.0, 0.5 * det));
-            lmax = tr3 + 2.0 * pp * cos(acos(r) / 3.0);
+        const float a00 = (float)c[0], a01 = (float)c[1], a02 = (float)c[2], a11 = (float)c[3], a12 = (float)c[4],
+                    a22 = (float)c[5];
+        const float tr3 = (a00 + a11 + a22) * (1.f / 3.f);
+        const float e0 = a00 - tr3, e1 = a11 - tr3, e2 = a22 - tr3;
+        const float p2 = e0 * e0 + e1 * e1 + e2 * e2 + 2.f * (a01 * a01 + a02 * a02 + a12 * a12);
+        float lmax = 3.f * tr3;
+        if (p2 > 1e-30f) {
+            const float pp = sqrtf(p2 * (1.f / 6.f)), ip = 1.f / pp;
+            const float b00 = e0 * ip, b11 = e1 * ip, b22 = e2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+            const float det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                              b02 * (b01 * b12 - b11 * b02);
+            const float r = fminf(1.f, fmaxf(-1.f, 0.5f * det));
+            const float trig = tr3 + 2.f * pp * cosf(acosf(r) * (1.f / 3.f));
+            if (trig == trig) lmax = fminf(lmax, trig * (1.f + 1e-4f));
         }
-        lmax = fmax(lmax, fmax(c[0], fmax(c[3], c[5]))) * (1.0 + 1e-9);
-        base[2 * SLOT_S] = (float)(alpha * alpha / lmax * (1.0 - 1e-6));
+        lmax = fmaxf(lmax, fmaxf(a00, fmaxf(a11, a22)) * (1.f + 1e-4f));
+        base[2 * SLOT_S] = (float)(alpha * alpha) / lmax * (1.f - 1e-4f);
     }
     shift4[b] = make_float4(m32[0], m32[1], m32[2], 0.f);
     double* m = model64 + (size_t)b * MODEL;
@@ -1446,35 +1447,60 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
     }
 }
 
-// The same for per-warp partials of the point-stationary E-step ([k * NSTAT][rows],
-// live masks [nwords][rows]): only the rows whose warp's mask has the pair's bit
-// are read (the others were not written); fixed slices of warps, eight loads in
-// flight per thread, binary64 in warp order, slices summed in order.
+// The statistics of the pair of components b0, b0 + 1 (b0 even) from the per-warp
+// partial rows of the point-stationary E-step, in binary64: the rows whose live
+// mask has the pair's bit are listed in row order (segments of FIN_SEG rows,
+// compacted in shared memory), every output sums FIN_SPLIT fixed contiguous
+// slices of that list in binary32 groups of 8 and binary64 across groups, and
+// the slices are added in order.  The list depends only on the masks, so the
+// order of every addition is fixed.  Call with every thread of the block.
+constexpr int FIN_SEG = 4096;
 __device__ void reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
                                        int b0, int nout, double (*part)[FIN_CPB * NSTAT], double* S) {
-    const int t = threadIdx.x;
+    __shared__ uint16_t s_list[FIN_SEG];
+    __shared__ int s_wcnt[FIN_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
-    if (o < nout) {
-        const int b = b0 + o / NSTAT;
-        const uint32_t* mrow = masks + (size_t)((b >> 1) >> 5) * rows;
-        const uint32_t bit = 1u << ((b >> 1) & 31);
-        const float* src = partials + ((size_t)b0 * NSTAT + o) * rows;
-        const int w0 = q * rows / FIN_SPLIT, w1 = (q + 1) * rows / FIN_SPLIT;
-        double acc = 0.0;
-        for (int w = w0; w < w1; w += 8) {
-            uint32_t mk[8];
+    const uint32_t* mrow = masks + (size_t)((b0 >> 1) >> 5) * rows;
+    const uint32_t bit = 1u << ((b0 >> 1) & 31);
+    const float* src = partials + ((size_t)b0 * NSTAT + o) * rows;
+    double acc = 0.0;
+    for (int seg0 = 0; seg0 < rows; seg0 += FIN_SEG) {
+        const int seg1 = min(rows, seg0 + FIN_SEG);
+        int nl = 0;   // live rows listed so far in this segment (the same in every thread)
+        for (int r0 = seg0; r0 < seg1; r0 += FIN_THREADS) {
+            const int r = r0 + t;
+            const bool live = r < seg1 && (__ldg(mrow + r) & bit);
+            const uint32_t m = __ballot_sync(FULL, live);
+            if (lane == 0) s_wcnt[warp] = __popc(m);
+            __syncthreads();
+            int off = nl, total = 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) mk[u] = (w + u < w1) ? __ldg(mrow + w + u) : 0u;
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (mk[u] & bit) ? __ldcg(src + w + u) : 0.f;
-            float f = 0.f;   // binary32 groups of 8 (GB300 runs binary64 at 1/64 of the binary32 rate)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) f += v[u];
-            acc += (double)f;
+            for (int w = 0; w < FIN_THREADS / 32; ++w) {
+                const int c = s_wcnt[w];
+                off += (w < warp) ? c : 0;
+                total += c;
+            }
+            if (live) s_list[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(r - seg0);
+            nl += total;
+            __syncthreads();
         }
-        part[q][o] = acc;
+        if (o < nout) {
+            const int c0 = q * nl / FIN_SPLIT, c1 = (q + 1) * nl / FIN_SPLIT;
+            const float* sseg = src + seg0;
+            for (int c = c0; c < c1; c += 8) {   // eight loads in flight
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = (c + u < c1) ? __ldcg(sseg + s_list[c + u]) : 0.f;
+                float f = 0.f;   // binary32 groups of 8 (GB300 runs binary64 at 1/64 of the binary32 rate)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) f += v[u];
+                acc += (double)f;
+            }
+        }
+        __syncthreads();   // the list is rebuilt for the next segment
     }
+    if (o < nout) part[q][o] = acc;
     __syncthreads();
     if (t < nout) {
         double v = 0.0;
@@ -1774,7 +1800,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_components_kernel(const d
                                                                         DeviceState* st,
                                                                         const BatchInst* __restrict__ insts) {
     extern __shared__ unsigned long long keys[];   // kp2 = power of two >= k
-    __shared__ double s_lo[3][32], s_hi[3][32];
+    __shared__ float s_lo[3][32], s_hi[3][32];
     if (insts) {
         const BatchInst I = insts[blockIdx.x];
         k = I.k;
@@ -1788,18 +1814,19 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_components_kernel(const d
         while (kp2 < k) kp2 <<= 1;
     }
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    // binary32 (the order only needs coarse cells; rounding to binary32 keeps min and max)
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = t; b < k; b += blockDim.x)
         for (int i = 0; i < 3; ++i) {
-            const double v = old[(size_t)b * MODEL + 1 + i];
-            lo[i] = fmin(lo[i], v);
-            hi[i] = fmax(hi[i], v);
+            const float v = (float)old[(size_t)b * MODEL + 1 + i];
+            lo[i] = fminf(lo[i], v);
+            hi[i] = fmaxf(hi[i], v);
         }
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            lo[i] = fmin(lo[i], __shfl_xor_sync(FULL, lo[i], o));
-            hi[i] = fmax(hi[i], __shfl_xor_sync(FULL, hi[i], o));
+            lo[i] = fminf(lo[i], __shfl_xor_sync(FULL, lo[i], o));
+            hi[i] = fmaxf(hi[i], __shfl_xor_sync(FULL, hi[i], o));
         }
         if (lane == 0) {
             s_lo[i][warp] = lo[i];
@@ -1808,22 +1835,23 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_components_kernel(const d
     }
     __syncthreads();
     const int nw = blockDim.x >> 5;
+    float scale[3];
     for (int i = 0; i < 3; ++i) {
         lo[i] = s_lo[i][0];
         hi[i] = s_hi[i][0];
         for (int w = 1; w < nw; ++w) {
-            lo[i] = fmin(lo[i], s_lo[i][w]);
-            hi[i] = fmax(hi[i], s_hi[i][w]);
+            lo[i] = fminf(lo[i], s_lo[i][w]);
+            hi[i] = fmaxf(hi[i], s_hi[i][w]);
         }
+        scale[i] = hi[i] > lo[i] ? 1024.f / (hi[i] - lo[i]) : 0.f;
     }
     for (int b = t; b < kp2; b += blockDim.x) {
         unsigned long long key = ~0ull;
         if (b < k) {
             unsigned code = 0;
             for (int i = 0; i < 3; ++i) {
-                const double span = hi[i] - lo[i];
-                const double u = span > 0.0 ? (old[(size_t)b * MODEL + 1 + i] - lo[i]) / span : 0.0;
-                const unsigned q = (unsigned)fmin(1023.0, fmax(0.0, floor(u * 1024.0)));
+                const float u = ((float)old[(size_t)b * MODEL + 1 + i] - lo[i]) * scale[i];
+                const unsigned q = (unsigned)fminf(1023.f, fmaxf(0.f, floorf(u)));
                 code |= spread10(q) << i;
             }
             key = ((unsigned long long)code << 32) | (unsigned)b;
@@ -1846,12 +1874,30 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_components_kernel(const d
             }
             __syncthreads();
         }
-    for (int slot = t; slot < k; slot += blockDim.x) {
-        const int b = (int)(keys[slot] & 0xffffffffu);
-        perm[slot] = b;
-        const double* r = old + (size_t)b * MODEL;
-        build_component(slot, r[0], r + 1, r + 4, params, shift4, model64, st, b);
+    for (int slot = t; slot < k; slot += blockDim.x) perm[slot] = (int)(keys[slot] & 0xffffffffu);
+}
+
+// Slot s of every fit takes component perm[s]: its row of `old` rebuilt into slot s
+// of model64, params and shift4 (one thread per slot; insts / comp_inst: batched).
+__global__ void rebuild_components_kernel(const double* __restrict__ old, const int* __restrict__ perm, int total_k,
+                                          double* model64, float* params, float4* shift4, DeviceState* st,
+                                          const BatchInst* __restrict__ insts, const int* __restrict__ comp_inst) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_k) return;
+    int slot = g;
+    if (insts) {
+        const int i = comp_inst[g];
+        const BatchInst I = insts[i];
+        slot = g - I.comp_off;
+        old += (size_t)I.comp_off * MODEL;
+        model64 += (size_t)I.comp_off * MODEL;
+        params += I.par_off;
+        shift4 += I.comp_off;
+        st += i;
     }
+    const int b = perm[g];
+    const double* r = old + (size_t)b * MODEL;
+    build_component(slot, r[0], r + 1, r + 4, params, shift4, model64, st, b);
 }
 
 // ------------------------------------------------------------------ differentiable log-likelihood
@@ -2210,12 +2256,14 @@ cudaError_t launch_order_components(double* model64, double* scratch, int k, int
     if (e != cudaSuccess) return e;
     order_components_kernel<<<1, ORDER_THREADS, smem, s>>>(scratch, k, kp2, perm, model64, params, shift4, st,
                                                            nullptr);
+    rebuild_components_kernel<<<(k + 63) / 64, 64, 0, s>>>(scratch, perm, k, model64, params, shift4, st, nullptr,
+                                                           nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_order_components_batched(double* model64, double* scratch, int total_k, int kmax,
-                                            const BatchInst* insts, int batch, int* perm, float* params,
-                                            float4* shift4, DeviceState* states, cudaStream_t s) {
+                                            const BatchInst* insts, int batch, const int* comp_inst, int* perm,
+                                            float* params, float4* shift4, DeviceState* states, cudaStream_t s) {
     if (kmax > ORDER_MAX_K) return cudaErrorInvalidValue;
     cudaError_t e =
         cudaMemcpyAsync(scratch, model64, sizeof(double) * (size_t)total_k * MODEL, cudaMemcpyDeviceToDevice, s);
@@ -2227,6 +2275,8 @@ cudaError_t launch_order_components_batched(double* model64, double* scratch, in
     if (e != cudaSuccess) return e;
     order_components_kernel<<<batch, ORDER_THREADS, smem, s>>>(scratch, 0, 0, perm, model64, params, shift4, states,
                                                                insts);
+    rebuild_components_kernel<<<(total_k + 63) / 64, 64, 0, s>>>(scratch, perm, total_k, model64, params, shift4,
+                                                                 states, insts, comp_inst);
     return cudaGetLastError();
 }
 

@@ -657,7 +657,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     } b{};
     // the E-steps run on the points in a spatial order (a warp's points then reach
     // fewer components); k-means++ and Lloyd on the caller's order
-    const bool sorted = !chunked;
+    const bool sorted = !chunked && n <= point_order_max_n();
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
         b.perm = cv.take<int>(k);
@@ -772,7 +772,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     // (the E-step then skips the many point-component pairs out of reach);
     // model_out puts them back in the caller's order
     const int* perm = b.perm;
-    COUNTED(prof, 1, launch_order_components(b.model64, b.stats64, k, b.perm, b.params, b.shift4, b.st, c.s));
+    COUNTED(prof, 2, launch_order_components(b.model64, b.stats64, k, b.perm, b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
 
     if (chunked) {
@@ -1177,9 +1177,10 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         void* osc;
     } b{};
     // the E-steps run on every instance's points in a spatial order
-    const int64_t nounits = point_order_box_units(offsets, batch);
+    const bool sorted = total_n <= point_order_max_n();
+    const int64_t nounits = sorted ? point_order_box_units(offsets, batch) : 0;
     std::vector<int2> ounits((size_t)nounits);
-    point_order_fill_units(offsets, batch, ounits.data());
+    if (sorted) point_order_fill_units(offsets, batch, ounits.data());
     // KInit tables: every instance; the seeding clusters grouped by cluster size
     // (instances beyond one 16-CTA cluster are seeded alone); Lloyd tiles
     std::vector<KppInst> ktab(batch);
@@ -1211,9 +1212,9 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         b.pin = cv.take<float>(kp == Kind::Host ? 3 * (size_t)total_n : 0);
         b.p4 = cv.take<float4>(kinit ? (size_t)total_n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)total_n);
-        b.p8s = cv.take<float4>(2 * (size_t)total_n);
+        b.p8s = cv.take<float4>(sorted ? 2 * (size_t)total_n : 0);
         b.ounits = cv.take<int2>((size_t)nounits);
-        b.osc = cv.take<char>(point_order_scratch_bytes(total_n, batch));
+        b.osc = cv.take<char>(sorted ? point_order_scratch_bytes(total_n, batch) : 0);
         b.params = cv.take<float>((size_t)par_floats);
         b.shift4 = cv.take<float4>(total_k);
         b.model64 = cv.take<double>((size_t)total_k * MODEL);
@@ -1278,9 +1279,11 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         pts = b.pin;
     }
     COUNTED(prof, 1, launch_pack_batched(pts, total_n, b.offs, batch, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
-    GIRA_CUDA(cudaMemcpyAsync(b.ounits, ounits.data(), sizeof(int2) * ounits.size(), cudaMemcpyHostToDevice, c.s));
-    COUNTED(prof, point_order_launches(batch),
-            launch_point_order(b.p8, total_n, b.offs, b.ounits, (int)nounits, batch, b.osc, b.p8s, nullptr, c.s));
+    if (sorted) {
+        GIRA_CUDA(cudaMemcpyAsync(b.ounits, ounits.data(), sizeof(int2) * ounits.size(), cudaMemcpyHostToDevice, c.s));
+        COUNTED(prof, point_order_launches(batch),
+                launch_point_order(b.p8, total_n, b.offs, b.ounits, (int)nounits, batch, b.osc, b.p8s, nullptr, c.s));
+    }
     COUNTED(prof, 1, launch_fill_padding_batched(b.params, b.insts, batch, 0, b.npairs, c.s));
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
     float* mu_d = (km == Kind::Device) ? means : b.mmu;
@@ -1330,11 +1333,11 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                                                           b.params, b.shift4, b.st, c.s));
     }
     // every instance's components along a space-filling curve of their means (as in the single fit)
-    COUNTED(prof, 1, launch_order_components_batched(b.model64, b.stats64, total_k, kmax_all, b.insts, batch, b.perm,
-                                                     b.params, b.shift4, b.st, c.s));
+    COUNTED(prof, 2, launch_order_components_batched(b.model64, b.stats64, total_k, kmax_all, b.insts, batch,
+                                                     b.comp_inst, b.perm, b.params, b.shift4, b.st, c.s));
     prof.t_init = prof.mark();
 
-    EStepLaunch base{b.p8s, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
+    EStepLaunch base{sorted ? b.p8s : b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
     base.insts = b.insts;
     base.units = b.units;
     base.states = b.st;

@@ -401,6 +401,7 @@ int64_t point_order_box_units(const int64_t* offsets, int batch);
 void point_order_fill_units(const int64_t* offsets, int batch, int2* units);
 size_t point_order_scratch_bytes(int64_t n, int batch);
 int point_order_launches(int batch);   // kernels one launch_point_order makes
+int64_t point_order_max_n();          // larger inputs keep the caller's order
 cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offsets_d, const int2* units_d,
                                int nunits, int batch, void* scratch, float4* p8_out, int* order_out,
                                cudaStream_t s);
@@ -472,8 +473,8 @@ cudaError_t launch_model_out_batched(const double* model64, const BatchInst* ins
                                      const int* perm = nullptr);
 // launch_order_components for every instance of a batch (one block each, k <= 8192).
 cudaError_t launch_order_components_batched(double* model64, double* scratch, int total_k, int kmax,
-                                            const BatchInst* insts, int batch, int* perm, float* params,
-                                            float4* shift4, DeviceState* states, cudaStream_t s);
+                                            const BatchInst* insts, int batch, const int* comp_inst, int* perm,
+                                            float* params, float4* shift4, DeviceState* states, cudaStream_t s);
 // Per-instance sums of the log-likelihood partials into states[i].ll_sum.
 cudaError_t launch_ll_reduce_batched(const double* ll_partials, const BatchInst* insts, int batch,
                                      DeviceState* states, cudaStream_t s);

@@ -9,7 +9,7 @@
 // bounding cube of their cloud, so that a warp holds a few neighbouring cells.
 //
 // The sort is a stable least-significant-digit radix sort on 9-bit digits,
-// deterministic (no order decided by atomics): per tile of 2048 keys a
+// deterministic (no order decided by atomics): per tile of 512 keys a
 // histogram, one exclusive scan over (digit, tile), and a scatter in which
 // one warp walks its tile in order and ranks equal digits with match_any.  A
 // batch sorts by (instance, code), which keeps every instance in its own range.
@@ -27,7 +27,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RADIX_BITS = 9;
 constexpr int RADIX = 1 << RADIX_BITS;   // 512 digits
-constexpr int TILE = 2048;               // keys per histogram / scatter tile (one warp)
+constexpr int TILE = 512;                // keys per histogram / scatter tile (one warp)
 constexpr int BOX_CHUNK = 4096;          // points per bounding-box block
 constexpr int SCAN_PER_BLOCK = 8192;     // scan: 1024 threads x 8
 constexpr int MORTON_BITS = 18;
@@ -221,7 +221,9 @@ __global__ void __launch_bounds__(1024) scan_bsum_kernel(int* bsum, int nb) {
     }
 }
 
-__global__ void __launch_bounds__(1024) scan_apply_kernel(int* a, int64_t m, const int* __restrict__ bsum) {
+// (writes the offsets tile-major too, [tile][digit], for the scatter's coalesced loads)
+__global__ void __launch_bounds__(1024) scan_apply_kernel(const int* __restrict__ a, int64_t m,
+                                                          const int* __restrict__ bsum, int ntiles, int* at) {
     __shared__ int s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_PER_BLOCK + 8 * threadIdx.x;
     int v[8], t = 0;
@@ -233,7 +235,10 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(int* a, int64_t m, con
     int run = block_exclusive_scan(t, s_warp, nullptr) + bsum[blockIdx.x];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        if (base + j < m) a[base + j] = run;
+        if (base + j < m) {
+            const int i = (int)(base + j);   // digit i / ntiles, tile i % ntiles (m < 2^31)
+            at[(size_t)(i % ntiles) * RADIX + i / ntiles] = run;
+        }
         run += v[j];
     }
 }
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __re
     const int tile = blockIdx.x * 8 + warp;
     if (tile >= ntiles) return;
     int* c = cnt[warp];
-    for (int d = lane; d < RADIX; d += 32) c[d] = offs[(size_t)d * ntiles + tile];
+    for (int d = lane; d < RADIX; d += 32) c[d] = offs[(size_t)tile * RADIX + d];   // tile-major offsets
     __syncwarp();
     const int64_t b = (int64_t)tile * TILE, e = min(n, b + TILE);
     const uint32_t lt = (1u << lane) - 1u;
@@ -302,6 +307,9 @@ void point_order_fill_units(const int64_t* offsets, int batch, int2* units) {
 
 int point_order_launches(int batch) { return 3 + 5 * radix_passes(batch); }
 
+// the largest n the scan's two levels hold (every tile's 512 digit counts)
+int64_t point_order_max_n() { return (int64_t)SCAN_PER_BLOCK * SCAN_PER_BLOCK / RADIX * TILE; }
+
 size_t point_order_scratch_bytes(int64_t n, int batch) {
     const int64_t ntiles = ceil_div(n, TILE);
     const int64_t m = ntiles * RADIX;
@@ -312,7 +320,8 @@ size_t point_order_scratch_bytes(int64_t n, int batch) {
     add(sizeof(uint32_t) * n);
     add(sizeof(int) * n);                   // indices, two buffers
     add(sizeof(int) * n);
-    add(sizeof(int) * m);                   // digit counts / offsets
+    add(sizeof(int) * m);                   // digit counts, digit-major
+    add(sizeof(int) * m);                   // their offsets, tile-major
     add(sizeof(int) * ceil_div(m, SCAN_PER_BLOCK));
     return bytes;
 }
@@ -336,6 +345,7 @@ cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offse
     int* i0 = reinterpret_cast<int*>(take(sizeof(int) * n));
     int* i1 = reinterpret_cast<int*>(take(sizeof(int) * n));
     int* counts = reinterpret_cast<int*>(take(sizeof(int) * m));
+    int* toffs = reinterpret_cast<int*>(take(sizeof(int) * m));
     int* bsum = reinterpret_cast<int*>(take(sizeof(int) * nb));
 
     box_init_kernel<<<(unsigned)ceil_div(6 * (int64_t)batch, 256), 256, 0, s>>>(box, batch);
@@ -351,9 +361,9 @@ cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offse
         radix_hist_kernel<<<tblocks, 256, 0, s>>>(k0, n, shift, (int)ntiles, counts);
         scan_sums_kernel<<<(unsigned)nb, 1024, 0, s>>>(counts, m, bsum);
         scan_bsum_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
-        scan_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(counts, m, bsum);
+        scan_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(counts, m, bsum, (int)ntiles, toffs);
         int* io = (last && order_out) ? order_out : iout;
-        radix_scatter_kernel<<<tblocks, 256, 0, s>>>(k0, iin, n, shift, (int)ntiles, counts, k1, io, p8,
+        radix_scatter_kernel<<<tblocks, 256, 0, s>>>(k0, iin, n, shift, (int)ntiles, toffs, k1, io, p8,
                                                      last ? p8_out : nullptr);
         std::swap(k0, k1);
         iout = iin;   // the input indices are free for the next pass's output

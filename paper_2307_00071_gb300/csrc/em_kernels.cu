@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     // extra slots are padding components with c = -inf); mask words for pt_pairs(k)
     const int npairs = ((((a.k + 1) >> 1) + 1) & ~1);
     const int nwords = pt_pairs(a.k) / 32;
-    const float4* spar = reinterpret_cast<const float4*>(dsm);   // [npairs][8]
+    const float4* spar = reinterpret_cast<const float4*>(dsm);   // [npairs][PAIR_F4]
     uint32_t* smask_all = reinterpret_cast<uint32_t*>(dsm + (size_t)pt_pairs(a.k) * PAIR_FLOATS * 4);
     uint32_t* smask = smask_all + warp * nwords;   // [nwords] live bits of the warp's pairs
     uint16_t* slist = reinterpret_cast<uint16_t*>(smask_all + PT_W * nwords) + warp * pt_pairs(a.k);
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     // reference cmax = max_b c_b and the weight normaliser (every warp, same order)
     float cm = -INFINITY, wsv = 0.f;
     for (int pp = lane; pp < npairs; pp += 32) {
-        const float4 v4 = spar[pp * 8 + 4], v6 = spar[pp * 8 + 6];
+        const float4 v4 = spar[pp * PAIR_F4 + 4], v6 = spar[pp * PAIR_F4 + 6];
         cm = fmaxf(cm, fmaxf(v4.z, v4.w));
         wsv += v6.z + v6.w;
     }
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     const float ref0 = s_norm ? cmax - __log2f(wsv) : cmax;
 
     auto load_pair = [&](int pp, PairParams& P) {
-        const float4* q = spar + (size_t)pp * 8;
+        const float4* q = spar + (size_t)pp * PAIR_F4;
         const float4 v0 = q[0], v1 = q[1], v2 = q[2], v4 = q[4], v5 = q[5], v6 = q[6];
         P.p[0] = f2(v0.x, v0.y); P.p[1] = f2(v0.z, v0.w);
         P.p[2] = f2(v1.x, v1.y); P.p[3] = f2(v1.z, v1.w);
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             const int pp = j0 + lane;
             bool live = false;
             if (any_point && pp < npairs) {
-                const float4* q = spar + (size_t)pp * 8;
+                const float4* q = spar + (size_t)pp * PAIR_F4;
                 const float4 v0 = q[0], v1 = q[1], v2 = q[2], v4 = q[4], v5 = q[5], v6 = q[6], v7 = q[7];
                 const float pc[2][6] = {{v0.x, v0.z, v1.x, v1.z, v2.x, v2.z}, {v0.y, v0.w, v1.y, v1.w, v2.y, v2.w}};
                 const float nm[2][3] = {{v5.x, v5.z, v6.x}, {v5.y, v5.w, v6.y}};

@@ -12,7 +12,8 @@
 //   slot 14     a lower bound of sigma_min(P')^2 = alpha^2 / lambda_max(Sigma): the
 //               point-stationary E-step's reach test (a pair whose q' is > 126 over a
 //               warp's box of points gives exact zeros and is skipped)
-//   slot 15     padding
+//   slot 15..17 padding: a pair owns 36 floats (144 bytes), so lanes reading the
+//               same slot of consecutive pairs in shared memory hit different banks
 // alpha = sqrt(log2(e) / 2), so that c - ||P' x + b'||^2 = log2(pi N(x|mu,Sigma))
 // (Eq. simplifiedGaussian scaled to base 2).  Padding components carry
 // c = -inf, P' = b' = mu = 0, so they contribute exactly zero.
@@ -25,7 +26,8 @@
 
 namespace gira {
 
-constexpr int PAIR_FLOATS = 32;
+constexpr int PAIR_FLOATS = 36;
+constexpr int PAIR_F4 = PAIR_FLOATS / 4;   // float4 per pair block
 constexpr int SLOT_P = 0, SLOT_B = 6, SLOT_C = 9, SLOT_NMU = 10, SLOT_W = 13, SLOT_S = 14;
 constexpr int NSTAT = 10;   // S0, S1[3], S2[6] (00,01,02,11,12,22)
 constexpr int MODEL = 10;   // w, mu[3], Sigma[6] (00,01,02,11,12,22), binary64; w = N_b or caller weight

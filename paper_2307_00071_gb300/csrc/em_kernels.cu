@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
 // the other kernels' in another order.
 constexpr int PT_P = 4;           // points per lane
 constexpr int PT_W = 4;           // warps per CTA
-constexpr int PT_PTS = 32 * PT_P * PT_W;   // points per CTA
+constexpr int PT_H = 2;           // warps sharing a block of 32 * PT_P points (the pairs split between them)
+constexpr int PT_B = PT_W / PT_H; // point blocks per CTA: partial rows and mask rows per CTA
+constexpr int PT_PTS = 32 * PT_P * PT_B;   // points per CTA
 
 // Pairs the kernel reads for k components: ceil(k / 2) rounded up to a multiple
 // of 32 (never beyond the padded parameter block, whose extra slots are padding
@@ -551,6 +553,14 @@ __device__ __forceinline__ float pt_warp_reduce20(const float2 (&S)[NSTAT], int 
     return i == 0 ? z[0] : i == 1 ? z[1] : i == 2 ? z[2] : i == 3 ? z[3] : z[4];
 }
 
+// The barrier of point block blk's PT_H warps (barrier ids known at compile time,
+// so the kernel holds PT_B + 1 of them).
+__device__ __forceinline__ void pt_block_sync(int blk) {
+    static_assert(PT_B == 2 && PT_H == 2, "one named barrier per point block");
+    if (blk == 0) asm volatile("bar.sync 1, %0;" ::"n"(32 * PT_H) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"n"(32 * PT_H) : "memory");
+}
+
 template <bool STATS>
 __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunch a_in) {
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -558,7 +568,9 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     __shared__ int s_skip, s_norm, s_dead;
     __shared__ double s_ll[PT_W];
     __shared__ unsigned s_pairs[PT_W][2];
+    __shared__ float2 s_tot[PT_W][PT_P][32];   // phase-1 sums of every warp, for its partner
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int blk = warp / PT_H, half = warp % PT_H;   // point block; which pairs (pp % PT_H == half)
     int cta = blockIdx.x;
     // the instance's first point (batched launches); the loads below index the
     // launch's own pointer by it (loads through the pointer advanced in the local
@@ -575,7 +587,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         a.params = a_in.params + I.par_off;
         a.partials = a_in.partials ? a_in.partials + I.part_off : nullptr;
         a.masks = a_in.masks ? a_in.masks + I.mask_off : nullptr;
-        a.pt_rows = (int64_t)I.ctas * PT_W;
+        a.pt_rows = (int64_t)I.ctas * PT_B;
         a.ll_partials = a_in.ll_partials ? a_in.ll_partials + I.ll_off : nullptr;
         a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
         a.st = a_in.states + u.inst;
@@ -590,7 +602,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     uint16_t* slist = reinterpret_cast<uint16_t*>(smask_all + PT_W * nwords) + warp * pt_pairs(a.k);
     // the lane's points (never written inside a fit: loaded before the wait); a slot
     // beyond n holds a point 1e18 m away, where every q' is +inf and e exactly 0
-    const int64_t base = (int64_t)cta * PT_PTS + (int64_t)warp * 32 * PT_P + lane;
+    const int64_t base = (int64_t)cta * PT_PTS + (int64_t)blk * 32 * PT_P + lane;
     float2 X[PT_P][3];
     bool valid[PT_P];
 #pragma unroll
@@ -691,8 +703,8 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             ctr[j] = 0.5f * (lo[j] + hi[j]);
             h[j] = fmaxf(hi[j] - ctr[j], ctr[j] - lo[j]);
         }
-        for (int j0 = 0; j0 < npairs; j0 += 32) {
-            const int pp = j0 + lane;
+        for (int j0 = 0; j0 < npairs; j0 += 32 * PT_H) {   // this warp's pairs: pp % PT_H == half
+            const int pp = j0 + PT_H * lane + half;
             bool live = false;
             if (any_point && pp < npairs) {
                 const float4* q = spar + (size_t)pp * PAIR_F4;
@@ -759,7 +771,11 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     }
     __syncwarp();
 
-    // ---- totals, log-likelihood, rare points
+    // ---- totals (the block's warps add their sums in the same order), log-likelihood,
+    // rare points
+#pragma unroll
+    for (int p = 0; p < PT_P; ++p) s_tot[warp][p][lane] = tot[p];
+    pt_block_sync(blk);
     float2 pr[PT_P];   // (shift, 1 / total) per point
     double ll = 0.0;
     bool rare_any = false;
@@ -767,7 +783,12 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     for (int p = 0; p < PT_P; ++p) {
         pr[p] = f2(0.f, 0.f);
         if (!valid[p]) continue;
-        float t = tot[p].x + tot[p].y;
+        float t = 0.f;
+#pragma unroll
+        for (int h = 0; h < PT_H; ++h) {
+            const float2 u = s_tot[blk * PT_H + h][p][lane];
+            t += u.x + u.y;
+        }
         float sh = 0.f;
         if (!(t >= 0x1p-100f)) {
             // every component is > 100 binades below cmax at this point: the exact maximum
@@ -795,29 +816,37 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         }
         pr[p] = f2(sh, __frcp_rn(t));
         const float lse2 = lg2_approx(t) + ref0 - sh;   // log2 sum_b pi_b N(x|b)
-        ll += (double)lse2;
-        if (!STATS && a.per_point) a.per_point[base + 32 * p] = lse2 * LN2F;
+        if (half == 0) {   // (every warp of the block has the same totals)
+            ll += (double)lse2;
+            if (!STATS && a.per_point) a.per_point[base + 32 * p] = lse2 * LN2F;
+        }
     }
 
     if (STATS) {
         __syncwarp();
-        if (__any_sync(FULL, rare_any) && lane < nwords) {   // every evaluated pair, this warp
+        if (__any_sync(FULL, rare_any) && lane < nwords) {   // every evaluated pair of this warp
             const int lo = lane * 32;
-            smask[lane] = (lo + 32 <= npairs) ? 0xffffffffu : (lo < npairs) ? ((1u << (npairs - lo)) - 1u) : 0u;
+            const uint32_t mine = PT_H == 1 ? 0xffffffffu : (half ? 0xaaaaaaaau : 0x55555555u);
+            smask[lane] = mine & ((lo + 32 <= npairs) ? 0xffffffffu : (lo < npairs) ? ((1u << (npairs - lo)) - 1u) : 0u);
         }
-        __syncwarp();
+        pt_block_sync(blk);   // the block's masks are final
+        const int64_t gw = (int64_t)cta * PT_B + blk;
+        const int64_t rows = a.pt_rows;
+        if (half == 0 && lane < nwords) {
+            uint32_t m = 0u;
+#pragma unroll
+            for (int h = 0; h < PT_H; ++h) m |= smask_all[(blk * PT_H + h) * nwords + lane];
+            a.masks[lane * rows + gw] = m;
+        }
         if (lane == 0) {
             unsigned live = 0;
             for (int wd = 0; wd < nwords; ++wd) live += __popc(smask[wd]);
             s_pairs[warp][0] = (unsigned)nlive;
             s_pairs[warp][1] = live;
         }
-        // ---- phase 2: the live pairs; partials [k * NSTAT][rows], masks [nwords][rows]
-        const int64_t gw = (int64_t)cta * PT_W + warp;
-        const int64_t rows = a.pt_rows;
+        // ---- phase 2: this warp's live pairs; partials [k * NSTAT][rows], masks [nwords][rows]
         for (int wd = 0; wd < nwords; ++wd) {
             uint32_t m = smask[wd];
-            if (lane == 0) a.masks[wd * rows + gw] = m;
             while (m) {
                 const int pp = wd * 32 + __ffs(m) - 1;
                 m &= m - 1u;
@@ -1063,7 +1092,7 @@ void note_estep_kernel(const void* fn) {
 const char* last_estep_kernel() { return t_estep_name.c_str(); }
 
 int estep_pt_grid(int64_t n) { return (int)std::max<int64_t>(1, (n + PT_PTS - 1) / PT_PTS); }
-int estep_pt_rows(int grid) { return grid * PT_W; }
+int estep_pt_rows(int grid) { return grid * PT_B; }
 int estep_pt_mask_words(int k) { return pt_pairs(k) / 32; }
 
 cudaError_t launch_estep_pt(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool pdl) {
@@ -1088,7 +1117,7 @@ cudaError_t launch_estep_pt_units(const EStepLaunch& a, bool stats, int nunits, 
 }
 
 int estep_pt_points() { return PT_PTS; }
-int estep_pt_warps() { return PT_W; }
+int estep_pt_blocks() { return PT_B; }
 
 cudaError_t launch_estep(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool grad, bool pdl) {
     const Shape sh = shape_for(a.k);
@@ -1677,7 +1706,7 @@ __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_batched_kernel(co
     f.perm = base.perm ? base.perm + I.comp_off : nullptr;
     if (base.masks) {   // point-stationary E-step: per-warp rows, live masks, one ll slot per CTA
         f.masks = base.masks + I.mask_off;
-        f.grid = I.ctas * PT_W;
+        f.grid = I.ctas * PT_B;
         f.ll_count = I.ctas;
     }
     f.stats64 = base.stats64 ? base.stats64 + (size_t)I.comp_off * NSTAT : nullptr;

@@ -1135,7 +1135,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     int64_t part_floats = 0, mask_words = 0, ll_slots = 0;
     int kmax_all = 0;
     {
-        const int PTS = estep_pt_points(), W = estep_pt_warps();
+        const int PTS = estep_pt_points(), W = estep_pt_blocks();
         for (int i = 0; i < batch; ++i) {
             BatchInst& I = hi[i];
             I.ppc = PTS;

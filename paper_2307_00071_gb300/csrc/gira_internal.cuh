@@ -430,7 +430,7 @@ cudaError_t launch_estep_pt(const EStepLaunch& a, bool stats, int grid, cudaStre
 // instance's part_off, mask_off, ll_off and ctas for PT points per CTA).
 cudaError_t launch_estep_pt_units(const EStepLaunch& a, bool stats, int nunits, int kmax, cudaStream_t s);
 int estep_pt_points();   // points per CTA
-int estep_pt_warps();    // warps per CTA (partial rows per CTA)
+int estep_pt_blocks();   // point blocks per CTA (partial and mask rows per CTA)
 cudaError_t launch_params_from_model(const float* w, const float* mu, const float* cov, int k, double* model64,
                                      float* params, float4* shift4, DeviceState* st, cudaStream_t s);
 // perm (nullable): slot s of model64 is the caller's component perm[s].

@@ -1497,9 +1497,19 @@ __device__ void reduce_partials_masked(const float* __restrict__ partials, int r
     for (int seg0 = 0; seg0 < rows; seg0 += FIN_SEG) {
         const int seg1 = min(rows, seg0 + FIN_SEG);
         int nl = 0;   // live rows listed so far in this segment (the same in every thread)
-        for (int r0 = seg0; r0 < seg1; r0 += FIN_THREADS) {
+        constexpr int RND = (FIN_SEG + FIN_THREADS - 1) / FIN_THREADS;
+        uint32_t mk[RND];   // this thread's mask words of the segment, loaded together
+#pragma unroll
+        for (int u = 0; u < RND; ++u) {
+            const int r = seg0 + u * FIN_THREADS + t;
+            mk[u] = r < seg1 ? __ldg(mrow + r) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < RND; ++u) {
+            const int r0 = seg0 + u * FIN_THREADS;
+            if (r0 >= seg1) break;
             const int r = r0 + t;
-            const bool live = r < seg1 && (__ldg(mrow + r) & bit);
+            const bool live = (mk[u] & bit) != 0u;
             const uint32_t m = __ballot_sync(FULL, live);
             if (lane == 0) s_wcnt[warp] = __popc(m);
             __syncthreads();
@@ -1650,14 +1660,19 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
         build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st, f.perm ? f.perm[b] : b);
         if (b == 0) f.st->w_raw = 1;
     }
-    if (f.em && f.do_ll && blk == 0 && t >= 32 && t < 64) {   // warp 1: log-likelihood, trace, convergence
-        const int lane = t - 32;
+    if (f.em && f.do_ll && blk == 0 && t >= 32) {   // warps 1 ..: log-likelihood, trace, convergence
+        __shared__ double s_llw[FIN_THREADS / 32];
+        const int lane = t & 31, w = t >> 5;
         double v = 0.0;
         const int nll = f.ll_count ? f.ll_count : f.grid;
-        for (int c = lane; c < nll; c += 32) v += f.llp[c];
+        for (int c = t - 32; c < nll; c += FIN_THREADS - 32) v += f.llp[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (lane == 0) {
+        if (lane == 0) s_llw[w] = v;
+        asm volatile("bar.sync 1, %0;" ::"n"(FIN_THREADS - 32) : "memory");   // warps 1 .. only
+        if (t == 32) {
+            v = 0.0;
+            for (int u = 1; u < FIN_THREADS / 32; ++u) v += s_llw[u];
             DeviceState* st = f.st;
             st->ll_sum = v;
             const double ll = v / (double)f.n;

@@ -378,16 +378,22 @@ __global__ void __launch_bounds__(KPPP_THREADS, 1) kpp_persistent_kernel(
 // synchronisation at all.  Each of the cs CTAs (one per SM) keeps its points'
 // coordinates in shared memory and their D^2 in registers; each lane keeps the
 // exact fixed-point sum of its own D^2, recomputed only when a new centre
-// lowers one of them.  Per centre j:
-//  1. update D^2 and the lane sums; warp / CTA prefixes of the lane sums; each
-//     CTA stores its total into every CTA's shared memory (st.async, DSMEM),
+// lowers one of them.  The points are dealt to warps in blocks of KC_BLOCK
+// consecutive points, round-robin over the CTAs, so the points a new centre
+// reaches (a patch of consecutive image rows) are spread over the cluster.
+// Per centre j:
+//  1. lanes whose box is out of the new centre's reach skip it; the others
+//     update D^2 and their lane sums; every warp scans its lane sums and stores
+//     its block total into every CTA's shared memory (st.async, DSMEM),
 //     completing bytes on the receiver's mbarrier;
-//  2. once its mbarrier has all cs totals, every CTA evaluates the same prefix
-//     over them and finds the CTA holding the threshold;
-//  3. that CTA locates the point (warp, lane, then the lane's points in order)
-//     and stores it into every CTA's shared memory the same way; every CTA
-//     waits for it on a second mbarrier.
-// No cluster barrier per centre: each CTA waits only for the bytes it reads.
+//  2. once its mbarrier has every block total, warp 0 of every CTA evaluates the
+//     same prefix over them and finds the block holding the threshold;
+//  3. the warp holding that block locates the point (lane, then the lane's
+//     points in order, their weights handed over through shared memory) and
+//     stores it into every CTA's shared memory the same way; every CTA waits
+//     for it on a second mbarrier.
+// No cluster barrier per centre and one CTA barrier: each CTA waits only for
+// the bytes it reads.
 // Buffers and mbarriers alternate by the parity of j: a CTA can send centre
 // j + 1's total while a slower peer still has centre j's in flight, but not
 // centre j + 2's (that needs centre j + 1's point, which needs every total of
@@ -401,18 +407,18 @@ constexpr int KC_THREADS = 512;
 constexpr int KC_WARPS = KC_THREADS / 32;
 constexpr int KC_PMAX = 18;               // point pairs per lane
 constexpr int KC_LMAX = 2 * KC_PMAX;      // points per lane
+constexpr int KC_BLOCK = 32 * KC_LMAX;    // points per warp (one block of the running sum)
 constexpr int KC_MAX_CS = 16;
 
 constexpr long long KC_WAIT_NS = 2000000000ll;   // bound on any wait: 2 s of wall time
 
 struct KcShared {
-    u128 wtot[KC_WARPS], wincl[KC_WARPS];
-    u128 csum[2][KC_MAX_CS];   // by parity of j: stored by every CTA of the cluster
+    u128 csum[2][KC_MAX_CS * KC_WARPS];   // by parity of j: every block's total, stored by its warp
     float4 cen[2];             // by parity of j: stored by the CTA holding the chosen point
     long long idx[2];
     uint64_t bar_sum[2], bar_cen[2];
-    u128 rel;
-    int win, mode;
+    u128 rel;                  // the threshold within the chosen block
+    int win, wwin, mode;       // the block's CTA and warp; 0 normal, 2 every weight zero
     float2 dsrc[KC_PMAX];      // the D^2 of the lane holding the chosen point
 };
 
@@ -527,15 +533,15 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
     }
     if (st->error) return;   // set before the launch: every CTA of the cluster leaves
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // contiguous ranges: CTA, warp, lane (the running sum in point order is
-    // CTA prefix, warp prefix, lane prefix, then the lane's points in order)
-    const int64_t per = (n + cs - 1) / cs;
-    const int64_t clo = min(n, (int64_t)me * per), chi = min(n, clo + per);
-    const int64_t pw = (chi - clo + KC_WARPS - 1) / KC_WARPS;
-    const int64_t wlo = min(chi, clo + warp * pw), whi = min(chi, wlo + pw);
-    const int64_t pl = (whi - wlo + 31) / 32;
-    const int64_t llo = min(whi, wlo + lane * pl), lhi = min(whi, llo + pl);
-    const int mcnt = (int)min(lhi - llo, (int64_t)KC_LMAX);   // <= KC_LMAX by the host's size check
+    // blocks of KC_BLOCK consecutive points, dealt round-robin: block g belongs to
+    // warp g / cs of CTA g % cs, so a neighbourhood of consecutive points (a patch of
+    // image rows) is spread over the cluster; within a block, lane l holds points
+    // l KC_LMAX .. in order.  The running sum in point order is then: the prefix of
+    // the blocks before g, the lane prefix in block g, the lane's points in order.
+    const int g = warp * cs + me;
+    const int64_t llo = min(n, (int64_t)g * KC_BLOCK + (int64_t)lane * KC_LMAX);
+    const int mcnt = (int)min(n - llo, (int64_t)KC_LMAX);   // every point has a block by the host's size check
+    float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};   // the lane's box
 #pragma unroll
     for (int p = 0; p < KC_PMAX; ++p) {
         const float4 v0 = (2 * p < mcnt) ? __ldg(pts + llo + 2 * p) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -543,7 +549,16 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         xs[p * KC_THREADS + tid] = f2(v0.x, v1.x);
         ys[p * KC_THREADS + tid] = f2(v0.y, v1.y);
         zs[p * KC_THREADS + tid] = f2(v0.z, v1.z);
+        if (2 * p < mcnt) {
+            blo[0] = fminf(blo[0], v0.x); blo[1] = fminf(blo[1], v0.y); blo[2] = fminf(blo[2], v0.z);
+            bhi[0] = fmaxf(bhi[0], v0.x); bhi[1] = fmaxf(bhi[1], v0.y); bhi[2] = fmaxf(bhi[2], v0.z);
+        }
+        if (2 * p + 1 < mcnt) {
+            blo[0] = fminf(blo[0], v1.x); blo[1] = fminf(blo[1], v1.y); blo[2] = fminf(blo[2], v1.z);
+            bhi[0] = fmaxf(bhi[0], v1.x); bhi[1] = fmaxf(bhi[1], v1.y); bhi[2] = fmaxf(bhi[2], v1.z);
+        }
     }
+    float lmax = -INFINITY;   // the largest D^2 of the lane's points (an upper bound once set)
     float2 D[KC_PMAX];   // D^2 of points 2p, 2p+1 (padding lanes: +inf, never chosen, fx48 0 not used)
     u128 ls{0ull, 0ull};
     int64_t idx = (int64_t)floor(uniform53(seed, 0) * (double)n);
@@ -571,22 +586,36 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         //         the lane beats per-point differences)
         const float2 ncx = dup(-cen.x), ncy = dup(-cen.y), ncz = dup(-cen.z);
         bool changed = (j == 1);
+        // a new centre farther from the lane's box than the lane's largest D^2 lowers none
+        // of them (the slack covers the rounding of the box distance and of every D^2):
+        // the lane skips the update
+        const float gx = fmaxf(fmaxf(blo[0] - cen.x, cen.x - bhi[0]), 0.f);
+        const float gy = fmaxf(fmaxf(blo[1] - cen.y, cen.y - bhi[1]), 0.f);
+        const float gz = fmaxf(fmaxf(blo[2] - cen.z, cen.z - bhi[2]), 0.f);
+        if (j == 1 || fmaf(gz, gz, fmaf(gy, gy, gx * gx)) * (1.f - 1e-5f) <= lmax) {
 #pragma unroll
-        for (int p = 0; p < KC_PMAX; ++p) {
-            if (2 * p < mcnt) {
-                const float2 d0 = add2(xs[p * KC_THREADS + tid], ncx);
-                const float2 d1 = add2(ys[p * KC_THREADS + tid], ncy);
-                const float2 d2 = add2(zs[p * KC_THREADS + tid], ncz);
-                const float2 dd = add2(add2(mul2(d0, d0), mul2(d1, d1)), mul2(d2, d2));
-                if (j == 1) {
-                    D[p] = dd;
-                } else {
-                    changed |= (dd.x < D[p].x) || (dd.y < D[p].y);
-                    D[p] = f2(fminf(D[p].x, dd.x), fminf(D[p].y, dd.y));
+            for (int p = 0; p < KC_PMAX; ++p) {
+                if (2 * p < mcnt) {
+                    const float2 d0 = add2(xs[p * KC_THREADS + tid], ncx);
+                    const float2 d1 = add2(ys[p * KC_THREADS + tid], ncy);
+                    const float2 d2 = add2(zs[p * KC_THREADS + tid], ncz);
+                    const float2 dd = add2(add2(mul2(d0, d0), mul2(d1, d1)), mul2(d2, d2));
+                    if (j == 1) {
+                        D[p] = dd;
+                    } else {
+                        changed |= (dd.x < D[p].x) || (dd.y < D[p].y);
+                        D[p] = f2(fminf(D[p].x, dd.x), fminf(D[p].y, dd.y));
+                    }
                 }
             }
         }
         if (changed) {
+            lmax = -INFINITY;
+#pragma unroll
+            for (int p = 0; p < KC_PMAX; ++p) {
+                if (2 * p < mcnt) lmax = fmaxf(lmax, D[p].x);
+                if (2 * p + 1 < mcnt) lmax = fmaxf(lmax, D[p].y);
+            }
             bool big = false;   // a weight >= 2^10: sum in 128 bits
             unsigned ah = 0u, am = 0u, al = 0u;
 #pragma unroll
@@ -606,34 +635,52 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 }
             }
         }
-        // this phase of bar_sum[b] expects the cs totals (the previous phase of it
+        // this phase of bar_sum[b] expects every block's total (the previous phase of it
         // completed before this CTA read centre j - 2's totals)
-        if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)cs * (uint32_t)sizeof(u128));
+        const int nblk = cs * KC_WARPS;
+        if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)nblk * (uint32_t)sizeof(u128));
         const u128 linc = u128_warp_incl_scan(ls, lane);
-        if (lane == 31) sh.wtot[warp] = linc;
-        __syncthreads();
+        {   // this warp's block total, to every CTA's slot g
+            const u128 total = u128_shfl(linc, 31);
+            if (lane < cs && !dead) kc_send_u128(kc_peer(&sh.csum[b][g], lane), total, kc_peer(&sh.bar_sum[b], lane));
+        }
         if (warp == 0) {
-            const u128 wv = (lane < KC_WARPS) ? sh.wtot[lane] : u128{0ull, 0ull};
-            const u128 wi = u128_warp_incl_scan(wv, lane);
-            if (lane < KC_WARPS) sh.wincl[lane] = wi;
-            const u128 total = u128_shfl(wi, KC_WARPS - 1);
-            if (lane < cs && !dead)
-                kc_send_u128(kc_peer(&sh.csum[b][me], lane), total, kc_peer(&sh.bar_sum[b], lane));
-            // ---- 2. every CTA's total has arrived
+            // ---- 2. every block's total has arrived: the block holding the threshold
             if (!dead && !kc_wait(&sh.bar_sum[b], (ph_sum >> b) & 1u)) {
                 dead = true;
                 set_error(st, GIRA_ERR_TIMEOUT);
             }
-            const u128 v = (lane < cs) ? sh.csum[b][lane] : u128{0ull, 0ull};
-            const u128 inc = u128_warp_incl_scan(v, lane);
-            const u128 T = u128_shfl(inc, 31);
+            constexpr int PER = KC_MAX_CS * KC_WARPS / 32;   // blocks per lane, in order
+            u128 run{0ull, 0ull};
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int gq = lane * PER + q;
+                run = u128_add(run, gq < nblk ? sh.csum[b][gq] : u128{0ull, 0ull});
+            }
+            const u128 lincl = u128_warp_incl_scan(run, lane);
+            const u128 before = u128_sub(lincl, run);   // the blocks of lower lanes
+            const u128 T = u128_shfl(lincl, 31);
             if (!u128_zero(T)) {
                 const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
-                const unsigned hits = __ballot_sync(FULL, lane < cs && u128_gt(inc, t));   // t < T: not empty
-                const int w = hits ? __ffs(hits) - 1 : 0;
-                if (lane == w) {
-                    sh.win = w;
-                    sh.rel = u128_sub(t, u128_sub(inc, v));
+                const unsigned hits = __ballot_sync(FULL, u128_gt(lincl, t));   // t < T: not empty
+                const int hl = hits ? __ffs(hits) - 1 : 0;
+                if (lane == hl) {   // the first of this lane's blocks whose running sum exceeds r
+                    const u128 r = u128_sub(t, before);
+                    u128 acc{0ull, 0ull}, prev{0ull, 0ull};
+                    int q = PER - 1;
+                    for (int u = 0; u < PER; ++u) {
+                        const int gq = lane * PER + u;
+                        acc = u128_add(acc, gq < nblk ? sh.csum[b][gq] : u128{0ull, 0ull});
+                        if (u128_gt(acc, r)) {
+                            q = u;
+                            break;
+                        }
+                        prev = acc;
+                    }
+                    const int gw = lane * PER + q;
+                    sh.win = gw % cs;
+                    sh.wwin = gw / cs;
+                    sh.rel = u128_sub(r, prev);
                     sh.mode = 0;
                 }
                 // this phase of bar_cen[b] expects the chosen point and its index
@@ -654,16 +701,11 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         __syncthreads();
         const int mode = sh.mode;
         if (mode == 0 && sh.win == me) {
-            // ---- 3. this CTA holds the point: warp, lane, then the lane's points
-            const u128 rel = sh.rel;
-            const u128 wi = (lane < KC_WARPS) ? sh.wincl[lane] : u128{0ull, 0ull};
-            const unsigned wh = __ballot_sync(FULL, lane < KC_WARPS && u128_gt(wi, rel));
-            const int ww = wh ? __ffs(wh) - 1 : 0;   // wh != 0: rel < this CTA's total
-            if (warp == ww) {
-                const u128 wrel = u128_sub(rel, u128_sub(sh.wincl[ww], sh.wtot[ww]));
+            // ---- 3. this CTA holds the point: lane, then the lane's points
+            if (warp == sh.wwin) {
+                const u128 wrel = sh.rel;
                 const unsigned lh = __ballot_sync(FULL, mcnt > 0 && u128_gt(linc, wrel));
                 const int src = lh ? __ffs(lh) - 1 : 0;
-                // the src lane's points, spread over the warp: lane l takes points l and 32 + l
                 const u128 base = u128_sub(u128_shfl(linc, src), u128_shfl(ls, src));
                 const u128 rel2 = u128_sub(wrel, base);
                 const int cnt = __shfl_sync(FULL, mcnt, src);

@@ -51,7 +51,9 @@ typedef enum {
     GIRA_ERR_CUDA = 4,             /* a CUDA runtime call failed; the message carries cudaGetErrorString */
     GIRA_ERR_OOM = 5,              /* the device workspace could not be allocated */
     GIRA_ERR_TIMEOUT = 6,          /* reserved for bounded device-side waits */
-    GIRA_ERR_NUMERIC = 7           /* a point's likelihood underflows binary32 under every component */
+    GIRA_ERR_NUMERIC = 7,          /* a point's likelihood underflows binary32 under every component */
+    GIRA_ERR_BOUNDS = 8            /* libraries built with GIRA_DEBUG only: a device-side index fell outside
+                                      its buffer; the access was skipped */
 } gira_status;
 
 /* Largest number of mixture components one call accepts. */

@@ -33,16 +33,27 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "gira.h")]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+LIB_DEBUG = os.path.join(OUT_DIR, "libgira_debug.so")
+
+
+def lib_path(debug: bool = False) -> str:
+    """libgira.so, or libgira_debug.so: the build with -DGIRA_DEBUG, whose kernels check
+    their indices against their buffers and report GIRA_ERR_BOUNDS instead of an access."""
+    return LIB_DEBUG if debug else LIB
+
+
+def is_stale(debug: bool = False) -> bool:
+    lib = lib_path(debug)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, debug: bool) -> str:
+    obj_dir = os.path.join(OUT_DIR, "debug") if debug else OUT_DIR
+    obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [NVCC, *ARCH, *FLAGS, *(["-DGIRA_DEBUG"] if debug else []), "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,19 +64,20 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and not is_stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = lib_path(debug)
+    os.makedirs(os.path.join(OUT_DIR, "debug") if debug else OUT_DIR, exist_ok=True)
+    if not force and not is_stale(debug):
+        return lib
     with cf.ThreadPoolExecutor(max_workers=len(sources())) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), sources()))
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

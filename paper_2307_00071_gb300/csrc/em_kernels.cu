@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
 #pragma unroll
     for (int p = 0; p < PT_P; ++p) {
         const int64_t i = base + 32 * p;
-        valid[p] = i < a.n;
+        valid[p] = i < a.n && GIRA_IN(a_in.n_buf == 0 || pt0 + i < a_in.n_buf, a.st);
         if (valid[p]) {
             const float4 xy = a_in.pts8[2 * (pt0 + i)], zz = a_in.pts8[2 * (pt0 + i) + 1];
             X[p][0] = f2(xy.x, xy.y);
@@ -656,6 +656,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     const float ref0 = s_norm ? cmax - __log2f(wsv) : cmax;
 
     auto load_pair = [&](int pp, PairParams& P) {
+        if (!GIRA_IN(pp >= 0 && pp < npairs, a.st)) pp = 0;
         const float4* q = spar + (size_t)pp * PAIR_F4;
         const float4 v0 = q[0], v1 = q[1], v2 = q[2], v4 = q[4], v5 = q[5], v6 = q[6];
         P.p[0] = f2(v0.x, v0.y); P.p[1] = f2(v0.z, v0.w);
@@ -730,7 +731,8 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
                 }
             }
             const uint32_t m = __ballot_sync(FULL, live);
-            if (live) slist[nlive + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pp;
+            const int at = nlive + __popc(m & ((1u << lane) - 1u));
+            if (live && GIRA_IN(at < pt_pairs(a.k), a.st)) slist[at] = (uint16_t)pp;
             nlive += __popc(m);
         }
     }
@@ -836,7 +838,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             uint32_t m = 0u;
 #pragma unroll
             for (int h = 0; h < PT_H; ++h) m |= smask_all[(blk * PT_H + h) * nwords + lane];
-            a.masks[lane * rows + gw] = m;
+            if (GIRA_IN(gw < rows, a.st)) a.masks[lane * rows + gw] = m;
         }
         if (lane == 0) {
             unsigned live = 0;
@@ -876,7 +878,8 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
                 int v;
                 const float r = pt_warp_reduce20(S, lane, &v);
                 const int b = 2 * pp + (v >= NSTAT ? 1 : 0);
-                if ((lane & 7) < 5 && b < a.k) a.partials[((size_t)b * NSTAT + (v % NSTAT)) * rows + gw] = r;
+                if ((lane & 7) < 5 && b < a.k && GIRA_IN(gw < rows, a.st))
+                    a.partials[((size_t)b * NSTAT + (v % NSTAT)) * rows + gw] = r;
             }
         }
     }
@@ -888,7 +891,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
     if (threadIdx.x == 0) {
         double v = s_ll[0];
         for (int w = 1; w < PT_W; ++w) v += s_ll[w];
-        a.ll_partials[cta] = v * LN2;
+        if (GIRA_IN(cta < (a_in.units ? a.pt_rows / PT_B : (int64_t)gridDim.x), a.st)) a.ll_partials[cta] = v * LN2;
         if (STATS) {
             unsigned long long near = 0, live = 0;
             for (int w = 0; w < PT_W; ++w) {
@@ -1485,7 +1488,8 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
 // order of every addition is fixed.  Call with every thread of the block.
 constexpr int FIN_SEG = 4096;
 __device__ void reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
-                                       int b0, int nout, double (*part)[FIN_CPB * NSTAT], double* S) {
+                                       int b0, int nout, double (*part)[FIN_CPB * NSTAT], double* S,
+                                       DeviceState* st) {
     __shared__ uint16_t s_list[FIN_SEG];
     __shared__ int s_wcnt[FIN_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1520,7 +1524,8 @@ __device__ void reduce_partials_masked(const float* __restrict__ partials, int r
                 off += (w < warp) ? c : 0;
                 total += c;
             }
-            if (live) s_list[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(r - seg0);
+            const int at = off + __popc(m & ((1u << lane) - 1u));
+            if (live && GIRA_IN(at < FIN_SEG, st)) s_list[at] = (uint16_t)(r - seg0);
             nl += total;
             __syncthreads();
         }
@@ -1530,7 +1535,8 @@ __device__ void reduce_partials_masked(const float* __restrict__ partials, int r
             for (int c = c0; c < c1; c += 8) {   // eight loads in flight
                 float v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (c + u < c1) ? __ldcg(sseg + s_list[c + u]) : 0.f;
+                for (int u = 0; u < 8; ++u)
+                    v[u] = (c + u < c1 && GIRA_IN(s_list[c + u] < seg1 - seg0, st)) ? __ldcg(sseg + s_list[c + u]) : 0.f;
                 float f = 0.f;   // binary32 groups of 8 (GB300 runs binary64 at 1/64 of the binary32 rate)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) f += v[u];
@@ -1593,7 +1599,7 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
     const int nb = min(FIN_CPB, f.k - b0);
     const int nout = nb * NSTAT;
     if (f.partials && f.masks) {
-        reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, part, S);
+        reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, part, S, f.st);
     } else if (f.partials) {
         reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
     } else if (t < nout) {
@@ -1814,6 +1820,7 @@ __global__ void model_out_kernel(const double* __restrict__ model64, int k, floa
     const int s = blockIdx.x * blockDim.x + threadIdx.x;   // slot; the caller's index is perm[s]
     if (s >= k) return;
     const int b = perm ? perm[s] : s;
+    if (!GIRA_IN(b >= 0 && b < k, const_cast<DeviceState*>(st))) return;
     const double* m = model64 + (size_t)s * MODEL;
     w[b] = (float)(st->w_raw ? m[0] / nsum : m[0]);
     for (int i = 0; i < 3; ++i) mu[3 * (size_t)b + i] = (float)m[1 + i];
@@ -1822,7 +1829,7 @@ __global__ void model_out_kernel(const double* __restrict__ model64, int k, floa
 }
 
 // Components in the order of a space-filling curve of their means: the Morton
-// code (10 bits per axis over the means' bounding box, binary64) with the index
+// code (10 bits per axis over the means' bounding box, binary32) with the index
 // as the low bits, sorted by one block (bitonic network in shared memory).
 // Slot s then takes the component perm[s]: its row of `old` (a copy of model64)
 // is rebuilt into slot s of model64, params and shift4.  Only the order of the
@@ -1940,6 +1947,7 @@ __global__ void rebuild_components_kernel(const double* __restrict__ old, const 
         st += i;
     }
     const int b = perm[g];
+    if (!GIRA_IN(b >= 0 && b < (insts ? insts[comp_inst[g]].k : total_k), st)) return;
     const double* r = old + (size_t)b * MODEL;
     build_component(slot, r[0], r + 1, r + 4, params, shift4, model64, st, b);
 }

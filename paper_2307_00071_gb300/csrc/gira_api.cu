@@ -280,6 +280,7 @@ gira_status gira::device_status(const DeviceState& h) {
         case GIRA_ERR_NUMERIC:
             return fail(GIRA_ERR_NUMERIC, "a point's likelihood underflows binary32 under every component");
         case GIRA_ERR_TIMEOUT: return fail(GIRA_ERR_TIMEOUT, "a bounded device-side wait ran out (k-means++ seeding)");
+        case GIRA_ERR_BOUNDS: return fail(GIRA_ERR_BOUNDS, "a device-side index fell outside its buffer (debug build)");
         default: return fail((gira_status)h.error, "device error %d", h.error);
     }
 }
@@ -783,6 +784,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         if (final_loglik) GIRA_CUDA(chunk_lse(P, cb, b.p8, n, k, b.st, 0, true, &prof.launches, c.s));
     }
     EStepLaunch a{sorted ? b.p8s : b.p8, n, k, b.params, 0, b.partials, b.llp, nullptr, b.st, 0};
+    a.n_buf = n;
     a.masks = b.masks;
     a.pt_rows = rows;
     for (int t = 1; t <= o.iters && !chunked; ++t) {
@@ -924,6 +926,7 @@ gira_status gira_gmm_loglik(const float* points, int64_t n, int k, const float* 
         prof.t_init = prof.mark();
         prof.t_em = prof.t_init;
         EStepLaunch a{b.p8, n, k, b.params, 0, nullptr, b.llp, ppd, b.st, 0};
+        a.n_buf = n;
         COUNTED(prof, 1, launch_estep_pt(a, false, grid, c.s));
         COUNTED(prof, 1, launch_ll_reduce(b.llp, grid, b.st, c.s));
     }
@@ -1338,6 +1341,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     prof.t_init = prof.mark();
 
     EStepLaunch base{sorted ? b.p8s : b.p8, 0, 0, b.params, 0, b.partials, b.llp, nullptr, nullptr, 0};
+    base.n_buf = total_n;
     base.insts = b.insts;
     base.units = b.units;
     base.states = b.st;

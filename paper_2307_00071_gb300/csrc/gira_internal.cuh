@@ -51,6 +51,19 @@ struct DeviceState {
 
 __device__ __forceinline__ void set_error(DeviceState* st, int code) { atomicCAS(&st->error, 0, code); }
 
+// Index checks of the debug build (-DGIRA_DEBUG): GIRA_IN(cond, st) is cond, and a
+// false cond records GIRA_ERR_BOUNDS in st (the caller skips the access).  In
+// release builds it is true and the condition is not evaluated.
+#ifdef GIRA_DEBUG
+__device__ __forceinline__ bool gira_in(bool ok, DeviceState* st) {
+    if (!ok && st) set_error(st, GIRA_ERR_BOUNDS);
+    return ok;
+}
+#define GIRA_IN(cond, st) ::gira::gira_in((cond), (st))
+#else
+#define GIRA_IN(cond, st) true
+#endif
+
 // ---------------------------------------------------------------- packed FP32
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
@@ -359,7 +372,8 @@ struct EStepLaunch {
     // bit, and the live masks [npairs / 32][rows] (bit p: pair p reaches some point
     // of the warp)
     uint32_t* masks = nullptr;
-    int64_t pt_rows = 0;   // warps of the launch (the row count of partials and masks)
+    int64_t pt_rows = 0;   // point blocks of the launch (the row count of partials and masks)
+    int64_t n_buf = 0;     // points in pts8 (index checks of the debug build; 0: unchecked)
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count

@@ -137,6 +137,7 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
     NA_CUDA(launch_fill_padding(params, k, npairs, s));
     NA_CUDA(launch_params_from_model(weights, means, covs, k, model64, params, shift4, st, s));
     EStepLaunch a{p8, n, k, params, 0, nullptr, llp, per_point, st, 0};
+    a.n_buf = n;
     NA_CUDA(launch_estep_pt(a, false, grid, s));
     NA_CUDA(launch_ll_reduce(llp, grid, st, s));
     NA_CUDA(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s));

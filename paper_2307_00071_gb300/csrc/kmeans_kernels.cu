@@ -743,6 +743,7 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                              pz = zs[(qf >> 1) * KC_THREADS + ft];
                 const float4 pf = (qf & 1) ? make_float4(px.y, py.y, pz.y, 0.f) : make_float4(px.x, py.x, pz.x, 0.f);
                 const long long lo_src = __shfl_sync(FULL, (long long)llo, src);
+                (void)GIRA_IN(lo_src + qf < n && qf < cnt, st);   // the point is one of the lane's
                 const long long found = min((long long)n - 1, lo_src + qf);   // clamp never taken
                 if (lane < cs && !dead) {
                     const uint32_t bar = kc_peer(&sh.bar_cen[b], lane);
@@ -962,6 +963,7 @@ __global__ void label_stats_kernel(const float4* __restrict__ pts, int64_t n, in
             const int64_t i = i0 + r;
             if (i < n) {
                 const int b = labels[i];
+                if (!GIRA_IN(b >= 0 && b < k, st)) continue;
                 if (b != key) {
                     if (key >= 0) label_stats_flush(stats64, key, a);
 #pragma unroll
@@ -1000,6 +1002,7 @@ __global__ void label_stats_batched_kernel(const float4* __restrict__ pts, int64
             if (offsets[mid] <= i) lo = mid; else hi = mid;
         }
         if (states[lo].error) continue;
+        if (!GIRA_IN(labels[i] >= 0 && labels[i] < table[lo].k, states + lo)) continue;
         const int b = table[lo].comp_off + labels[i];
         const float4 x = pts[i], s = shift4[b];
         const double d[3] = {(double)x.x - (double)s.x, (double)x.y - (double)s.y, (double)x.z - (double)s.z};

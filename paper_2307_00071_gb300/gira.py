@@ -18,6 +18,7 @@ from . import build_lib
 
 OK = 0
 ERR_INVALID_ARG, ERR_NONFINITE_INPUT, ERR_NOT_PD, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC = 1, 2, 3, 4, 5, 6, 7
+ERR_BOUNDS = 8   # libraries built with GIRA_DEBUG: a device-side index outside its buffer
 INIT_KMEANS, INIT_PARAMS = 0, 1
 MAX_K, MAX_K_BATCHED, MAX_K4 = 8192, 1024, 8192
 
@@ -42,9 +43,11 @@ class Profile(C.Structure):
 
 
 def _load():
-    path = build_lib.LIB
-    if not os.path.exists(path) or build_lib.is_stale():
-        path = build_lib.build()   # raises if nvcc fails: no fallback
+    # GIRA_DEBUG=1 loads the build with device-side index checks (libgira_debug.so)
+    debug = os.environ.get("GIRA_DEBUG", "") not in ("", "0")
+    path = build_lib.lib_path(debug)
+    if not os.path.exists(path) or build_lib.is_stale(debug):
+        path = build_lib.build(debug=debug)   # raises if nvcc fails: no fallback
     lib = C.CDLL(path)
     vp, i64, dp, ip = C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int)
     lib.gira_fit_opts_default.argtypes = [C.POINTER(FitOpts)]
@@ -88,7 +91,7 @@ def _load():
 
 
 _lib = _load()
-LIB_PATH = build_lib.LIB
+LIB_PATH = _lib._name   # the library this process loaded
 
 
 def _check(status: int):
@@ -239,7 +242,9 @@ def gira_gmm_loglik_noalloc(points, weights, means, covs, per_point: bool = Fals
     """gira_gmm_loglik for callers that cannot allocate device memory (CUDA tensors only).
 
     The library keeps this call's scratch in a static device array instead of
-    allocating it, for code inside CUDA-graph capture or allocation-free loops.
+    allocating it (real-time loops that forbid allocation after start-up, hosts
+    whose device memory belongs to a pool).  The call copies its status through
+    host memory and synchronises its stream.
     """
     n = _check_points(points)
     k = int(weights.shape[0])

@@ -182,3 +182,11 @@ def test_profile_levels_without_gpu():
         p = gira.gira_profile_read(reset=True)
         assert p["calls"] == 0 and p["estep_launches"] == 0 and p["estep_ms"] == 0.0
     gira.gira_profile_enable(False)
+
+
+def test_debug_build_compiles_and_exports_the_same_symbols():
+    """The build with device-side index checks (GIRA_DEBUG) cross-compiles for sm_103a."""
+    from paper_2307_00071_gb300 import build_lib
+    dbg = C.CDLL(build_lib.build(debug=True))
+    for s in declared_symbols():
+        assert hasattr(dbg, s), s

@@ -653,11 +653,12 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         int *ksync, *perm;
         uint32_t* masks;
         unsigned long long* chg;
-        float4* p8s;
+        float4 *p8s, *p4s;
         void* osc;
     } b{};
-    // the E-steps run on the points in a spatial order (a warp's points then reach
-    // fewer components); k-means++ and Lloyd on the caller's order
+    // the E-steps and Lloyd run on the points in a spatial order (a warp's points then
+    // reach fewer components and centres); k-means++ on the caller's order, which
+    // defines its draws
     const bool sorted = !chunked && n <= point_order_max_n();
     auto layout = [&](Carver& cv) {
         b.st = cv.take<DeviceState>(1);
@@ -666,6 +667,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.p4 = cv.take<float4>(kinit ? n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)n);
         b.p8s = cv.take<float4>(sorted ? 2 * (size_t)n : 0);
+        b.p4s = cv.take<float4>(sorted && kinit ? (size_t)n : 0);
         b.osc = cv.take<char>(sorted ? point_order_scratch_bytes(n, 1) : 0);
         b.params = cv.take<float>((size_t)npairs * PAIR_FLOATS);
         b.shift4 = cv.take<float4>(k);
@@ -718,7 +720,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     COUNTED(prof, 1, launch_pack(pts, n, kinit ? b.p4 : nullptr, b.p8, b.st, c.s));
     if (sorted)
         COUNTED(prof, point_order_launches(1),
-                launch_point_order(b.p8, n, nullptr, nullptr, 0, 1, b.osc, b.p8s, nullptr, c.s));
+                launch_point_order(b.p8, n, nullptr, nullptr, 0, 1, b.osc, b.p8s, kinit ? b.p4s : nullptr, nullptr, c.s));
     if (chunked) {
         GIRA_CUDA(upload_chunks(P, cb, c.s));
         b.params = cb.params;
@@ -744,9 +746,9 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         GIRA_CUDA(cudaMemsetAsync(b.sums, 0, sizeof(double) * 4 * k, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.chg, 0, sizeof(unsigned long long) * (o.lloyd_iters + 1), c.s));
         COUNTED(prof, 1 + 2 * o.lloyd_iters,
-                launch_lloyd(b.p4, n, k, o.lloyd_iters, b.c4, b.lab, b.sums, b.chg, b.st, c.s));
+                launch_lloyd(sorted ? b.p4s : b.p4, n, k, o.lloyd_iters, b.c4, b.lab, b.sums, b.chg, b.st, c.s));
         GIRA_CUDA(cudaMemsetAsync(b.stats64, 0, sizeof(double) * NSTAT * k, c.s));
-        COUNTED(prof, 1, launch_label_stats(b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
+        COUNTED(prof, 1, launch_label_stats(sorted ? b.p4s : b.p4, n, k, b.lab, b.c4, b.stats64, b.st, c.s));
         GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * k, cudaMemcpyDeviceToDevice, c.s));
         if (chunked) {
             COUNTED(prof, 1, launch_reduce_finalize_chunks(nullptr, nullptr, 0, b.stats64, b.shift4, cb.insts,
@@ -1175,7 +1177,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         unsigned long long* chg;
         KppInst *ktab, *kseed;
         BatchUnit* lunits;
-        float4* p8s;
+        float4 *p8s, *p4s;
         int2* ounits;
         void* osc;
     } b{};
@@ -1216,6 +1218,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
         b.p4 = cv.take<float4>(kinit ? (size_t)total_n : 0);
         b.p8 = cv.take<float4>(2 * (size_t)total_n);
         b.p8s = cv.take<float4>(sorted ? 2 * (size_t)total_n : 0);
+        b.p4s = cv.take<float4>(sorted && kinit ? (size_t)total_n : 0);
         b.ounits = cv.take<int2>((size_t)nounits);
         b.osc = cv.take<char>(sorted ? point_order_scratch_bytes(total_n, batch) : 0);
         b.params = cv.take<float>((size_t)par_floats);
@@ -1285,7 +1288,8 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
     if (sorted) {
         GIRA_CUDA(cudaMemcpyAsync(b.ounits, ounits.data(), sizeof(int2) * ounits.size(), cudaMemcpyHostToDevice, c.s));
         COUNTED(prof, point_order_launches(batch),
-                launch_point_order(b.p8, total_n, b.offs, b.ounits, (int)nounits, batch, b.osc, b.p8s, nullptr, c.s));
+                launch_point_order(b.p8, total_n, b.offs, b.ounits, (int)nounits, batch, b.osc, b.p8s,
+                                   kinit ? b.p4s : nullptr, nullptr, c.s));
     }
     COUNTED(prof, 1, launch_fill_padding_batched(b.params, b.insts, batch, 0, b.npairs, c.s));
     float* w_d = (kw == Kind::Device) ? weights : b.mw;
@@ -1316,10 +1320,11 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
                                                   b.d2 + I.pt_off, b.bs + nblk_off[i], b.ch + I.comp_off, b.st + i,
                                                   c.s));
         }
+        const float4* p4l = sorted ? b.p4s : b.p4;   // Lloyd and the one-hot statistics: sorted points
         COUNTED(prof, 1 + 2 * o.lloyd_iters,
-                launch_lloyd_batched(b.p4, b.ktab, b.lunits, (int)lloyd_units.size(), total_k, b.comp_inst,
+                launch_lloyd_batched(p4l, b.ktab, b.lunits, (int)lloyd_units.size(), total_k, b.comp_inst,
                                      o.lloyd_iters, b.c4, b.lab, b.sums, b.chg, b.st, c.s));
-        COUNTED(prof, 1, launch_label_stats_batched(b.p4, total_n, b.offs, batch, b.ktab, b.lab, b.c4, b.stats64,
+        COUNTED(prof, 1, launch_label_stats_batched(p4l, total_n, b.offs, batch, b.ktab, b.lab, b.c4, b.stats64,
                                                     b.st, c.s));
         GIRA_CUDA(cudaMemcpyAsync(b.shift4, b.c4, sizeof(float4) * total_k, cudaMemcpyDeviceToDevice, c.s));
         COUNTED(prof, 1, launch_reduce_finalize_batched(nullptr, nullptr, b.stats64, b.shift4, b.insts, b.blocks,
@@ -2388,7 +2393,7 @@ gira_status gira_test_point_order(const float* points, int64_t n, int batch, con
     GIRA_CUDA(cudaMemcpyAsync(b.offs, offs.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, c.s));
     GIRA_CUDA(cudaMemcpyAsync(b.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, c.s));
     GIRA_CUDA(launch_pack(points, n, nullptr, b.p8, b.st, c.s));
-    GIRA_CUDA(launch_point_order(b.p8, n, b.offs, b.units, (int)nunits, batch, b.osc, nullptr, order, c.s));
+    GIRA_CUDA(launch_point_order(b.p8, n, b.offs, b.units, (int)nunits, batch, b.osc, nullptr, nullptr, order, c.s));
     GIRA_CUDA(cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, c.s));
     GIRA_CUDA(cudaStreamSynchronize(c.s));
     return device_status(h);

@@ -411,15 +411,15 @@ cudaError_t launch_pack(const float* pts3, int64_t n, float4* pts4, float4* pts8
 // (instance, 18-bit Morton code in the instance's bounding cube).  offsets_d /
 // units_d: the batch's point offsets and its (instance, chunk) bounding-box
 // blocks (point_order_fill_units), or nullptr for one instance of n points.
-// Writes the sorted points to p8_out and, if order_out, the source index of
-// every sorted point.  scratch: point_order_scratch_bytes(n, batch) bytes.
+// Writes the sorted points to p8_out (and, if p4_out, as (x, y, z, 0)) and, if
+// order_out, the source index of every sorted point.  scratch: point_order_scratch_bytes(n, batch) bytes.
 int64_t point_order_box_units(const int64_t* offsets, int batch);
 void point_order_fill_units(const int64_t* offsets, int batch, int2* units);
 size_t point_order_scratch_bytes(int64_t n, int batch);
 int point_order_launches(int batch);   // kernels one launch_point_order makes
 int64_t point_order_max_n();          // larger inputs keep the caller's order
 cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offsets_d, const int2* units_d,
-                               int nunits, int batch, void* scratch, float4* p8_out, int* order_out,
+                               int nunits, int batch, void* scratch, float4* p8_out, float4* p4_out, int* order_out,
                                cudaStream_t s);
 cudaError_t launch_fill_padding(float* params, int k, int npairs_pad, cudaStream_t s);
 // Sum of the per-CTA log-likelihoods into st->ll_sum (fixed order).

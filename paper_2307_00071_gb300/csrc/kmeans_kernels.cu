@@ -788,7 +788,14 @@ struct CPair {
 // each) against the k centres in shared memory.
 __device__ void lloyd_assign_groups(const float4* __restrict__ pts, int64_t n, int npair, const CPair* sc,
                                     int32_t* labels, double* sums, unsigned long long* changed, int it,
-                                    int64_t first, int64_t stride);
+                                    int64_t first, int64_t stride, uint16_t* lists);
+
+// Shared memory of an assignment block: the centre pairs, then (centre pairs up
+// to LL_LIST_MAX) one list of candidate pairs per warp.
+constexpr int LL_LIST_MAX = 1024;
+__host__ __device__ inline size_t lloyd_smem_bytes(int npair) {
+    return sizeof(CPair) * (size_t)npair + (npair <= LL_LIST_MAX ? (LL_THREADS / 32) * (size_t)npair * 2 : 0);
+}
 
 __global__ void __launch_bounds__(LL_THREADS) lloyd_assign_kernel(
     const float4* __restrict__ pts, int64_t n, int k, const float4* __restrict__ centers, int32_t* labels,
@@ -804,8 +811,9 @@ __global__ void __launch_bounds__(LL_THREADS) lloyd_assign_kernel(
     }
     __syncthreads();
     const int64_t group = (int64_t)LL_THREADS * LL_PPT;
+    uint16_t* lists = npair <= LL_LIST_MAX ? reinterpret_cast<uint16_t*>(sc + npair) : nullptr;
     lloyd_assign_groups(pts, n, npair, sc, labels, sums, changed, it, (int64_t)blockIdx.x * group,
-                        (int64_t)gridDim.x * group);
+                        (int64_t)gridDim.x * group, lists);
 }
 
 // Batched: CTA u assigns tile units[u].cta of instance units[u].inst.
@@ -828,14 +836,16 @@ __global__ void __launch_bounds__(LL_THREADS) lloyd_assign_batched_kernel(
     }
     __syncthreads();
     const int64_t group = (int64_t)LL_THREADS * LL_PPT;
+    uint16_t* lists = npair <= LL_LIST_MAX ? reinterpret_cast<uint16_t*>(sc + npair) : nullptr;
     lloyd_assign_groups(pts + e.pt_off, e.n, npair, sc, labels + e.pt_off, sums + 4 * (size_t)e.comp_off, chg, it,
-                        (int64_t)u.cta * group, INT64_MAX / 2);
+                        (int64_t)u.cta * group, INT64_MAX / 2, lists);
 }
 
 __device__ void lloyd_assign_groups(const float4* __restrict__ pts, int64_t n, int npair, const CPair* sc,
                                     int32_t* labels, double* sums, unsigned long long* changed, int it,
-                                    int64_t first, int64_t stride) {
+                                    int64_t first, int64_t stride, uint16_t* lists) {
     const int lane = threadIdx.x & 31;
+    uint16_t* slist = lists ? lists + (threadIdx.x >> 5) * npair : nullptr;
     unsigned long long cnt = 0;
     for (int64_t g0 = first; g0 < n; g0 += stride) {
         // point r of this thread: g0 + warp_base + r * 32 + lane (coalesced per r)
@@ -853,7 +863,58 @@ __device__ void lloyd_assign_groups(const float4* __restrict__ pts, int64_t n, i
             bd[r] = INFINITY;
             best[r] = 0;
         }
-        for (int p = 0; p < npair; ++p) {
+        // After the first assignment: every point's previous centre bounds its nearest
+        // distance from above (U, the warp's largest), and a centre whose distance to the
+        // box of the warp's points exceeds U (with slack for the binary32 rounding of
+        // both) is farther than that from every point: only the other pairs are scanned,
+        // in increasing order, so the argmin and its ties are those of the full scan.
+        int nl = npair;
+        if (it > 0 && slist) {
+            float U = 0.f, lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+            for (int r = 0; r < LL_PPT; ++r) {
+                const int64_t i = min(wb + r * 32 + lane, n - 1);
+                const int lp = labels[i];
+                const CPair c = sc[lp >> 1];
+                const float cx = (lp & 1) ? c.x.y : c.x.x, cy = (lp & 1) ? c.y.y : c.y.x, cz = (lp & 1) ? c.z.y : c.z.x;
+                const float dx = __fadd_rn(X[r].x, cx), dy = __fadd_rn(Y[r].x, cy), dz = __fadd_rn(Z[r].x, cz);
+                const float d = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                U = fmaxf(U, d);
+                lo[0] = fminf(lo[0], X[r].x); lo[1] = fminf(lo[1], Y[r].x); lo[2] = fminf(lo[2], Z[r].x);
+                hi[0] = fmaxf(hi[0], X[r].x); hi[1] = fmaxf(hi[1], Y[r].x); hi[2] = fmaxf(hi[2], Z[r].x);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                U = fmaxf(U, __shfl_xor_sync(FULL, U, o));
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    lo[j] = fminf(lo[j], __shfl_xor_sync(FULL, lo[j], o));
+                    hi[j] = fmaxf(hi[j], __shfl_xor_sync(FULL, hi[j], o));
+                }
+            }
+            nl = 0;
+            for (int j0 = 0; j0 < npair; j0 += 32) {
+                const int p = j0 + lane;
+                bool live = false;
+                if (p < npair) {
+                    const CPair c = sc[p];
+                    const float ncx[2] = {c.x.x, c.x.y}, ncy[2] = {c.y.x, c.y.y}, ncz[2] = {c.z.x, c.z.y};
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {   // the centre is (-ncx, -ncy, -ncz)
+                        const float gx = fmaxf(fmaxf(lo[0] + ncx[m], -ncx[m] - hi[0]), 0.f);
+                        const float gy = fmaxf(fmaxf(lo[1] + ncy[m], -ncy[m] - hi[1]), 0.f);
+                        const float gz = fmaxf(fmaxf(lo[2] + ncz[m], -ncz[m] - hi[2]), 0.f);
+                        live = live || !(fmaf(gz, gz, fmaf(gy, gy, gx * gx)) * (1.f - 1e-5f) > U);
+                    }
+                }
+                const uint32_t mk = __ballot_sync(FULL, live);
+                if (live) slist[nl + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)p;
+                nl += __popc(mk);
+            }
+            __syncwarp();
+        }
+        for (int q = 0; q < nl; ++q) {
+            const int p = nl == npair ? q : slist[q];
             const CPair c = sc[p];
 #pragma unroll
             for (int r = 0; r < LL_PPT; ++r) {
@@ -1156,7 +1217,7 @@ cudaError_t launch_lloyd(const float4* pts4, int64_t n, int k, int lloyd_iters, 
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(CPair) * (size_t)((k + 1) / 2);
+    const size_t smem = lloyd_smem_bytes((k + 1) / 2);
     const int threads = LL_THREADS;
     const int64_t want = (n + (int64_t)threads * LL_PPT - 1) / ((int64_t)threads * LL_PPT);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
@@ -1177,7 +1238,7 @@ int lloyd_tile() { return LL_THREADS * LL_PPT; }
 cudaError_t launch_lloyd_batched(const float4* pts4, const KppInst* table, const BatchUnit* units, int nunits,
                                  int total_k, const int* comp_inst, int lloyd_iters, float4* centers, int32_t* labels,
                                  double* sums, unsigned long long* changed, DeviceState* states, cudaStream_t s) {
-    const size_t smem = sizeof(CPair) * (size_t)((GIRA_MAX_K_BATCHED + 1) / 2);
+    const size_t smem = lloyd_smem_bytes((GIRA_MAX_K_BATCHED + 1) / 2);
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024)
         e = cudaFuncSetAttribute(lloyd_assign_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -246,12 +246,13 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(const int* __restrict_
 // Stable scatter: one warp walks its tile 32 keys at a time, in order; lanes with
 // equal digits rank among themselves (match_any) after the count of that digit so
 // far in the tile, which starts at the tile's scanned offset.  The last pass also
-// moves the points (p8 -> p8_out).
+// moves the points (p8 -> p8_out, and p4_out: (x, y, z, 0)).
 __global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __restrict__ keys_in,
                                                             const int* __restrict__ idx_in, int64_t n, int shift,
                                                             int ntiles, const int* __restrict__ offs,
                                                             uint32_t* keys_out, int* idx_out,
-                                                            const float4* __restrict__ p8, float4* p8_out) {
+                                                            const float4* __restrict__ p8, float4* p8_out,
+                                                            float4* p4_out) {
     __shared__ int cnt[8][RADIX];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * 8 + warp;
@@ -276,8 +277,10 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __re
             keys_out[pos] = key;
             idx_out[pos] = src;
             if (p8_out) {
-                p8_out[2 * (int64_t)pos] = p8[2 * (int64_t)src];
-                p8_out[2 * (int64_t)pos + 1] = p8[2 * (int64_t)src + 1];
+                const float4 a = p8[2 * (int64_t)src], b = p8[2 * (int64_t)src + 1];
+                p8_out[2 * (int64_t)pos] = a;
+                p8_out[2 * (int64_t)pos + 1] = b;
+                if (p4_out) p4_out[pos] = make_float4(a.x, a.z, b.x, 0.f);
             }
         }
     }
@@ -327,7 +330,7 @@ size_t point_order_scratch_bytes(int64_t n, int batch) {
 }
 
 cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offsets_d, const int2* units_d,
-                               int nunits, int batch, void* scratch, float4* p8_out, int* order_out,
+                               int nunits, int batch, void* scratch, float4* p8_out, float4* p4_out, int* order_out,
                                cudaStream_t s) {
     const int64_t ntiles = ceil_div(n, TILE);
     const int64_t m = ntiles * RADIX;
@@ -364,7 +367,7 @@ cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offse
         scan_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(counts, m, bsum, (int)ntiles, toffs);
         int* io = (last && order_out) ? order_out : iout;
         radix_scatter_kernel<<<tblocks, 256, 0, s>>>(k0, iin, n, shift, (int)ntiles, toffs, k1, io, p8,
-                                                     last ? p8_out : nullptr);
+                                                     last ? p8_out : nullptr, last ? p4_out : nullptr);
         std::swap(k0, k1);
         iout = iin;   // the input indices are free for the next pass's output
         iin = io;

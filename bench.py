@@ -251,7 +251,7 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- extras
 GRAD_K, GRAD_SCAN = 1024, 100_000
-GRAD_FP32_OPS = 44   # per unit: d-form logit 12 + exp-sum 1 + statistics 17 + P'^T P' d and its sums 14
+GRAD_FP32_OPS = 32   # per unit, survey conventions: the fit's 23 + z = P'^T y (6) + sum of gamma z (3)
 
 
 def bench_grad(gira, frame_pts, sms, mhz, reps=20):
@@ -495,7 +495,7 @@ D4_K = 512
 # per unit, the fewest FP32 operations the 4D step needs: logit P'x + b' and its squares 14,
 # sum 1, statistics 20 (gamma, S0, gamma d, S1, S2); the kernel issues 8 more (d = x - mu
 # in both passes) and one MUFU ex2
-D4_FP32_OPS = 35
+D4_FP32_OPS = 33     # per unit, survey conventions: y 10, q 4, l 1, LSE 2, gamma 1, S0 1, S1 4, S2 10
 
 
 def bench_d4(gira, frame_pts, sms, mhz, reps=5):

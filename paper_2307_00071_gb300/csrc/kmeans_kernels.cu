@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
     }
     float lmax = -INFINITY;   // the largest D^2 of the lane's points (an upper bound once set)
     float2 D[KC_PMAX];   // D^2 of points 2p, 2p+1 (padding lanes: +inf, never chosen, fx48 0 not used)
-    u128 ls{0ull, 0ull};
+    u128 ls{0ull, 0ull}, linc{0ull, 0ull};   // the lane sum and its inclusive warp prefix
     int64_t idx = (int64_t)floor(uniform53(seed, 0) * (double)n);
     if (idx > n - 1) idx = n - 1;
     float4 cen = __ldg(pts + idx);
@@ -639,7 +639,8 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         // completed before this CTA read centre j - 2's totals)
         const int nblk = cs * KC_WARPS;
         if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)nblk * (uint32_t)sizeof(u128));
-        const u128 linc = u128_warp_incl_scan(ls, lane);
+        const unsigned long long k53 = splitmix64(seed, (uint64_t)j) >> 11;   // the draw: no data dependence
+        if (__any_sync(FULL, changed)) linc = u128_warp_incl_scan(ls, lane);   // else unchanged since j - 1
         {   // this warp's block total, to every CTA's slot g
             const u128 total = u128_shfl(linc, 31);
             if (lane < cs && !dead) kc_send_u128(kc_peer(&sh.csum[b][g], lane), total, kc_peer(&sh.bar_sum[b], lane));
@@ -661,7 +662,7 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
             const u128 before = u128_sub(lincl, run);   // the blocks of lower lanes
             const u128 T = u128_shfl(lincl, 31);
             if (!u128_zero(T)) {
-                const u128 t = fx_threshold(splitmix64(seed, (uint64_t)j) >> 11, T);
+                const u128 t = fx_threshold(k53, T);
                 const unsigned hits = __ballot_sync(FULL, u128_gt(lincl, t));   // t < T: not empty
                 const int hl = hits ? __ffs(hits) - 1 : 0;
                 if (lane == hl) {   // the first of this lane's blocks whose running sum exceeds r

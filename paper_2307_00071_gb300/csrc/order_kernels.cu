@@ -245,45 +245,57 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(const int* __restrict_
 
 // Stable scatter: one warp walks its tile 32 keys at a time, in order; lanes with
 // equal digits rank among themselves (match_any) after the count of that digit so
-// far in the tile, which starts at the tile's scanned offset.  The last pass also
-// moves the points (p8 -> p8_out, and p4_out: (x, y, z, 0)).
+// far in the tile, which starts at the tile's scanned offset.  The tile's keys and
+// indices are loaded before the walk (all loads in flight at once).
+constexpr int SC_ROUNDS = TILE / 32;
 __global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __restrict__ keys_in,
                                                             const int* __restrict__ idx_in, int64_t n, int shift,
                                                             int ntiles, const int* __restrict__ offs,
-                                                            uint32_t* keys_out, int* idx_out,
-                                                            const float4* __restrict__ p8, float4* p8_out,
-                                                            float4* p4_out) {
+                                                            uint32_t* keys_out, int* idx_out) {
     __shared__ int cnt[8][RADIX];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * 8 + warp;
     if (tile >= ntiles) return;
+    const int64_t b = (int64_t)tile * TILE, e = min(n, b + TILE);
+    uint32_t key[SC_ROUNDS];
+    int src[SC_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < SC_ROUNDS; ++r) {
+        const int64_t i = b + r * 32 + lane;
+        key[r] = i < e ? keys_in[i] : 0u;
+        src[r] = i < e ? idx_in[i] : 0;
+    }
     int* c = cnt[warp];
     for (int d = lane; d < RADIX; d += 32) c[d] = offs[(size_t)tile * RADIX + d];   // tile-major offsets
     __syncwarp();
-    const int64_t b = (int64_t)tile * TILE, e = min(n, b + TILE);
     const uint32_t lt = (1u << lane) - 1u;
-    for (int64_t i0 = b; i0 < e; i0 += 32) {
-        const int64_t i = i0 + lane;
-        const bool valid = i < e;
-        const uint32_t key = valid ? keys_in[i] : 0u;
-        const int d = valid ? (int)((key >> shift) & (RADIX - 1)) : RADIX;   // RADIX: no slot
+#pragma unroll
+    for (int r = 0; r < SC_ROUNDS; ++r) {
+        const bool valid = b + r * 32 + lane < e;
+        const int d = valid ? (int)((key[r] >> shift) & (RADIX - 1)) : RADIX;   // RADIX: no slot
         const uint32_t peers = __match_any_sync(FULL, d);
         const int pos = valid ? c[d] + __popc(peers & lt) : 0;
         __syncwarp();
         if (valid && (peers & lt) == 0u) c[d] += __popc(peers);   // the lowest lane of each digit
         __syncwarp();
         if (valid && pos >= 0 && pos < n) {   // (the scanned counts place every key inside [0, n))
-            const int src = idx_in[i];
-            keys_out[pos] = key;
-            idx_out[pos] = src;
-            if (p8_out) {
-                const float4 a = p8[2 * (int64_t)src], b = p8[2 * (int64_t)src + 1];
-                p8_out[2 * (int64_t)pos] = a;
-                p8_out[2 * (int64_t)pos + 1] = b;
-                if (p4_out) p4_out[pos] = make_float4(a.x, a.z, b.x, 0.f);
-            }
+            keys_out[pos] = key[r];
+            idx_out[pos] = src[r];
         }
     }
+}
+
+// The points in the sorted order: p8_out[j] = p8[order[j]] (and p4_out: (x, y, z, 0)).
+__global__ void __launch_bounds__(256) gather_kernel(const int* __restrict__ order, int64_t n,
+                                                     const float4* __restrict__ p8, float4* p8_out, float4* p4_out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t s = order[j];
+    if (s < 0 || s >= n) return;
+    const float4 a = p8[2 * s], b = p8[2 * s + 1];
+    p8_out[2 * j] = a;
+    p8_out[2 * j + 1] = b;
+    if (p4_out) p4_out[j] = make_float4(a.x, a.z, b.x, 0.f);
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -308,7 +320,7 @@ void point_order_fill_units(const int64_t* offsets, int batch, int2* units) {
         for (int64_t c = 0; c * BOX_CHUNK < offsets[i + 1] - offsets[i]; ++c) units[u++] = make_int2(i, (int)c);
 }
 
-int point_order_launches(int batch) { return 3 + 5 * radix_passes(batch); }
+int point_order_launches(int batch) { return 4 + 5 * radix_passes(batch); }   // with the gather
 
 // the largest n the scan's two levels hold (every tile's 512 digit counts)
 int64_t point_order_max_n() { return (int64_t)SCAN_PER_BLOCK * SCAN_PER_BLOCK / RADIX * TILE; }
@@ -366,12 +378,12 @@ cudaError_t launch_point_order(const float4* p8, int64_t n, const int64_t* offse
         scan_bsum_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
         scan_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(counts, m, bsum, (int)ntiles, toffs);
         int* io = (last && order_out) ? order_out : iout;
-        radix_scatter_kernel<<<tblocks, 256, 0, s>>>(k0, iin, n, shift, (int)ntiles, toffs, k1, io, p8,
-                                                     last ? p8_out : nullptr, last ? p4_out : nullptr);
+        radix_scatter_kernel<<<tblocks, 256, 0, s>>>(k0, iin, n, shift, (int)ntiles, toffs, k1, io);
         std::swap(k0, k1);
         iout = iin;   // the input indices are free for the next pass's output
         iin = io;
     }
+    if (p8_out) gather_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(iin, n, p8, p8_out, p4_out);
     return cudaGetLastError();
 }
 

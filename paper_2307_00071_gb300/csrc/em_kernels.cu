@@ -1373,72 +1373,123 @@ constexpr int FIN_THREADS = FIN_CPB * NSTAT * FIN_SPLIT;   // 320
 constexpr int ORDER_THREADS = 1024;   // order_components_kernel: one block
 constexpr int ORDER_MAX_K = 8192;     // keys in dynamic shared memory (64 KB)
 
-// From (w, mu, Sigma) in binary64 to the E-step parameters of component b:
-// Cholesky Sigma = L L^T (closed form 3x3), P = L^{-1}, scaled to base 2.
+// ---- the parameter build, shared by the scalar and the warp-parallel forms.
+// Every helper fixes its binary64 operations (explicit rounding intrinsics, no
+// contraction left to the compiler), so both forms give the same bits.
+
+// Cholesky Sigma = L L^T of c = (00, 01, 02, 11, 12, 22) by Schur complements,
+// in terms of the pivots' reciprocal square roots:
+//   u = a00^-1/2, r0 = u^2, h0 = a01 r0,
+//   s11 = a11 - h0 a01, s12 = a12 - h0 a02, s22 = a22 - (a02 r0) a02,
+//   v = s11^-1/2, t = s12 v^2, a22' = s22 - t s12, z = a22'^-1/2, g = a02 - a01 t;
+// then P = L^-1 has P00 = u, P11 = v, P22 = z, P10 = -h0 v, P21 = -t z,
+// P20 = -(r0 g) z, and prod_j P_jj = u v z.  pd: every pivot positive.
+struct CholInv {
+    double u, v, z, r0, h0, t, g;
+    bool pd;
+};
+
+__device__ __forceinline__ CholInv chol_inv(const double c[6]) {
+    CholInv k;
+    k.u = rsqrt(c[0]);
+    k.r0 = __dmul_rn(k.u, k.u);
+    k.h0 = __dmul_rn(c[1], k.r0);
+    const double h1 = __dmul_rn(c[2], k.r0);
+    const double s11 = __fma_rn(-k.h0, c[1], c[3]);
+    const double s12 = __fma_rn(-k.h0, c[2], c[4]);
+    const double s22 = __fma_rn(-h1, c[2], c[5]);
+    k.v = rsqrt(s11);
+    k.t = __dmul_rn(s12, __dmul_rn(k.v, k.v));
+    const double a22 = __fma_rn(-k.t, s12, s22);
+    k.z = rsqrt(a22);
+    k.g = __fma_rn(-c[1], k.t, c[2]);
+    k.pd = c[0] > 0.0 && s11 > 0.0 && a22 > 0.0;
+    return k;
+}
+
+constexpr double ALPHA = 0.84932180028801904272;   // sqrt(log2(e) / 2)
+
+// Entry e of P' = alpha L^-1 in the order (00, 10, 11, 20, 21, 22).
+__device__ __forceinline__ double chol_q(const CholInv& k, int e) {
+    double p;
+    switch (e) {
+        case 0: p = k.u; break;
+        case 1: p = -__dmul_rn(k.h0, k.v); break;
+        case 2: p = k.v; break;
+        case 3: p = -__dmul_rn(__dmul_rn(k.r0, k.g), k.z); break;
+        case 4: p = -__dmul_rn(k.t, k.z); break;
+        default: p = k.z; break;
+    }
+    return __dmul_rn(ALPHA, p);
+}
+
+// b_i = -(P' mu)_i from the row (a0, a1, a2) of P' (zeros above the diagonal).
+__device__ __forceinline__ double bias_row(double a0, double a1, double a2, const double mu[3]) {
+    return -__fma_rn(a2, mu[2], __fma_rn(a1, mu[1], __dmul_rn(a0, mu[0])));
+}
+
+// c = log2(w prod_j P_jj) - (3/2) log2(2 pi) in binary32: the exponent of
+// x = w u v z exactly, log2f of its significand rounded to 24 bits (error a
+// few 1e-8), the constant 4 - (3/2) log2(2 pi) = 0.0227558057915218 folded in.
+__device__ __forceinline__ float log2_norm(double w, const CholInv& k) {
+    const double x = __dmul_rn(w, __dmul_rn(__dmul_rn(k.u, k.v), k.z));
+    if (!(x >= DBL_MIN && x <= DBL_MAX)) return (float)(log2(x) - 3.9772441942084782);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ffu) - 1023;
+    const unsigned int m24 = (unsigned int)(((bits & 0xfffffffffffffull) + (1ull << 28)) >> 29);   // 0 .. 2^23
+    const float m = __int_as_float((127 << 23) + (int)m24);   // the significand in [1, 2]
+    return __fadd_rn((float)(e - 4), __fadd_rn(log2f(m), 0.0227558057915218f));
+}
+
+// alpha^2 / lambda_max(Sigma), lowered by 1e-4 relative: a lower bound of
+// sigma_min(P')^2 for the E-step's reach test.  lambda_max by the trigonometric
+// solution of the characteristic cubic of a symmetric 3x3 matrix in binary32
+// (error a few ulps), raised by 1e-4 relative; trace(Sigma) where the cubic is
+// degenerate; never below the largest diagonal entry.
+__device__ __forceinline__ float sigma_min_sq_bound(const float a[6]) {
+    const float a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
+    const float tr3 = (a00 + a11 + a22) * (1.f / 3.f);
+    const float e0 = a00 - tr3, e1 = a11 - tr3, e2 = a22 - tr3;
+    const float p2 = e0 * e0 + e1 * e1 + e2 * e2 + 2.f * (a01 * a01 + a02 * a02 + a12 * a12);
+    float lmax = 3.f * tr3;
+    if (p2 > 1e-30f) {
+        const float pp = sqrtf(p2 * (1.f / 6.f)), ip = 1.f / pp;
+        const float b00 = e0 * ip, b11 = e1 * ip, b22 = e2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+        const float det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+        const float r = fminf(1.f, fmaxf(-1.f, 0.5f * det));
+        const float trig = tr3 + 2.f * pp * cosf(acosf(r) * (1.f / 3.f));
+        if (trig == trig) lmax = fminf(lmax, trig * (1.f + 1e-4f));
+    }
+    lmax = fmaxf(lmax, fmaxf(a00, fmaxf(a11, a22)) * (1.f + 1e-4f));
+    return (float)(ALPHA * ALPHA) / lmax * (1.f - 1e-4f);
+}
+
+// From (w, mu, Sigma) in binary64 to the E-step parameters of component b
+// (scalar form; the EM finalize runs the same helpers lane-parallel).
 // Returns false (and flags GIRA_ERR_NOT_PD) if a pivot is not positive.
 // report: the caller's index of the component (differs from b when the fit
 // holds its components in another order).
 __device__ bool build_component(int b, double w, const double mu[3], const double c[6], float* params,
                                 float4* shift4, double* model64, DeviceState* st, int report) {
-    // c = (00, 01, 02, 11, 12, 22)
-    const double a00 = c[0];
-    bool pd = a00 > 0.0;
-    const double L00 = pd ? sqrt(a00) : 1.0;
-    const double P00 = 1.0 / L00;
-    const double L10 = c[1] * P00, L20 = c[2] * P00;
-    const double a11 = c[3] - L10 * L10;
-    pd = pd && a11 > 0.0;
-    const double L11 = pd ? sqrt(a11) : 1.0;
-    const double P11 = 1.0 / L11;
-    const double L21 = (c[4] - L20 * L10) * P11;
-    const double a22 = c[5] - L20 * L20 - L21 * L21;
-    pd = pd && a22 > 0.0;
-    const double L22 = pd ? sqrt(a22) : 1.0;
-    if (!pd) {
+    const CholInv k = chol_inv(c);
+    if (!k.pd) {
         atomicMin(&st->bad_component, report);
         set_error(st, GIRA_ERR_NOT_PD);
         return false;
     }
-    const double P22 = 1.0 / L22;
-    const double P10 = -L10 * P00 * P11;
-    const double P21 = -L21 * P11 * P22;
-    const double P20 = -(L20 * P00 + L21 * P10) * P22;
-    const double alpha = 0.84932180028801904272;   // sqrt(log2(e) / 2)
-    const double q[6] = {alpha * P00, alpha * P10, alpha * P11, alpha * P20, alpha * P21, alpha * P22};
-    const double bb[3] = {-(q[0] * mu[0]), -(q[1] * mu[0] + q[2] * mu[1]), -(q[3] * mu[0] + q[4] * mu[1] + q[5] * mu[2])};
-    const double LOG2_2PI = 2.6514961294723187980;     // log2(2 pi)
-    // log2 w + sum_j log2 P_jj - (3/2) log2(2 pi), one logarithm of the product
-    const double cc = log2(w * (P00 * P11 * P22)) - 1.5 * LOG2_2PI;
+    double q[6];
+    for (int e = 0; e < 6; ++e) q[e] = chol_q(k, e);
     float* base = params + (size_t)(b >> 1) * PAIR_FLOATS + (b & 1);
     for (int i = 0; i < 6; ++i) base[2 * (SLOT_P + i)] = (float)q[i];
-    for (int i = 0; i < 3; ++i) base[2 * (SLOT_B + i)] = (float)bb[i];
-    base[2 * SLOT_C] = (float)cc;
-    float m32[3] = {(float)mu[0], (float)mu[1], (float)mu[2]};
+    base[2 * (SLOT_B + 0)] = (float)bias_row(q[0], 0.0, 0.0, mu);
+    base[2 * (SLOT_B + 1)] = (float)bias_row(q[1], q[2], 0.0, mu);
+    base[2 * (SLOT_B + 2)] = (float)bias_row(q[3], q[4], q[5], mu);
+    base[2 * SLOT_C] = log2_norm(w, k);
+    const float m32[3] = {(float)mu[0], (float)mu[1], (float)mu[2]};
     for (int i = 0; i < 3; ++i) base[2 * (SLOT_NMU + i)] = -m32[i];
     base[2 * SLOT_W] = (float)w;
-    // lambda_max(Sigma) by the trigonometric solution of the characteristic cubic of a
-    // symmetric 3x3 matrix, in binary32 (its error is a few ulps of lambda_max), raised
-    // by 1e-4 relative to an upper bound; trace(Sigma) where the cubic is degenerate.
-    // alpha^2 over it, lowered by 1e-4 relative, bounds sigma_min(P')^2 from below.
-    {
-        const float a00 = (float)c[0], a01 = (float)c[1], a02 = (float)c[2], a11 = (float)c[3], a12 = (float)c[4],
-                    a22 = (float)c[5];
-        const float tr3 = (a00 + a11 + a22) * (1.f / 3.f);
-        const float e0 = a00 - tr3, e1 = a11 - tr3, e2 = a22 - tr3;
-        const float p2 = e0 * e0 + e1 * e1 + e2 * e2 + 2.f * (a01 * a01 + a02 * a02 + a12 * a12);
-        float lmax = 3.f * tr3;
-        if (p2 > 1e-30f) {
-            const float pp = sqrtf(p2 * (1.f / 6.f)), ip = 1.f / pp;
-            const float b00 = e0 * ip, b11 = e1 * ip, b22 = e2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
-            const float det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                              b02 * (b01 * b12 - b11 * b02);
-            const float r = fminf(1.f, fmaxf(-1.f, 0.5f * det));
-            const float trig = tr3 + 2.f * pp * cosf(acosf(r) * (1.f / 3.f));
-            if (trig == trig) lmax = fminf(lmax, trig * (1.f + 1e-4f));
-        }
-        lmax = fmaxf(lmax, fmaxf(a00, fmaxf(a11, a22)) * (1.f + 1e-4f));
-        base[2 * SLOT_S] = (float)(alpha * alpha) / lmax * (1.f - 1e-4f);
-    }
+    const float c32[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
+    base[2 * SLOT_S] = sigma_min_sq_bound(c32);
     shift4[b] = make_float4(m32[0], m32[1], m32[2], 0.f);
     double* m = model64 + (size_t)b * MODEL;
     m[0] = w;
@@ -1479,87 +1530,115 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
     }
 }
 
+// Compensated binary32 accumulation (Knuth's TwoSum: the rounding error of each
+// addition, exact under round-to-nearest, is carried in e).
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    e = __fadd_rn(e, err);
+}
+
+// Per-component binary64 work area of the finalize (shared memory), in doubles.
+constexpr int FW = 64;
+constexpr int W_S = 0;      // S0, S1[3], S2[6]
+constexpr int W_QS = 10;    // P' (00,10,11,20,21,22) and the shift s[3]; later the new P' and b
+constexpr int W_R = 19;     // 1/q00, 1/q11, 1/q22, 1/N_b
+constexpr int W_T = 23;     // ybar[3], m10, m21
+constexpr int W_M = 28;     // M = P'^-1 (3x3 row-major; the identity for one-hot statistics)
+constexpr int W_CY = 37;    // C (3x3, both halves)
+constexpr int W_MU = 46;    // the new mean
+constexpr int W_MC = 49;    // M C (3x3)
+constexpr int W_C = 58;     // the new Sigma (00,01,02,11,12,22)
+constexpr int FF = 20;      // binary32 copies per component: P'[6], b[3], mu[3], w, Sigma[6]
+
 // The statistics of the pair of components b0, b0 + 1 (b0 even) from the per-warp
-// partial rows of the point-stationary E-step, in binary64: the rows whose live
-// mask has the pair's bit are listed in row order (segments of FIN_SEG rows,
-// compacted in shared memory), every output sums FIN_SPLIT fixed contiguous
-// slices of that list in binary32 groups of 8 and binary64 across groups, and
-// the slices are added in order.  The list depends only on the masks, so the
-// order of every addition is fixed.  Call with every thread of the block.
+// partial rows of the point-stationary E-step: the rows whose live mask has the
+// pair's bit are listed in row order (one block scan per segment of FIN_SEG rows,
+// each thread ranking a contiguous run of rows).  Output o (component o / NSTAT,
+// statistic o % NSTAT) belongs to the half-warp 2 warp + lane / 16: its lane q sums
+// the q-th of FIN_SPLIT fixed contiguous slices of the list in compensated binary32,
+// a fixed butterfly of compensated additions joins the 16 slices, and the pair
+// (sum, error) becomes one binary64 value in W.  The list depends only on the masks,
+// so the order of every addition is fixed.  Call with every thread of the block;
+// s_skip (set by thread 0 before the call) is read after the first barrier, and a
+// skipped block returns false before touching W.
 constexpr int FIN_SEG = 4096;
-__device__ void reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
-                                       int b0, int nout, double (*part)[FIN_CPB * NSTAT], double* S,
-                                       DeviceState* st) {
+static_assert(FIN_THREADS == 16 * FIN_CPB * NSTAT && FIN_SPLIT == 16, "one half-warp per output of the pair");
+__device__ bool reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
+                                       int b0, int nout, double (*W)[FW], const int* s_skip, DeviceState* st) {
     __shared__ uint16_t s_list[FIN_SEG];
-    __shared__ int s_wcnt[FIN_THREADS / 32];
+    __shared__ int s_wsum[FIN_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
+    const int o = 2 * warp + (lane >> 4), q = lane & 15;
     const uint32_t* mrow = masks + (size_t)((b0 >> 1) >> 5) * rows;
     const uint32_t bit = 1u << ((b0 >> 1) & 31);
     const float* src = partials + ((size_t)b0 * NSTAT + o) * rows;
-    double acc = 0.0;
+    float sum = 0.f, err = 0.f;
     for (int seg0 = 0; seg0 < rows; seg0 += FIN_SEG) {
         const int seg1 = min(rows, seg0 + FIN_SEG);
-        int nl = 0;   // live rows listed so far in this segment (the same in every thread)
         constexpr int RND = (FIN_SEG + FIN_THREADS - 1) / FIN_THREADS;
-        uint32_t mk[RND];   // this thread's mask words of the segment, loaded together
+        const int per = (seg1 - seg0 + FIN_THREADS - 1) / FIN_THREADS;   // rows ranked by one thread
+        const int r0 = seg0 + t * per;
+        uint32_t live = 0u;   // bit u: row r0 + u is live
 #pragma unroll
-        for (int u = 0; u < RND; ++u) {
-            const int r = seg0 + u * FIN_THREADS + t;
-            mk[u] = r < seg1 ? __ldg(mrow + r) : 0u;
+        for (int u = 0; u < RND; ++u)
+            if (u < per && r0 + u < seg1 && (__ldg(mrow + r0 + u) & bit)) live |= 1u << u;
+        const int cnt = __popc(live);
+        int incl = cnt;   // inclusive scan of the counts over the warp
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += v;
         }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (*s_skip) return false;
+        int off = incl - cnt, nl = 0;
 #pragma unroll
-        for (int u = 0; u < RND; ++u) {
-            const int r0 = seg0 + u * FIN_THREADS;
-            if (r0 >= seg1) break;
-            const int r = r0 + t;
-            const bool live = (mk[u] & bit) != 0u;
-            const uint32_t m = __ballot_sync(FULL, live);
-            if (lane == 0) s_wcnt[warp] = __popc(m);
-            __syncthreads();
-            int off = nl, total = 0;
-#pragma unroll
-            for (int w = 0; w < FIN_THREADS / 32; ++w) {
-                const int c = s_wcnt[w];
-                off += (w < warp) ? c : 0;
-                total += c;
-            }
-            const int at = off + __popc(m & ((1u << lane) - 1u));
-            if (live && GIRA_IN(at < FIN_SEG, st)) s_list[at] = (uint16_t)(r - seg0);
-            nl += total;
-            __syncthreads();
+        for (int w = 0; w < FIN_THREADS / 32; ++w) {
+            const int c = s_wsum[w];
+            off += (w < warp) ? c : 0;
+            nl += c;
         }
+        for (uint32_t m = live; m; m &= m - 1u) {
+            const int r = r0 + __ffs(m) - 1;
+            if (GIRA_IN(off < FIN_SEG, st)) s_list[off] = (uint16_t)(r - seg0);
+            ++off;
+        }
+        __syncthreads();
         if (o < nout) {
             const int c0 = q * nl / FIN_SPLIT, c1 = (q + 1) * nl / FIN_SPLIT;
             const float* sseg = src + seg0;
-            for (int c = c0; c < c1; c += 8) {   // eight loads in flight
-                float v[8];
+            for (int c = c0; c < c1; c += 16) {   // sixteen loads in flight
+                float v[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
+                for (int u = 0; u < 16; ++u)
                     v[u] = (c + u < c1 && GIRA_IN(s_list[c + u] < seg1 - seg0, st)) ? __ldcg(sseg + s_list[c + u]) : 0.f;
-                float f = 0.f;   // binary32 groups of 8 (GB300 runs binary64 at 1/64 of the binary32 rate)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) f += v[u];
-                acc += (double)f;
+                for (int u = 0; u < 16; ++u)
+                    if (c + u < c1) two_sum_acc(sum, err, v[u]);
             }
         }
         __syncthreads();   // the list is rebuilt for the next segment
     }
-    if (o < nout) part[q][o] = acc;
-    __syncthreads();
-    if (t < nout) {
-        double v = 0.0;
-        for (int q2 = 0; q2 < FIN_SPLIT; ++q2) v += part[q2][t];
-        S[t] = v;
+#pragma unroll
+    for (int d = 8; d > 0; d >>= 1) {   // butterfly over the half-warp: the same total in every lane
+        const float s2 = __shfl_xor_sync(FULL, sum, d), e2 = __shfl_xor_sync(FULL, err, d);
+        float e = __fadd_rn(err, e2);
+        two_sum_acc(sum, e, s2);
+        err = e;
     }
+    if (o < nout && q == 0) W[o / NSTAT][W_S + o % NSTAT] = __dadd_rn((double)sum, (double)err);
+    return true;
 }
 
 // M-step (the standard full-covariance update) from shifted statistics:
 //   N_b = S0 + 10 eps; with v = y = P'(x - s_b) (E-step partials, whitened) or
-//   v = d = x - s_b (one-hot KInit statistics), vbar = S1 / N_b and
-//   sum r (v - vbar)(v - vbar)^T = S2 - vbar S1^T - S1 vbar^T + S0 vbar vbar^T;
-//   mu = s + vbar (d) or s + P'^-1 vbar (y), and Sigma the centred sum / N_b,
-//   mapped back by P'^-1 (.) P'^-T in the whitened case, plus reg I.  The
+//   v = d = x - s_b (one-hot KInit statistics): vbar = S1 / N_b and the centred
+//   second moment C = S2 / N_b - vbar vbar^T (S1 = N_b vbar); mu = s + M vbar and
+//   Sigma = M C M^T + reg I with M = P'^-1 (whitened) or M = I (one-hot).  The
 //   weight N_b is normalised by sum_a N_a where it is used (E-step reference,
 //   model output).
 struct FinArgs {
@@ -1585,86 +1664,179 @@ struct FinArgs {
     int nwords;
 };
 
+__device__ __forceinline__ int sym_i(int u) { return u < 3 ? 0 : (u < 5 ? 1 : 2); }   // (00,01,02,11,12,22)
+__device__ __forceinline__ int sym_j(int u) { return u < 3 ? u : (u < 5 ? u - 2 : 2); }
+__device__ __forceinline__ double dneg(double x) {   // sign flip on the integer pipe
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// The M-step and the parameter build of components b0 + h (h = 0, 1) by one
+// warp: lanes 16 h .. 16 h + 15 take component b0 + h, and each stage computes
+// its entries in parallel lanes, every entry by a fixed sequence of binary64
+// operations (GB300 issues one binary64 warp instruction every 64 cycles per
+// warp, whatever the number of active lanes, so a stage costs what one entry
+// costs).  W[h][W_S ..] holds the statistics; pre is this lane's binary32 P'
+// entry (l < 6) or shift coordinate (6 <= l < 9), loaded at the kernel's start.
+__device__ void finalize_update_warp(const FinArgs& f, int b0, int nb, float pre, double (*W)[FW], float (*F)[FF]) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int b = b0 + h;
+    const bool on = h < nb;
+    double* w = W[h];
+    const bool white = f.partials != nullptr;
+    if (on && l < 9) w[W_QS + l] = (double)pre;
+    __syncwarp();
+    const double nbw = __dadd_rn(w[W_S], 10.0 * DBL_EPSILON);
+    // the reciprocals of q00, q11, q22 (the diagonal of M) and of N_b
+    if (on && l < 4) {
+        const double x = l == 3 ? nbw : (white ? w[W_QS + (l == 0 ? 0 : (l == 1 ? 2 : 5))] : 1.0);
+        w[W_R + l] = __drcp_rn(x);
+    }
+    __syncwarp();
+    const double inv = w[W_R + 3];
+    // vbar = S1 / N_b (l < 3); m10 = -q10 m00 m11 (l == 3), m21 = -q21 m11 m22 (l == 4)
+    if (on && l < 5) {
+        double A, B, C;
+        if (l < 3) {
+            A = w[W_S + 1 + l]; B = inv; C = 1.0;
+        } else {
+            const int j = l - 3;
+            A = dneg(w[W_QS + (j == 0 ? 1 : 4)]); B = w[W_R + j]; C = w[W_R + j + 1];
+        }
+        w[W_T + l] = __dmul_rn(__dmul_rn(A, B), C);
+    }
+    __syncwarp();
+    // C = S2 / N_b - vbar vbar^T (l < 6), m20 = -(q20 m00 + q21 m10) m22 (l == 6);
+    // lanes 7 .. 14 place the other entries of M
+    if (on && l < 7) {
+        const int i = sym_i(l < 6 ? l : 0), j = sym_j(l < 6 ? l : 0);
+        double A0, B0, A1, B1, C;
+        if (l < 6) {
+            A0 = w[W_S + 4 + l]; B0 = inv; A1 = dneg(w[W_T + i]); B1 = w[W_T + j]; C = 1.0;
+        } else {
+            A0 = w[W_QS + 3]; B0 = w[W_R + 0]; A1 = w[W_QS + 4]; B1 = w[W_T + 3]; C = dneg(w[W_R + 2]);
+        }
+        const double v = __dmul_rn(__fma_rn(A1, B1, __dmul_rn(A0, B0)), C);
+        if (l < 6) {
+            w[W_CY + 3 * i + j] = v;
+            w[W_CY + 3 * j + i] = v;
+        } else {
+            w[W_M + 6] = white ? v : 0.0;
+        }
+    } else if (on && l < 15) {
+        const int e = l - 7 + (l >= 13 ? 1 : 0);   // 0 .. 5, 7, 8
+        double v;
+        if (!white) v = (e == 0 || e == 4 || e == 8) ? 1.0 : 0.0;
+        else v = e == 0 ? w[W_R + 0] : e == 3 ? w[W_T + 3] : e == 4 ? w[W_R + 1] : e == 7 ? w[W_T + 4]
+                                     : e == 8 ? w[W_R + 2] : 0.0;
+        w[W_M + e] = v;
+    }
+    __syncwarp();
+    // mu = s + M vbar (l < 3); M C (3 <= l < 12)
+    if (on && l < 12) {
+        const int i = l < 3 ? l : (l - 3) / 3, j = l < 3 ? 0 : (l - 3) % 3;
+        const int bs = l < 3 ? 1 : 3;
+        const double* Bv = l < 3 ? w + W_T : w + W_CY + j;
+        const double* Mi = w + W_M + 3 * i;
+        const double c0 = l < 3 ? w[W_QS + 6 + l] : 0.0;
+        const double v = __fma_rn(Mi[2], Bv[2 * bs], __fma_rn(Mi[1], Bv[bs], __fma_rn(Mi[0], Bv[0], c0)));
+        if (l < 3) w[W_MU + l] = v;
+        else w[W_MC + l - 3] = v;
+    }
+    __syncwarp();
+    // Sigma = M C M^T + reg I (l < 6)
+    if (on && l < 6) {
+        const int i = sym_i(l), j = sym_j(l);
+        const double* a = w + W_MC + 3 * i;
+        const double* m = w + W_M + 3 * j;
+        w[W_C + l] = __fma_rn(a[2], m[2], __fma_rn(a[1], m[1], __fma_rn(a[0], m[0], i == j ? f.reg : 0.0)));
+    }
+    __syncwarp();
+    // the parameters (the scalar build_component's helpers, entries in parallel lanes)
+    double c[6], mu[3];
+    for (int e = 0; e < 6; ++e) c[e] = w[W_C + e];
+    for (int i = 0; i < 3; ++i) mu[i] = w[W_MU + i];
+    const CholInv k = chol_inv(c);
+    const bool ok = on && k.pd;
+    if (on && !k.pd && l == 0) {
+        atomicMin(&f.st->bad_component, f.perm ? f.perm[b] : b);
+        set_error(f.st, GIRA_ERR_NOT_PD);
+    }
+    if (ok && l < MODEL) {
+        double* m = f.model64 + (size_t)b * MODEL;
+        m[l] = l == 0 ? nbw : (l < 4 ? w[W_MU + l - 1] : w[W_C + l - 4]);
+    }
+    if (ok && l < 6) w[W_QS + l] = chol_q(k, l);
+    __syncwarp();
+    if (ok && l < 3) {
+        const double* qq = w + W_QS;
+        const double a0 = l == 0 ? qq[0] : (l == 1 ? qq[1] : qq[3]);
+        const double a1 = l == 0 ? 0.0 : (l == 1 ? qq[2] : qq[4]);
+        const double a2 = l == 2 ? qq[5] : 0.0;
+        w[W_QS + 6 + l] = bias_row(a0, a1, a2, mu);
+    }
+    const float cc = log2_norm(nbw, k);
+    __syncwarp();
+    // binary32 copies: P'[6] and b[3] (W_QS ..), mu[3], w, Sigma[6]
+    float* fc = F[h];
+    if (ok) {
+        for (int e = l; e < FF - 1; e += 16)
+            fc[e] = (float)(e < 9 ? w[W_QS + e] : (e < 12 ? w[W_MU + e - 9] : (e == 12 ? nbw : w[W_C + e - 13])));
+    }
+    __syncwarp();
+    if (ok) {
+        float* base = f.params + (size_t)(b >> 1) * PAIR_FLOATS + (b & 1);
+        static_assert(SLOT_B == SLOT_P + 6, "P' and b are consecutive slots");
+        if (l < 9) base[2 * (SLOT_P + l)] = fc[l];
+        else if (l == 9) base[2 * SLOT_C] = cc;
+        else if (l < 13) base[2 * (SLOT_NMU + l - 10)] = -fc[l - 1];
+        else if (l == 13) base[2 * SLOT_W] = fc[12];
+        else if (l == 14) base[2 * SLOT_S] = sigma_min_sq_bound(fc + 13);
+        else f.shift4[b] = make_float4(fc[9], fc[10], fc[11], 0.f);
+    }
+}
+
 // Components blk * FIN_CPB .. of one fit; block index blk == 0 also does the
 // log-likelihood, trace and convergence of an EM iteration.
 __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
-    __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
-    __shared__ double S[FIN_CPB * NSTAT];
+    __shared__ double W[FIN_CPB][FW];
+    __shared__ float F[FIN_CPB][FF];
     __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = (f.em && f.iter > f.st->stop_after) || f.st->error != 0;
-    __syncthreads();
-    if (s_skip) return;
+    static_assert(FIN_CPB == 2, "one half-warp per component in the update");
     const int t = threadIdx.x;
     const int b0 = blk * FIN_CPB;
     const int nb = min(FIN_CPB, f.k - b0);
     const int nout = nb * NSTAT;
-    if (f.partials && f.masks) {
-        reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, part, S, f.st);
-    } else if (f.partials) {
-        reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
-    } else if (t < nout) {
-        S[t] = f.stats64[(size_t)b0 * NSTAT + t];
-    }
-    __syncthreads();
-    if (t < nb) {
-        const int b = b0 + t;
-        const double* Sb = S + t * NSTAT;
-        const float4 sh = f.shift4[b];
-        const double s[3] = {sh.x, sh.y, sh.z};
-        const double s0 = Sb[0];
-        const double nbw = s0 + 10.0 * DBL_EPSILON;
-        const double inv = 1.0 / nbw;
-        // S2 index: 00->4, 01->5, 02->6, 11->7, 12->8, 22->9
-        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-        double mu[3], c[6];
-        if (f.partials) {
-            // E-step statistics: S1 = sum r y, S2 = sum r y y^T in the whitened
-            // coordinates y = P'(x - s) of the parameters the E-step used (P' the
-            // binary32 lower triangle alpha L^-1 in params, s = shift4).  With
-            // ybar = S1 / N_b and C = sum r (y - ybar)(y - ybar)^T / N_b:
-            // mu = s + P'^-1 ybar, Sigma = P'^-1 C P'^-T + reg I.  Every direction
-            // of a thin component keeps binary32 relative precision in y.
-            const float* pp = f.params + (size_t)(b >> 1) * PAIR_FLOATS + (b & 1);
-            const double q00 = pp[2 * (SLOT_P + 0)], q10 = pp[2 * (SLOT_P + 1)], q11 = pp[2 * (SLOT_P + 2)];
-            const double q20 = pp[2 * (SLOT_P + 3)], q21 = pp[2 * (SLOT_P + 4)], q22 = pp[2 * (SLOT_P + 5)];
-            // M = P'^-1 (lower triangular, forward substitution)
-            const double m00 = 1.0 / q00, m11 = 1.0 / q11, m22 = 1.0 / q22;
-            const double m10 = -q10 * m00 * m11;
-            const double m21 = -q21 * m11 * m22;
-            const double m20 = -(q20 * m00 + q21 * m10) * m22;
-            const double M[3][3] = {{m00, 0.0, 0.0}, {m10, m11, 0.0}, {m20, m21, m22}};
-            double yb[3];
-            for (int i = 0; i < 3; ++i) yb[i] = Sb[1 + i] * inv;
-            double Cy[3][3];
-            for (int u = 0; u < 6; ++u) {
-                const int i = ij[u][0], j = ij[u][1];
-                const double v = (Sb[4 + u] - yb[i] * Sb[1 + j] - Sb[1 + i] * yb[j] + s0 * yb[i] * yb[j]) * inv;
-                Cy[i][j] = Cy[j][i] = v;
-            }
-            for (int i = 0; i < 3; ++i) mu[i] = s[i] + M[i][0] * yb[0] + M[i][1] * yb[1] + M[i][2] * yb[2];
-            double MC[3][3];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) MC[i][j] = M[i][0] * Cy[0][j] + M[i][1] * Cy[1][j] + M[i][2] * Cy[2][j];
-            for (int u = 0; u < 6; ++u) {
-                const int i = ij[u][0], j = ij[u][1];
-                const double v = MC[i][0] * M[j][0] + MC[i][1] * M[j][1] + MC[i][2] * M[j][2];
-                c[u] = v + ((i == j) ? f.reg : 0.0);
-            }
-        } else {
-            // one-hot statistics about the centres (KInit): S1, S2 of d = x - s
-            double dl[3];
-            for (int i = 0; i < 3; ++i) {
-                mu[i] = (s0 * s[i] + Sb[1 + i]) * inv;
-                dl[i] = mu[i] - s[i];
-            }
-            for (int u = 0; u < 6; ++u) {
-                const int i = ij[u][0], j = ij[u][1];
-                const double v = Sb[4 + u] - dl[i] * Sb[1 + j] - Sb[1 + i] * dl[j] + s0 * dl[i] * dl[j];
-                c[u] = v * inv + ((i == j) ? f.reg : 0.0);
+    float pre = 0.f;   // warp 0: this lane's binary32 P' entry or shift coordinate, loaded early
+    if (t < 32) {
+        const int h = t >> 4, l = t & 15, b = b0 + h;
+        if (h < nb && l < 9) {
+            if (l < 6) {
+                pre = f.partials ? f.params[(size_t)(b >> 1) * PAIR_FLOATS + (b & 1) + 2 * (SLOT_P + l)] : 0.f;
+            } else {
+                const float4 sh = f.shift4[b];
+                pre = l == 6 ? sh.x : (l == 7 ? sh.y : sh.z);
             }
         }
-        build_component(b, nbw, mu, c, f.params, f.shift4, f.model64, f.st, f.perm ? f.perm[b] : b);
-        if (b == 0) f.st->w_raw = 1;
+    }
+    if (t == 0) s_skip = (f.em && f.iter > f.st->stop_after) || f.st->error != 0;
+    if (f.partials && f.masks) {
+        if (!reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, W, &s_skip, f.st)) return;
+    } else {
+        __syncthreads();
+        if (s_skip) return;
+        if (f.partials) {
+            __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
+            __shared__ double S[FIN_CPB * NSTAT];
+            reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
+            if (t < nout) W[t / NSTAT][W_S + t % NSTAT] = S[t];
+        } else if (t < nout) {
+            W[t / NSTAT][W_S + t % NSTAT] = f.stats64[(size_t)b0 * NSTAT + t];
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        finalize_update_warp(f, b0, nb, pre, W, F);
+        if (t == 0 && b0 == 0) f.st->w_raw = 1;
     }
     if (f.em && f.do_ll && blk == 0 && t >= 32) {   // warps 1 ..: log-likelihood, trace, convergence
         __shared__ double s_llw[FIN_THREADS / 32];

@@ -520,6 +520,8 @@ constexpr int PT_PTS = 32 * PT_P * PT_B;   // points per CTA
 // of 32 (never beyond the padded parameter block, whose extra slots are padding
 // components with c = -inf).
 __host__ __device__ constexpr int pt_pairs(int k) { return (((k + 1) / 2) + 31) & ~31; }
+// floats of one partial row: [pairs][2 NSTAT], a pair's values 80 contiguous bytes
+__host__ __device__ constexpr int pt_row_floats(int k) { return ((k + 1) / 2) * 2 * NSTAT; }
 constexpr float PT_REACH = 128.f;  // q' above which a component is out of reach (e = 0 from q' > 126)
 // parameters, then per warp the live-mask words and the list of reachable pairs
 __host__ __device__ constexpr size_t pt_smem_bytes(int k) {
@@ -846,7 +848,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             s_pairs[warp][0] = (unsigned)nlive;
             s_pairs[warp][1] = live;
         }
-        // ---- phase 2: this warp's live pairs; partials [k * NSTAT][rows], masks [nwords][rows]
+        // ---- phase 2: this warp's live pairs; partials [rows][pairs][2 NSTAT], masks [nwords][rows]
         for (int wd = 0; wd < nwords; ++wd) {
             uint32_t m = smask[wd];
             while (m) {
@@ -879,7 +881,7 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
                 const float r = pt_warp_reduce20(S, lane, &v);
                 const int b = 2 * pp + (v >= NSTAT ? 1 : 0);
                 if ((lane & 7) < 5 && b < a.k && GIRA_IN(gw < rows, a.st))
-                    a.partials[((size_t)b * NSTAT + (v % NSTAT)) * rows + gw] = r;
+                    a.partials[(size_t)gw * pt_row_floats(a.k) + (size_t)pp * 2 * NSTAT + v] = r;
             }
         }
     }
@@ -1096,6 +1098,7 @@ const char* last_estep_kernel() { return t_estep_name.c_str(); }
 
 int estep_pt_grid(int64_t n) { return (int)std::max<int64_t>(1, (n + PT_PTS - 1) / PT_PTS); }
 int estep_pt_rows(int grid) { return grid * PT_B; }
+int estep_pt_row_floats(int k) { return pt_row_floats(k); }
 int estep_pt_mask_words(int k) { return pt_pairs(k) / 32; }
 
 cudaError_t launch_estep_pt(const EStepLaunch& a, bool stats, int grid, cudaStream_t s, bool pdl) {
@@ -1368,8 +1371,9 @@ cudaError_t launch_ll_reduce(const double* ll_partials, int grid, DeviceState* s
 namespace {
 
 constexpr int FIN_CPB = 2;          // components per block: spreads the binary64 work over SMs
-constexpr int FIN_SPLIT = 16;       // the CTA partials of one output are summed in 16 fixed slices
-constexpr int FIN_THREADS = FIN_CPB * NSTAT * FIN_SPLIT;   // 320
+constexpr int FIN_SPLIT_CTA = 16;   // per-CTA partials: one output summed in 16 fixed slices
+constexpr int FIN_SPLIT = 64;       // per-warp rows: one float4 of outputs summed in 64 fixed slices
+constexpr int FIN_THREADS = FIN_CPB * NSTAT * FIN_SPLIT_CTA;   // 320
 constexpr int ORDER_THREADS = 1024;   // order_components_kernel: one block
 constexpr int ORDER_MAX_K = 8192;     // keys in dynamic shared memory (64 KB)
 
@@ -1409,18 +1413,14 @@ __device__ __forceinline__ CholInv chol_inv(const double c[6]) {
 
 constexpr double ALPHA = 0.84932180028801904272;   // sqrt(log2(e) / 2)
 
-// Entry e of P' = alpha L^-1 in the order (00, 10, 11, 20, 21, 22).
+// Entry e of P' = alpha L^-1 in the order (00, 10, 11, 20, 21, 22), as
+// alpha ((A B) C) with (A, B, C) = (u, 1, 1), (h0, v, -1), (v, 1, 1), (r0, g, -z),
+// (t, z, -1), (z, 1, 1): the same three products for every entry.
 __device__ __forceinline__ double chol_q(const CholInv& k, int e) {
-    double p;
-    switch (e) {
-        case 0: p = k.u; break;
-        case 1: p = -__dmul_rn(k.h0, k.v); break;
-        case 2: p = k.v; break;
-        case 3: p = -__dmul_rn(__dmul_rn(k.r0, k.g), k.z); break;
-        case 4: p = -__dmul_rn(k.t, k.z); break;
-        default: p = k.z; break;
-    }
-    return __dmul_rn(ALPHA, p);
+    const double A = e == 0 ? k.u : e == 1 ? k.h0 : e == 2 ? k.v : e == 3 ? k.r0 : e == 4 ? k.t : k.z;
+    const double B = e == 1 ? k.v : e == 3 ? k.g : e == 4 ? k.z : 1.0;
+    const double C = e == 1 || e == 4 ? -1.0 : e == 3 ? -k.z : 1.0;
+    return __dmul_rn(ALPHA, __dmul_rn(__dmul_rn(A, B), C));
 }
 
 // b_i = -(P' mu)_i from the row (a0, a1, a2) of P' (zeros above the diagonal).
@@ -1499,7 +1499,7 @@ __device__ bool build_component(int b, double w, const double mu[3], const doubl
 }
 
 // The statistics of components b0 .. b0 + nout / NSTAT - 1 summed over the
-// per-CTA partials into S (binary64): FIN_SPLIT fixed slices of CTAs, binary32
+// per-CTA partials into S (binary64): FIN_SPLIT_CTA fixed slices of CTAs, binary32
 // groups of 8 within a slice, binary64 across groups and slices.  Call with
 // every thread of the block; ends with S valid after a barrier.
 __device__ void reduce_partials(const float* __restrict__ partials, int grid, int k, int b0, int nout,
@@ -1507,7 +1507,7 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
     const int t = threadIdx.x;
     const int o = t % (FIN_CPB * NSTAT), q = t / (FIN_CPB * NSTAT);
     if (o < nout) {
-        const int c0 = q * grid / FIN_SPLIT, c1 = (q + 1) * grid / FIN_SPLIT;
+        const int c0 = q * grid / FIN_SPLIT_CTA, c1 = (q + 1) * grid / FIN_SPLIT_CTA;
         const float* src = partials + (size_t)b0 * NSTAT + o;
         const size_t stride = (size_t)k * NSTAT;
         double acc = 0.0;
@@ -1525,7 +1525,7 @@ __device__ void reduce_partials(const float* __restrict__ partials, int grid, in
     __syncthreads();
     if (t < nout) {
         double v = 0.0;
-        for (int q2 = 0; q2 < FIN_SPLIT; ++q2) v += part[q2][t];
+        for (int q2 = 0; q2 < FIN_SPLIT_CTA; ++q2) v += part[q2][t];
         S[t] = v;
     }
 }
@@ -1554,28 +1554,33 @@ constexpr int W_C = 58;     // the new Sigma (00,01,02,11,12,22)
 constexpr int FF = 20;      // binary32 copies per component: P'[6], b[3], mu[3], w, Sigma[6]
 
 // The statistics of the pair of components b0, b0 + 1 (b0 even) from the per-warp
-// partial rows of the point-stationary E-step: the rows whose live mask has the
-// pair's bit are listed in row order (one block scan per segment of FIN_SEG rows,
-// each thread ranking a contiguous run of rows).  Output o (component o / NSTAT,
-// statistic o % NSTAT) belongs to the half-warp 2 warp + lane / 16: its lane q sums
-// the q-th of FIN_SPLIT fixed contiguous slices of the list in compensated binary32,
-// a fixed butterfly of compensated additions joins the 16 slices, and the pair
-// (sum, error) becomes one binary64 value in W.  The list depends only on the masks,
-// so the order of every addition is fixed.  Call with every thread of the block;
-// s_skip (set by thread 0 before the call) is read after the first barrier, and a
-// skipped block returns false before touching W.
+// partial rows of the point-stationary E-step ([rows][pairs][2 NSTAT] binary32, a
+// pair's 20 values 80 contiguous bytes): the rows whose live mask has the pair's bit
+// are listed in row order (one block scan per segment of FIN_SEG rows, each thread
+// ranking a contiguous run of rows).  Thread (c, q) = (t / 64, t % 64) sums float4 c
+// of the pair's values (outputs 4c .. 4c + 3; output o is component o / NSTAT,
+// statistic o % NSTAT) over the q-th of FIN_SPLIT fixed contiguous slices of the list
+// in compensated binary32; a fixed butterfly of compensated additions joins the 32
+// slices of a warp, then the two warps of c in order, and each (sum, error) becomes
+// one binary64 value in W.  The list depends only on the masks, so the order of every
+// addition is fixed.  Call with every thread of the block; s_skip (set by thread 0
+// before the call) is read after the first barrier, and a skipped block returns false
+// before touching W.
 constexpr int FIN_SEG = 4096;
-static_assert(FIN_THREADS == 16 * FIN_CPB * NSTAT && FIN_SPLIT == 16, "one half-warp per output of the pair");
-__device__ bool reduce_partials_masked(const float* __restrict__ partials, int rows, const uint32_t* __restrict__ masks,
-                                       int b0, int nout, double (*W)[FW], const int* s_skip, DeviceState* st) {
+static_assert(FIN_THREADS == 5 * 64 && FIN_SPLIT == 64 && 2 * NSTAT == 20, "five float4 of a pair, 64 slices each");
+__device__ bool reduce_partials_masked(const float* __restrict__ partials, int rows, int row_floats,
+                                       const uint32_t* __restrict__ masks, int b0, int nout, double (*W)[FW],
+                                       const int* s_skip, DeviceState* st) {
     __shared__ uint16_t s_list[FIN_SEG];
     __shared__ int s_wsum[FIN_THREADS / 32];
+    __shared__ float s_hi[FIN_THREADS / 64][8];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int o = 2 * warp + (lane >> 4), q = lane & 15;
+    const int c = t >> 6, q = t & 63;
     const uint32_t* mrow = masks + (size_t)((b0 >> 1) >> 5) * rows;
     const uint32_t bit = 1u << ((b0 >> 1) & 31);
-    const float* src = partials + ((size_t)b0 * NSTAT + o) * rows;
-    float sum = 0.f, err = 0.f;
+    const float4* src = reinterpret_cast<const float4*>(partials + (size_t)(b0 >> 1) * 2 * NSTAT) + c;
+    const size_t stride4 = (size_t)row_floats / 4;
+    float sum[4] = {0.f, 0.f, 0.f, 0.f}, err[4] = {0.f, 0.f, 0.f, 0.f};
     for (int seg0 = 0; seg0 < rows; seg0 += FIN_SEG) {
         const int seg1 = min(rows, seg0 + FIN_SEG);
         constexpr int RND = (FIN_SEG + FIN_THREADS - 1) / FIN_THREADS;
@@ -1583,8 +1588,10 @@ __device__ bool reduce_partials_masked(const float* __restrict__ partials, int r
         const int r0 = seg0 + t * per;
         uint32_t live = 0u;   // bit u: row r0 + u is live
 #pragma unroll
-        for (int u = 0; u < RND; ++u)
-            if (u < per && r0 + u < seg1 && (__ldg(mrow + r0 + u) & bit)) live |= 1u << u;
+        for (int u = 0; u < RND; ++u) {
+            const uint32_t mw = (u < per && r0 + u < seg1) ? __ldg(mrow + r0 + u) : 0u;
+            if (mw & bit) live |= 1u << u;
+        }
         const int cnt = __popc(live);
         int incl = cnt;   // inclusive scan of the counts over the warp
 #pragma unroll
@@ -1598,9 +1605,9 @@ __device__ bool reduce_partials_masked(const float* __restrict__ partials, int r
         int off = incl - cnt, nl = 0;
 #pragma unroll
         for (int w = 0; w < FIN_THREADS / 32; ++w) {
-            const int c = s_wsum[w];
-            off += (w < warp) ? c : 0;
-            nl += c;
+            const int cw = s_wsum[w];
+            off += (w < warp) ? cw : 0;
+            nl += cw;
         }
         for (uint32_t m = live; m; m &= m - 1u) {
             const int r = r0 + __ffs(m) - 1;
@@ -1608,29 +1615,53 @@ __device__ bool reduce_partials_masked(const float* __restrict__ partials, int r
             ++off;
         }
         __syncthreads();
-        if (o < nout) {
-            const int c0 = q * nl / FIN_SPLIT, c1 = (q + 1) * nl / FIN_SPLIT;
-            const float* sseg = src + seg0;
-            for (int c = c0; c < c1; c += 16) {   // sixteen loads in flight
-                float v[16];
+        const int c0 = q * nl / FIN_SPLIT, c1 = (q + 1) * nl / FIN_SPLIT;
+        const float4* sseg = src + (size_t)seg0 * stride4;
+        for (int i = c0; i < c1; i += 8) {   // eight float4 loads in flight
+            float4 v[8];
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    v[u] = (c + u < c1 && GIRA_IN(s_list[c + u] < seg1 - seg0, st)) ? __ldcg(sseg + s_list[c + u]) : 0.f;
+            for (int u = 0; u < 8; ++u)
+                v[u] = (i + u < c1 && GIRA_IN(s_list[i + u] < seg1 - seg0, st))
+                           ? __ldcg(sseg + (size_t)s_list[i + u] * stride4) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    if (c + u < c1) two_sum_acc(sum, err, v[u]);
+            for (int u = 0; u < 8; ++u) {
+                if (i + u < c1) {
+                    two_sum_acc(sum[0], err[0], v[u].x);
+                    two_sum_acc(sum[1], err[1], v[u].y);
+                    two_sum_acc(sum[2], err[2], v[u].z);
+                    two_sum_acc(sum[3], err[3], v[u].w);
+                }
             }
         }
         __syncthreads();   // the list is rebuilt for the next segment
     }
 #pragma unroll
-    for (int d = 8; d > 0; d >>= 1) {   // butterfly over the half-warp: the same total in every lane
-        const float s2 = __shfl_xor_sync(FULL, sum, d), e2 = __shfl_xor_sync(FULL, err, d);
-        float e = __fadd_rn(err, e2);
-        two_sum_acc(sum, e, s2);
-        err = e;
+    for (int d = 16; d > 0; d >>= 1) {   // butterfly over the warp: the same totals in every lane
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float s2 = __shfl_xor_sync(FULL, sum[j], d), e2 = __shfl_xor_sync(FULL, err[j], d);
+            float e = __fadd_rn(err[j], e2);
+            two_sum_acc(sum[j], e, s2);
+            err[j] = e;
+        }
     }
-    if (o < nout && q == 0) W[o / NSTAT][W_S + o % NSTAT] = __dadd_rn((double)sum, (double)err);
+    if ((warp & 1) && lane == 0) {   // the second warp of c: slices 32 .. 63
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s_hi[c][j] = sum[j];
+            s_hi[c][4 + j] = err[j];
+        }
+    }
+    __syncthreads();
+    if (!(warp & 1) && lane < 4) {
+        const int j = lane;
+        float sj = j == 0 ? sum[0] : j == 1 ? sum[1] : j == 2 ? sum[2] : sum[3];
+        float ej = j == 0 ? err[0] : j == 1 ? err[1] : j == 2 ? err[2] : err[3];
+        ej = __fadd_rn(ej, s_hi[c][4 + j]);
+        two_sum_acc(sj, ej, s_hi[c][j]);
+        const int o = 4 * c + j;
+        if (o < nout) W[o / NSTAT][W_S + o % NSTAT] = __dadd_rn((double)sj, (double)ej);
+    }
     return true;
 }
 
@@ -1658,8 +1689,9 @@ struct FinArgs {
     int ll_count;   // log-likelihood partials to sum (grid when 0)
     int do_ll;      // this launch's block 0 does the log-likelihood / convergence step
     const int* perm;   // slot b holds the caller's component perm[b] (nullptr: b)
-    // point-stationary E-step: partials per warp ([grid warps][k][NSTAT]), a row
-    // valid only where the warp's live mask ([grid][nwords]) has the pair's bit
+    // point-stationary E-step: partial rows per block of points ([grid rows][pairs]
+    // [2 NSTAT]), a pair's values valid only where the row's live mask ([nwords]
+    // [grid rows]) has the pair's bit
     const uint32_t* masks;
     int nwords;
 };
@@ -1820,12 +1852,13 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
     }
     if (t == 0) s_skip = (f.em && f.iter > f.st->stop_after) || f.st->error != 0;
     if (f.partials && f.masks) {
-        if (!reduce_partials_masked(f.partials, f.grid, f.masks, b0, nout, W, &s_skip, f.st)) return;
+        if (!reduce_partials_masked(f.partials, f.grid, pt_row_floats(f.k), f.masks, b0, nout, W, &s_skip, f.st))
+            return;
     } else {
         __syncthreads();
         if (s_skip) return;
         if (f.partials) {
-            __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
+            __shared__ double part[FIN_SPLIT_CTA][FIN_CPB * NSTAT];
             __shared__ double S[FIN_CPB * NSTAT];
             reduce_partials(f.partials, f.grid, f.k, b0, nout, part, S);
             if (t < nout) W[t / NSTAT][W_S + t % NSTAT] = S[t];
@@ -2297,7 +2330,7 @@ __global__ void __launch_bounds__(FIN_THREADS) grad_finalize_batched_kernel(cons
     grad_finalize_body(f, bi.y);
 }
 __device__ void grad_finalize_body(const GradFinArgs& f, int blk) {
-    __shared__ double part[FIN_SPLIT][FIN_CPB * NSTAT];
+    __shared__ double part[FIN_SPLIT_CTA][FIN_CPB * NSTAT];
     __shared__ double S[FIN_CPB * NSTAT];
     __shared__ int s_skip;
     const float* __restrict__ partials = f.partials;

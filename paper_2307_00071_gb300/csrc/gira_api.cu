@@ -673,7 +673,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.shift4 = cv.take<float4>(k);
         b.model64 = cv.take<double>((size_t)k * MODEL);
         b.stats64 = cv.take<double>((size_t)k * NSTAT);
-        b.partials = cv.take<float>((size_t)rows * k * NSTAT);
+        b.partials = cv.take<float>((size_t)rows * estep_pt_row_floats(k));
         b.masks = cv.take<uint32_t>((size_t)rows * nwords);
         b.llp = cv.take<double>(grid);
         b.trace = cv.take<double>(std::max(o.iters, 1));
@@ -1148,7 +1148,7 @@ gira_status gira_gmm_fit_batched(const float* points, const int64_t* offsets, in
             I.part_off = part_floats;
             I.mask_off = mask_words;
             I.ll_off = ll_slots;
-            part_floats += (int64_t)I.ctas * W * I.k * NSTAT;
+            part_floats += (int64_t)I.ctas * W * estep_pt_row_floats(I.k);
             mask_words += (int64_t)I.ctas * W * estep_pt_mask_words(I.k);
             ll_slots += I.ctas;
             kmax_all = std::max(kmax_all, I.k);

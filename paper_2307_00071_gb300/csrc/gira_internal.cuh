@@ -436,6 +436,7 @@ cudaError_t launch_reduce_finalize(const float* partials, int grid, const double
 // points; partial rows (warps) of a grid; live-mask words per warp for k.
 int estep_pt_grid(int64_t n);
 int estep_pt_rows(int grid);
+int estep_pt_row_floats(int k);   // floats of one partial row of the point-stationary E-step
 int estep_pt_mask_words(int k);
 // a.partials: [k * NSTAT][rows] (stats), a.masks: [mask words][rows], a.pt_rows = rows,
 // a.ll_partials: [grid]

@@ -510,6 +510,15 @@ __global__ void __launch_bounds__(MAXT, MINB) estep_kernel(const EStepLaunch a_i
 // points reach about a sixth of the pairs (the depth frame at K = 512), and the
 // other pairs cost only phase 1.  The statistics are sums of the same terms as
 // the other kernels' in another order.
+// Relative costs of a listed pair (phase 1) and a live pair (phase 2) per point,
+// and the 8-bit logarithmic key of a CTA's work (16 steps per octave) by which
+// the finalize orders the CTAs of a later iteration.
+constexpr unsigned PT_COST_NEAR = 26, PT_COST_LIVE = 54;
+__device__ __forceinline__ uint8_t work_key(unsigned w) {
+    const int e = 31 - __clz(w | 1u);
+    const unsigned m = (e >= 4 ? (w >> (e - 4)) : (w << (4 - e))) & 15u;
+    return (uint8_t)min(255u, (unsigned)e * 16u + m);
+}
 constexpr int PT_P = 4;           // points per lane
 constexpr int PT_W = 4;           // warps per CTA
 constexpr int PT_H = 2;           // warps sharing a block of 32 * PT_P points (the pairs split between them)
@@ -593,6 +602,10 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
         a.ll_partials = a_in.ll_partials ? a_in.ll_partials + I.ll_off : nullptr;
         a.per_point = a_in.per_point ? a_in.per_point + I.pt_off : nullptr;
         a.st = a_in.states + u.inst;
+    }
+    if (a_in.cta_perm && a_in.iter >= 3) {   // the order the finalize chose two iterations ago
+        const int c = a_in.cta_perm[(size_t)(a_in.iter & 1) * gridDim.x + blockIdx.x];
+        if (GIRA_IN(c >= 0 && c < (int)gridDim.x, a.st)) cta = c;
     }
     // pairs evaluated: ceil(k / 2) rounded up to even (within the padded block, whose
     // extra slots are padding components with c = -inf); mask words for pt_pairs(k)
@@ -902,6 +915,12 @@ __global__ void __launch_bounds__(32 * PT_W, 4) estep_pt_kernel(const EStepLaunc
             }
             atomicAdd(&a.st->pairs_near, near);
             atomicAdd(&a.st->pairs_live, live);
+            if (a_in.cta_key) {   // the CTA's slowest warp, in units of a point's pair evaluations
+                unsigned wmax = 0;
+                for (int w = 0; w < PT_W; ++w)
+                    wmax = max(wmax, PT_COST_NEAR * s_pairs[w][0] + PT_COST_LIVE * s_pairs[w][1]);
+                if (GIRA_IN(cta < (int)gridDim.x, a.st)) a_in.cta_key[cta] = work_key(wmax);
+            }
         }
     }
 }
@@ -1694,6 +1713,11 @@ struct FinArgs {
     // [grid rows]) has the pair's bit
     const uint32_t* masks;
     int nwords;
+    // a single fit's CTA order: the launch's last block ranks the E-step's cta_grid
+    // CTAs by cta_key into cta_perm[(iter & 1) * cta_grid ..] for iteration iter + 2
+    const uint8_t* cta_key = nullptr;
+    int* cta_perm = nullptr;
+    int cta_grid = 0;
 };
 
 __device__ __forceinline__ int sym_i(int u) { return u < 3 ? 0 : (u < 5 ? 1 : 2); }   // (00,01,02,11,12,22)
@@ -1895,9 +1919,72 @@ __device__ void reduce_finalize_body(const FinArgs& f, int blk) {
     }
 }
 
+// The E-step's CTA order for iteration f.iter + 2: descending work key, ties in
+// index order (a counting sort: position = keys above + equal keys before).  The
+// order changes only which SM runs which point blocks when, never a result.
+__device__ void order_ctas(const FinArgs& f) {
+    __shared__ int s_above[256], s_run[256];
+    __shared__ uint16_t s_wc[FIN_THREADS / 32][256];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int grid = f.cta_grid;
+    int* out = f.cta_perm + (size_t)(f.iter & 1) * grid;
+    for (int b = t; b < 256; b += FIN_THREADS) s_above[b] = s_run[b] = 0;
+    __syncthreads();
+    for (int i = t; i < grid; i += FIN_THREADS) atomicAdd(&s_above[f.cta_key[i]], 1);
+    __syncthreads();
+    if (warp == 0) {   // s_above[b] = number of keys above b (8 buckets per lane, from the top)
+        int v[8], tot = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            v[u] = s_above[255 - (lane * 8 + u)];
+            tot += v[u];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += x;
+        }
+        __syncwarp();
+        int run = incl - tot;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            s_above[255 - (lane * 8 + u)] = run;
+            run += v[u];
+        }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < grid; c0 += FIN_THREADS) {
+        const int i = c0 + t;
+        const int key = i < grid ? (int)f.cta_key[i] : -1;
+        const unsigned peers = __match_any_sync(FULL, key);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        for (int b = lane; b < 256; b += 32) s_wc[warp][b] = 0;
+        __syncwarp();
+        if (key >= 0 && rank == 0) s_wc[warp][key] = (uint16_t)__popc(peers);
+        __syncthreads();
+        if (key >= 0) {
+            int pos = s_above[key] + s_run[key] + rank;
+            for (int w = 0; w < warp; ++w) pos += s_wc[w][key];
+            if (GIRA_IN(pos < grid, f.st)) out[pos] = i;
+        }
+        __syncthreads();
+        for (int b = t; b < 256; b += FIN_THREADS) {
+            int add = 0;
+            for (int w = 0; w < FIN_THREADS / 32; ++w) add += s_wc[w][b];
+            s_run[b] += add;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(FIN_THREADS) reduce_finalize_kernel(const FinArgs f) {
     pdl_wait();         // the E-step's partials (dependent launch)
     pdl_allow_next();   // the next E-step may stage its points meanwhile
+    if (f.cta_key && blockIdx.x == gridDim.x - 1) {
+        order_ctas(f);
+        return;
+    }
     reduce_finalize_body(f, blockIdx.x);
 }
 
@@ -2432,10 +2519,16 @@ cudaError_t launch_reduce_finalize(const float* partials, int grid, const double
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
                                    cudaStream_t s, bool pdl, const int* perm, const uint32_t* masks, int nwords,
-                                   int ll_count) {
-    const FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
-                    em ? 1 : 0, ll_count, 1, perm, masks, nwords};
-    PdlConfig c(dim3((k + FIN_CPB - 1) / FIN_CPB), dim3(FIN_THREADS), 0, s, pdl);
+                                   int ll_count, const uint8_t* cta_key, int* cta_perm, int cta_grid) {
+    FinArgs f{partials, grid, ll_partials, stats64, shift4, k, n, reg, tol, model64, params, trace, st, iter,
+              em ? 1 : 0, ll_count, 1, perm, masks, nwords};
+    const bool order = em && cta_key && cta_perm && cta_grid > 0;
+    if (order) {
+        f.cta_key = cta_key;
+        f.cta_perm = cta_perm;
+        f.cta_grid = cta_grid;
+    }
+    PdlConfig c(dim3((k + FIN_CPB - 1) / FIN_CPB + (order ? 1 : 0)), dim3(FIN_THREADS), 0, s, pdl);
     return cudaLaunchKernelEx(&c.cfg, reduce_finalize_kernel, f);
 }
 

@@ -655,6 +655,8 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         unsigned long long* chg;
         float4 *p8s, *p4s;
         void* osc;
+        uint8_t* cta_key;
+        int* cta_perm;
     } b{};
     // the E-steps and Lloyd run on the points in a spatial order (a warp's points then
     // reach fewer components and centres); k-means++ on the caller's order, which
@@ -677,6 +679,8 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         b.masks = cv.take<uint32_t>((size_t)rows * nwords);
         b.llp = cv.take<double>(grid);
         b.trace = cv.take<double>(std::max(o.iters, 1));
+        b.cta_key = cv.take<uint8_t>(chunked ? 0 : grid);
+        b.cta_perm = cv.take<int>(chunked ? 0 : 2 * (size_t)grid);
         if (chunked) carve_chunks(cv, P, n, true, &cb);
         b.mw = cv.take<float>(model_host ? k : 0);
         b.mmu = cv.take<float>(model_host ? 3 * (size_t)k : 0);
@@ -789,6 +793,8 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
     a.n_buf = n;
     a.masks = b.masks;
     a.pt_rows = rows;
+    a.cta_perm = b.cta_perm;   // from the third iteration on: the CTAs of most work first
+    a.cta_key = b.cta_key;
     for (int t = 1; t <= o.iters && !chunked; ++t) {
         a.iter = t;
         // dependent launches unless an event pair brackets each E-step: each
@@ -801,7 +807,7 @@ gira_status gira_gmm_fit(const float* points, int64_t n, int k, const gira_fit_o
         if (prof.per_launch) prof.timed(e0, e1);
         COUNTED(prof, 1, launch_reduce_finalize(b.partials, rows, b.llp, nullptr, b.shift4, k, n, o.reg_covar,
                                                 o.tol, b.model64, b.params, b.trace, b.st, t, true, c.s, pdl, perm,
-                                                b.masks, nwords, grid));
+                                                b.masks, nwords, grid, b.cta_key, b.cta_perm, grid));
     }
     if (!chunked) prof.t_em = prof.mark();
     if (final_loglik && !chunked) {

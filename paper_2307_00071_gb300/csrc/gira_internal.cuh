@@ -367,13 +367,19 @@ struct EStepLaunch {
     const float* gref = nullptr;   // [0] cmax over all K, [1] log-likelihood reference (base 2)
     float* psum = nullptr;
     const float2* pref = nullptr;
-    // point-stationary E-step (estep_pt_kernel): per-warp partials [k * NSTAT][rows],
-    // row cta * W + warp written only where the warp's live mask has the pair's
+    // point-stationary E-step (estep_pt_kernel): partial rows [rows][pairs][2 NSTAT],
+    // row cta * PT_B + block written only where the block's live mask has the pair's
     // bit, and the live masks [npairs / 32][rows] (bit p: pair p reaches some point
-    // of the warp)
+    // of the block)
     uint32_t* masks = nullptr;
     int64_t pt_rows = 0;   // point blocks of the launch (the row count of partials and masks)
     int64_t n_buf = 0;     // points in pts8 (index checks of the debug build; 0: unchecked)
+    // CTA order of a single fit's E-step: from iteration 3 on, CTA blockIdx.x takes the
+    // point blocks of CTA cta_perm[(iter & 1) * grid + blockIdx.x] (longest expected
+    // work first, written by the finalize two iterations earlier); cta_key[cta]
+    // receives the CTA's work key for that order (nullptr: launch order, no keys)
+    const int* cta_perm = nullptr;
+    uint8_t* cta_key = nullptr;
 };
 
 // Chooses the template instance and block shape for K; returns the CTA count
@@ -431,7 +437,8 @@ cudaError_t launch_reduce_finalize(const float* partials, int grid, const double
                                    const double* stats64, float4* shift4, int k, int64_t n, double reg, double tol,
                                    double* model64, float* params, double* trace, DeviceState* st, int iter, bool em,
                                    cudaStream_t s, bool pdl = false, const int* perm = nullptr,
-                                   const uint32_t* masks = nullptr, int nwords = 0, int ll_count = 0);
+                                   const uint32_t* masks = nullptr, int nwords = 0, int ll_count = 0,
+                                   const uint8_t* cta_key = nullptr, int* cta_perm = nullptr, int cta_grid = 0);
 // Point-stationary E-step (3-D fits and log-likelihood, k <= 1024): CTAs for n
 // points; partial rows (warps) of a grid; live-mask words per warp for k.
 int estep_pt_grid(int64_t n);

@@ -138,3 +138,23 @@ def test_full_size_batch_sampled_instances_match_oracle(gira):
         ref = oracle.gmm_fit(clouds[i], int(kk[i]), iters=3, tol=0.0, reg=1e-6, seed=0, lloyd_iters=5)
         assert np.max(np.abs(r["trace"][i] - ref["trace"])) <= LL_ABS, i
         assert_model_close((ws[i], ms[i], cs[i]), (ref["weights"], ref["means"], ref["covs"]))
+
+
+def test_single_fit_equals_batch_of_one(gira):
+    """From the same start model, a single fit (its E-step's CTAs reordered by their
+    previous work from the third iteration on) and a batch holding that one instance
+    (launch order) give the same bits: the CTA order changes which SM runs which
+    point blocks, never an addition's order."""
+    import torch
+    cl = synth.depth_frame(seed=3).points[::3].copy()
+    k = 96
+    init = oracle.kinit(cl, k, seed=0, lloyd_iters=5, reg=1e-6)
+    w0, m0, c0 = (init[key].astype(np.float32) for key in ("weights", "means", "covs"))
+    x = torch.as_tensor(cl, device="cuda")
+    one = gira.gira_gmm_fit(x, k, iters=12, tol=0.0, init=(w0, m0, c0))
+    bat = gira.gira_gmm_fit_batched(x, np.array([0, len(cl)], np.int64), np.array([k], np.int32), iters=12,
+                                    tol=0.0, init=(w0, m0, c0))
+    assert one["iters_done"] == 12 and bat["iters_done"][0] == 12
+    for key in ("weights", "means", "covs"):
+        np.testing.assert_array_equal(to_np(one[key]), to_np(bat[key]))
+    np.testing.assert_array_equal(np.asarray(one["trace"]), np.asarray(bat["trace"][0]))

@@ -412,13 +412,19 @@ constexpr int KC_MAX_CS = 16;
 
 constexpr long long KC_WAIT_NS = 2000000000ll;   // bound on any wait: 2 s of wall time
 
+constexpr int KC_PER = KC_MAX_CS * KC_WARPS / 32;   // blocks per lane of the search, in order
+
 struct KcShared {
-    u128 csum[2][KC_MAX_CS * KC_WARPS];   // by parity of j: every block's total, stored by its warp
+    // by parity of j: every block's total, stored by its warp at slot (g % KC_PER) * 32 +
+    // g / KC_PER (lane l's blocks l KC_PER .. in consecutive banks); once the total of
+    // every weight is below 2^64 the first half holds 64-bit totals instead
+    u128 csum[2][KC_MAX_CS * KC_WARPS];
     float4 cen[2];             // by parity of j: stored by the CTA holding the chosen point
     long long idx[2];
     uint64_t bar_sum[2], bar_cen[2];
     u128 rel;                  // the threshold within the chosen block
     int win, wwin, mode;       // the block's CTA and warp; 0 normal, 2 every weight zero
+    int m64;                   // the total of every weight was below 2^64 (it never grows)
     float2 dsrc[KC_PMAX];      // the D^2 of the lane holding the chosen point
 };
 
@@ -573,6 +579,7 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
             mbar_init(&sh.bar_sum[b], 1);
             mbar_init(&sh.bar_cen[b], 1);
         }
+        sh.m64 = 0;
         mbar_fence_init();
     }
     cluster.sync();   // every CTA has started and initialised its mbarriers before any DSMEM access
@@ -580,6 +587,9 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
     bool dead = false;                    // this thread gave up a wait: stop waiting, run to the end
     for (int j = 1; j < k; ++j) {
         const int b = j & 1;
+        // 64-bit totals: set by this CTA's warp 0 at centre j - 1 or before, from the same
+        // totals in every CTA; every warp reads it before warp 0 can change it again
+        const bool m64 = sh.m64 != 0;
         // ---- 1. D^2 (packed: each lane of FADD2/FMUL2 rounds like dist2_f32) and,
         //         where any D^2 dropped, the lane's exact sum from scratch (raster-
         //         order lanes see their points' D^2 drop together, so one pass over
@@ -638,12 +648,21 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
         // this phase of bar_sum[b] expects every block's total (the previous phase of it
         // completed before this CTA read centre j - 2's totals)
         const int nblk = cs * KC_WARPS;
-        if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)nblk * (uint32_t)sizeof(u128));
+        if (tid == 0 && !dead) mbar_expect_tx(&sh.bar_sum[b], (uint32_t)nblk * (m64 ? 8u : 16u));
         const unsigned long long k53 = splitmix64(seed, (uint64_t)j) >> 11;   // the draw: no data dependence
-        if (__any_sync(FULL, changed)) linc = u128_warp_incl_scan(ls, lane);   // else unchanged since j - 1
-        {   // this warp's block total, to every CTA's slot g
+        if (__any_sync(FULL, changed)) {   // else unchanged since j - 1
+            if (m64) linc = u128{u64_warp_incl_scan(ls.lo, lane), 0ull};   // the block's total < 2^64
+            else linc = u128_warp_incl_scan(ls, lane);
+        }
+        {   // this warp's block total, to every CTA's slot of block g
             const u128 total = u128_shfl(linc, 31);
-            if (lane < cs && !dead) kc_send_u128(kc_peer(&sh.csum[b][g], lane), total, kc_peer(&sh.bar_sum[b], lane));
+            const int slot = (g % KC_PER) * 32 + g / KC_PER;
+            if (lane < cs && !dead) {
+                const uint32_t bar = kc_peer(&sh.bar_sum[b], lane);
+                if (m64) kc_send_s64(kc_peer(reinterpret_cast<unsigned long long*>(sh.csum[b]) + slot, lane),
+                                     (long long)total.lo, bar);
+                else kc_send_u128(kc_peer(&sh.csum[b][slot], lane), total, bar);
+            }
         }
         if (warp == 0) {
             // ---- 2. every block's total has arrived: the block holding the threshold
@@ -651,39 +670,86 @@ __global__ void __launch_bounds__(KC_THREADS, 1) kpp_cluster_kernel(const float4
                 dead = true;
                 set_error(st, GIRA_ERR_TIMEOUT);
             }
-            constexpr int PER = KC_MAX_CS * KC_WARPS / 32;   // blocks per lane, in order
-            u128 run{0ull, 0ull};
+            constexpr int PER = KC_PER;   // blocks per lane, in order
+            bool tz;   // every weight is zero
+            if (m64) {
+                // 64-bit totals: lane l's blocks in registers, their sum, the warp's prefix
+                const unsigned long long* c64 = reinterpret_cast<const unsigned long long*>(sh.csum[b]);
+                unsigned long long run = 0ull;
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int gq = lane * PER + q;
-                run = u128_add(run, gq < nblk ? sh.csum[b][gq] : u128{0ull, 0ull});
-            }
-            const u128 lincl = u128_warp_incl_scan(run, lane);
-            const u128 before = u128_sub(lincl, run);   // the blocks of lower lanes
-            const u128 T = u128_shfl(lincl, 31);
-            if (!u128_zero(T)) {
-                const u128 t = fx_threshold(k53, T);
-                const unsigned hits = __ballot_sync(FULL, u128_gt(lincl, t));   // t < T: not empty
-                const int hl = hits ? __ffs(hits) - 1 : 0;
-                if (lane == hl) {   // the first of this lane's blocks whose running sum exceeds r
-                    const u128 r = u128_sub(t, before);
-                    u128 acc{0ull, 0ull}, prev{0ull, 0ull};
-                    int q = PER - 1;
-                    for (int u = 0; u < PER; ++u) {
-                        const int gq = lane * PER + u;
-                        acc = u128_add(acc, gq < nblk ? sh.csum[b][gq] : u128{0ull, 0ull});
-                        if (u128_gt(acc, r)) {
-                            q = u;
-                            break;
+                for (int q = 0; q < PER; ++q) run += lane * PER + q < nblk ? c64[q * 32 + lane] : 0ull;
+                const unsigned long long lincl = u64_warp_incl_scan(run, lane);
+                const unsigned long long T = __shfl_sync(FULL, lincl, 31);
+                tz = T == 0ull;
+                if (!tz) {
+                    const unsigned long long t = fx_threshold(k53, u128{T, 0ull}).lo;   // t < T
+                    const unsigned hits = __ballot_sync(FULL, lincl > t);
+                    const int hl = hits ? __ffs(hits) - 1 : 0;
+                    if (lane == hl) {   // the first of this lane's blocks whose running sum exceeds r
+                        const unsigned long long r = t - (lincl - run);
+                        unsigned long long pre = 0ull, prev = 0ull;   // pre: the running sum through block u
+                        int q = -1;
+                        unsigned long long v[PER];   // the lane's blocks again (independent loads)
+#pragma unroll
+                        for (int u = 0; u < PER; ++u) v[u] = lane * PER + u < nblk ? c64[u * 32 + lane] : 0ull;
+#pragma unroll
+                        for (int u = 0; u < PER; ++u) {
+                            const unsigned long long nx = pre + v[u];
+                            if (q < 0 && nx > r) {
+                                q = u;
+                                prev = pre;
+                            }
+                            pre = nx;
                         }
-                        prev = acc;
+                        if (q < 0) {   // never: r is below the lane's sum
+                            q = PER - 1;
+                            prev = pre - v[PER - 1];
+                        }
+                        const int gw = lane * PER + q;
+                        sh.win = gw % cs;
+                        sh.wwin = gw / cs;
+                        sh.rel = u128{r - prev, 0ull};
+                        sh.mode = 0;
                     }
-                    const int gw = lane * PER + q;
-                    sh.win = gw % cs;
-                    sh.wwin = gw / cs;
-                    sh.rel = u128_sub(r, prev);
-                    sh.mode = 0;
                 }
+            } else {
+                u128 run{0ull, 0ull};
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    const int gq = lane * PER + q;
+                    run = u128_add(run, gq < nblk ? sh.csum[b][q * 32 + lane] : u128{0ull, 0ull});
+                }
+                const u128 lincl = u128_warp_incl_scan(run, lane);
+                const u128 before = u128_sub(lincl, run);   // the blocks of lower lanes
+                const u128 T = u128_shfl(lincl, 31);
+                tz = u128_zero(T);
+                if (lane == 0 && T.hi == 0ull) sh.m64 = 1;   // from the next centre on: 64-bit totals
+                if (!tz) {
+                    const u128 t = fx_threshold(k53, T);
+                    const unsigned hits = __ballot_sync(FULL, u128_gt(lincl, t));   // t < T: not empty
+                    const int hl = hits ? __ffs(hits) - 1 : 0;
+                    if (lane == hl) {   // the first of this lane's blocks whose running sum exceeds r
+                        const u128 r = u128_sub(t, before);
+                        u128 acc{0ull, 0ull}, prev{0ull, 0ull};
+                        int q = PER - 1;
+                        for (int u = 0; u < PER; ++u) {
+                            const int gq = lane * PER + u;
+                            acc = u128_add(acc, gq < nblk ? sh.csum[b][u * 32 + lane] : u128{0ull, 0ull});
+                            if (u128_gt(acc, r)) {
+                                q = u;
+                                break;
+                            }
+                            prev = acc;
+                        }
+                        const int gw = lane * PER + q;
+                        sh.win = gw % cs;
+                        sh.wwin = gw / cs;
+                        sh.rel = u128_sub(r, prev);
+                        sh.mode = 0;
+                    }
+                }
+            }
+            if (!tz) {
                 // this phase of bar_cen[b] expects the chosen point and its index
                 if (lane == 0 && !dead) mbar_expect_tx(&sh.bar_cen[b], (uint32_t)(sizeof(float4) + sizeof(long long)));
             } else if (lane == 0) {   // every weight is zero: uniform index, the same in every CTA

@@ -392,7 +392,9 @@ gira_status gira_profile_read(gira_profile *out, int reset);
  * previous call's contents (the call re-initialises what it reads), so calls
  * that overlap on the GPU -- on different streams, or from processes sharing a
  * context -- race and must not be issued; calls from several host threads are
- * serialised by a lock.  The call synchronises `stream` before returning.
+ * serialised by a lock.  The call synchronises `stream` before returning, so
+ * it cannot be recorded into a CUDA graph: on a stream under capture it
+ * returns GIRA_ERR_INVALID_ARG and leaves the capture untouched.
  */
 #define GIRA_NOALLOC_MAX_N 524288
 gira_status gira_gmm_loglik_noalloc(const float *points, int64_t n, int k, const float *weights,

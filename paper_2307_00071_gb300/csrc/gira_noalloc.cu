@@ -94,6 +94,13 @@ extern "C" gira_status gira_gmm_loglik_noalloc(const float* points, int64_t n, i
                        (long long)NOALLOC_MAX_N);
     if (k < 1 || k > GIRA_MAX_K_BATCHED || k > n) return na_fail(GIRA_ERR_INVALID_ARG, "k = %d outside [1, min(n, %d)]", k, GIRA_MAX_K_BATCHED);
     if (!points || !weights || !means || !covs) return na_fail(GIRA_ERR_INVALID_ARG, "a required pointer is NULL");
+    {   // the call reads its status back to the host and synchronises the stream, neither of
+        // which a stream under capture allows: refuse before any other CUDA call
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        NA_CUDA(cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return na_fail(GIRA_ERR_INVALID_ARG, "the stream is being captured; this call synchronises it");
+    }
     int dev = 0, sms = 1;
     NA_CUDA(cudaGetDevice(&dev));
     NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -101,3 +101,25 @@ def test_noalloc_rejects_what_it_cannot_hold():
     host = np.zeros((100, 3), np.float32)
     assert f(host.ctypes.data, 100, 4, w.data_ptr(), mu.data_ptr(), cov.data_ptr(), None, None,
              None) == gira.ERR_INVALID_ARG
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """On a stream under capture the call returns GIRA_ERR_INVALID_ARG before any CUDA call
+    that could break the capture (it synchronises its stream); the caller's graph still
+    completes and replays."""
+    from paper_2307_00071_gb300 import gira
+    f = _noalloc(gira._lib)
+    pts, w, mu, cov = [torch.as_tensor(x, device="cuda") for x in _case(6, 1_000, 8)]
+    y = torch.zeros(4, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        st = f(pts.data_ptr(), len(pts), 8, w.data_ptr(), mu.data_ptr(), cov.data_ptr(), None, None, s.cuda_stream)
+        y += 1
+    assert st == gira.ERR_INVALID_ARG
+    msg = gira._lib.gira_last_error_message()
+    assert "captur" in (msg.decode() if isinstance(msg, bytes) else str(msg))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.all(y == 1)

@@ -186,3 +186,52 @@ def test_cta_order_is_a_stable_descending_sort(grid):
     order = cta_order(keys)
     assert sorted(order.tolist()) == list(range(grid))
     np.testing.assert_array_equal(order, np.argsort(-keys, kind="stable"))
+
+
+def whitened_mstep(S, q, s, reg):
+    """The finalize's M-step from whitened statistics (binary64, the kernel's formulas):
+    S = (S0, S1[3], S2[6]) of y = P'(x - s), q = P' (00, 10, 11, 20, 21, 22) in binary32."""
+    q = np.asarray(q, np.float64)
+    nbw = S[0] + 10 * np.finfo(np.float64).eps
+    inv = 1.0 / nbw
+    m00, m11, m22 = 1.0 / q[0], 1.0 / q[2], 1.0 / q[5]
+    m10 = (-q[1] * m00) * m11
+    m21 = (-q[4] * m11) * m22
+    m20 = (q[4] * m10 + q[3] * m00) * (-m22)
+    M = np.array([[m00, 0, 0], [m10, m11, 0], [m20, m21, m22]])
+    yb = np.array(S[1:4]) * inv
+    ij = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    C = np.zeros((3, 3))
+    for u, (i, j) in enumerate(ij):
+        C[i, j] = C[j, i] = -yb[i] * yb[j] + S[4 + u] * inv
+    mu = s + M @ yb
+    Sig = M @ C @ M.T + reg * np.eye(3)
+    return nbw, mu, Sig
+
+
+def test_whitened_mstep_equals_direct_weighted_moments():
+    """mu = s + P'^-1 ybar and Sigma = P'^-1 C P'^-T + reg I from whitened statistics are
+    the responsibility-weighted mean and covariance of the points (the standard M-step)."""
+    rng = np.random.default_rng(5)
+    alpha = np.sqrt(np.log2(np.e) / 2)
+    for trial in range(50):
+        n = int(rng.integers(5, 400))
+        x = rng.normal(size=(n, 3)) * rng.uniform(0.01, 2.0, 3) + rng.uniform(-5, 5, 3)
+        r = rng.uniform(0, 1, n) ** 3
+        S_old = random_spd(rng, thin=trial % 3 == 0)
+        q32 = (alpha * np.linalg.inv(np.linalg.cholesky(S_old))).astype(np.float32)
+        q = np.array([q32[0, 0], q32[1, 0], q32[1, 1], q32[2, 0], q32[2, 1], q32[2, 2]])
+        s = (x.mean(0) + rng.normal(size=3) * 0.1).astype(np.float32).astype(np.float64)
+        P = q32.astype(np.float64)
+        y = (x - s) @ P.T
+        S = [r.sum(), *(r[:, None] * y).sum(0)]
+        for i, j in [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]:
+            S.append((r * y[:, i] * y[:, j]).sum())
+        nbw, mu, Sig = whitened_mstep(S, q, s, 1e-6)
+        Nb = r.sum() + 10 * np.finfo(np.float64).eps
+        mu_ref = (r[:, None] * x).sum(0) / Nb
+        d = x - mu_ref
+        Sig_ref = (r[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0) / Nb + 1e-6 * np.eye(3)
+        assert nbw == pytest.approx(Nb, rel=1e-15)
+        assert np.allclose(mu, mu_ref, rtol=0, atol=1e-9 * (1 + np.abs(mu_ref).max()))
+        assert np.allclose(Sig, Sig_ref, rtol=1e-8, atol=1e-12)
